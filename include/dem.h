@@ -1,0 +1,225 @@
+/*
+ * dem.h -- C ABI of the GB300 soft-sphere DEM library (libdem.so).
+ *
+ * The library advances a scene of frictional spheres with the discrete element
+ * method of the Yade documentation (3rd ed.), chapter 2 "DEM formulation":
+ * the bounding-volume collider (section 2.1.1), the sphere-sphere and
+ * wall-sphere contact geometry with incremental shear transport
+ * (section 2.1.3; ScGeom, Ig2_Sphere_Sphere_ScGeom, Ig2_Wall_Sphere_ScGeom), the
+ * FrictPhys stiffnesses (section 2.1.2; Ip2_FrictMat_FrictMat_FrictPhys), the
+ * Cundall-Strack linear elastic-frictional law (section 2.1.4;
+ * Law2_ScGeom_FrictPhys_CundallStrack), per-body force/torque summation and the
+ * damped leapfrog of NewtonIntegrator (section 2.1.5, eq. 2.9), in an open box
+ * with axis-aligned walls or in a deformable periodic cell (section 2.1.6).
+ * Every step runs in CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * General rules
+ *  - Every array argument is a HOST pointer unless its name ends in _dev.  The
+ *    caller owns every host array: the library copies in or out and keeps no
+ *    pointer after the call returns.  The library owns all device memory of a
+ *    scene and frees it in dem_scene_destroy.
+ *  - Vectors are packed xyz triples (n*3 doubles, row-major); quaternions are
+ *    (w, x, y, z); 3x3 matrices are row-major with the periodic cell's base
+ *    vectors in the COLUMNS (Cell.hSize).
+ *  - Body ids are 0..n-1 in insertion order (section 1.1.2 "Bodies").  Arrays
+ *    in and out of the library are in id order.
+ *  - A scene is not thread-safe: drive one scene from one host thread.
+ *    Different scenes may run concurrently on different streams.
+ *  - Every call returns a dem_status; on error, dem_last_error(scene) returns a
+ *    one-line message (valid until the next call on that scene).  Errors never
+ *    leave the scene half-updated except where noted (DEM_ERR_CUDA,
+ *    DEM_ERR_TIMEOUT: the scene is then unusable and should be destroyed).
+ *  - Host waits are bounded (DEM_TIMEOUT_S environment variable, default 120
+ *    seconds): a wait that expires returns DEM_ERR_TIMEOUT.
+ */
+#ifndef GB300_DEM_H
+#define GB300_DEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dem_scene dem_scene; /* opaque, library-owned */
+
+typedef enum dem_status {
+    DEM_OK = 0,
+    DEM_ERR_INVALID_ARG = 1,  /* bad argument (null pointer, negative size, unknown material) */
+    DEM_ERR_OUT_OF_RANGE = 2, /* body id out of range (section 1.1.2, O.bodies[id]) */
+    DEM_ERR_OOM = 3,          /* device or host allocation failed */
+    DEM_ERR_CAPACITY = 4,     /* a fixed limit was exceeded (cell shift, cell count) */
+    DEM_ERR_NONFINITE = 5,    /* NaN/Inf in an input or a body state during stepping */
+    DEM_ERR_GEOMETRY = 6,     /* a sphere spans more than half the periodic cell (2.1.6) */
+    DEM_ERR_TIMEOUT = 7,      /* a bounded host wait expired */
+    DEM_ERR_CUDA = 8,         /* a CUDA runtime call failed */
+    DEM_ERR_STATE = 9,        /* call not valid in the scene's state (e.g. no dt, lost history) */
+    DEM_ERR_UNSUPPORTED = 10  /* valid request this version does not implement */
+} dem_status;
+
+enum { DEM_FP64 = 0, DEM_MIXED = 1 };
+
+/* Scene description (POD).  Initialise with dem_scene_desc_init, then edit. */
+typedef struct dem_scene_desc {
+    int periodic;            /* 1: periodic cell cell_h (section 2.1.6); 0: open space */
+    double cell_h[9];        /* periodic cell, base vectors in columns; must be diagonal */
+    double box_lo[3];        /* walls: lower corner of the box */
+    double box_hi[3];        /* walls: upper corner of the box */
+    int wall_mask;           /* bit (2*axis + side): infinite wall at box_lo[axis] (side 0)
+                                or box_hi[axis] (side 1), normal along axis, both senses;
+                                ignored in periodic scenes (Wall shape, utils.wall) */
+    double gravity[3];       /* NewtonIntegrator.gravity [m/s^2] */
+    double damping;          /* NewtonIntegrator.damping, eq. 2.9 (default 0.2) */
+    double dt;               /* time step; <= 0: 0.5 * PWaveTimeStep at the first step */
+    double verlet_dist;      /* collider sweep margin dL (section 2.1.1, "Verlet distance"):
+                                > 0 absolute; < 0 fraction of the smallest radius
+                                (default -0.5, InsertionSortCollider.verletDist) */
+    int precision;           /* DEM_FP64 (only value supported in this version) */
+    long long capacity_bodies;   /* initial device capacity hint (0: grow on demand) */
+    long long capacity_contacts; /* initial contact-table rows hint (0: grow on demand) */
+    void *cuda_stream;       /* cudaStream_t to run on; NULL: the scene creates its own */
+    int device;              /* CUDA device ordinal; < 0: the current device */
+} dem_scene_desc;
+
+/* Statistics of the current state (utils module reference: kineticEnergy,
+ * unbalancedForce, avgNumInteractions, porosity, getStress). */
+typedef struct dem_stats {
+    long long iter;          /* steps taken (O.iter) */
+    double time;             /* simulated time (O.time) */
+    double dt;
+    long long n_bodies;
+    long long n_contacts;    /* real sphere-sphere contacts */
+    long long n_wall_contacts;
+    long long n_candidates;  /* rows of the contact table (potential interactions) */
+    long long n_rebuilds;    /* collider runs */
+    double kinetic_energy;   /* sum 1/2 (m v^2 + I w^2) */
+    double unbalanced_force; /* mean |contact force on body| / mean |contact force| */
+    double coordination;     /* Z = 2 C / N (sphere-sphere contacts) */
+    double packing_fraction; /* sum of sphere volumes / cell (or box) volume */
+    double stress[9];        /* Love-Weber (1/V) sum f l, compression negative */
+} dem_stats;
+
+/* Per-phase device time of dem_step, measured with CUDA events recorded on the
+ * scene's stream around every launch while timing is enabled (Yade's per-engine
+ * execTime / execCount, section 3.1.6 "Timing").  Times in milliseconds. */
+typedef struct dem_timing {
+    double contact_ms;            /* fused geometry + law kernel */
+    double integrate_ms;          /* gather + integrator kernel */
+    double cell_ms;               /* cell / clock advance */
+    double collider_ms;           /* collider runs (all of their kernels and copies) */
+    long long contact_launches;
+    long long integrate_launches;
+    long long cell_launches;
+    long long collider_runs;
+    long long rows_processed;     /* sum over contact launches of table rows */
+    long long kernel_launches;    /* every kernel this scene launched (timing on or off) */
+} dem_timing;
+
+/* Fill *desc with the defaults listed above.  Never fails. */
+void dem_scene_desc_init(dem_scene_desc *desc);
+
+/* Create an empty scene on the GPU.  desc is copied.  On success *out is a new
+ * handle (free it with dem_scene_destroy).  Errors: INVALID_ARG (null, non-diagonal
+ * or singular periodic cell, negative damping), CUDA, OOM. */
+dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out);
+
+/* Release every resource of the scene (waits for its work to finish). NULL is a no-op. */
+void dem_scene_destroy(dem_scene *scene);
+
+/* FrictMat (Material / ElastMat / FrictMat class reference): density [kg/m^3],
+ * young [Pa], poisson = ks/kn ratio, friction angle [rad] in [0, pi/2).
+ * mat_id in [0, 63].  Must precede dem_add_spheres that use it: mass and inertia
+ * are fixed at insertion (utils.sphere).  Errors: INVALID_ARG. */
+dem_status dem_set_material(dem_scene *scene, int mat_id, double density, double young,
+                            double poisson, double friction_angle);
+
+/* Append n spheres (utils.sphere): pos n*3, radius n (> 0), mat_id n (NULL: all 0),
+ * vel/angvel n*3 (NULL: zero), fixed n (NULL: none; a fixed body keeps its velocities
+ * and is not moved by forces).  Mass = density * 4/3 pi r^3, inertia = 2/5 m r^2.
+ * *first_id (nullable) receives the id of the first new body.  Errors: INVALID_ARG,
+ * NONFINITE, OOM, CUDA. */
+dem_status dem_add_spheres(dem_scene *scene, long long n, const double *pos,
+                           const double *radius, const int *mat_id, const double *vel,
+                           const double *angvel, const unsigned char *fixed,
+                           long long *first_id);
+
+/* Time step (O.dt).  dt > 0.  dem_get_dt returns the step in use (computing the
+ * default 0.5 * PWaveTimeStep if none was set and bodies exist). */
+dem_status dem_set_dt(dem_scene *scene, double dt);
+dem_status dem_get_dt(dem_scene *scene, double *dt);
+
+/* Cell.velGrad for a periodic scene; like Cell.velGrad assignment the value takes
+ * effect at the next step.  Must be diagonal.  Errors: INVALID_ARG, STATE (aperiodic). */
+dem_status dem_set_cell_velgrad(dem_scene *scene, const double velgrad[9]);
+
+/* Advance nsteps time steps (O.run(nsteps, wait=True)).  Blocks until done.
+ * Errors: STATE (no bodies' dt), NONFINITE (a body state became NaN/Inf),
+ * GEOMETRY, CAPACITY, OOM, TIMEOUT, CUDA.  On NONFINITE the scene stops at the
+ * failing step. */
+dem_status dem_step(dem_scene *scene, long long nsteps);
+
+/* Copy the state out in id order.  pos/vel/angvel/force/torque n*3, ori n*4; each
+ * nullable.  force/torque are the contact forces and torques of the last step
+ * (O.forces.f / O.forces.t: gravity excluded). */
+dem_status dem_get_state(dem_scene *scene, double *pos, double *vel, double *angvel, double *ori,
+                         double *force, double *torque);
+
+/* Overwrite body states (id order, each nullable).  Contact histories are kept and
+ * re-matched at the next step; the collider re-runs. */
+dem_status dem_set_state(dem_scene *scene, const double *pos, const double *vel,
+                         const double *angvel, const double *ori);
+
+/* Periodic cell state: H (hSize), velGrad in effect, previous velGrad and previous H
+ * (each nullable).  Errors: STATE (aperiodic). */
+dem_status dem_get_cell(dem_scene *scene, double *H, double *velgrad, double *prev_velgrad,
+                        double *prev_H);
+dem_status dem_set_cell(dem_scene *scene, const double *H, const double *velgrad,
+                        const double *prev_velgrad, const double *prev_H);
+
+/* O.iter and O.time. */
+dem_status dem_get_clock(dem_scene *scene, long long *iter, double *time);
+dem_status dem_set_clock(dem_scene *scene, long long iter, double time);
+
+/* Number of real contacts (sphere-sphere plus sphere-wall) after the last step. */
+dem_status dem_count_contacts(dem_scene *scene, long long *count);
+
+/* Real interactions after the last step (O.interactions, which skips potential
+ * ones), canonical order: sorted by (id1, id2), id1 < id2; a wall contact has
+ * id1 = -(wall + 1) (wall = 2*axis + side) and sorts first.  Per row:
+ * cell_dist 3 ints (Interaction.cellDist, applied to id2), normal_force and
+ * shear_force 3 doubles each (FrictPhys normalForce / shearForce: acting on id2),
+ * normal 3 (ScGeom.normal, from id1 to id2), contact_point 3 (x1 + (r1 - pen/2) n at
+ * the current positions), phys 3 (kn, ks, tan(phi)), pen 1 (penetrationDepth).
+ * Writes min(count, cap) rows; *count receives the total.  Output arrays nullable. */
+dem_status dem_get_contacts(dem_scene *scene, long long cap, long long *count, int *id1,
+                            int *id2, int *cell_dist, double *normal_force,
+                            double *shear_force, double *normal, double *contact_point,
+                            double *phys, double *pen);
+
+/* Replace the contact history (checkpoint/resume): n rows in the canonical order of
+ * dem_get_contacts, each with cell_dist (NULL: zero), the shear force on id2, the
+ * normal of the last step and phys = (kn, ks, tan(phi)).  Rows whose pair is not in
+ * contact at the next step are dropped there.  Errors: INVALID_ARG, OUT_OF_RANGE. */
+dem_status dem_set_contacts(dem_scene *scene, long long n, const int *id1, const int *id2,
+                            const int *cell_dist, const double *shear_force,
+                            const double *normal_prev, const double *phys);
+
+/* Statistics of the current state. */
+dem_status dem_get_stats(dem_scene *scene, dem_stats *out);
+
+/* Enable (1) or disable (0) per-phase timing; either call resets the counters
+ * except kernel_launches.  Timing adds two event records per launch. */
+dem_status dem_set_timing(dem_scene *scene, int enable);
+dem_status dem_get_timing(dem_scene *scene, dem_timing *out);
+
+/* Message of the last error on this scene ("" if none).  NULL scene: the last
+ * error of a failed dem_scene_create in this thread. */
+const char *dem_last_error(const dem_scene *scene);
+
+/* Library version string. */
+const char *dem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,164 @@
+// Internal declarations of the GB300 DEM library: device data layout, the
+// per-scene cell state and the host-side launchers of every kernel.
+//
+// Layout in HBM (one scene):
+//   bodies, in "slot" order (Morton order of the collider grid cell, ties by id),
+//   struct-of-arrays of 32-byte records so that one body field is one sector:
+//     pos    double4_32a (x, y, z, r)         vel    double4_32a (vx, vy, vz, 0)
+//     angvel double4_32a (wx, wy, wz, 0)      ori    double4_32a (qw, qx, qy, qz)
+//     xref   double4_32a (x at the last collider run, 0)
+//     mprop  double4_32a (m, I, 1/m, 1/I)     id int, mat int, flags uint8
+//     whist  double4_32a[6][N] wall-contact history (Fs xyz, signed Fn)
+//   contact table (one row per potential interaction = collider candidate),
+//   rows sorted by (s1, s2) with s1 < s2 the slots of the two spheres:
+//     pair int2, cpack int (cell shift of s2, 3 x 10-bit signed),
+//     hfs double4_32a (Fs on body 2, kn)       kn == 0 <=> not in contact
+//     hn  double4_32a (normal of the last step, ks), tanphi double,
+//     oF  double4_32a (F on body 2, arm d1)    oM double4_32a (-(n x F), arm d2)
+//   so that the torques are T1 = d1*oM, T2 = d2*oM (section 2.1.4 with the
+//   contact point of eq. 2.8: C - x1 = d1 n, C - x2' = -d2 n).
+//   Per-body CSR over the table: row_start[s] (rows with s1 = s, contiguous) and
+//   down_start/down (rows with s2 = s), both in a fixed order, so the force sum
+//   of every body is a gather in one deterministic order (no atomics).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dem {
+
+constexpr int kMaxMat = 64;
+constexpr int kMaxGridSide = 256;   // cells per axis (Morton code of 24 bits)
+
+// error bits set by kernels (DevStatus::error)
+enum : int {
+  kErrNonFinite = 1,
+  kErrHistoryLost = 2,
+  kErrShiftRange = 4,
+};
+
+struct Mat {
+  double density, young, poisson, tanphi;
+};
+
+struct Bodies {
+  double4_32a *pos, *vel, *angvel, *ori, *xref, *mprop;
+  int *id, *mat;
+  uint8_t *flags;   // bit0 fixed; bit (1+w) in contact with wall w
+  double4_32a *whist;   // [6 * cap] or null
+};
+
+struct Table {
+  int2 *pair;
+  int *cpack;
+  double4_32a *hfs, *hn, *oF, *oM;
+  double *tanphi;
+  int *row_start;   // [nbody + 1]
+  int *down_start;  // [nbody + 1]
+  int *down;        // [cap]
+  int *found;       // [cap]
+  long long cap;    // rows
+  long long nbody_cap;
+  long long P;      // rows in use
+};
+
+// Cell and clock state of a scene, kept in device memory and advanced by a
+// one-thread kernel after every step (so that a batch of steps needs no host
+// round trip).  Matrices row-major.
+struct CellState {
+  double H[9], Hprev[9], L[9], Lprev[9];
+  double W[9];      // image velocity matrix Lprev * Hprev (velocity of a cell shift)
+  double dL[9];     // L - Lprev (homoDeform first term)
+  double Hnext[9];  // (I + L dt) H
+  double E[9];      // (Hnext - Href) Href^-1: affine strain since the collider run
+  double Href[9], Hrefinv[9];
+  double dt, time;
+  double verlet, rmax;  // sweep margin dL and largest radius
+  double thr2;          // squared displacement bound that triggers the collider
+  long long iter;
+  int periodic, pad;
+};
+
+// Small status block read back by the host after a batch of steps.
+struct DevStatus {
+  int pending;    // collider run needed before the next step (steps are skipped)
+  int request;    // set by the integrator when a displacement exceeds the bound
+  int error;      // kErr* bits
+  int pad;
+};
+
+struct Grid {
+  int n[3];         // cells per axis
+  int B;            // Morton side (power of two >= max n)
+  double lo[3];     // aperiodic: origin of the grid
+  double scale[3];  // aperiodic: cells per metre; periodic: 1 / L (fraction per metre)
+  double L[3];      // periodic cell edges (diagonal H)
+  int periodic;
+  double reach;     // candidate margin: pair kept when |d| < r1 + r2 + reach
+};
+
+struct SceneConst {
+  long long N;
+  double gravity[3];
+  double damping;
+  double box_lo[3], box_hi[3];
+  int wall_mask;
+  int periodic;
+};
+
+// ---- cell shift packing: 3 x 10-bit two's complement in one int
+__host__ __device__ inline int pack_shift(int c0, int c1, int c2) {
+  return (c0 & 1023) | ((c1 & 1023) << 10) | ((c2 & 1023) << 20);
+}
+__host__ __device__ inline void unpack_shift(int p, int &c0, int &c1, int &c2) {
+  c0 = (int)((unsigned)p << 22) >> 22;
+  c1 = (int)((unsigned)p << 12) >> 22;
+  c2 = (int)((unsigned)p << 2) >> 22;
+}
+constexpr int kShiftMax = 511;
+
+// ---- launchers (each .cu file owns its kernels)
+// scan.cu
+size_t scan_workspace_bytes(long long n);
+void exclusive_scan(const int *in, int *out, long long n, int *workspace, cudaStream_t st);
+
+// collider.cu
+void launch_bbox(const Bodies &b, long long N, double *partials, int nblk, cudaStream_t st);
+int bbox_blocks(long long N);
+void launch_bin(const Bodies &b, long long N, const Grid &g, uint32_t *key, int *count,
+                cudaStream_t st);
+void launch_scatter(long long N, const uint32_t *key, const int *start, int *fill, int *tmp,
+                    cudaStream_t st);
+void launch_cellsort(const int *count, const int *start, long long ncell, const int *id,
+                     int *tmp, cudaStream_t st);
+void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
+                    const int *new_to_old, int *slot_of_id, int has_walls, cudaStream_t st);
+void launch_count(const Bodies &b, long long N, const Grid &g, const int *count,
+                  const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st);
+void launch_emit(const Bodies &b, long long N, const Grid &g, const int *count,
+                 const int *start, const Table &t, cudaStream_t st);
+void launch_down(const Bodies &b, long long N, const Grid &g, const int *count,
+                 const int *start, const Table &t, cudaStream_t st);
+void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
+                  cudaStream_t st);
+void launch_lost(const Table &ot, int *err, cudaStream_t st);
+
+// contact.cu
+void launch_contact(const Table &t, const Bodies &b, const CellState *cs, const DevStatus *ds,
+                    const Mat *mats, int periodic, int nsm, cudaStream_t st);
+
+// integrate.cu
+void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
+                      const Mat *mats, const SceneConst &sc, long long cap, cudaStream_t st);
+void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st);
+void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
+                          const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
+                          cudaStream_t st);
+// stats: per-block partial sums (deterministic tree), summed on the host in block order
+int stats_blocks(long long n);
+void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, double *partials,
+                       cudaStream_t st);
+void launch_row_stats(const Table &t, const Bodies &b, double *partials, cudaStream_t st);
+void launch_wall_stats(const Bodies &b, const SceneConst &sc, const Mat *mats, long long cap,
+                       double *partials, cudaStream_t st);
+
+}  // namespace dem

@@ -1,0 +1,372 @@
+// Per-body kernel of the step: force/torque gather over the body's contact
+// rows in one fixed order (the ForceContainer sum made reproducible, cf. the
+// summation-order example of section 2.1.7 "Result indeterminism"),
+// sphere-wall contacts (Ig2_Wall_Sphere_ScGeom with the same law), gravity,
+// Cundall non-viscous damping (eq. 2.9), leapfrog for position and spherical
+// rotation (section 2.1.5), the orientation quaternion q+ = dq(w dt) q, the
+// homoDeform = 2 velocity terms of a deforming periodic cell (Cell class
+// reference), and the collider trigger (eq. 2.3-2.4) -- all fused in one pass
+// over the body arrays.
+//
+// Also here: the one-thread cell/clock advance (F+ = (I + grad(v) dt) F,
+// section 2.1.6), the force-only gather used by queries, and the statistics
+// reductions (block partial sums in a fixed tree, summed on the host in
+// block order, so every statistic is reproducible bit for bit).
+#include "dem_internal.cuh"
+
+namespace dem {
+
+namespace {
+constexpr int kT = 256;
+
+__device__ inline double sgn(double x) { return (double)((x > 0) - (x < 0)); }
+
+__device__ inline void gather_rows(const Table &t, int s, double F[3], double T[3]) {
+  const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
+  for (int k = r0; k < r1; ++k) {   // rows where s is body 1: force -F, torque d1 M
+    const double4_32a f = t.oF[k], m = t.oM[k];
+    F[0] -= f.x; F[1] -= f.y; F[2] -= f.z;
+    T[0] += f.w * m.x; T[1] += f.w * m.y; T[2] += f.w * m.z;
+  }
+  const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
+  for (int e = e0; e < e1; ++e) {   // rows where s is body 2: force +F, torque d2 M
+    const int k = t.down[e];
+    if (k < 0) continue;
+    const double4_32a f = t.oF[k], m = t.oM[k];
+    F[0] += f.x; F[1] += f.y; F[2] += f.z;
+    T[0] += m.w * m.x; T[1] += m.w * m.y; T[2] += m.w * m.z;
+  }
+}
+
+// FrictPhys of a sphere-wall contact: equivalent wall radius = sphere radius,
+// wall material = material 0.
+__device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn, double &ks,
+                                 double &tanphi) {
+  const Mat mw = mats[0], ms = mats[mat];
+  const double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
+  kn = k1 * k2 / (k1 + k2);
+  const double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
+  ks = s1 * s2 / (s1 + s2);
+  tanphi = fmin(mw.tanphi, ms.tanphi);
+}
+
+__global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
+                                                  DevStatus *ds, const Mat *__restrict__ mats,
+                                                  SceneConst sc, long long cap) {
+  if (ds->pending) return;
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= sc.N) return;
+  const int s = (int)sl;
+  const double dt = cs->dt;
+  double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+  gather_rows(t, s, F, T);
+
+  const double4_32a p = b.pos[s];
+  const double4_32a v = b.vel[s];
+  const double4_32a w = b.angvel[s];
+  const double4_32a mp = b.mprop[s];   // m, I, 1/m, 1/I
+  uint8_t flags = b.flags[s];
+  const double x[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z}, ww[3] = {w.x, w.y, w.z};
+  const double r = p.w;
+
+  if (sc.wall_mask) {
+    for (int wi = 0; wi < 6; ++wi) {
+      if (!(sc.wall_mask & (1 << wi))) continue;
+      const int ax = wi >> 1;
+      const double wc = (wi & 1) ? sc.box_hi[ax] : sc.box_lo[ax];
+      const double dist = x[ax] - wc;
+      const bool was = flags & (2 << wi);
+      if (!(fabs(dist) < r)) {
+        if (was) {
+          b.whist[wi * cap + s] = make_double4_32a(0, 0, 0, 0);
+          flags &= ~(2 << wi);
+        }
+        continue;
+      }
+      const double sn = dist >= 0 ? 1.0 : -1.0;
+      double n[3] = {0, 0, 0};
+      n[ax] = sn;
+      const double pen = r - fabs(dist);
+      double kn, ks, tanphi;
+      wall_phys(mats, b.mat[s], r, kn, ks, tanphi);
+      double fs[3] = {0, 0, 0};
+      if (was) {
+        const double4_32a h = b.whist[wi * cap + s];
+        fs[0] = h.x; fs[1] = h.y; fs[2] = h.z;
+      }
+      // frame motion: n- x n = 0 (the normal is fixed); twist dt/2 n.(0 + w)
+      const double tw = 0.5 * dt * (sn * ww[ax]);
+      const double tn[3] = {tw * n[0], tw * n[1], tw * n[2]};
+      const double c0 = fs[1] * tn[2] - fs[2] * tn[1];
+      const double c1 = fs[2] * tn[0] - fs[0] * tn[2];
+      const double c2 = fs[0] * tn[1] - fs[1] * tn[0];
+      fs[0] -= c0; fs[1] -= c1; fs[2] -= c2;
+      // ratchet-free relative velocity with refR1 = refR2 = r, l = 2r - pen, wall at rest
+      const double rr[3] = {r * ww[0], r * ww[1], r * ww[2]};
+      const double cr[3] = {rr[1] * n[2] - rr[2] * n[1], rr[2] * n[0] - rr[0] * n[2],
+                            rr[0] * n[1] - rr[1] * n[0]};
+      const double fac = (r + r) / (2 * r - pen);
+      double u[3];
+      for (int q = 0; q < 3; ++q) u[q] = fac * vv[q] - cr[q];
+      const double vn = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+      for (int q = 0; q < 3; ++q) fs[q] -= ks * (dt * (u[q] - vn * n[q]));
+      const double Fn = kn * pen;
+      const double maxFs = Fn * tanphi;
+      const double fs2 = fs[0] * fs[0] + fs[1] * fs[1] + fs[2] * fs[2];
+      if (fs2 > maxFs * maxFs) {
+        const double scl = maxFs / sqrt(fs2);
+        fs[0] *= scl; fs[1] *= scl; fs[2] *= scl;
+      }
+      const double F2[3] = {Fn * n[0] + fs[0], Fn * n[1] + fs[1], Fn * n[2] + fs[2]};
+      const double arm = -(r - 0.5 * pen);   // C - x = arm * n
+      const double a[3] = {arm * n[0], arm * n[1], arm * n[2]};
+      F[0] += F2[0]; F[1] += F2[1]; F[2] += F2[2];
+      T[0] += a[1] * F2[2] - a[2] * F2[1];
+      T[1] += a[2] * F2[0] - a[0] * F2[2];
+      T[2] += a[0] * F2[1] - a[1] * F2[0];
+      b.whist[wi * cap + s] = make_double4_32a(fs[0], fs[1], fs[2], sn * Fn);
+      flags |= (2 << wi);
+    }
+  }
+
+  double vn_[3], wn_[3];
+  const bool fixed = flags & 1;
+  if (!fixed) {
+    const double lam = sc.damping;
+    double vref[3] = {vv[0], vv[1], vv[2]};
+    if (sc.periodic) {   // fluctuation velocity for eq. 2.9 in a deforming cell
+      const double *Lp = cs->Lprev;
+      for (int q = 0; q < 3; ++q) vref[q] -= Lp[3 * q] * x[0] + Lp[3 * q + 1] * x[1] + Lp[3 * q + 2] * x[2];
+    }
+    for (int q = 0; q < 3; ++q) {
+      const double Ft = F[q] + mp.x * sc.gravity[q];
+      const double acc = Ft * mp.z;
+      const double Fd = Ft * (1 - lam * sgn(Ft * (vref[q] + 0.5 * dt * acc)));
+      vn_[q] = vv[q] + dt * Fd * mp.z;
+      const double aacc = T[q] * mp.w;
+      const double Td = T[q] * (1 - lam * sgn(T[q] * (ww[q] + 0.5 * dt * aacc)));
+      wn_[q] = ww[q] + dt * Td * mp.w;
+    }
+    if (sc.periodic) {   // homoDeform = 2
+      const double *dL = cs->dL, *L = cs->L;
+      for (int q = 0; q < 3; ++q)
+        vn_[q] += (dL[3 * q] * x[0] + dL[3 * q + 1] * x[1] + dL[3 * q + 2] * x[2]) +
+                  dt * (L[3 * q] * vv[0] + L[3 * q + 1] * vv[1] + L[3 * q + 2] * vv[2]);
+    }
+  } else {
+    for (int q = 0; q < 3; ++q) { vn_[q] = vv[q]; wn_[q] = ww[q]; }
+  }
+  const double xn[3] = {x[0] + dt * vn_[0], x[1] + dt * vn_[1], x[2] + dt * vn_[2]};
+  b.pos[s] = make_double4_32a(xn[0], xn[1], xn[2], r);
+  b.vel[s] = make_double4_32a(vn_[0], vn_[1], vn_[2], 0.0);
+  b.angvel[s] = make_double4_32a(wn_[0], wn_[1], wn_[2], 0.0);
+  if (flags != b.flags[s]) b.flags[s] = flags;
+
+  // orientation: q+ = dq(w+ dt) q
+  const double wmag = sqrt(wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2]);
+  if (wmag > 0) {
+    const double4_32a q0 = b.ori[s];
+    double sh, ch;
+    sincos(0.5 * (wmag * dt), &sh, &ch);
+    const double iw = sh / wmag;
+    const double dw = ch, dx = iw * wn_[0], dy = iw * wn_[1], dz = iw * wn_[2];
+    b.ori[s] = make_double4_32a(dw * q0.x - dx * q0.y - dy * q0.z - dz * q0.w,
+                            dw * q0.y + dx * q0.x + dy * q0.w - dz * q0.z,
+                            dw * q0.z - dx * q0.w + dy * q0.x + dz * q0.y,
+                            dw * q0.w + dx * q0.z - dy * q0.y + dz * q0.x);
+  }
+
+  // collider trigger: displacement since the last run, minus the affine part
+  const double4_32a xr = b.xref[s];
+  const double *E = cs->E;
+  const double ux = (xn[0] - xr.x) - (E[0] * xr.x + E[1] * xr.y + E[2] * xr.z);
+  const double uy = (xn[1] - xr.y) - (E[3] * xr.x + E[4] * xr.y + E[5] * xr.z);
+  const double uz = (xn[2] - xr.z) - (E[6] * xr.x + E[7] * xr.y + E[8] * xr.z);
+  const double u2 = ux * ux + uy * uy + uz * uz;
+  if (!(u2 <= cs->thr2)) {
+    if (!ds->request) ds->request = 1;
+  }
+  if (!isfinite(xn[0] + xn[1] + xn[2] + vn_[0] + vn_[1] + vn_[2] + wn_[0] + wn_[1] + wn_[2]))
+    atomicOr(&ds->error, kErrNonFinite);
+}
+
+// Row-major 3x3 helpers evaluated with round-to-nearest operations in a fixed
+// order (the same order the oracle writes them), so the cell history is
+// reproducible on every platform.
+__device__ inline void m_mul_rn(const double *A, const double *B, double *O) {
+  double Tm[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      Tm[3 * r + c] = __dadd_rn(__dadd_rn(__dmul_rn(A[3 * r], B[c]), __dmul_rn(A[3 * r + 1], B[3 + c])),
+                                __dmul_rn(A[3 * r + 2], B[6 + c]));
+  for (int q = 0; q < 9; ++q) O[q] = Tm[q];
+}
+
+__global__ void k_cell_advance(CellState *cs, DevStatus *ds) {
+  if (ds->pending) return;
+  const double dt = cs->dt;
+  if (cs->periodic) {
+    for (int q = 0; q < 9; ++q) {
+      cs->Hprev[q] = cs->H[q];
+      cs->H[q] = cs->Hnext[q];
+      cs->Lprev[q] = cs->L[q];
+      cs->dL[q] = 0.0;   // L - Lprev after the assignment above
+    }
+    m_mul_rn(cs->Lprev, cs->Hprev, cs->W);
+    double A[9];
+    for (int q = 0; q < 9; ++q) A[q] = __dadd_rn((q % 4 == 0) ? 1.0 : 0.0, __dmul_rn(cs->L[q], dt));
+    m_mul_rn(A, cs->H, cs->Hnext);
+    double D[9];
+    for (int q = 0; q < 9; ++q) D[q] = cs->Hnext[q] - cs->Href[q];
+    m_mul_rn(D, cs->Hrefinv, cs->E);
+    double e2 = 0;
+    for (int q = 0; q < 9; ++q) e2 += cs->E[q] * cs->E[q];
+    const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
+    cs->thr2 = eff > 0 ? eff * eff : -1.0;
+  }
+  cs->iter += 1;
+  cs->time = __dadd_rn(cs->time, dt);
+  if (ds->request) ds->pending = 1;
+}
+
+__global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats, SceneConst sc,
+                                long long cap, double4_32a *Fo, double4_32a *To) {
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= sc.N) return;
+  const int s = (int)sl;
+  double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+  gather_rows(t, s, F, T);
+  const uint8_t flags = b.flags[s];
+  if (sc.wall_mask && (flags & 0x7e)) {
+    const double r = b.pos[s].w;
+    for (int wi = 0; wi < 6; ++wi) {
+      if (!(flags & (2 << wi))) continue;
+      const double4_32a h = b.whist[wi * cap + s];
+      const int ax = wi >> 1;
+      const double sn = h.w >= 0 ? 1.0 : -1.0;
+      const double Fn = fabs(h.w);
+      double kn, ks, tanphi;
+      wall_phys(mats, b.mat[s], r, kn, ks, tanphi);
+      const double pen = Fn / kn;
+      double n[3] = {0, 0, 0};
+      n[ax] = sn;
+      const double F2[3] = {Fn * n[0] + h.x, Fn * n[1] + h.y, Fn * n[2] + h.z};
+      const double arm = -(r - 0.5 * pen);
+      const double a[3] = {arm * n[0], arm * n[1], arm * n[2]};
+      F[0] += F2[0]; F[1] += F2[1]; F[2] += F2[2];
+      T[0] += a[1] * F2[2] - a[2] * F2[1];
+      T[1] += a[2] * F2[0] - a[0] * F2[2];
+      T[2] += a[0] * F2[1] - a[1] * F2[0];
+    }
+  }
+  Fo[s] = make_double4_32a(F[0], F[1], F[2], 0);
+  To[s] = make_double4_32a(T[0], T[1], T[2], 0);
+}
+
+// ---- deterministic block reductions of K doubles
+template <int K>
+__device__ inline void block_reduce_store(double (&v)[K], double *partials) {
+  __shared__ double sh[K][kT];
+  for (int q = 0; q < K; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < K; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < K; ++q) partials[K * blockIdx.x + q] = sh[q][0];
+}
+
+// ke, sum |F contact| over free bodies, number of free bodies
+__global__ void k_body_stats(Bodies b, const double4_32a *__restrict__ F, long long N, double *partials) {
+  double v[3] = {0, 0, 0};
+  for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < N; i += (long long)gridDim.x * kT) {
+    const double4_32a u = b.vel[i], w = b.angvel[i], mp = b.mprop[i];
+    v[0] += 0.5 * mp.x * (u.x * u.x + u.y * u.y + u.z * u.z) + 0.5 * mp.y * (w.x * w.x + w.y * w.y + w.z * w.z);
+    if (!(b.flags[i] & 1)) {
+      const double4_32a f = F[i];
+      v[1] += sqrt(f.x * f.x + f.y * f.y + f.z * f.z);
+      v[2] += 1.0;
+    }
+  }
+  block_reduce_store<3>(v, partials);
+}
+
+// real sphere-sphere rows: count, sum |F|, Love-Weber stress sum F_i (x1 - x2')_j
+__global__ void k_row_stats(Table t, double *partials) {
+  double v[11] = {0};
+  for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
+    const double4_32a fs = t.hfs[k];
+    if (fs.w == 0.0) continue;
+    const double4_32a f = t.oF[k], m = t.oM[k], n = t.hn[k];
+    const double l = f.w + m.w;
+    v[0] += 1.0;
+    v[1] += sqrt(f.x * f.x + f.y * f.y + f.z * f.z);
+    const double F3[3] = {f.x, f.y, f.z}, br[3] = {-l * n.x, -l * n.y, -l * n.z};
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) v[2 + 3 * a + c] += F3[a] * br[c];
+  }
+  block_reduce_store<11>(v, partials);
+}
+
+// wall contacts: count, sum |F|
+__global__ void k_wall_stats(Bodies b, SceneConst sc, const Mat *__restrict__ mats, long long cap,
+                             double *partials) {
+  double v[2] = {0, 0};
+  for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < sc.N; i += (long long)gridDim.x * kT) {
+    const uint8_t fl = b.flags[i];
+    if (!(fl & 0x7e)) continue;
+    for (int wi = 0; wi < 6; ++wi) {
+      if (!(fl & (2 << wi))) continue;
+      const double4_32a h = b.whist[wi * cap + i];
+      const int ax = wi >> 1;
+      const double sn = h.w >= 0 ? 1.0 : -1.0;
+      double F2[3] = {h.x, h.y, h.z};
+      F2[ax] += sn * fabs(h.w);
+      v[0] += 1.0;
+      v[1] += sqrt(F2[0] * F2[0] + F2[1] * F2[1] + F2[2] * F2[2]);
+    }
+  }
+  block_reduce_store<2>(v, partials);
+}
+
+inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
+}  // namespace
+
+void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
+                          const Mat *mats, const SceneConst &sc, long long cap, cudaStream_t st) {
+  if (sc.N > 0) k_integrate<<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+}
+
+void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st) {
+  k_cell_advance<<<1, 1, 0, st>>>(cs, ds);
+}
+
+void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
+                              const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
+                              cudaStream_t st) {
+  if (sc.N > 0) k_gather_forces<<<blocks(sc.N), kT, 0, st>>>(b, t, mats, sc, cap, F, T);
+}
+
+int stats_blocks(long long n) {
+  long long b = (n + kT - 1) / kT;
+  return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, double *partials,
+                       cudaStream_t st) {
+  k_body_stats<<<stats_blocks(N), kT, 0, st>>>(b, F, N, partials);
+}
+
+void launch_row_stats(const Table &t, const Bodies &b, double *partials, cudaStream_t st) {
+  (void)b;
+  k_row_stats<<<stats_blocks(t.P), kT, 0, st>>>(t, partials);
+}
+
+void launch_wall_stats(const Bodies &b, const SceneConst &sc, const Mat *mats, long long cap,
+                           double *partials, cudaStream_t st) {
+  k_wall_stats<<<stats_blocks(sc.N), kT, 0, st>>>(b, sc, mats, cap, partials);
+}
+
+}  // namespace dem

@@ -1,0 +1,1348 @@
+// Host side of the library: scene lifetime, device arenas, the step driver
+// and the extern "C" entry points declared in include/dem.h.
+//
+// Step driver.  A step is: contact kernel (rows) -> integrate kernel (bodies)
+// -> one-thread cell/clock advance.  Steps are queued in batches with no host
+// round trip: the integrator raises a request when some body has moved more
+// than the sweep margin since the last collider run (eq. 2.3-2.4, corrected for
+// the affine strain of a deforming cell), the cell advance turns it into
+// "pending", and every kernel of a later step returns immediately while
+// pending is set.  After each batch the host reads a small status block; if a
+// collider run is pending it runs the collider (collider.cu) and continues.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dem_internal.cuh"
+#include "dem.h"
+
+using namespace dem;
+
+namespace {
+thread_local std::string g_create_error;
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+double timeout_s() {
+  const char *e = std::getenv("DEM_TIMEOUT_S");
+  double t = e ? std::atof(e) : 120.0;
+  return t > 0 ? t : 120.0;
+}
+
+// host twin of the device cell derivations (same operation order as the oracle)
+void m_mul(const double *A, const double *B, double *O) {
+  double T[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      T[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+  std::memcpy(O, T, sizeof T);
+}
+double m_det(const double *M) {
+  return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+         M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+bool m_inv(const double *M, double *O) {
+  double d = m_det(M);
+  if (d == 0 || !std::isfinite(d)) return false;
+  double T[9];
+  T[0] = (M[4] * M[8] - M[5] * M[7]) / d;
+  T[1] = (M[2] * M[7] - M[1] * M[8]) / d;
+  T[2] = (M[1] * M[5] - M[2] * M[4]) / d;
+  T[3] = (M[5] * M[6] - M[3] * M[8]) / d;
+  T[4] = (M[0] * M[8] - M[2] * M[6]) / d;
+  T[5] = (M[2] * M[3] - M[0] * M[5]) / d;
+  T[6] = (M[3] * M[7] - M[4] * M[6]) / d;
+  T[7] = (M[1] * M[6] - M[0] * M[7]) / d;
+  T[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+  std::memcpy(O, T, sizeof T);
+  return true;
+}
+bool is_diag(const double *M) {
+  return M[1] == 0 && M[2] == 0 && M[3] == 0 && M[5] == 0 && M[6] == 0 && M[7] == 0;
+}
+
+// Quantities of the next step that follow from (H, L, Lprev, Hprev, dt, Href).
+void cell_derive(CellState &c) {
+  if (!c.periodic) {
+    for (int q = 0; q < 9; ++q) { c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0; }
+    c.thr2 = c.verlet * c.verlet;
+    return;
+  }
+  m_mul(c.Lprev, c.Hprev, c.W);
+  for (int q = 0; q < 9; ++q) c.dL[q] = c.L[q] - c.Lprev[q];
+  double A[9];
+  for (int q = 0; q < 9; ++q) A[q] = ((q % 4 == 0) ? 1.0 : 0.0) + c.L[q] * c.dt;
+  m_mul(A, c.H, c.Hnext);
+  double D[9];
+  for (int q = 0; q < 9; ++q) D[q] = c.Hnext[q] - c.Href[q];
+  m_mul(D, c.Hrefinv, c.E);
+  double e2 = 0;
+  for (int q = 0; q < 9; ++q) e2 += c.E[q] * c.E[q];
+  double eff = c.verlet - std::sqrt(e2) * (c.rmax + c.verlet);
+  c.thr2 = eff > 0 ? eff * eff : -1.0;
+}
+
+unsigned next_pow2(unsigned v) {
+  unsigned p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+}  // namespace
+
+struct Readback {
+  CellState cs;
+  DevStatus ds;
+  int totals[4];
+};
+
+struct dem_scene {
+  dem_scene_desc desc{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int nsm = 152;
+  std::string err;
+
+  Mat mats_h[kMaxMat]{};
+  bool mat_set[kMaxMat]{};
+  Mat *mats_d = nullptr;
+
+  long long N = 0, cap = 0;
+  double rmin = INFINITY, rmax = 0, vsolid = 0;
+  std::vector<double> radius_h;  // by id
+  std::vector<int> mat_h;        // by id
+  std::vector<unsigned char> fixed_h;
+
+  Bodies cur{}, alt{};
+  int *slot_of_id = nullptr, *new_to_old = nullptr, *cnt_up = nullptr, *cnt_down = nullptr;
+  uint32_t *key = nullptr;
+  double4_32a *gF = nullptr, *gT = nullptr;
+
+  Table tab[2]{};
+  long long tab_nbody[2]{0, 0};
+  int tc = 0;
+
+  int *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
+  long long cell_cap = 0;
+  int *scan_ws = nullptr;
+  size_t scan_ws_bytes = 0;
+  double *partials = nullptr;  // 1024 blocks x 16 doubles
+  double *partials_h = nullptr;
+
+  CellState cs_h{};
+  CellState *cs_d = nullptr;
+  DevStatus *ds_d = nullptr;
+  Readback *rb_h = nullptr;  // pinned
+  cudaEvent_t ev = nullptr;
+
+  bool need_rebuild = true;
+  bool check_lost = false;
+  bool cs_dirty = true;
+  bool dt_set = false;
+  bool has_walls = false;
+  long long n_rebuilds = 0;
+  bool velgrad_pending = false;
+  double velgrad_next[9]{};
+  bool broken = false;
+  long long batch = 16;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;   // event pool: 6 per step of a batch + 2 for the collider
+  dem_timing tm{};
+  long long launches = 0;
+};
+
+namespace {
+
+dem_status fail(dem_scene *s, dem_status code, const std::string &msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+dem_status cuda_fail(dem_scene *s, cudaError_t e, const char *what) {
+  if (s) s->broken = true;
+  return fail(s, DEM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                       \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, #call);             \
+  } while (0)
+
+template <class T>
+dem_status dalloc(dem_scene *s, T **p, long long count) {
+  *p = nullptr;
+  if (count <= 0) return DEM_OK;
+  cudaError_t e = cudaMallocAsync((void **)p, sizeof(T) * (size_t)count, s->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(s, DEM_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  return DEM_OK;
+}
+
+template <class T>
+void dfree(dem_scene *s, T *&p) {
+  if (p) cudaFreeAsync(p, s->st);
+  p = nullptr;
+}
+
+dem_status wait(dem_scene *s) {
+  CK(cudaEventRecord(s->ev, s->st));
+  const double deadline = now_s() + timeout_s();
+  int spins = 0;
+  while (true) {
+    cudaError_t e = cudaEventQuery(s->ev);
+    if (e == cudaSuccess) return DEM_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(s, e, "stream wait");
+    if (now_s() > deadline) {
+      s->broken = true;
+      return fail(s, DEM_ERR_TIMEOUT, "timed out waiting for the GPU");
+    }
+    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    else std::this_thread::yield();
+  }
+}
+
+void free_bodies(dem_scene *s, Bodies &b) {
+  dfree(s, b.pos); dfree(s, b.vel); dfree(s, b.angvel); dfree(s, b.ori); dfree(s, b.xref);
+  dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.mat); dfree(s, b.flags); dfree(s, b.whist);
+}
+
+dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
+  dem_status r;
+  if ((r = dalloc(s, &b.pos, cap)) || (r = dalloc(s, &b.vel, cap)) ||
+      (r = dalloc(s, &b.angvel, cap)) || (r = dalloc(s, &b.ori, cap)) ||
+      (r = dalloc(s, &b.xref, cap)) || (r = dalloc(s, &b.mprop, cap)) ||
+      (r = dalloc(s, &b.id, cap)) || (r = dalloc(s, &b.mat, cap)) ||
+      (r = dalloc(s, &b.flags, cap)))
+    return r;
+  if (s->has_walls && (r = dalloc(s, &b.whist, 6 * cap))) return r;
+  return DEM_OK;
+}
+
+void free_table(dem_scene *s, Table &t) {
+  dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oF);
+  dfree(s, t.oM); dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
+  dfree(s, t.row_start); dfree(s, t.down_start);
+  t.cap = 0; t.nbody_cap = 0; t.P = 0;
+}
+
+// capacity for `rows` rows and `nbody` bodies; keeps nothing (callers rebuild)
+dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody) {
+  dem_status r;
+  if (rows > t.cap) {
+    long long P = t.P;
+    long long nc = std::max<long long>(rows + rows / 4, 1024);
+    dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oF);
+    dfree(s, t.oM); dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
+    if ((r = dalloc(s, &t.pair, nc)) || (r = dalloc(s, &t.cpack, nc)) ||
+        (r = dalloc(s, &t.hfs, nc)) || (r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oF, nc)) ||
+        (r = dalloc(s, &t.oM, nc)) || (r = dalloc(s, &t.tanphi, nc)) ||
+        (r = dalloc(s, &t.down, nc)) || (r = dalloc(s, &t.found, nc)))
+      return r;
+    t.cap = nc;
+    t.P = std::min(P, nc);
+  }
+  if (nbody + 1 > t.nbody_cap) {
+    long long nb = std::max<long long>(nbody + 1, 64);
+    dfree(s, t.row_start); dfree(s, t.down_start);
+    if ((r = dalloc(s, &t.row_start, nb)) || (r = dalloc(s, &t.down_start, nb))) return r;
+    t.nbody_cap = nb;
+  }
+  return DEM_OK;
+}
+
+dem_status ensure_bodies(dem_scene *s, long long need) {
+  if (need <= s->cap) return DEM_OK;
+  long long nc = std::max<long long>(need, std::max<long long>(s->cap * 2, 1024));
+  Bodies nb{}, na{};
+  dem_status r;
+  if ((r = alloc_bodies(s, nb, nc)) || (r = alloc_bodies(s, na, nc))) return r;
+  const long long N = s->N;
+  if (N > 0) {
+    size_t d4 = sizeof(double4_32a) * N;
+    CK(cudaMemcpyAsync(nb.pos, s->cur.pos, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.vel, s->cur.vel, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.angvel, s->cur.angvel, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.ori, s->cur.ori, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.xref, s->cur.xref, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.mprop, s->cur.mprop, d4, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.id, s->cur.id, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.mat, s->cur.mat, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.flags, s->cur.flags, N, cudaMemcpyDeviceToDevice, s->st));
+    if (s->has_walls)
+      for (int w = 0; w < 6; ++w)
+        CK(cudaMemcpyAsync(nb.whist + w * nc, s->cur.whist + w * s->cap, d4,
+                           cudaMemcpyDeviceToDevice, s->st));
+  }
+  free_bodies(s, s->cur);
+  free_bodies(s, s->alt);
+  s->cur = nb;
+  s->alt = na;
+  int *sid = nullptr;
+  if ((r = dalloc(s, &sid, nc))) return r;
+  if (N > 0) CK(cudaMemcpyAsync(sid, s->slot_of_id, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
+  dfree(s, s->slot_of_id);
+  s->slot_of_id = sid;
+  dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down); dfree(s, s->key);
+  dfree(s, s->gF); dfree(s, s->gT);
+  if ((r = dalloc(s, &s->new_to_old, nc)) || (r = dalloc(s, &s->cnt_up, nc)) ||
+      (r = dalloc(s, &s->cnt_down, nc)) || (r = dalloc(s, &s->key, nc)) ||
+      (r = dalloc(s, &s->gF, nc)) || (r = dalloc(s, &s->gT, nc)))
+    return r;
+  s->cap = nc;
+  size_t ws = scan_workspace_bytes(nc + 1);
+  if (ws > s->scan_ws_bytes) {
+    dfree(s, s->scan_ws);
+    if ((r = dalloc(s, &s->scan_ws, (long long)(ws / sizeof(int) + 1)))) return r;
+    s->scan_ws_bytes = ws;
+  }
+  return DEM_OK;
+}
+
+SceneConst scene_const(const dem_scene *s) {
+  SceneConst c{};
+  c.N = s->N;
+  for (int k = 0; k < 3; ++k) {
+    c.gravity[k] = s->desc.gravity[k];
+    c.box_lo[k] = s->desc.box_lo[k];
+    c.box_hi[k] = s->desc.box_hi[k];
+  }
+  c.damping = s->desc.damping;
+  c.wall_mask = s->has_walls ? s->desc.wall_mask : 0;
+  c.periodic = s->desc.periodic;
+  return c;
+}
+
+// 0.5 * utils.PWaveTimeStep: min over spheres of SpherePWaveTimeStep = r / sqrt(E / rho)
+double default_dt(const dem_scene *s) {
+  double dt = INFINITY;
+  for (long long i = 0; i < s->N; ++i) {
+    const Mat &m = s->mats_h[s->mat_h[i]];
+    double d = s->radius_h[i] / std::sqrt(m.young / m.density);
+    if (d < dt) dt = d;
+  }
+  return 0.5 * dt;
+}
+
+dem_status ensure_dt(dem_scene *s) {
+  if (s->dt_set) return DEM_OK;
+  if (s->N == 0) return fail(s, DEM_ERR_STATE, "no time step: the scene has no bodies");
+  s->cs_h.dt = default_dt(s);
+  s->dt_set = true;
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status upload_cell(dem_scene *s) {
+  cell_derive(s->cs_h);
+  CK(cudaMemcpyAsync(s->cs_d, &s->cs_h, sizeof(CellState), cudaMemcpyHostToDevice, s->st));
+  s->cs_dirty = false;
+  return DEM_OK;
+}
+
+dem_status status_error(dem_scene *s, int e) {
+  if (e & kErrNonFinite) return fail(s, DEM_ERR_NONFINITE, "a body state became NaN or Inf");
+  if (e & kErrShiftRange)
+    return fail(s, DEM_ERR_CAPACITY, "a periodic cell shift exceeds +-511 cells");
+  if (e & kErrHistoryLost)
+    return fail(s, DEM_ERR_STATE,
+                "a real contact was missing from the collider candidates (sweep margin violated)");
+  return fail(s, DEM_ERR_STATE, "device error");
+}
+
+// ------------------------------------------------------------------ collider
+dem_status rebuild_core(dem_scene *s);
+
+// kernels the collider launches (bin, scan x2-3, scatter, cellsort, reorder, count,
+// scans, emit, merge, down, lost): counted approximately from its phases
+dem_status rebuild(dem_scene *s) {
+  if (s->timing) CK(cudaEventRecord(s->tev[0], s->st));
+  dem_status r = rebuild_core(s);
+  if (r) return r;
+  s->launches += 14;
+  if (s->timing) {
+    CK(cudaEventRecord(s->tev[1], s->st));
+    CK(cudaEventSynchronize(s->tev[1]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, s->tev[0], s->tev[1]));
+    s->tm.collider_ms += ms;
+    s->tm.collider_runs += 1;
+  }
+  return DEM_OK;
+}
+
+dem_status rebuild_core(dem_scene *s) {
+  const long long N = s->N;
+  const double verlet = s->cs_h.verlet;
+  const double reach = 2 * verlet;
+  const double hmin = 2 * s->rmax + reach;
+  Grid g{};
+  g.periodic = s->desc.periodic;
+  g.reach = reach;
+  if (g.periodic) {
+    for (int k = 0; k < 3; ++k) {
+      double L = s->cs_h.H[4 * k];
+      int n = (int)std::floor(L / hmin);
+      if (n < 3)
+        return fail(s, DEM_ERR_GEOMETRY,
+                    "periodic cell edge shorter than 3 * (2 r_max + 2 verlet_dist): a sphere "
+                    "spans too large a part of the cell");
+      g.n[k] = std::min(n, kMaxGridSide);
+      g.L[k] = L;
+      g.scale[k] = 1.0 / L;
+      g.lo[k] = 0;
+    }
+  } else {
+    int nblk = bbox_blocks(N);
+    launch_bbox(s->cur, N, s->partials, nblk, s->st);
+    CK(cudaMemcpyAsync(s->partials_h, s->partials, sizeof(double) * 6 * nblk,
+                       cudaMemcpyDeviceToHost, s->st));
+    dem_status r = wait(s);
+    if (r) return r;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nblk; ++b)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], s->partials_h[6 * b + k]);
+        hi[k] = std::max(hi[k], s->partials_h[6 * b + 3 + k]);
+      }
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(lo[k]) || !std::isfinite(hi[k]))
+        return fail(s, DEM_ERR_NONFINITE, "non-finite body position");
+      double ext = std::max(hi[k] - lo[k], hmin);
+      int n = (int)std::floor(ext / hmin);
+      n = std::max(1, std::min(n, kMaxGridSide));
+      g.n[k] = n;
+      g.lo[k] = lo[k];
+      g.scale[k] = n / ext;
+      g.L[k] = 0;
+    }
+  }
+  g.B = (int)next_pow2((unsigned)std::max(g.n[0], std::max(g.n[1], g.n[2])));
+  const long long ncell = (long long)g.B * g.B * g.B;
+  dem_status r;
+  if (ncell > s->cell_cap) {
+    dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
+    if ((r = dalloc(s, &s->cell_count, ncell)) || (r = dalloc(s, &s->cell_start, ncell + 1)) ||
+        (r = dalloc(s, &s->cell_fill, ncell)))
+      return r;
+    s->cell_cap = ncell;
+    size_t ws = scan_workspace_bytes(ncell + 1);
+    if (ws > s->scan_ws_bytes) {
+      dfree(s, s->scan_ws);
+      if ((r = dalloc(s, &s->scan_ws, (long long)(ws / sizeof(int) + 1)))) return r;
+      s->scan_ws_bytes = ws;
+    }
+  }
+  CK(cudaMemsetAsync(s->cell_count, 0, sizeof(int) * ncell, s->st));
+  CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(int) * ncell, s->st));
+  CK(cudaMemsetAsync(&s->ds_d->error, 0, sizeof(int), s->st));
+  // 1-3: bin, counting sort into Morton order, permute the bodies
+  launch_bin(s->cur, N, g, s->key, s->cell_count, s->st);
+  exclusive_scan(s->cell_count, s->cell_start, ncell, s->scan_ws, s->st);
+  launch_scatter(N, s->key, s->cell_start, s->cell_fill, s->new_to_old, s->st);
+  launch_cellsort(s->cell_count, s->cell_start, ncell, s->cur.id, s->new_to_old, s->st);
+  launch_reorder(s->cur, s->alt, N, s->cap, s->new_to_old, s->slot_of_id, s->has_walls, s->st);
+  std::swap(s->cur, s->alt);
+  // 4: candidates (count, prefix sums, emit)
+  Table &ot = s->tab[s->tc];
+  Table &nt = s->tab[1 - s->tc];
+  if ((r = ensure_table(s, nt, 0, N))) return r;
+  launch_count(s->cur, N, g, s->cell_count, s->cell_start, s->cnt_up, s->cnt_down,
+               &s->ds_d->error, s->st);
+  exclusive_scan(s->cnt_up, nt.row_start, N, s->scan_ws, s->st);
+  exclusive_scan(s->cnt_down, nt.down_start, N, s->scan_ws, s->st);
+  CK(cudaMemcpyAsync(&s->rb_h->totals[0], nt.row_start + N, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&s->rb_h->totals[1], nt.down_start + N, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&s->rb_h->ds, s->ds_d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->st));
+  if ((r = wait(s))) return r;
+  if (s->rb_h->ds.error) return status_error(s, s->rb_h->ds.error);
+  const long long P = s->rb_h->totals[0];
+  if (P != s->rb_h->totals[1]) return fail(s, DEM_ERR_STATE, "internal: candidate count mismatch");
+  if ((r = ensure_table(s, nt, P, N))) return r;
+  nt.P = P;
+  launch_emit(s->cur, N, g, s->cell_count, s->cell_start, nt, s->st);
+  // 5: carry the contact history of the previous table
+  ot.P = std::min(ot.P, ot.cap);
+  if (ot.P > 0) CK(cudaMemsetAsync(ot.found, 0, sizeof(int) * ot.P, s->st));
+  Table otv = ot;
+  if (ot.P == 0 || ot.row_start == nullptr) otv.P = 0;
+  launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->st);
+  // 6: rows where each body is the second sphere
+  launch_down(s->cur, N, g, s->cell_count, s->cell_start, nt, s->st);
+  if (s->check_lost) launch_lost(otv, &s->ds_d->error, s->st);
+  s->tab_nbody[1 - s->tc] = N;
+  s->tc = 1 - s->tc;
+  // reference configuration of this collider run
+  std::memcpy(s->cs_h.Href, s->cs_h.H, sizeof s->cs_h.H);
+  if (!m_inv(s->cs_h.Href, s->cs_h.Hrefinv))
+    return fail(s, DEM_ERR_INVALID_ARG, "singular periodic cell");
+  if ((r = upload_cell(s))) return r;
+  // clear pending/request; the error word keeps the history check of this run,
+  // which the host reads with the next status block
+  CK(cudaMemsetAsync(s->ds_d, 0, 2 * sizeof(int), s->st));
+  s->need_rebuild = false;
+  s->check_lost = true;
+  s->n_rebuilds += 1;
+  CK(cudaGetLastError());
+  return DEM_OK;
+}
+
+dem_status read_status(dem_scene *s) {
+  CK(cudaMemcpyAsync(&s->rb_h->cs, s->cs_d, sizeof(CellState), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&s->rb_h->ds, s->ds_d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->st));
+  dem_status r = wait(s);
+  if (r) return r;
+  s->cs_h = s->rb_h->cs;
+  return DEM_OK;
+}
+
+dem_status sync_host(dem_scene *s) {
+  if (s->broken) return fail(s, DEM_ERR_STATE, "scene unusable after an earlier CUDA error");
+  return wait(s);
+}
+
+// Bring pending host-side changes (velGrad, dt) into the device cell state.
+dem_status prepare_step(dem_scene *s) {
+  if (s->velgrad_pending) {
+    std::memcpy(s->cs_h.L, s->velgrad_next, sizeof s->velgrad_next);
+    s->velgrad_pending = false;
+    s->cs_dirty = true;
+  }
+  if (s->cs_dirty) return upload_cell(s);
+  return DEM_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void dem_scene_desc_init(dem_scene_desc *d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof *d);
+  d->periodic = 0;
+  for (int q = 0; q < 9; ++q) d->cell_h[q] = (q % 4 == 0) ? 1.0 : 0.0;
+  for (int k = 0; k < 3; ++k) { d->box_lo[k] = 0; d->box_hi[k] = 1; d->gravity[k] = 0; }
+  d->wall_mask = 0;
+  d->damping = 0.2;
+  d->dt = 0;
+  d->verlet_dist = -0.5;
+  d->precision = DEM_FP64;
+  d->capacity_bodies = 0;
+  d->capacity_contacts = 0;
+  d->cuda_stream = nullptr;
+  d->device = -1;
+}
+
+const char *dem_version(void) { return "gb300-dem 0.1 (sm_103a, fp64)"; }
+
+const char *dem_last_error(const dem_scene *s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
+  g_create_error.clear();
+  if (!desc || !out) {
+    g_create_error = "null argument";
+    return DEM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (desc->precision != DEM_FP64) {
+    g_create_error = "only DEM_FP64 precision is available in this version";
+    return DEM_ERR_UNSUPPORTED;
+  }
+  if (!(desc->damping >= 0) || !(desc->damping < 1)) {
+    g_create_error = "damping must be in [0, 1)";
+    return DEM_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(desc->gravity[k]) || !std::isfinite(desc->box_lo[k]) ||
+        !std::isfinite(desc->box_hi[k])) {
+      g_create_error = "non-finite gravity or box";
+      return DEM_ERR_INVALID_ARG;
+    }
+  if (desc->periodic) {
+    if (!is_diag(desc->cell_h) || !(desc->cell_h[0] > 0) || !(desc->cell_h[4] > 0) ||
+        !(desc->cell_h[8] > 0)) {
+      g_create_error = "the periodic cell must be diagonal with positive edges";
+      return DEM_ERR_INVALID_ARG;
+    }
+  } else if (desc->wall_mask) {
+    for (int k = 0; k < 3; ++k)
+      if (!(desc->box_hi[k] > desc->box_lo[k])) {
+        g_create_error = "box_hi must exceed box_lo";
+        return DEM_ERR_INVALID_ARG;
+      }
+  }
+  dem_scene *s = new (std::nothrow) dem_scene();
+  if (!s) {
+    g_create_error = "out of host memory";
+    return DEM_ERR_OOM;
+  }
+  s->desc = *desc;
+  s->has_walls = !desc->periodic && (desc->wall_mask & 0x3F);
+  if (!s->has_walls) s->desc.wall_mask = 0;
+  auto bad = [&](cudaError_t e, const char *what) {
+    g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+  };
+  cudaError_t e;
+  if (desc->device >= 0) {
+    if ((e = cudaSetDevice(desc->device)) != cudaSuccess) { bad(e, "cudaSetDevice"); delete s; return DEM_ERR_CUDA; }
+    s->device = desc->device;
+  } else if ((e = cudaGetDevice(&s->device)) != cudaSuccess) {
+    bad(e, "cudaGetDevice");
+    delete s;
+    return DEM_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
+  if (desc->cuda_stream) {
+    s->st = (cudaStream_t)desc->cuda_stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking)) != cudaSuccess) {
+      bad(e, "cudaStreamCreate");
+      delete s;
+      return DEM_ERR_CUDA;
+    }
+    s->own_stream = true;
+  }
+  if ((e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&s->rb_h, sizeof(Readback))) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&s->partials_h, sizeof(double) * 1024 * 16)) != cudaSuccess) {
+    bad(e, "scene setup");
+    dem_scene_destroy(s);
+    return DEM_ERR_CUDA;
+  }
+  if (dalloc(s, &s->mats_d, kMaxMat) || dalloc(s, &s->cs_d, 1) || dalloc(s, &s->ds_d, 1) ||
+      dalloc(s, &s->partials, 1024 * 16)) {
+    g_create_error = s->err;
+    dem_scene_destroy(s);
+    return DEM_ERR_OOM;
+  }
+  // cell state
+  CellState &c = s->cs_h;
+  std::memset(&c, 0, sizeof c);
+  c.periodic = s->desc.periodic;
+  for (int q = 0; q < 9; ++q) {
+    c.H[q] = s->desc.periodic ? s->desc.cell_h[q] : ((q % 4 == 0) ? 1.0 : 0.0);
+    c.Hprev[q] = c.H[q];
+    c.Href[q] = c.H[q];
+  }
+  m_inv(c.Href, c.Hrefinv);
+  DevStatus z{};
+  if ((e = cudaMemcpyAsync(s->ds_d, &z, sizeof z, cudaMemcpyHostToDevice, s->st)) != cudaSuccess) {
+    bad(e, "status init");
+    dem_scene_destroy(s);
+    return DEM_ERR_CUDA;
+  }
+  if (desc->capacity_bodies > 0 && ensure_bodies(s, desc->capacity_bodies)) {
+    g_create_error = s->err;
+    dem_scene_destroy(s);
+    return DEM_ERR_OOM;
+  }
+  if (desc->capacity_contacts > 0 &&
+      (ensure_table(s, s->tab[0], desc->capacity_contacts, std::max<long long>(s->cap, 1)) ||
+       ensure_table(s, s->tab[1], desc->capacity_contacts, std::max<long long>(s->cap, 1)))) {
+    g_create_error = s->err;
+    dem_scene_destroy(s);
+    return DEM_ERR_OOM;
+  }
+  s->dt_set = desc->dt > 0;
+  c.dt = s->dt_set ? desc->dt : 0;
+  *out = s;
+  return DEM_OK;
+}
+
+void dem_scene_destroy(dem_scene *s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  free_bodies(s, s->cur);
+  free_bodies(s, s->alt);
+  free_table(s, s->tab[0]);
+  free_table(s, s->tab[1]);
+  dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
+  dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT);
+  dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
+  dfree(s, s->scan_ws); dfree(s, s->partials);
+  dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
+  if (s->st) cudaStreamSynchronize(s->st);
+  if (s->rb_h) cudaFreeHost(s->rb_h);
+  if (s->partials_h) cudaFreeHost(s->partials_h);
+  if (s->ev) cudaEventDestroy(s->ev);
+  for (auto &e : s->tev) cudaEventDestroy(e);
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+dem_status dem_set_material(dem_scene *s, int mat, double density, double young, double poisson,
+                            double friction) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (mat < 0 || mat >= kMaxMat) return fail(s, DEM_ERR_INVALID_ARG, "material id out of [0, 63]");
+  if (!(density > 0) || !(young > 0) || !(poisson >= 0) || !(friction >= 0) ||
+      !(friction < 1.5707963267948966) || !std::isfinite(density) || !std::isfinite(young) ||
+      !std::isfinite(poisson))
+    return fail(s, DEM_ERR_INVALID_ARG, "bad material parameters");
+  Mat m{density, young, poisson, std::tan(friction)};
+  s->mats_h[mat] = m;
+  s->mat_set[mat] = true;
+  CK(cudaMemcpyAsync(s->mats_d + mat, &s->mats_h[mat], sizeof(Mat), cudaMemcpyHostToDevice, s->st));
+  return sync_host(s);
+}
+
+dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const double *radius,
+                           const int *mat, const double *vel, const double *angvel,
+                           const unsigned char *fixed, long long *first_id) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (n < 0) return fail(s, DEM_ERR_INVALID_ARG, "negative count");
+  if (n == 0) {
+    if (first_id) *first_id = s->N;
+    return DEM_OK;
+  }
+  if (!pos || !radius) return fail(s, DEM_ERR_INVALID_ARG, "null pos or radius");
+  if (s->N + n > 0x7fffffffLL) return fail(s, DEM_ERR_CAPACITY, "more than 2^31-1 bodies");
+  for (long long i = 0; i < n; ++i) {
+    int m = mat ? mat[i] : 0;
+    if (m < 0 || m >= kMaxMat || !s->mat_set[m])
+      return fail(s, DEM_ERR_INVALID_ARG, "unknown material id (set_material first)");
+    if (!(radius[i] > 0) || !std::isfinite(radius[i]))
+      return fail(s, DEM_ERR_INVALID_ARG, "radius must be positive and finite");
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(pos[3 * i + k]) || (vel && !std::isfinite(vel[3 * i + k])) ||
+          (angvel && !std::isfinite(angvel[3 * i + k])))
+        return fail(s, DEM_ERR_NONFINITE, "non-finite position or velocity");
+    }
+  }
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if ((r = ensure_bodies(s, s->N + n))) return r;
+  std::vector<double4_32a> P(n), V(n), A(n), O(n), M(n);
+  std::vector<int> ID(n), MT(n);
+  std::vector<uint8_t> FL(n);
+  std::vector<int> SL(n);
+  const double pi = 3.14159265358979323846;
+  for (long long t = 0; t < n; ++t) {
+    int m = mat ? mat[t] : 0;
+    double rr = radius[t];
+    P[t] = make_double4_32a(pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], rr);
+    V[t] = vel ? make_double4_32a(vel[3 * t], vel[3 * t + 1], vel[3 * t + 2], 0) : make_double4_32a(0, 0, 0, 0);
+    A[t] = angvel ? make_double4_32a(angvel[3 * t], angvel[3 * t + 1], angvel[3 * t + 2], 0)
+                  : make_double4_32a(0, 0, 0, 0);
+    O[t] = make_double4_32a(1, 0, 0, 0);
+    // utils.sphere: m = density 4/3 pi r^3, I = 2/5 m r^2
+    double mass = s->mats_h[m].density * (4.0 / 3.0) * pi * rr * rr * rr;
+    double I = 0.4 * mass * rr * rr;
+    M[t] = make_double4_32a(mass, I, 1.0 / mass, 1.0 / I);
+    ID[t] = (int)(s->N + t);
+    MT[t] = m;
+    FL[t] = (fixed && fixed[t]) ? 1 : 0;
+    SL[t] = (int)(s->N + t);
+    s->rmin = std::min(s->rmin, rr);
+    s->rmax = std::max(s->rmax, rr);
+    s->vsolid += (4.0 / 3.0) * pi * rr * rr * rr;
+    s->radius_h.push_back(rr);
+    s->mat_h.push_back(m);
+    s->fixed_h.push_back(FL[t]);
+  }
+  const long long o = s->N;
+  const size_t d4 = sizeof(double4_32a) * n;
+  CK(cudaMemcpyAsync(s->cur.pos + o, P.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.vel + o, V.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.angvel + o, A.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.ori + o, O.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.xref + o, P.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.mprop + o, M.data(), d4, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.id + o, ID.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.mat + o, MT.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.flags + o, FL.data(), n, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->slot_of_id + o, SL.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  if (s->has_walls)
+    for (int w = 0; w < 6; ++w) CK(cudaMemsetAsync(s->cur.whist + w * s->cap + o, 0, d4, s->st));
+  if (first_id) *first_id = s->N;
+  s->N += n;
+  s->need_rebuild = true;
+  s->check_lost = false;
+  // sweep margin: > 0 absolute, < 0 fraction of the smallest radius
+  double vd = s->desc.verlet_dist;
+  s->cs_h.verlet = vd > 0 ? vd : (vd < 0 ? -vd * s->rmin : 0.5 * s->rmin);
+  s->cs_h.rmax = s->rmax;
+  s->cs_dirty = true;
+  return sync_host(s);
+}
+
+dem_status dem_set_dt(dem_scene *s, double dt) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(s, DEM_ERR_INVALID_ARG, "dt must be positive");
+  s->cs_h.dt = dt;
+  s->dt_set = true;
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_get_dt(dem_scene *s, double *dt) {
+  if (!s || !dt) return DEM_ERR_INVALID_ARG;
+  dem_status r = ensure_dt(s);
+  if (r) return r;
+  *dt = s->cs_h.dt;
+  return DEM_OK;
+}
+
+dem_status dem_set_cell_velgrad(dem_scene *s, const double *L) {
+  if (!s || !L) return DEM_ERR_INVALID_ARG;
+  if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "velGrad needs a periodic scene");
+  if (!is_diag(L)) return fail(s, DEM_ERR_UNSUPPORTED, "only a diagonal velGrad is supported");
+  for (int q = 0; q < 9; ++q)
+    if (!std::isfinite(L[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite velGrad");
+  std::memcpy(s->velgrad_next, L, sizeof s->velgrad_next);
+  s->velgrad_pending = true;
+  return DEM_OK;
+}
+
+
+dem_status dem_step(dem_scene *s, long long nsteps) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(s, DEM_ERR_INVALID_ARG, "negative step count");
+  if (s->broken) return fail(s, DEM_ERR_STATE, "scene unusable after an earlier CUDA error");
+  if (nsteps == 0) return DEM_OK;
+  dem_status r;
+  if (s->N == 0) {
+    if (!s->dt_set) return fail(s, DEM_ERR_STATE, "no bodies and no time step");
+    for (long long k = 0; k < nsteps; ++k) s->cs_h.time += s->cs_h.dt;
+    s->cs_h.iter += nsteps;
+    s->cs_dirty = true;
+    return DEM_OK;
+  }
+  if ((r = ensure_dt(s))) return r;
+  if ((r = prepare_step(s))) return r;
+  const SceneConst sc = scene_const(s);
+  long long remaining = nsteps;
+  while (remaining > 0) {
+    if (s->need_rebuild && (r = rebuild(s))) return r;
+    const long long B = std::min<long long>(remaining, s->batch);
+    const long long it0 = s->cs_h.iter;
+    const Table &t = s->tab[s->tc];
+    cudaEvent_t *ev = s->timing ? s->tev.data() + 2 : nullptr;
+    for (long long i = 0; i < B; ++i) {
+      if (ev) CK(cudaEventRecord(ev[6 * i], s->st));
+      launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
+      if (ev) { CK(cudaEventRecord(ev[6 * i + 1], s->st)); CK(cudaEventRecord(ev[6 * i + 2], s->st)); }
+      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->st);
+      if (ev) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
+      launch_cell_advance(s->cs_d, s->ds_d, s->st);
+      if (ev) CK(cudaEventRecord(ev[6 * i + 5], s->st));
+    }
+    s->launches += B * ((t.P > 0 ? 1 : 0) + 2);
+    CK(cudaGetLastError());
+    if ((r = read_status(s))) return r;
+    if (ev) {
+      for (long long i = 0; i < B; ++i) {
+        float a = 0, b = 0, c = 0;
+        CK(cudaEventElapsedTime(&a, ev[6 * i], ev[6 * i + 1]));
+        CK(cudaEventElapsedTime(&b, ev[6 * i + 2], ev[6 * i + 3]));
+        CK(cudaEventElapsedTime(&c, ev[6 * i + 4], ev[6 * i + 5]));
+        s->tm.contact_ms += a;
+        s->tm.integrate_ms += b;
+        s->tm.cell_ms += c;
+      }
+      s->tm.contact_launches += t.P > 0 ? B : 0;
+      s->tm.integrate_launches += B;
+      s->tm.cell_launches += B;
+      s->tm.rows_processed += B * t.P;
+    }
+    const DevStatus ds = s->rb_h->ds;
+    const long long done = s->cs_h.iter - it0;
+    if (ds.error) return status_error(s, ds.error);
+    remaining -= done;
+    if (ds.pending) {
+      s->need_rebuild = true;
+      // aim the next batch at the observed interval between collider runs
+      s->batch = std::max<long long>(4, std::min<long long>(64, done + 1));
+    } else if (done != B) {
+      return fail(s, DEM_ERR_STATE, "internal: steps were skipped without a collider request");
+    } else {
+      s->batch = std::min<long long>(64, s->batch + 4);
+    }
+  }
+  return DEM_OK;
+}
+
+static dem_status fetch4(dem_scene *s, const double4_32a *src, const std::vector<int> &sid, double *out,
+                         int comps) {
+  const long long N = s->N;
+  std::vector<double4_32a> h(N);
+  CK(cudaMemcpyAsync(h.data(), src, sizeof(double4_32a) * N, cudaMemcpyDeviceToHost, s->st));
+  dem_status r = wait(s);
+  if (r) return r;
+  for (long long i = 0; i < N; ++i) {
+    const double4_32a &v = h[sid[i]];
+    const double c[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < comps; ++k) out[comps * i + k] = c[k];
+  }
+  return DEM_OK;
+}
+
+static dem_status fetch_sid(dem_scene *s, std::vector<int> &sid) {
+  sid.resize(s->N);
+  if (s->N == 0) return DEM_OK;
+  CK(cudaMemcpyAsync(sid.data(), s->slot_of_id, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->st));
+  return wait(s);
+}
+
+dem_status dem_get_state(dem_scene *s, double *pos, double *vel, double *angvel, double *ori,
+                         double *force, double *torque) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (s->N == 0) return DEM_OK;
+  std::vector<int> sid;
+  if ((r = fetch_sid(s, sid))) return r;
+  if (pos && (r = fetch4(s, s->cur.pos, sid, pos, 3))) return r;
+  if (vel && (r = fetch4(s, s->cur.vel, sid, vel, 3))) return r;
+  if (angvel && (r = fetch4(s, s->cur.angvel, sid, angvel, 3))) return r;
+  if (ori && (r = fetch4(s, s->cur.ori, sid, ori, 4))) return r;
+  if (force || torque) {
+    if (s->need_rebuild) {
+      // no contact table matches the current body order yet: no contact forces
+      if (force) std::memset(force, 0, sizeof(double) * 3 * s->N);
+      if (torque) std::memset(torque, 0, sizeof(double) * 3 * s->N);
+      return DEM_OK;
+    }
+    launch_gather_forces(s->cur, s->tab[s->tc], s->mats_d, scene_const(s), s->cap, s->gF, s->gT,
+                         s->st);
+    CK(cudaGetLastError());
+    if (force && (r = fetch4(s, s->gF, sid, force, 3))) return r;
+    if (torque && (r = fetch4(s, s->gT, sid, torque, 3))) return r;
+  }
+  return DEM_OK;
+}
+
+dem_status dem_set_state(dem_scene *s, const double *pos, const double *vel, const double *angvel,
+                         const double *ori) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  const long long N = s->N;
+  if (N == 0) return DEM_OK;
+  for (long long i = 0; i < 3 * N; ++i)
+    if ((pos && !std::isfinite(pos[i])) || (vel && !std::isfinite(vel[i])) ||
+        (angvel && !std::isfinite(angvel[i])))
+      return fail(s, DEM_ERR_NONFINITE, "non-finite state");
+  std::vector<int> sid;
+  if ((r = fetch_sid(s, sid))) return r;
+  std::vector<double4_32a> h(N);
+  auto put = [&](const double *src, double4_32a *dst, int comps, bool radius_w) -> dem_status {
+    for (long long i = 0; i < N; ++i) {
+      const double *p = src + comps * i;
+      double w = radius_w ? s->radius_h[i] : (comps == 4 ? p[3] : 0.0);
+      h[sid[i]] = make_double4_32a(p[0], p[1], p[2], w);
+    }
+    CK(cudaMemcpyAsync(dst, h.data(), sizeof(double4_32a) * N, cudaMemcpyHostToDevice, s->st));
+    return wait(s);
+  };
+  if (pos && (r = put(pos, s->cur.pos, 3, true))) return r;
+  if (vel && (r = put(vel, s->cur.vel, 3, false))) return r;
+  if (angvel && (r = put(angvel, s->cur.angvel, 3, false))) return r;
+  if (ori && (r = put(ori, s->cur.ori, 4, false))) return r;
+  if (pos) {
+    s->need_rebuild = true;
+    s->check_lost = false;
+  }
+  return DEM_OK;
+}
+
+dem_status dem_get_cell(dem_scene *s, double *H, double *velgrad, double *prev_velgrad,
+                        double *prev_H) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the scene is not periodic");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (H) std::memcpy(H, s->cs_h.H, sizeof s->cs_h.H);
+  if (velgrad) std::memcpy(velgrad, s->velgrad_pending ? s->velgrad_next : s->cs_h.L, sizeof s->cs_h.L);
+  if (prev_velgrad) std::memcpy(prev_velgrad, s->cs_h.Lprev, sizeof s->cs_h.Lprev);
+  if (prev_H) std::memcpy(prev_H, s->cs_h.Hprev, sizeof s->cs_h.Hprev);
+  return DEM_OK;
+}
+
+dem_status dem_set_cell(dem_scene *s, const double *H, const double *velgrad,
+                        const double *prev_velgrad, const double *prev_H) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the scene is not periodic");
+  for (const double *M : {H, velgrad, prev_velgrad, prev_H})
+    if (M) {
+      if (!is_diag(M)) return fail(s, DEM_ERR_UNSUPPORTED, "cell matrices must be diagonal");
+      for (int q = 0; q < 9; ++q)
+        if (!std::isfinite(M[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite cell matrix");
+    }
+  if (H && !(H[0] > 0 && H[4] > 0 && H[8] > 0))
+    return fail(s, DEM_ERR_INVALID_ARG, "cell edges must be positive");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (H) {
+    std::memcpy(s->cs_h.H, H, sizeof s->cs_h.H);
+    s->need_rebuild = true;
+    s->check_lost = false;
+  }
+  if (velgrad) {
+    std::memcpy(s->cs_h.L, velgrad, sizeof s->cs_h.L);
+    s->velgrad_pending = false;
+  }
+  if (prev_velgrad) std::memcpy(s->cs_h.Lprev, prev_velgrad, sizeof s->cs_h.Lprev);
+  if (prev_H) std::memcpy(s->cs_h.Hprev, prev_H, sizeof s->cs_h.Hprev);
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_get_clock(dem_scene *s, long long *iter, double *time) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (iter) *iter = s->cs_h.iter;
+  if (time) *time = s->cs_h.time;
+  return DEM_OK;
+}
+
+dem_status dem_set_clock(dem_scene *s, long long iter, double time) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (iter < 0 || !std::isfinite(time)) return fail(s, DEM_ERR_INVALID_ARG, "bad clock");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  s->cs_h.iter = iter;
+  s->cs_h.time = time;
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+namespace {
+struct HostContact {
+  int id1, id2, c[3];
+  double fn[3], fs[3], n[3], cp[3], phys[3], pen;
+};
+
+void wall_phys_h(const dem_scene *s, int mat, double r, double &kn, double &ks, double &tp) {
+  const Mat &mw = s->mats_h[0], &ms = s->mats_h[mat];
+  double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
+  kn = k1 * k2 / (k1 + k2);
+  double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
+  ks = s1 * s2 / (s1 + s2);
+  tp = std::min(mw.tanphi, ms.tanphi);
+}
+
+dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
+  out.clear();
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  const long long N = s->N;
+  if (N == 0 || s->need_rebuild) return DEM_OK;
+  const Table &t = s->tab[s->tc];
+  const long long P = t.P;
+  std::vector<int2> pair(P);
+  std::vector<int> cp(P), id(N);
+  std::vector<double4_32a> hfs(P), hn(P), oF(P), oM(P), pos(N);
+  std::vector<double> tp(P);
+  if (P > 0) {
+    CK(cudaMemcpyAsync(pair.data(), t.pair, sizeof(int2) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(cp.data(), t.cpack, sizeof(int) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(hfs.data(), t.hfs, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(hn.data(), t.hn, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(oF.data(), t.oF, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(oM.data(), t.oM, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(tp.data(), t.tanphi, sizeof(double) * P, cudaMemcpyDeviceToHost, s->st));
+  }
+  CK(cudaMemcpyAsync(id.data(), s->cur.id, sizeof(int) * N, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(pos.data(), s->cur.pos, sizeof(double4_32a) * N, cudaMemcpyDeviceToHost, s->st));
+  std::vector<uint8_t> flags(N);
+  std::vector<double4_32a> wh;
+  CK(cudaMemcpyAsync(flags.data(), s->cur.flags, N, cudaMemcpyDeviceToHost, s->st));
+  if (s->has_walls) {
+    wh.resize(6 * N);
+    for (int w = 0; w < 6; ++w)
+      CK(cudaMemcpyAsync(wh.data() + w * N, s->cur.whist + w * s->cap, sizeof(double4_32a) * N,
+                         cudaMemcpyDeviceToHost, s->st));
+  }
+  if ((r = wait(s))) return r;
+  for (long long k = 0; k < P; ++k) {
+    if (hfs[k].w == 0.0) continue;
+    HostContact h{};
+    int a = pair[k].x, b = pair[k].y;
+    int c0, c1, c2;
+    unpack_shift(cp[k], c0, c1, c2);
+    double sg = 1.0;
+    const double F[3] = {oF[k].x, oF[k].y, oF[k].z};
+    const double fs[3] = {hfs[k].x, hfs[k].y, hfs[k].z};
+    const double n[3] = {hn[k].x, hn[k].y, hn[k].z};
+    const double d1 = oF[k].w;
+    const double r1 = pos[a].w;
+    const double pen = 2.0 * (r1 - d1);
+    if (id[a] < id[b]) {
+      h.id1 = id[a]; h.id2 = id[b]; h.c[0] = c0; h.c[1] = c1; h.c[2] = c2;
+    } else {
+      h.id1 = id[b]; h.id2 = id[a]; h.c[0] = -c0; h.c[1] = -c1; h.c[2] = -c2; sg = -1.0;
+    }
+    for (int q = 0; q < 3; ++q) {
+      h.fs[q] = sg * fs[q];
+      h.fn[q] = sg * (F[q] - fs[q]);
+      h.n[q] = sg * n[q];
+    }
+    // contact point x1 + (r1 - pen/2) n from the current position of the slot-first body
+    const double pa[3] = {pos[a].x, pos[a].y, pos[a].z};
+    for (int q = 0; q < 3; ++q) h.cp[q] = pa[q] + d1 * n[q];
+    h.phys[0] = hfs[k].w; h.phys[1] = hn[k].w; h.phys[2] = tp[k];
+    h.pen = pen;
+    out.push_back(h);
+  }
+  if (s->has_walls) {
+    for (long long sl = 0; sl < N; ++sl) {
+      if (!(flags[sl] & 0x7e)) continue;
+      for (int w = 0; w < 6; ++w) {
+        if (!(flags[sl] & (2 << w))) continue;
+        const double4_32a hw = wh[w * N + sl];
+        HostContact h{};
+        int ax = w >> 1;
+        double sn = hw.w >= 0 ? 1.0 : -1.0, Fn = std::fabs(hw.w);
+        h.id1 = -(w + 1);
+        h.id2 = id[sl];
+        double kn, ks, tanp;
+        const double rr = pos[sl].w;
+        wall_phys_h(s, s->mat_h[id[sl]], rr, kn, ks, tanp);
+        h.n[ax] = sn;
+        h.fn[ax] = sn * Fn;
+        h.fs[0] = hw.x; h.fs[1] = hw.y; h.fs[2] = hw.z;
+        h.pen = Fn / kn;
+        const double pp[3] = {pos[sl].x, pos[sl].y, pos[sl].z};
+        for (int q = 0; q < 3; ++q) h.cp[q] = pp[q] - (rr - 0.5 * h.pen) * h.n[q];
+        h.phys[0] = kn; h.phys[1] = ks; h.phys[2] = tanp;
+        out.push_back(h);
+      }
+    }
+  }
+  std::sort(out.begin(), out.end(), [](const HostContact &x, const HostContact &y) {
+    return x.id1 != y.id1 ? x.id1 < y.id1 : x.id2 < y.id2;
+  });
+  return DEM_OK;
+}
+}  // namespace
+
+dem_status dem_count_contacts(dem_scene *s, long long *count) {
+  if (!s || !count) return DEM_ERR_INVALID_ARG;
+  std::vector<HostContact> v;
+  dem_status r = collect_contacts(s, v);
+  if (r) return r;
+  *count = (long long)v.size();
+  return DEM_OK;
+}
+
+dem_status dem_get_contacts(dem_scene *s, long long cap, long long *count, int *id1, int *id2,
+                            int *cell_dist, double *normal_force, double *shear_force,
+                            double *normal, double *contact_point, double *phys, double *pen) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (cap < 0) return fail(s, DEM_ERR_INVALID_ARG, "negative capacity");
+  std::vector<HostContact> v;
+  dem_status r = collect_contacts(s, v);
+  if (r) return r;
+  if (count) *count = (long long)v.size();
+  long long m = std::min<long long>(cap, (long long)v.size());
+  for (long long k = 0; k < m; ++k) {
+    const HostContact &h = v[k];
+    if (id1) id1[k] = h.id1;
+    if (id2) id2[k] = h.id2;
+    for (int q = 0; q < 3; ++q) {
+      if (cell_dist) cell_dist[3 * k + q] = h.c[q];
+      if (normal_force) normal_force[3 * k + q] = h.fn[q];
+      if (shear_force) shear_force[3 * k + q] = h.fs[q];
+      if (normal) normal[3 * k + q] = h.n[q];
+      if (contact_point) contact_point[3 * k + q] = h.cp[q];
+      if (phys) phys[3 * k + q] = h.phys[q];
+    }
+    if (pen) pen[k] = h.pen;
+  }
+  return DEM_OK;
+}
+
+dem_status dem_set_contacts(dem_scene *s, long long n, const int *id1, const int *id2,
+                            const int *cell_dist, const double *shear_force,
+                            const double *normal_prev, const double *phys) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!id1 || !id2 || !shear_force || !normal_prev || !phys)))
+    return fail(s, DEM_ERR_INVALID_ARG, "null contact arrays");
+  const long long N = s->N;
+  for (long long k = 0; k < n; ++k) {
+    if (id2[k] < 0 || id2[k] >= N || id1[k] >= id2[k] || id1[k] < -6)
+      return fail(s, DEM_ERR_OUT_OF_RANGE, "contact id out of range or not canonical");
+    if (id1[k] < 0 && (!s->has_walls || !(s->desc.wall_mask & (1 << (-id1[k] - 1)))))
+      return fail(s, DEM_ERR_INVALID_ARG, "wall contact with a wall the scene does not have");
+    if (k > 0 && (id1[k - 1] > id1[k] || (id1[k - 1] == id1[k] && id2[k - 1] >= id2[k])))
+      return fail(s, DEM_ERR_INVALID_ARG, "contacts must be sorted by (id1, id2) without repeats");
+    for (int q = 0; q < 3; ++q)
+      if (!std::isfinite(shear_force[3 * k + q]) || !std::isfinite(normal_prev[3 * k + q]) ||
+          !std::isfinite(phys[3 * k + q]))
+        return fail(s, DEM_ERR_NONFINITE, "non-finite contact history");
+    if (cell_dist)
+      for (int q = 0; q < 3; ++q)
+        if (std::abs(cell_dist[3 * k + q]) > kShiftMax)
+          return fail(s, DEM_ERR_CAPACITY, "cell shift beyond +-511");
+  }
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  std::vector<int> sid;
+  if ((r = fetch_sid(s, sid))) return r;
+  struct Row { int a, b, cp; double4_32a fs, hn; double tp; };
+  std::vector<Row> rows;
+  std::vector<uint8_t> flags(N);
+  std::vector<double4_32a> wh;
+  if (N > 0) CK(cudaMemcpyAsync(flags.data(), s->cur.flags, N, cudaMemcpyDeviceToHost, s->st));
+  if ((r = wait(s))) return r;
+  if (s->has_walls) wh.assign(6 * N, make_double4_32a(0, 0, 0, 0));
+  for (long long sl = 0; sl < N; ++sl) flags[sl] &= 1;
+  for (long long k = 0; k < n; ++k) {
+    const double *f = shear_force + 3 * k, *nn = normal_prev + 3 * k, *ph = phys + 3 * k;
+    if (id1[k] < 0) {
+      int w = -id1[k] - 1, ax = w >> 1;
+      int sl = sid[id2[k]];
+      double sn = nn[ax] >= 0 ? 1.0 : -1.0;
+      wh[w * N + sl] = make_double4_32a(f[0], f[1], f[2], sn);
+      flags[sl] |= (2 << w);
+      continue;
+    }
+    int a = sid[id1[k]], b = sid[id2[k]];
+    int c[3] = {0, 0, 0};
+    if (cell_dist) for (int q = 0; q < 3; ++q) c[q] = cell_dist[3 * k + q];
+    double sg = 1.0;
+    if (a > b) { std::swap(a, b); sg = -1.0; for (int q = 0; q < 3; ++q) c[q] = -c[q]; }
+    rows.push_back(Row{a, b, pack_shift(c[0], c[1], c[2]),
+                       make_double4_32a(sg * f[0], sg * f[1], sg * f[2], ph[0]),
+                       make_double4_32a(sg * nn[0], sg * nn[1], sg * nn[2], ph[1]), ph[2]});
+  }
+  std::sort(rows.begin(), rows.end(), [](const Row &x, const Row &y) {
+    return x.a != y.a ? x.a < y.a : x.b < y.b;
+  });
+  const long long P = (long long)rows.size();
+  Table &t = s->tab[s->tc];
+  if ((r = ensure_table(s, t, std::max<long long>(P, 1), N))) return r;
+  std::vector<int2> pair(P);
+  std::vector<int> cp(P), rs(N + 1, 0);
+  std::vector<double4_32a> hfs(P), hn(P);
+  std::vector<double> tp(P);
+  for (long long k = 0; k < P; ++k) {
+    pair[k] = make_int2(rows[k].a, rows[k].b);
+    cp[k] = rows[k].cp;
+    hfs[k] = rows[k].fs;
+    hn[k] = rows[k].hn;
+    tp[k] = rows[k].tp;
+    rs[rows[k].a + 1] += 1;
+  }
+  for (long long i = 0; i < N; ++i) rs[i + 1] += rs[i];
+  if (P > 0) {
+    CK(cudaMemcpyAsync(t.pair, pair.data(), sizeof(int2) * P, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(t.cpack, cp.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(t.hfs, hfs.data(), sizeof(double4_32a) * P, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(t.hn, hn.data(), sizeof(double4_32a) * P, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(t.tanphi, tp.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s->st));
+  }
+  CK(cudaMemcpyAsync(t.row_start, rs.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s->st));
+  t.P = P;
+  s->tab_nbody[s->tc] = N;
+  if (N > 0) CK(cudaMemcpyAsync(s->cur.flags, flags.data(), N, cudaMemcpyHostToDevice, s->st));
+  if (s->has_walls)
+    for (int w = 0; w < 6; ++w)
+      CK(cudaMemcpyAsync(s->cur.whist + w * s->cap, wh.data() + w * N, sizeof(double4_32a) * N,
+                         cudaMemcpyHostToDevice, s->st));
+  s->need_rebuild = true;
+  s->check_lost = false;
+  return wait(s);
+}
+
+dem_status dem_set_timing(dem_scene *s, int enable) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (enable && s->tev.empty()) {
+    s->tev.resize(2 + 6 * 64);
+    for (auto &e : s->tev) CK(cudaEventCreate(&e));
+  }
+  s->timing = enable != 0;
+  long long keep = s->launches;
+  s->tm = dem_timing{};
+  s->tm.kernel_launches = keep;
+  return DEM_OK;
+}
+
+dem_status dem_get_timing(dem_scene *s, dem_timing *out) {
+  if (!s || !out) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  *out = s->tm;
+  out->kernel_launches = s->launches;
+  return DEM_OK;
+}
+
+dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
+  if (!s || !o) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  std::memset(o, 0, sizeof *o);
+  o->iter = s->cs_h.iter;
+  o->time = s->cs_h.time;
+  o->dt = s->cs_h.dt;
+  o->n_bodies = s->N;
+  o->n_rebuilds = s->n_rebuilds;
+  double V;
+  if (s->desc.periodic) V = std::fabs(m_det(s->cs_h.H));
+  else V = (s->desc.box_hi[0] - s->desc.box_lo[0]) * (s->desc.box_hi[1] - s->desc.box_lo[1]) *
+           (s->desc.box_hi[2] - s->desc.box_lo[2]);
+  o->packing_fraction = V > 0 ? s->vsolid / V : 0;
+  if (s->N == 0) return DEM_OK;
+  const bool have_table = !s->need_rebuild;
+  const Table &t = s->tab[s->tc];
+  const SceneConst sc = scene_const(s);
+  o->n_candidates = have_table ? t.P : 0;
+  double *ph = s->partials_h;
+  // bodies: kinetic energy, |F| of free bodies
+  if (have_table) launch_gather_forces(s->cur, t, s->mats_d, sc, s->cap, s->gF, s->gT, s->st);
+  else CK(cudaMemsetAsync(s->gF, 0, sizeof(double4_32a) * s->N, s->st));
+  int nb = stats_blocks(s->N);
+  launch_body_stats(s->cur, s->gF, s->N, s->partials, s->st);
+  CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s->st));
+  if ((r = wait(s))) return r;
+  double ke = 0, sumF = 0, ndyn = 0;
+  for (int b = 0; b < nb; ++b) { ke += ph[3 * b]; sumF += ph[3 * b + 1]; ndyn += ph[3 * b + 2]; }
+  double nc = 0, sumC = 0, sig[9] = {0};
+  if (have_table && t.P > 0) {
+    int nr = stats_blocks(t.P);
+    launch_row_stats(t, s->cur, s->partials, s->st);
+    CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 11 * nr, cudaMemcpyDeviceToHost, s->st));
+    if ((r = wait(s))) return r;
+    for (int b = 0; b < nr; ++b) {
+      nc += ph[11 * b];
+      sumC += ph[11 * b + 1];
+      for (int q = 0; q < 9; ++q) sig[q] += ph[11 * b + 2 + q];
+    }
+  }
+  double nw = 0, sumW = 0;
+  if (s->has_walls) {
+    launch_wall_stats(s->cur, sc, s->mats_d, s->cap, s->partials, s->st);
+    CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s->st));
+    if ((r = wait(s))) return r;
+    for (int b = 0; b < nb; ++b) { nw += ph[2 * b]; sumW += ph[2 * b + 1]; }
+  }
+  o->kinetic_energy = ke;
+  o->n_contacts = (long long)nc;
+  o->n_wall_contacts = (long long)nw;
+  const double call = nc + nw;
+  o->unbalanced_force = (call > 0 && ndyn > 0) ? (sumF / ndyn) / ((sumC + sumW) / call) : NAN;
+  o->coordination = 2.0 * nc / s->N;
+  for (int q = 0; q < 9; ++q) o->stress[q] = V > 0 ? sig[q] / V : 0;
+  return DEM_OK;
+}
+
+}  // extern "C"

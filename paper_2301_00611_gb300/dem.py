@@ -1,0 +1,370 @@
+"""ctypes binding of ``libdem.so`` (declared in ``include/dem.h``).
+
+Argument marshalling only: every step of the DEM path runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library is missing or cannot
+be loaded, every call raises.  Names follow the C ABI (``dem_step`` ->
+``Scene.step`` and so on).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdem.so")
+
+DEM_OK = 0
+STATUS_NAMES = {
+    0: "DEM_OK", 1: "DEM_ERR_INVALID_ARG", 2: "DEM_ERR_OUT_OF_RANGE", 3: "DEM_ERR_OOM",
+    4: "DEM_ERR_CAPACITY", 5: "DEM_ERR_NONFINITE", 6: "DEM_ERR_GEOMETRY", 7: "DEM_ERR_TIMEOUT",
+    8: "DEM_ERR_CUDA", 9: "DEM_ERR_STATE", 10: "DEM_ERR_UNSUPPORTED",
+}
+DEM_FP64 = 0
+DEM_MIXED = 1
+
+
+class DemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [
+        ("periodic", ctypes.c_int),
+        ("cell_h", ctypes.c_double * 9),
+        ("box_lo", ctypes.c_double * 3),
+        ("box_hi", ctypes.c_double * 3),
+        ("wall_mask", ctypes.c_int),
+        ("gravity", ctypes.c_double * 3),
+        ("damping", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("verlet_dist", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("capacity_bodies", ctypes.c_longlong),
+        ("capacity_contacts", ctypes.c_longlong),
+        ("cuda_stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("iter", ctypes.c_longlong),
+        ("time", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("n_bodies", ctypes.c_longlong),
+        ("n_contacts", ctypes.c_longlong),
+        ("n_wall_contacts", ctypes.c_longlong),
+        ("n_candidates", ctypes.c_longlong),
+        ("n_rebuilds", ctypes.c_longlong),
+        ("kinetic_energy", ctypes.c_double),
+        ("unbalanced_force", ctypes.c_double),
+        ("coordination", ctypes.c_double),
+        ("packing_fraction", ctypes.c_double),
+        ("stress", ctypes.c_double * 9),
+    ]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [
+        ("contact_ms", ctypes.c_double),
+        ("integrate_ms", ctypes.c_double),
+        ("cell_ms", ctypes.c_double),
+        ("collider_ms", ctypes.c_double),
+        ("contact_launches", ctypes.c_longlong),
+        ("integrate_launches", ctypes.c_longlong),
+        ("cell_launches", ctypes.c_longlong),
+        ("collider_runs", ctypes.c_longlong),
+        ("rows_processed", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
+# C ABI: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "dem_scene_desc_init": (None, [_P]),
+    "dem_scene_create": (ctypes.c_int, [_P, _P]),
+    "dem_scene_destroy": (None, [_P]),
+    "dem_set_material": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double]),
+    "dem_add_spheres": (ctypes.c_int, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P, _P, _P]),
+    "dem_set_dt": (ctypes.c_int, [_P, ctypes.c_double]),
+    "dem_get_dt": (ctypes.c_int, [_P, _P]),
+    "dem_set_cell_velgrad": (ctypes.c_int, [_P, _P]),
+    "dem_step": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "dem_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "dem_set_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "dem_get_cell": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "dem_set_cell": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "dem_get_clock": (ctypes.c_int, [_P, _P, _P]),
+    "dem_set_clock": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double]),
+    "dem_count_contacts": (ctypes.c_int, [_P, _P]),
+    "dem_get_contacts": (ctypes.c_int, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P, _P, _P, _P,
+                                        _P, _P]),
+    "dem_set_contacts": (ctypes.c_int, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P, _P]),
+    "dem_get_stats": (ctypes.c_int, [_P, _P]),
+    "dem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "dem_get_timing": (ctypes.c_int, [_P, _P]),
+    "dem_last_error": (ctypes.c_char_p, [_P]),
+    "dem_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdem.so (fails loudly: there is no fallback implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Scene:
+    """One DEM scene on the GPU (a handle of the C ABI)."""
+
+    def __init__(self, periodic=False, cell=None, box_lo=(0, 0, 0), box_hi=(1, 1, 1),
+                 wall_mask=0, gravity=(0, 0, 0), damping=0.2, dt=0.0, verlet_dist=-0.5,
+                 precision=DEM_FP64, capacity_bodies=0, capacity_contacts=0, stream=None,
+                 device=-1, use_torch_stream=True):
+        self._lib = load_library()
+        d = SceneDesc()
+        self._lib.dem_scene_desc_init(ctypes.byref(d))
+        d.periodic = int(bool(periodic))
+        H = np.eye(3) if cell is None else np.asarray(cell, dtype=np.float64).reshape(3, 3)
+        for q in range(9):
+            d.cell_h[q] = float(H.flat[q])
+        for k in range(3):
+            d.box_lo[k] = float(box_lo[k])
+            d.box_hi[k] = float(box_hi[k])
+            d.gravity[k] = float(gravity[k])
+        d.wall_mask = int(wall_mask)
+        d.damping = float(damping)
+        d.dt = float(dt)
+        d.verlet_dist = float(verlet_dist)
+        d.precision = int(precision)
+        d.capacity_bodies = int(capacity_bodies)
+        d.capacity_contacts = int(capacity_contacts)
+        if stream is None and use_torch_stream:
+            stream = _current_stream()
+        d.cuda_stream = stream
+        d.device = int(device)
+        h = ctypes.c_void_p()
+        rc = self._lib.dem_scene_create(ctypes.byref(d), ctypes.byref(h))
+        if rc != DEM_OK:
+            raise DemError(rc, self._lib.dem_last_error(None).decode())
+        self._h = h
+        self._n = 0
+        self.periodic = bool(periodic)
+        self.desc = d
+
+    @classmethod
+    def from_workload(cls, w, dt=None, **kw):
+        s = cls(periodic=w.periodic, cell=w.cell, box_lo=w.box_lo, box_hi=w.box_hi,
+                wall_mask=w.wall_mask, gravity=w.gravity, damping=w.damping, **kw)
+        for k, m in enumerate(w.materials):
+            s.set_material(k, m.density, m.young, m.poisson, m.friction)
+        s.add_spheres(w.pos, w.radius, w.mat_id, w.vel, w.angvel)
+        if dt is not None:
+            s.set_dt(dt)
+        if w.periodic and np.any(w.velgrad):
+            s.set_cell_velgrad(w.velgrad)
+        return s
+
+    def _check(self, rc):
+        if rc != DEM_OK:
+            raise DemError(rc, self._lib.dem_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dem_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- scene construction
+    def set_material(self, mat_id, density, young, poisson, friction_angle):
+        self._check(self._lib.dem_set_material(self._h, int(mat_id), float(density), float(young),
+                                               float(poisson), float(friction_angle)))
+
+    def add_spheres(self, pos, radius, mat_id=None, vel=None, angvel=None, fixed=None):
+        pos = _f64(pos, (-1, 3))
+        radius = _f64(radius)
+        mat = None if mat_id is None else np.ascontiguousarray(mat_id, dtype=np.int32)
+        vel = _f64(vel, (-1, 3))
+        angvel = _f64(angvel, (-1, 3))
+        fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        first = ctypes.c_longlong()
+        self._check(self._lib.dem_add_spheres(self._h, radius.size, _ptr(pos), _ptr(radius),
+                                              _ptr(mat), _ptr(vel), _ptr(angvel), _ptr(fx),
+                                              ctypes.byref(first)))
+        self._n += radius.size
+        return first.value
+
+    def set_dt(self, dt):
+        self._check(self._lib.dem_set_dt(self._h, float(dt)))
+
+    def dt(self):
+        v = ctypes.c_double()
+        self._check(self._lib.dem_get_dt(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_cell_velgrad(self, L):
+        L = _f64(L, (3, 3))
+        self._check(self._lib.dem_set_cell_velgrad(self._h, _ptr(L)))
+
+    # --- stepping
+    def step(self, n=1):
+        self._check(self._lib.dem_step(self._h, int(n)))
+
+    # --- queries
+    def state(self, force=True):
+        it = ctypes.c_longlong()
+        self._check(self._lib.dem_get_clock(self._h, ctypes.byref(it), None))
+        n = self.n
+        out = {k: np.empty((n, 3)) for k in ("pos", "vel", "angvel")}
+        out["ori"] = np.empty((n, 4))
+        if force:
+            out["force"] = np.empty((n, 3))
+            out["torque"] = np.empty((n, 3))
+        self._check(self._lib.dem_get_state(self._h, _ptr(out["pos"]), _ptr(out["vel"]),
+                                            _ptr(out["angvel"]), _ptr(out["ori"]),
+                                            _ptr(out.get("force")), _ptr(out.get("torque"))))
+        return out
+
+    def get_state_into(self, pos=None, vel=None, angvel=None, ori=None, force=None, torque=None):
+        """Copy state into caller-provided float64 host arrays (no allocation here)."""
+        self._check(self._lib.dem_get_state(self._h, *(_ptr(a) for a in
+                                                       (pos, vel, angvel, ori, force, torque))))
+
+    def set_state(self, pos=None, vel=None, angvel=None, ori=None):
+        keep = [_f64(pos, (-1, 3)), _f64(vel, (-1, 3)), _f64(angvel, (-1, 3)), _f64(ori, (-1, 4))]
+        n = self.n
+        for a, k in zip(keep, (3, 3, 3, 4)):
+            if a is not None and a.shape != (n, k):
+                raise ValueError("state array has the wrong shape")
+        self._check(self._lib.dem_set_state(self._h, *(_ptr(a) for a in keep)))
+
+    @property
+    def n(self):
+        return self._n
+
+    def cell(self):
+        H, L, Lp, Hp = (np.empty((3, 3)) for _ in range(4))
+        self._check(self._lib.dem_get_cell(self._h, _ptr(H), _ptr(L), _ptr(Lp), _ptr(Hp)))
+        return {"H": H, "velgrad": L, "prev_velgrad": Lp, "prev_H": Hp}
+
+    def set_cell(self, H=None, velgrad=None, prev_velgrad=None, prev_H=None):
+        keep = [_f64(a, (3, 3)) for a in (H, velgrad, prev_velgrad, prev_H)]
+        self._check(self._lib.dem_set_cell(self._h, *(_ptr(a) for a in keep)))
+
+    def clock(self):
+        it = ctypes.c_longlong()
+        t = ctypes.c_double()
+        self._check(self._lib.dem_get_clock(self._h, ctypes.byref(it), ctypes.byref(t)))
+        return it.value, t.value
+
+    def set_clock(self, it, t):
+        self._check(self._lib.dem_set_clock(self._h, int(it), float(t)))
+
+    def count_contacts(self):
+        c = ctypes.c_longlong()
+        self._check(self._lib.dem_count_contacts(self._h, ctypes.byref(c)))
+        return c.value
+
+    def contacts(self):
+        m = self.count_contacts()
+        out = {"id1": np.empty(m, np.int32), "id2": np.empty(m, np.int32),
+               "c": np.empty((m, 3), np.int32), "fn": np.empty((m, 3)), "fs": np.empty((m, 3)),
+               "normal": np.empty((m, 3)), "cpoint": np.empty((m, 3)), "phys": np.empty((m, 3)),
+               "pen": np.empty(m)}
+        cnt = ctypes.c_longlong()
+        self._check(self._lib.dem_get_contacts(
+            self._h, m, ctypes.byref(cnt), *(_ptr(out[k]) for k in
+                                             ("id1", "id2", "c", "fn", "fs", "normal", "cpoint",
+                                              "phys", "pen"))))
+        return out
+
+    def set_contacts(self, id1, id2, c, fs, nprev, phys):
+        id1 = np.ascontiguousarray(id1, np.int32)
+        id2 = np.ascontiguousarray(id2, np.int32)
+        c = None if c is None else np.ascontiguousarray(c, np.int32).reshape(-1, 3)
+        fs, nprev, phys = _f64(fs, (-1, 3)), _f64(nprev, (-1, 3)), _f64(phys, (-1, 3))
+        if not (fs.shape[0] == nprev.shape[0] == phys.shape[0] == id1.size == id2.size):
+            raise ValueError("contact arrays disagree in length")
+        self._check(self._lib.dem_set_contacts(self._h, id1.size, _ptr(id1), _ptr(id2), _ptr(c),
+                                               _ptr(fs), _ptr(nprev), _ptr(phys)))
+
+    def stats(self):
+        st = Stats()
+        self._check(self._lib.dem_get_stats(self._h, ctypes.byref(st)))
+        out = {name: getattr(st, name) for name, _ in Stats._fields_ if name != "stress"}
+        out["stress"] = np.array(list(st.stress)).reshape(3, 3)
+        return out
+
+
+def _timing_methods():
+    def set_timing(self, enable=True):
+        self._check(self._lib.dem_set_timing(self._h, int(bool(enable))))
+
+    def timing(self):
+        t = Timing()
+        self._check(self._lib.dem_get_timing(self._h, ctypes.byref(t)))
+        return {name: getattr(t, name) for name, _ in Timing._fields_}
+    Scene.set_timing = set_timing
+    Scene.timing = timing
+
+
+_timing_methods()
+
+
+def version() -> str:
+    return load_library().dem_version().decode()

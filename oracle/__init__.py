@@ -7,8 +7,8 @@ product package.
 
 Parity status of each oracle function (what pins it, in ``tests/test_oracle_*``):
 
-* contact detection (sort-and-sweep + exact test): pinned by brute force on
-  small inputs, aperiodic and periodic.
+* contact detection (cell list + exact test; a sort-and-sweep variant): pinned
+  by brute force on small inputs, aperiodic, periodic and sheared.
 * Ip2 stiffness and Law2 normal force: pinned by the closed-form binary impact
   (duration pi*sqrt(m*/kn), restitution 1) and the sphere resting on a wall
   (pen = m g / kn).
@@ -91,6 +91,7 @@ def _load():
         "orc_pwave_dt": (_d, [_p]),
         "orc_pairs_bruteforce": (_l, [_l, _p, _p, _i, _p, _d, _l, _p, _p, _p]),
         "orc_pairs_sweep": (_l, [_l, _p, _p, _i, _p, _d, _l, _p, _p, _p]),
+        "orc_pairs_grid": (_l, [_l, _p, _p, _i, _p, _d, _l, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -116,14 +117,15 @@ def sphere_pwave_dt(radius: float, density: float, young: float) -> float:
     return _load().orc_sphere_pwave_dt(radius, density, young)
 
 
-def pairs(pos, radius, periodic=False, H=None, margin=0.0, method="sweep"):
+def pairs(pos, radius, periodic=False, H=None, margin=0.0, method="grid"):
     """All (i<j, c) with |x_j + H c - x_i| < r_i + r_j + margin, sorted by (i, j)."""
     lib = _load()
     pos = _f64(pos, (-1, 3))
     radius = _f64(radius)
     n = radius.size
     Hm = _f64(np.eye(3) if H is None else H, (3, 3))
-    fn = lib.orc_pairs_sweep if method == "sweep" else lib.orc_pairs_bruteforce
+    fn = {"sweep": lib.orc_pairs_sweep, "grid": lib.orc_pairs_grid,
+          "brute": lib.orc_pairs_bruteforce}[method]
     cap = max(16, 8 * n)
     while True:
         I = np.empty(cap, np.int32)

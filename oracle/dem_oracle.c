@@ -10,10 +10,12 @@
  * "Engines": ForceResetter -> collider -> InteractionLoop(Ig2, Ip2, Law2) ->
  * NewtonIntegrator), written the slow and obvious way:
  *
- *   - contact detection every step by a sort-and-sweep along one axis (the
- *     "initial step" of the sweep-and-prune collider, section 2.1.1) followed
- *     by the exact sphere test; no Verlet distance is needed because the
- *     search runs every step.  A brute-force O(N^2) search checks it;
+ *   - contact detection every step: candidates from a uniform cell list (cells
+ *     as wide as the largest contact distance, the "grid algorithms" of
+ *     section 2.1.1) followed by the exact sphere test; no Verlet distance is
+ *     needed because the search runs every step.  A brute-force O(N^2) search
+ *     and a sort-and-sweep along one axis (the "initial step" of the
+ *     sweep-and-prune collider) check it;
  *   - interactions keyed by (id1, id2) in a sorted list carried from step to
  *     step (potential/real lifecycle, section 3.1.7 "Interactions");
  *   - Ig2_Sphere_Sphere_ScGeom: normal and contact point (eq. 2.7, 2.8),
@@ -303,6 +305,104 @@ long orc_pairs_sweep(long n, const double *pos, const double *radius, int period
     return pairs_out(&L, cap, I, J, C);
 }
 
+/* Cell-list search: bodies hashed into a uniform grid whose cells are at least as
+ * wide as the largest possible contact distance (2 r_max + margin), each body
+ * tested against the bodies of its own and the 26 neighbouring cells.  In a
+ * periodic cell the grid lives in wrapped fractional coordinates, sized by the
+ * perpendicular widths.  Every candidate goes through test_pair, so the result is
+ * the same set as the brute-force search. */
+static long grid_core(long n, const double *pos, const double *radius, int periodic,
+                      const double *H9, double margin, pair_list *L) {
+    if (n <= 0) return 0;
+    double Hinv[9];
+    if (periodic && m_inv(H9, Hinv) != 0) return -1;
+    double rmax = 0;
+    for (long i = 0; i < n; ++i) if (radius[i] > rmax) rmax = radius[i];
+    double reach = (2 * rmax + margin) * (1 + 1e-9) + 1e-300;
+    double lo[3] = {0, 0, 0}, ext[3];
+    int nc[3];
+    if (periodic) {
+        double w[3];
+        cell_widths(H9, w);
+        for (int k = 0; k < 3; ++k) {
+            nc[k] = (int)floor(w[k] / reach);
+            if (nc[k] < 1) nc[k] = 1;
+            if (nc[k] > 512) nc[k] = 512;
+            ext[k] = 1.0;
+        }
+    } else {
+        double hi[3];
+        for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+        for (long i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) {
+                if (pos[3 * i + k] < lo[k]) lo[k] = pos[3 * i + k];
+                if (pos[3 * i + k] > hi[k]) hi[k] = pos[3 * i + k];
+            }
+        for (int k = 0; k < 3; ++k) {
+            ext[k] = hi[k] - lo[k];
+            nc[k] = (int)floor(ext[k] / reach);
+            if (nc[k] < 1) nc[k] = 1;
+            if (nc[k] > 512) nc[k] = 512;
+            if (ext[k] <= 0) ext[k] = 1;
+        }
+    }
+    long ncell = (long)nc[0] * nc[1] * nc[2];
+    long *head = (long *)malloc(sizeof(long) * ncell);
+    long *next = (long *)malloc(sizeof(long) * n);
+    int *cell = (int *)malloc(sizeof(int) * 3 * n);
+    if (!head || !next || !cell) { free(head); free(next); free(cell); return -2; }
+    for (long c = 0; c < ncell; ++c) head[c] = -1;
+    for (long i = n - 1; i >= 0; --i) {
+        double u[3];
+        if (periodic) {
+            m_vec(Hinv, pos + 3 * i, u);
+            for (int k = 0; k < 3; ++k) u[k] = u[k] - floor(u[k]);
+        } else {
+            for (int k = 0; k < 3; ++k) u[k] = (pos[3 * i + k] - lo[k]) / ext[k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            int c = (int)floor(u[k] * nc[k]);
+            if (c < 0) c = 0;
+            if (c >= nc[k]) c = nc[k] - 1;
+            cell[3 * i + k] = c;
+        }
+        long id = ((long)cell[3 * i] * nc[1] + cell[3 * i + 1]) * nc[2] + cell[3 * i + 2];
+        next[i] = head[id];
+        head[id] = i;
+    }
+    for (long i = 0; i < n; ++i) {
+        int nb[3][3], nnb[3];
+        for (int k = 0; k < 3; ++k) {
+            nnb[k] = 0;
+            for (int d = -1; d <= 1; ++d) {
+                int c = cell[3 * i + k] + d;
+                if (periodic) { c %= nc[k]; if (c < 0) c += nc[k]; }
+                else if (c < 0 || c >= nc[k]) continue;
+                int dup = 0;
+                for (int q = 0; q < nnb[k]; ++q) if (nb[k][q] == c) dup = 1;
+                if (!dup) nb[k][nnb[k]++] = c;
+            }
+        }
+        for (int a = 0; a < nnb[0]; ++a)
+            for (int b = 0; b < nnb[1]; ++b)
+                for (int c = 0; c < nnb[2]; ++c) {
+                    long id = ((long)nb[0][a] * nc[1] + nb[1][b]) * nc[2] + nb[2][c];
+                    for (long j = head[id]; j >= 0; j = next[j])
+                        if (j > i) test_pair(i, j, pos, radius, periodic, H9, Hinv, margin, L);
+                }
+    }
+    free(head); free(next); free(cell);
+    return L->oom ? -2 : 0;
+}
+
+long orc_pairs_grid(long n, const double *pos, const double *radius, int periodic,
+                    const double *H9, double margin, long cap, int *I, int *J, int *C) {
+    pair_list L = {0};
+    long rc = grid_core(n, pos, radius, periodic, H9, margin, &L);
+    if (rc < 0) { free(L.p); return rc; }
+    return pairs_out(&L, cap, I, J, C);
+}
+
 /* --------------------------------------------------------------- scene */
 orc_scene *orc_create(int periodic, const double *H9, const double *box_lo, const double *box_hi,
                       int wall_mask, const double *gravity, double damping, double dt) {
@@ -513,7 +613,7 @@ static int key_cmp_contact(const orc_key *k, const orc_contact *c) {
  * (same cell shift) was already real, else marked new (kn = 0). */
 static int detect_contacts(orc_scene *s, orc_contact **out, long *nout) {
     pair_list L = {0};
-    long rc = sweep_core(s->n, s->pos, s->radius, s->periodic, s->H, 0.0, &L);
+    long rc = grid_core(s->n, s->pos, s->radius, s->periodic, s->H, 0.0, &L);
     if (rc < 0 || L.oom) { free(L.p); return rc < 0 ? (int)rc : -2; }
     qsort(L.p, L.n, sizeof(orc_pair), pair_cmp);
     long m = 0;

@@ -74,6 +74,8 @@ long orc_pairs_bruteforce(long n, const double *pos, const double *radius, int p
                           const double *H9, double margin, long cap, int *i, int *j, int *c);
 long orc_pairs_sweep(long n, const double *pos, const double *radius, int periodic,
                      const double *H9, double margin, long cap, int *i, int *j, int *c);
+long orc_pairs_grid(long n, const double *pos, const double *radius, int periodic,
+                    const double *H9, double margin, long cap, int *i, int *j, int *c);
 
 #ifdef __cplusplus
 }

@@ -10,14 +10,17 @@
 //      resulting body order ("slots") is deterministic;
 //   3. permute the body arrays into that order (spatial locality for every
 //      later gather);
-//   4. each body scans the 27 neighbour cells and keeps the pairs with
-//      |x2 + H c - x1| < r1 + r2 + 2 dL (count, prefix sum, emit: no atomics);
+//   4. each body scans the forward half of its 27-cell neighbourhood (so each
+//      pair is met once) and keeps the pairs with |x2 + H c - x1| < r1 + r2 + 2 dL,
+//      tested conservatively in FP32 on wrapped coordinates (count, prefix sum,
+//      emit);
 //   5. merge the contact history of the previous table into the new rows by
 //      looking each pair up in the old per-body row ranges (the potential /
 //      real interaction lifecycle of section 3.1.7), flipping the stored
 //      vectors when the slot order of the pair changed;
 //   6. build the per-body "down" lists (rows where the body is the second
-//      sphere) for the deterministic force gather.
+//      sphere): filled in atomic order during the emit, then sorted per body, so
+//      the force gather reads them in a deterministic order.
 #include "dem_internal.cuh"
 
 namespace dem {
@@ -62,14 +65,16 @@ __device__ inline int neg_shift(int p) {
   return pack_shift(-a, -b, -c);
 }
 
-// Visit the bodies of the 27 neighbour cells of cell ci; f(j, w) receives the
-// body slot and the periodic wrap of the neighbour cell.
+// Forward half of the 27-cell stencil: own cell (partners with a higher slot)
+// plus the 13 offsets with (dz, dy, dx) lexicographically positive, so every pair
+// of neighbouring cells is visited from exactly one side.
 template <class F>
-__device__ inline void for_neighbours(const Grid &g, const int *__restrict__ count,
-                                      const int *__restrict__ start, const int ci[3], F &&f) {
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
+__device__ inline void for_half_shell(const Grid &g, const int *__restrict__ count,
+                                      const int *__restrict__ start, const int ci[3], int s,
+                                      F &&f) {
+  for (int dz = 0; dz <= 1; ++dz)
+    for (int dy = (dz ? -1 : 0); dy <= 1; ++dy)
+      for (int dx = ((dz || dy) ? -1 : 0); dx <= 1; ++dx) {
         const int d[3] = {dx, dy, dz};
         int cj[3], w[3];
         bool ok = true;
@@ -86,43 +91,31 @@ __device__ inline void for_neighbours(const Grid &g, const int *__restrict__ cou
           cj[k] = c;
         }
         if (!ok) continue;
+        const bool self = (dx == 0 && dy == 0 && dz == 0);
         const uint32_t m = morton3(cj[0], cj[1], cj[2]);
         const int s0 = start[m], cnt = count[m];
-        for (int j = s0; j < s0 + cnt; ++j) f(j, w);
+        for (int j = (self ? s + 1 : s0); j < s0 + cnt; ++j) f(j, w);
       }
 }
 
-// Candidate test of the pair (s, j) found from s through a cell wrap w, always
-// evaluated in the pair's canonical orientation (lower slot first) so that
-// both ends reach the same decision bit for bit.  Returns the packed shift of
-// the higher slot.
-struct Cand {
-  bool keep;
-  int cpack;
-  bool range_ok;
+// Per-slot collider record: FP32 position relative to the grid (periodic: the
+// wrapped position), radius, packed cell coordinates and the integer image.
+struct CellRec {
+  float4 *wpos;   // (x, y, z, r)
+  int4 *info;     // (cell0 | cell1 << 10 | cell2 << 20, img0, img1, img2)
 };
-__device__ inline Cand cand_test(const Grid &g, const double4_32a &ps, const int imgs[3], int s,
-                                 const double4_32a &pj, int j, const int w[3]) {
-  Cand out{false, 0, true};
-  int c[3] = {0, 0, 0};
-  if (g.periodic) {
-    int cj[3], imgj[3];
-    cell_of(g, pj.x, pj.y, pj.z, cj, imgj);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) c[k] = imgs[k] - imgj[k] + w[k];   // shift of j seen from s
-    if (j < s) { c[0] = -c[0]; c[1] = -c[1]; c[2] = -c[2]; }        // shift of s seen from j
-  }
-  const double4_32a &a = (s < j) ? ps : pj;
-  const double4_32a &b = (s < j) ? pj : ps;
-  const double h0 = g.L[0] * c[0], h1 = g.L[1] * c[1], h2 = g.L[2] * c[2];
-  const double d0 = (b.x + h0) - a.x, d1 = (b.y + h1) - a.y, d2 = (b.z + h2) - a.z;
-  const double R = (a.w + b.w) + g.reach;
-  out.keep = d0 * d0 + d1 * d1 + d2 * d2 < R * R;
-  if (out.keep) {
-    out.range_ok = abs(c[0]) <= kShiftMax && abs(c[1]) <= kShiftMax && abs(c[2]) <= kShiftMax;
-    out.cpack = pack_shift(c[0], c[1], c[2]);
-  }
-  return out;
+
+// Conservative FP32 candidate test of (s, j): keeps every pair whose FP64
+// distance is below r1 + r2 + reach (the slack covers the FP32 rounding of
+// coordinates bounded by the cell size), so the candidate set is a superset of
+// the exact one; count and emit evaluate it identically.
+__device__ inline bool cand_f32(const Grid &g, const float4 &a, const float4 &b, const int w[3],
+                                float slack) {
+  const float dx = (b.x + (float)w[0] * g.Lf[0]) - a.x;
+  const float dy = (b.y + (float)w[1] * g.Lf[1]) - a.y;
+  const float dz = (b.z + (float)w[2] * g.Lf[2]) - a.z;
+  const float R = (a.w + b.w) + g.reachf + slack;
+  return dx * dx + dy * dy + dz * dz < R * R;
 }
 
 __global__ void k_bbox(const double4_32a *__restrict__ pos, long long N, double *partials) {
@@ -210,69 +203,93 @@ __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
     for (int w = 0; w < 6; ++w) dst.whist[w * cap + p] = src.whist[w * cap + o];
 }
 
-__global__ void k_count(Bodies b, long long N, Grid g, const int *__restrict__ count,
+__global__ void k_cellrec(const double4_32a *__restrict__ pos, long long N, Grid g, CellRec cr) {
+  long long i = (long long)blockIdx.x * kT + threadIdx.x;
+  if (i >= N) return;
+  const double4_32a p = pos[i];
+  int c[3], img[3];
+  cell_of(g, p.x, p.y, p.z, c, img);
+  double x[3] = {p.x, p.y, p.z};
+  float f[3];
+  for (int k = 0; k < 3; ++k)
+    f[k] = g.periodic ? (float)(x[k] - g.L[k] * img[k]) : (float)(x[k] - g.lo[k]);
+  cr.wpos[i] = make_float4(f[0], f[1], f[2], (float)p.w);
+  cr.info[i] = make_int4(c[0] | (c[1] << 10) | (c[2] << 20), img[0], img[1], img[2]);
+}
+
+__device__ inline void unpack_cell(int v, int c[3]) {
+  c[0] = v & 1023;
+  c[1] = (v >> 10) & 1023;
+  c[2] = (v >> 20) & 1023;
+}
+
+__global__ void k_count(CellRec cr, long long N, Grid g, const int *__restrict__ count,
                         const int *__restrict__ start, int *cnt_up, int *cnt_down, int *err) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
-  const double4_32a ps = b.pos[s];
-  int ci[3], imgs[3];
-  cell_of(g, ps.x, ps.y, ps.z, ci, imgs);
-  int up = 0, down = 0;
+  const float4 a = cr.wpos[s];
+  const int4 inf = cr.info[s];
+  int ci[3];
+  unpack_cell(inf.x, ci);
+  int up = 0;
   bool bad = false;
-  for_neighbours(g, count, start, ci, [&](int j, const int w[3]) {
-    if (j == s) return;
-    Cand c = cand_test(g, ps, imgs, s, b.pos[j], j, w);
-    if (c.keep) {
-      if (j > s) ++up; else ++down;
-      bad |= !c.range_ok;
+  for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
+    if (cand_f32(g, a, cr.wpos[j], w, g.slack)) {
+      ++up;
+      atomicAdd(&cnt_down[j], 1);
+      if (g.periodic) {
+        const int4 ij = cr.info[j];
+        bad |= abs(inf.y - ij.y + w[0]) > kShiftMax || abs(inf.z - ij.z + w[1]) > kShiftMax ||
+               abs(inf.w - ij.w + w[2]) > kShiftMax;
+      }
     }
   });
   cnt_up[s] = up;
-  cnt_down[s] = down;
   if (bad) atomicOr(err, kErrShiftRange);
 }
 
-__global__ void k_emit(Bodies b, long long N, Grid g, const int *__restrict__ count,
-                       const int *__restrict__ start, Table t) {
+__global__ void k_emit(CellRec cr, long long N, Grid g, const int *__restrict__ count,
+                       const int *__restrict__ start, Table t, int *dfill) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
-  const double4_32a ps = b.pos[s];
-  int ci[3], imgs[3];
-  cell_of(g, ps.x, ps.y, ps.z, ci, imgs);
+  const float4 a = cr.wpos[s];
+  const int4 inf = cr.info[s];
+  int ci[3];
+  unpack_cell(inf.x, ci);
   int r = t.row_start[s];
   const int r_end = t.row_start[s + 1];
-  for_neighbours(g, count, start, ci, [&](int j, const int w[3]) {
-    if (j <= s) return;
-    Cand c = cand_test(g, ps, imgs, s, b.pos[j], j, w);
-    if (c.keep && r < r_end) {
-      t.pair[r] = make_int2(s, j);
-      t.cpack[r] = c.cpack;
+  for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
+    if (r < r_end && cand_f32(g, a, cr.wpos[j], w, g.slack)) {
+      int cp = 0;
+      if (g.periodic) {
+        const int4 ij = cr.info[j];
+        cp = pack_shift(inf.y - ij.y + w[0], inf.z - ij.z + w[1], inf.w - ij.w + w[2]);
+      }
+      t.pair[r] = make_int2(s, j);   // body 1 = the slot that found the pair
+      t.cpack[r] = cp;                // cell shift of body 2
+      const int e = t.down_start[j] + atomicAdd(&dfill[j], 1);
+      if (e < t.down_start[j + 1]) t.down[e] = r;
       ++r;
     }
   });
 }
 
-__global__ void k_down(Bodies b, long long N, Grid g, const int *__restrict__ count,
-                       const int *__restrict__ start, Table t) {
+// the down lists were filled in atomic order: sort each body's list by row index
+__global__ void k_downsort(Table t, long long N) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
-  const int s = (int)sl;
-  const double4_32a ps = b.pos[s];
-  int ci[3], imgs[3];
-  cell_of(g, ps.x, ps.y, ps.z, ci, imgs);
-  int e = t.down_start[s];
-  const int e_end = t.down_start[s + 1];
-  for_neighbours(g, count, start, ci, [&](int j, const int w[3]) {
-    if (j >= s) return;
-    Cand c = cand_test(g, ps, imgs, s, b.pos[j], j, w);
-    if (!c.keep || e >= e_end) return;
-    int row = -1;
-    for (int r = t.row_start[j]; r < t.row_start[j + 1]; ++r)
-      if (t.pair[r].y == s && t.cpack[r] == c.cpack) { row = r; break; }
-    t.down[e++] = row;   // -1 never happens when both ends agree; the gather skips it
-  });
+  const int e0 = t.down_start[sl], e1 = t.down_start[sl + 1];
+  for (int a = e0 + 1; a < e1; ++a) {
+    const int v = t.down[a];
+    int b = a - 1;
+    while (b >= e0 && t.down[b] > v) {
+      t.down[b + 1] = t.down[b];
+      --b;
+    }
+    t.down[b + 1] = v;
+  }
 }
 
 __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old) {
@@ -281,13 +298,17 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
   const int2 pr = nt.pair[k];
   const int cp = nt.cpack[k];
   const int o1 = new_to_old[pr.x], o2 = new_to_old[pr.y];
-  const bool flip = o1 > o2;
-  const int a = flip ? o2 : o1, bb = flip ? o1 : o2;
-  const int want = flip ? neg_shift(cp) : cp;
+  // the old row has the same orientation (found by o1) or the opposite one (by o2)
   long long hit = -1;
-  if (bb < N_old && ot.P > 0) {
-    for (int r = ot.row_start[a]; r < ot.row_start[a + 1]; ++r)
-      if (ot.pair[r].y == bb && ot.cpack[r] == want) { hit = r; break; }
+  bool flip = false;
+  if (o1 < N_old && o2 < N_old && ot.P > 0) {
+    for (int r = ot.row_start[o1]; r < ot.row_start[o1 + 1]; ++r)
+      if (ot.pair[r].y == o2 && ot.cpack[r] == cp) { hit = r; break; }
+    if (hit < 0) {
+      const int ncp = neg_shift(cp);
+      for (int r = ot.row_start[o2]; r < ot.row_start[o2 + 1]; ++r)
+        if (ot.pair[r].y == o1 && ot.cpack[r] == ncp) { hit = r; flip = true; break; }
+    }
   }
   double4_32a fs = make_double4_32a(0, 0, 0, 0), hn = make_double4_32a(0, 0, 0, 0);
   double tp = 0;
@@ -348,19 +369,24 @@ void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long
     k_reorder<<<blocks(N), kT, 0, st>>>(src, dst, N, cap, new_to_old, slot_of_id, has_walls);
 }
 
-void launch_count(const Bodies &b, long long N, const Grid &g, const int *count,
+void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
+                    cudaStream_t st) {
+  if (N > 0) k_cellrec<<<blocks(N), kT, 0, st>>>(b.pos, N, g, CellRec{wpos, info});
+}
+
+void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
                   const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st) {
-  if (N > 0) k_count<<<blocks(N), kT, 0, st>>>(b, N, g, count, start, cnt_up, cnt_down, err);
+  if (N > 0)
+    k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, N, g, count, start, cnt_up, cnt_down, err);
 }
 
-void launch_emit(const Bodies &b, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, cudaStream_t st) {
-  if (N > 0) k_emit<<<blocks(N), kT, 0, st>>>(b, N, g, count, start, t);
+void launch_emit(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
+                 const int *start, const Table &t, int *dfill, cudaStream_t st) {
+  if (N > 0) k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, N, g, count, start, t, dfill);
 }
 
-void launch_down(const Bodies &b, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, cudaStream_t st) {
-  if (N > 0) k_down<<<blocks(N), kT, 0, st>>>(b, N, g, count, start, t);
+void launch_downsort(const Table &t, long long N, cudaStream_t st) {
+  if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, N);
 }
 
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,

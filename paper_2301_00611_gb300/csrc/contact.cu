@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kT) k_contact(Table t, Bodies b, const CellSta
   const double dt = cs->dt;
   double H[9], W[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
+  for (int q = 0; q < 9; q += 4) {
     H[q] = periodic ? cs->H[q] : 0.0;
     W[q] = periodic ? cs->W[q] : 0.0;
   }
@@ -53,9 +53,11 @@ __global__ void __launch_bounds__(kT) k_contact(Table t, Bodies b, const CellSta
       int i0, i1, i2;
       unpack_shift(t.cpack[k], i0, i1, i2);
       c0 = i0; c1 = i1; c2 = i2;
-      h0 = __dadd_rn(__dadd_rn(__dmul_rn(H[0], c0), __dmul_rn(H[1], c1)), __dmul_rn(H[2], c2));
-      h1 = __dadd_rn(__dadd_rn(__dmul_rn(H[3], c0), __dmul_rn(H[4], c1)), __dmul_rn(H[5], c2));
-      h2 = __dadd_rn(__dadd_rn(__dmul_rn(H[6], c0), __dmul_rn(H[7], c1)), __dmul_rn(H[8], c2));
+      // the cell is diagonal (enforced at the C ABI): H c has one term per axis, the
+      // same value the full product gives (the off-diagonal terms are exact zeros)
+      h0 = __dmul_rn(H[0], c0);
+      h1 = __dmul_rn(H[4], c1);
+      h2 = __dmul_rn(H[8], c2);
     }
     // branch vector and the exact test (eq. 2.2, second pass; R1 of the oracle)
     const double dx = __dsub_rn(__dadd_rn(p2.x, h0), p1.x);
@@ -96,9 +98,9 @@ __global__ void __launch_bounds__(kT) k_contact(Table t, Bodies b, const CellSta
     double4_32a v2 = b.vel[pr.y];
     const double4_32a w2 = b.angvel[pr.y];
     if (periodic) {  // velocity of the image of body 2 (shift c moves with the cell)
-      v2.x += W[0] * c0 + W[1] * c1 + W[2] * c2;
-      v2.y += W[3] * c0 + W[4] * c1 + W[5] * c2;
-      v2.z += W[6] * c0 + W[7] * c1 + W[8] * c2;
+      v2.x += W[0] * c0;
+      v2.y += W[4] * c1;
+      v2.z += W[8] * c2;
     }
     // 1. motion of the contact frame: -Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)
     const double ax = hn.y * nz - hn.z * ny;

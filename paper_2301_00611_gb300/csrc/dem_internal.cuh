@@ -10,16 +10,17 @@
 //     mprop  double4_32a (m, I, 1/m, 1/I)     id int, mat int, flags uint8
 //     whist  double4_32a[6][N] wall-contact history (Fs xyz, signed Fn)
 //   contact table (one row per potential interaction = collider candidate),
-//   rows sorted by (s1, s2) with s1 < s2 the slots of the two spheres:
+//   rows grouped by s1 in slot order:
 //     pair int2, cpack int (cell shift of s2, 3 x 10-bit signed),
 //     hfs double4_32a (Fs on body 2, kn)       kn == 0 <=> not in contact
 //     hn  double4_32a (normal of the last step, ks), tanphi double,
 //     oF  double4_32a (F on body 2, arm d1)    oM double4_32a (-(n x F), arm d2)
 //   so that the torques are T1 = d1*oM, T2 = d2*oM (section 2.1.4 with the
 //   contact point of eq. 2.8: C - x1 = d1 n, C - x2' = -d2 n).
+//   Row (s1, s2): s1 is the body whose half-shell scan found the pair.
 //   Per-body CSR over the table: row_start[s] (rows with s1 = s, contiguous) and
-//   down_start/down (rows with s2 = s), both in a fixed order, so the force sum
-//   of every body is a gather in one deterministic order (no atomics).
+//   down_start/down (rows with s2 = s, sorted by row), so the force sum of every
+//   body is a gather in one deterministic order (no atomics on forces).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -94,6 +95,9 @@ struct Grid {
   double L[3];      // periodic cell edges (diagonal H)
   int periodic;
   double reach;     // candidate margin: pair kept when |d| < r1 + r2 + reach
+  float Lf[3];      // FP32 copies for the candidate test
+  float reachf;
+  float slack;      // FP32 rounding allowance of the candidate test (keeps it conservative)
 };
 
 struct SceneConst {
@@ -132,12 +136,13 @@ void launch_cellsort(const int *count, const int *start, long long ncell, const 
                      int *tmp, cudaStream_t st);
 void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
                     const int *new_to_old, int *slot_of_id, int has_walls, cudaStream_t st);
-void launch_count(const Bodies &b, long long N, const Grid &g, const int *count,
+void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
+                    cudaStream_t st);
+void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
                   const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st);
-void launch_emit(const Bodies &b, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, cudaStream_t st);
-void launch_down(const Bodies &b, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, cudaStream_t st);
+void launch_emit(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
+                 const int *start, const Table &t, int *dfill, cudaStream_t st);
+void launch_downsort(const Table &t, long long N, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
                   cudaStream_t st);
 void launch_lost(const Table &ot, int *err, cudaStream_t st);

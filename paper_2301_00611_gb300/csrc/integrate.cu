@@ -134,9 +134,10 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   if (!fixed) {
     const double lam = sc.damping;
     double vref[3] = {vv[0], vv[1], vv[2]};
+    // cell matrices are diagonal (enforced at the C ABI): only their diagonals enter
     if (sc.periodic) {   // fluctuation velocity for eq. 2.9 in a deforming cell
       const double *Lp = cs->Lprev;
-      for (int q = 0; q < 3; ++q) vref[q] -= Lp[3 * q] * x[0] + Lp[3 * q + 1] * x[1] + Lp[3 * q + 2] * x[2];
+      for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
     }
     for (int q = 0; q < 3; ++q) {
       const double Ft = F[q] + mp.x * sc.gravity[q];
@@ -149,9 +150,7 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
     }
     if (sc.periodic) {   // homoDeform = 2
       const double *dL = cs->dL, *L = cs->L;
-      for (int q = 0; q < 3; ++q)
-        vn_[q] += (dL[3 * q] * x[0] + dL[3 * q + 1] * x[1] + dL[3 * q + 2] * x[2]) +
-                  dt * (L[3 * q] * vv[0] + L[3 * q + 1] * vv[1] + L[3 * q + 2] * vv[2]);
+      for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
     }
   } else {
     for (int q = 0; q < 3; ++q) { vn_[q] = vv[q]; wn_[q] = ww[q]; }
@@ -162,26 +161,38 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   b.angvel[s] = make_double4_32a(wn_[0], wn_[1], wn_[2], 0.0);
   if (flags != b.flags[s]) b.flags[s] = flags;
 
-  // orientation: q+ = dq(w+ dt) q
-  const double wmag = sqrt(wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2]);
-  if (wmag > 0) {
+  // orientation: q+ = dq(w+ dt) q, dq = (cos x, (sin x / x) * w dt / 2), x = |w| dt / 2.
+  // For x < 1e-2 the Maclaurin series of cos x and sin x / x truncated after the x^8
+  // term is exact to double precision (next terms < 1e-26) and needs no square root,
+  // division or sincos; larger angles use sincos.
+  const double w2 = wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2];
+  if (w2 > 0) {
     const double4_32a q0 = b.ori[s];
-    double sh, ch;
-    sincos(0.5 * (wmag * dt), &sh, &ch);
-    const double iw = sh / wmag;
-    const double dw = ch, dx = iw * wn_[0], dy = iw * wn_[1], dz = iw * wn_[2];
+    const double x2 = 0.25 * (dt * dt) * w2;
+    double ch, sx;   // cos x, sin x / x
+    if (x2 < 1e-4) {
+      ch = 1.0 - 0.5 * x2 * (1.0 - x2 * (1.0 / 12.0) * (1.0 - x2 * (1.0 / 30.0) * (1.0 - x2 * (1.0 / 56.0))));
+      sx = 1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0) * (1.0 - x2 * (1.0 / 72.0))));
+    } else {
+      const double x = sqrt(x2);
+      double sh;
+      sincos(x, &sh, &ch);
+      sx = sh / x;
+    }
+    const double hs = 0.5 * dt * sx;
+    const double dw = ch, dx = hs * wn_[0], dy = hs * wn_[1], dz = hs * wn_[2];
     b.ori[s] = make_double4_32a(dw * q0.x - dx * q0.y - dy * q0.z - dz * q0.w,
-                            dw * q0.y + dx * q0.x + dy * q0.w - dz * q0.z,
-                            dw * q0.z - dx * q0.w + dy * q0.x + dz * q0.y,
-                            dw * q0.w + dx * q0.z - dy * q0.y + dz * q0.x);
+                                dw * q0.y + dx * q0.x + dy * q0.w - dz * q0.z,
+                                dw * q0.z - dx * q0.w + dy * q0.x + dz * q0.y,
+                                dw * q0.w + dx * q0.z - dy * q0.y + dz * q0.x);
   }
 
   // collider trigger: displacement since the last run, minus the affine part
   const double4_32a xr = b.xref[s];
-  const double *E = cs->E;
-  const double ux = (xn[0] - xr.x) - (E[0] * xr.x + E[1] * xr.y + E[2] * xr.z);
-  const double uy = (xn[1] - xr.y) - (E[3] * xr.x + E[4] * xr.y + E[5] * xr.z);
-  const double uz = (xn[2] - xr.z) - (E[6] * xr.x + E[7] * xr.y + E[8] * xr.z);
+  const double *E = cs->E;   // diagonal
+  const double ux = (xn[0] - xr.x) - E[0] * xr.x;
+  const double uy = (xn[1] - xr.y) - E[4] * xr.y;
+  const double uz = (xn[2] - xr.z) - E[8] * xr.z;
   const double u2 = ux * ux + uy * uy + uz * uz;
   if (!(u2 <= cs->thr2)) {
     if (!ds->request) ds->request = 1;

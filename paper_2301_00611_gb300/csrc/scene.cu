@@ -125,6 +125,8 @@ struct dem_scene {
   int *slot_of_id = nullptr, *new_to_old = nullptr, *cnt_up = nullptr, *cnt_down = nullptr;
   uint32_t *key = nullptr;
   double4_32a *gF = nullptr, *gT = nullptr;
+  float4 *wpos = nullptr;
+  int4 *cinfo = nullptr;
 
   Table tab[2]{};
   long long tab_nbody[2]{0, 0};
@@ -144,6 +146,7 @@ struct dem_scene {
   cudaEvent_t ev = nullptr;
 
   bool need_rebuild = true;
+  bool table_fresh = false;   // table rows hold the contacts of the last completed step
   bool check_lost = false;
   bool cs_dirty = true;
   bool dt_set = false;
@@ -296,10 +299,11 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
   dfree(s, s->slot_of_id);
   s->slot_of_id = sid;
   dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down); dfree(s, s->key);
-  dfree(s, s->gF); dfree(s, s->gT);
+  dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
   if ((r = dalloc(s, &s->new_to_old, nc)) || (r = dalloc(s, &s->cnt_up, nc)) ||
       (r = dalloc(s, &s->cnt_down, nc)) || (r = dalloc(s, &s->key, nc)) ||
-      (r = dalloc(s, &s->gF, nc)) || (r = dalloc(s, &s->gT, nc)))
+      (r = dalloc(s, &s->gF, nc)) || (r = dalloc(s, &s->gT, nc)) ||
+      (r = dalloc(s, &s->wpos, nc)) || (r = dalloc(s, &s->cinfo, nc)))
     return r;
   s->cap = nc;
   size_t ws = scan_workspace_bytes(nc + 1);
@@ -371,7 +375,7 @@ dem_status rebuild(dem_scene *s) {
   if (s->timing) CK(cudaEventRecord(s->tev[0], s->st));
   dem_status r = rebuild_core(s);
   if (r) return r;
-  s->launches += 14;
+  s->launches += 16;
   if (s->timing) {
     CK(cudaEventRecord(s->tev[1], s->st));
     CK(cudaEventSynchronize(s->tev[1]));
@@ -429,6 +433,14 @@ dem_status rebuild_core(dem_scene *s) {
       g.L[k] = 0;
     }
   }
+  double ext = 0;
+  for (int k = 0; k < 3; ++k) {
+    ext = std::max(ext, g.periodic ? g.L[k] : g.n[k] / g.scale[k]);
+    g.Lf[k] = (float)g.L[k];
+  }
+  g.reachf = (float)reach;
+  // FP32 coordinates are bounded by ext: a few ulps of ext plus a relative allowance
+  g.slack = (float)(8.0 * ext * std::ldexp(1.0, -23) + 1e-5 * hmin);
   g.B = (int)next_pow2((unsigned)std::max(g.n[0], std::max(g.n[1], g.n[2])));
   const long long ncell = (long long)g.B * g.B * g.B;
   dem_status r;
@@ -459,7 +471,9 @@ dem_status rebuild_core(dem_scene *s) {
   Table &ot = s->tab[s->tc];
   Table &nt = s->tab[1 - s->tc];
   if ((r = ensure_table(s, nt, 0, N))) return r;
-  launch_count(s->cur, N, g, s->cell_count, s->cell_start, s->cnt_up, s->cnt_down,
+  launch_cellrec(s->cur, N, g, s->wpos, s->cinfo, s->st);
+  CK(cudaMemsetAsync(s->cnt_down, 0, sizeof(int) * N, s->st));
+  launch_count(s->wpos, s->cinfo, N, g, s->cell_count, s->cell_start, s->cnt_up, s->cnt_down,
                &s->ds_d->error, s->st);
   exclusive_scan(s->cnt_up, nt.row_start, N, s->scan_ws, s->st);
   exclusive_scan(s->cnt_down, nt.down_start, N, s->scan_ws, s->st);
@@ -472,15 +486,16 @@ dem_status rebuild_core(dem_scene *s) {
   if (P != s->rb_h->totals[1]) return fail(s, DEM_ERR_STATE, "internal: candidate count mismatch");
   if ((r = ensure_table(s, nt, P, N))) return r;
   nt.P = P;
-  launch_emit(s->cur, N, g, s->cell_count, s->cell_start, nt, s->st);
+  int *dfill = reinterpret_cast<int *>(s->key);   // the bin keys are no longer needed
+  CK(cudaMemsetAsync(dfill, 0, sizeof(int) * N, s->st));
+  launch_emit(s->wpos, s->cinfo, N, g, s->cell_count, s->cell_start, nt, dfill, s->st);
+  launch_downsort(nt, N, s->st);
   // 5: carry the contact history of the previous table
   ot.P = std::min(ot.P, ot.cap);
   if (ot.P > 0) CK(cudaMemsetAsync(ot.found, 0, sizeof(int) * ot.P, s->st));
   Table otv = ot;
   if (ot.P == 0 || ot.row_start == nullptr) otv.P = 0;
   launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->st);
-  // 6: rows where each body is the second sphere
-  launch_down(s->cur, N, g, s->cell_count, s->cell_start, nt, s->st);
   if (s->check_lost) launch_lost(otv, &s->ds_d->error, s->st);
   s->tab_nbody[1 - s->tc] = N;
   s->tc = 1 - s->tc;
@@ -673,7 +688,7 @@ void dem_scene_destroy(dem_scene *s) {
   free_table(s, s->tab[0]);
   free_table(s, s->tab[1]);
   dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
-  dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT);
+  dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
   dfree(s, s->scan_ws); dfree(s, s->partials);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
@@ -772,6 +787,7 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
   if (first_id) *first_id = s->N;
   s->N += n;
   s->need_rebuild = true;
+  s->table_fresh = false;
   s->check_lost = false;
   // sweep margin: > 0 absolute, < 0 fraction of the smallest radius
   double vd = s->desc.verlet_dist;
@@ -845,6 +861,7 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
     s->launches += B * ((t.P > 0 ? 1 : 0) + 2);
     CK(cudaGetLastError());
     if ((r = read_status(s))) return r;
+    s->table_fresh = true;
     if (ev) {
       for (long long i = 0; i < B; ++i) {
         float a = 0, b = 0, c = 0;
@@ -912,7 +929,7 @@ dem_status dem_get_state(dem_scene *s, double *pos, double *vel, double *angvel,
   if (angvel && (r = fetch4(s, s->cur.angvel, sid, angvel, 3))) return r;
   if (ori && (r = fetch4(s, s->cur.ori, sid, ori, 4))) return r;
   if (force || torque) {
-    if (s->need_rebuild) {
+    if (!s->table_fresh) {
       // no contact table matches the current body order yet: no contact forces
       if (force) std::memset(force, 0, sizeof(double) * 3 * s->N);
       if (torque) std::memset(torque, 0, sizeof(double) * 3 * s->N);
@@ -956,6 +973,7 @@ dem_status dem_set_state(dem_scene *s, const double *pos, const double *vel, con
   if (ori && (r = put(ori, s->cur.ori, 4, false))) return r;
   if (pos) {
     s->need_rebuild = true;
+    s->table_fresh = false;
     s->check_lost = false;
   }
   return DEM_OK;
@@ -991,6 +1009,7 @@ dem_status dem_set_cell(dem_scene *s, const double *H, const double *velgrad,
   if (H) {
     std::memcpy(s->cs_h.H, H, sizeof s->cs_h.H);
     s->need_rebuild = true;
+    s->table_fresh = false;
     s->check_lost = false;
   }
   if (velgrad) {
@@ -1043,7 +1062,7 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
   dem_status r;
   if ((r = sync_host(s))) return r;
   const long long N = s->N;
-  if (N == 0 || s->need_rebuild) return DEM_OK;
+  if (N == 0 || !s->table_fresh) return DEM_OK;
   const Table &t = s->tab[s->tc];
   const long long P = t.P;
   std::vector<int2> pair(P);
@@ -1252,6 +1271,7 @@ dem_status dem_set_contacts(dem_scene *s, long long n, const int *id1, const int
   CK(cudaMemcpyAsync(t.row_start, rs.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s->st));
   t.P = P;
   s->tab_nbody[s->tc] = N;
+  s->table_fresh = false;
   if (N > 0) CK(cudaMemcpyAsync(s->cur.flags, flags.data(), N, cudaMemcpyHostToDevice, s->st));
   if (s->has_walls)
     for (int w = 0; w < 6; ++w)
@@ -1302,7 +1322,7 @@ dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
            (s->desc.box_hi[2] - s->desc.box_lo[2]);
   o->packing_fraction = V > 0 ? s->vsolid / V : 0;
   if (s->N == 0) return DEM_OK;
-  const bool have_table = !s->need_rebuild;
+  const bool have_table = s->table_fresh;
   const Table &t = s->tab[s->tc];
   const SceneConst sc = scene_const(s);
   o->n_candidates = have_table ? t.P : 0;

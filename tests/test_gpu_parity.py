@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 import workloads
-from tests.parity_util import (band_pairs, compare_contact_sets, compare_contacts,
-                               compare_states, export_oracle, import_into_gpu)
+from tests.parity_util import (band_pairs, compare_contacts, compare_states, export_oracle,
+                               import_into_gpu, masses_of, set_coord_scale, set_radii)
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +26,7 @@ def mods():
 
 def _pair(w, mods, dt=None, **kw):
     oracle, pkg = mods
+    set_radii(w.radius)
     orc = oracle.OracleScene.from_workload(w)
     if dt is not None:
         orc.set_dt(dt)
@@ -35,6 +36,8 @@ def _pair(w, mods, dt=None, **kw):
 
 def _one_step_check(orc, gpu, w, oracle):
     before = orc.state()
+    X = float(np.max(np.abs(before["pos"])))
+    set_coord_scale(X)
     H = orc.cell()["H"] if w.periodic else np.eye(3)
     band = band_pairs(before["pos"], w.radius, w.periodic, H, oracle.pairs)
     orc.step(1)
@@ -42,12 +45,8 @@ def _one_step_check(orc, gpu, w, oracle):
     co, cg = orc.contacts(), gpu.contacts()
     n, worst = compare_contacts(co, cg, band)
     so, sg = orc.state(), gpu.state()
-    L = float(np.max(w.box_hi - w.box_lo))
-    ws = compare_states(so, sg, L)
-    fscale = np.max(np.abs(so["force"])) + 1e-300
-    assert np.max(np.abs(sg["force"] - so["force"])) <= 1e-12 * fscale
-    tscale = np.max(np.abs(so["torque"])) + 1e-300
-    assert np.max(np.abs(sg["torque"] - so["torque"])) <= 1e-12 * tscale
+    ws = compare_states(so, sg, X, co=co, masses=masses_of(w), dt=orc.clock()[2],
+                        gravity=float(np.linalg.norm(w.gravity)))
     return n, worst, ws
 
 
@@ -82,22 +81,23 @@ def test_one_step_from_imported_history(mods):
     """The oracle builds a contact history over 40 steps; the GPU imports that state and
     history (checkpoint/resume) and both take one more step."""
     oracle, pkg = mods
-    w = workloads.periodic_cloud(1500, 7, phi=0.33, inflate=1.05, vel_scale=0.1,
-                                 angvel_scale=50.0)
+    w = workloads.periodic_cloud(1500, 7, phi=0.33, inflate=1.02, vel_scale=0.01,
+                                 angvel_scale=5.0)
     orc, gpu = _pair(w, mods)
-    orc.set_velgrad(np.diag([-5.0, -3.0, 2.0]))
+    orc.set_velgrad(np.diag([-50.0, -30.0, 20.0]))
     orc.step(40)
     ex = export_oracle(orc)
-    assert np.count_nonzero(np.linalg.norm(ex["contacts"]["fs"], axis=1)) > 500
+    assert np.count_nonzero(np.linalg.norm(ex["contacts"]["fs"], axis=1)) > 100
     import_into_gpu(gpu, ex)
     n, worst, ws = _one_step_check(orc, gpu, w, oracle)
-    assert n > 800
+    assert n > 100
 
 
 def test_fixed_bodies_and_gravity(mods):
     oracle, pkg = mods
     w = workloads.box_cloud(700, 9, phi=0.3, inflate=1.04, vel_scale=0.05, angvel_scale=10.0)
     fixed = (workloads.uniform(w.n, 99) < 0.2).astype(np.uint8)
+    set_radii(w.radius)
     orc = oracle.OracleScene(periodic=False, box_lo=w.box_lo, box_hi=w.box_hi,
                              wall_mask=w.wall_mask, gravity=w.gravity, damping=w.damping)
     gpu = pkg.Scene(periodic=False, box_lo=w.box_lo, box_hi=w.box_hi, wall_mask=w.wall_mask,
@@ -127,6 +127,7 @@ def test_trajectory_and_collider_reruns(mods):
         band = band_pairs(before["pos"], w.radius, True, orc.cell()["H"], oracle.pairs)
         orc.step(1)
         gpu.step(1)
+        set_coord_scale(float(np.max(np.abs(before["pos"]))))
         co, cg = orc.contacts(), gpu.contacts()
         compare_contacts(co, cg, band, tol=1e-9)
         if k % 20 == 19:

@@ -13,7 +13,7 @@ def test_hand_worked_periodic_pair(oracle_mod):
     # cell of edge 1: spheres at x=0.05 and x=0.95 (r=0.1) touch through the image c=(-1,0,0)
     pos = np.array([[0.05, 0.5, 0.5], [0.95, 0.5, 0.5], [0.5, 0.5, 0.5]])
     rad = np.array([0.1, 0.1, 0.1])
-    for method in ("sweep", "brute"):
+    for method in ("sweep", "grid", "brute"):
         I, J, C = oracle_mod.pairs(pos, rad, periodic=True, H=np.eye(3), method=method)
         assert _set(I, J, C) == {(0, 1, (-1, 0, 0))}
         I, J, C = oracle_mod.pairs(pos, rad, periodic=False, method=method)
@@ -42,7 +42,8 @@ def test_sweep_equals_bruteforce_aperiodic(oracle_mod, seed, margin):
     w = workloads.box_cloud(1500, seed, phi=0.3, inflate=1.05, wall_mask=0)
     a = oracle_mod.pairs(w.pos, w.radius, margin=margin, method="sweep")
     b = oracle_mod.pairs(w.pos, w.radius, margin=margin, method="brute")
-    assert _set(*a) == _set(*b)
+    g = oracle_mod.pairs(w.pos, w.radius, margin=margin, method="grid")
+    assert _set(*a) == _set(*b) == _set(*g)
     assert len(a[0]) > 500
 
 
@@ -57,8 +58,9 @@ def test_sweep_equals_bruteforce_periodic(oracle_mod, seed, margin):
     pos += shift * L
     a = oracle_mod.pairs(pos, w.radius, periodic=True, H=w.cell, margin=margin, method="sweep")
     b = oracle_mod.pairs(pos, w.radius, periodic=True, H=w.cell, margin=margin, method="brute")
+    g = oracle_mod.pairs(pos, w.radius, periodic=True, H=w.cell, margin=margin, method="grid")
     sa = _set(*a)
-    assert sa == _set(*b)
+    assert sa == _set(*b) == _set(*g)
     assert len(sa) > 500
     assert any(c != (0, 0, 0) for _, _, c in sa)
 
@@ -69,7 +71,8 @@ def test_sweep_equals_bruteforce_sheared_cell(oracle_mod):
     H[0, 1] = 0.3 * H[1, 1]       # sheared cell: second base vector leans along x
     a = oracle_mod.pairs(w.pos, w.radius, periodic=True, H=H, method="sweep")
     b = oracle_mod.pairs(w.pos, w.radius, periodic=True, H=H, method="brute")
-    assert _set(*a) == _set(*b)
+    g = oracle_mod.pairs(w.pos, w.radius, periodic=True, H=H, method="grid")
+    assert _set(*a) == _set(*b) == _set(*g)
 
 
 def test_planted_missing_image_is_caught(oracle_mod):
@@ -79,3 +82,11 @@ def test_planted_missing_image_is_caught(oracle_mod):
     a = _set(*oracle_mod.pairs(w.pos, w.radius, periodic=True, H=w.cell))
     b = {(i, j, (0, 0, 0)) for i, j, _ in _set(*oracle_mod.pairs(w.pos, w.radius))}
     assert a != b
+
+
+def test_grid_on_a_tiny_periodic_cell_with_few_cells(oracle_mod):
+    """Cells fewer than three per axis (neighbour cells repeat through the wrap)."""
+    w = workloads.periodic_cloud(40, 9, phi=0.3, inflate=1.05)
+    a = oracle_mod.pairs(w.pos, w.radius, periodic=True, H=w.cell, method="grid")
+    b = oracle_mod.pairs(w.pos, w.radius, periodic=True, H=w.cell, method="brute")
+    assert _set(*a) == _set(*b)

@@ -48,6 +48,17 @@ WORKLOAD = "periodic isotropic compaction, 1M log-normal spheres, phi 0.30->0.62
 #                  + writes Fs/kn, normal/ks, F/d1, M/d2 (4 x 32 = 128)
 ROW_BYTES_ALL = 8 + 4 + 32 + 64
 ROW_BYTES_REAL = 32 + 8 + 128 + 128
+# Algorithmic FP64 flops of the contact law per row (periodic cell, diagonal H; add, mul,
+# div, sqrt = 1, fused multiply-add = 2), counted from the operations of sections
+# 2.1.2-2.1.4 as the oracle writes them: image shift 3, branch 6, |d|^2 5, threshold 2
+# (every row = 16); real rows add l, n, pen 5, image velocity 6, n- x n 9, twist 13,
+# frame rotation of Fs 24, ratchet-free v12 28, perpendicular part 11, increment 9,
+# Fn and Coulomb test 8, F 6, torque arms 13 (= 132 more, 148 in all).
+ROW_FLOPS_ALL = 16
+ROW_FLOPS_REAL = 132
+# FP64 peak of GB300 from its unit counts: 152 SMs x 2 FP64 FMA per clock x 2 flops at the
+# 2070 MHz maximum clock (a probe measured 1.194 TFLOP/s, 95% of it).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def _peaks():
@@ -205,29 +216,15 @@ def cpu_baseline_sample(n, seconds_hint=20.0):
                       f"the seeded initial cloud, {el:.1f} s single-threaded"}
 
 
-def run_gpu(args):
+def _time_window(Scene, w, args, precision, world, local):
+    """Run the job to its timed window on one scene; returns the measurements."""
     import torch
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    import __graft_entry__
-    if rank == 0 or world == 1:
-        __graft_entry__.build()
-    if world > 1:
-        torch.distributed.barrier()
-        __graft_entry__.build()
-    from paper_2301_00611_gb300 import Scene
-
-    w = make_workload(args.n)
+    from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
     stream = torch.cuda.current_stream()
-    scene = Scene.from_workload(w, capacity_bodies=args.n)
+    prec = DEM_MIXED if precision == "mixed" else DEM_FP64
+    scene = Scene.from_workload(w, capacity_bodies=args.n, precision=prec)
     dt = scene.dt()
-    L = velgrad_for(dt)
-    scene.set_cell_velgrad(L)
+    scene.set_cell_velgrad(velgrad_for(dt))
     K, W = args.steps, args.warmup
     prelude = max(0, JOB_STEPS - W - K)
     if prelude:
@@ -249,31 +246,88 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     tm = scene.timing()
     st1 = scene.stats()
-    launches = tm["kernel_launches"] - t_before
+    scene.close()
     T = ms / 1e3
     if world > 1:
         tt = torch.tensor([T], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         T = float(tt.item())
-    value = world * args.n * K / T
     mean_real = 0.5 * (st0["n_contacts"] + st1["n_contacts"])
-    contact_updates = world * mean_real * K / T
-    rows_per_s = world * tm["rows_processed"] / T
-
-    # dominant kernel: the fused contact kernel
-    peak, peak_kind = _peaks()
     avg_ms = tm["contact_ms"] / max(1, tm["contact_launches"])
     rows_avg = tm["rows_processed"] / max(1, tm["contact_launches"])
+    return {"T": T, "ms": ms, "dt": dt, "prelude": prelude, "tm": tm, "st0": st0, "st1": st1,
+            "mean_real": mean_real, "avg_ms": avg_ms, "rows_avg": rows_avg,
+            "launches": tm["kernel_launches"] - t_before, "clocks": clk.summary()}
+
+
+# Algorithmic bytes of the mixed-precision contact kernel (per row), from its operand list:
+#   every row:     pair 8 + cell shift 4 + reference branch/kn 16 + two FP32 offsets 32 = 60
+#   real rows add: FP64 shear history 32 + normal/ks 16 + two FP32 velocity/spin 64
+#                  + writes history 32, normal 16, F/d1 16, M/d2 16 = 192
+ROW_BYTES_ALL_MIXED = 60
+ROW_BYTES_REAL_MIXED = 192
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+        __graft_entry__.build()
+    from paper_2301_00611_gb300 import Scene
+
+    w = make_workload(args.n)
+    K, W = args.steps, args.warmup
+    peak, peak_kind = _peaks()
+    res = _time_window(Scene, w, args, "fp64", world, local)
+    mixed = None
+    if args.precision in ("both", "mixed"):
+        mixed = _time_window(Scene, w, args, "mixed", world, local)
+
+    T, ms, tm = res["T"], res["ms"], res["tm"]
+    value = world * args.n * K / T
+    contact_updates = world * res["mean_real"] * K / T
+    rows_per_s = world * tm["rows_processed"] / T
+    avg_ms, rows_avg, mean_real = res["avg_ms"], res["rows_avg"], res["mean_real"]
     bytes_avg = ROW_BYTES_ALL * rows_avg + ROW_BYTES_REAL * mean_real
-    achieved = bytes_avg / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    flops_avg = ROW_FLOPS_ALL * rows_avg + ROW_FLOPS_REAL * mean_real
+    bw = bytes_avg / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    tflops = flops_avg / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
     share = {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms", "cell_ms",
                                                 "collider_ms")}
-    clocks = clk.summary()
+    mixed_line = None
+    if mixed is not None:
+        mb = (ROW_BYTES_ALL_MIXED * mixed["rows_avg"] + ROW_BYTES_REAL_MIXED * mixed["mean_real"])
+        mbw = mb / (mixed["avg_ms"] / 1e3) / 1e9 if mixed["avg_ms"] > 0 else 0.0
+        mixed_line = {
+            "value": world * args.n * K / mixed["T"], "unit": UNIT,
+            "ms_per_step": mixed["ms"] / K,
+            "dtype": "mixed: f32 contact geometry/law, f64 shear history, integration and "
+                     "reductions",
+            "contact_updates_per_s": world * mixed["mean_real"] * K / mixed["T"],
+            "phase_share": {k: mixed["tm"][k] / max(1e-9, mixed["ms"])
+                            for k in ("contact_ms", "integrate_ms", "cell_ms", "collider_ms")},
+            "collider_runs": mixed["tm"]["collider_runs"], "gpu_launches": mixed["launches"],
+            "clocks": mixed["clocks"],
+            "contacts": {"start": mixed["st0"]["n_contacts"], "end": mixed["st1"]["n_contacts"]},
+            "roofline": {"bound": "hbm", "kernel": "contact (fused geometry + law), mixed",
+                         "achieved": mbw, "peak": peak, "unit": "GB/s", "frac": mbw / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "avg_launch_ms": mixed["avg_ms"], "bytes_per_launch": mb},
+        }
 
     # end to end: host arrays in, the whole job through the public API, state out
     e2e = None
     if not args.no_e2e:
-        scene.close()
         torch.cuda.synchronize()
         pos_out = np.empty((args.n, 3))
         vel_out = np.empty((args.n, 3))
@@ -289,22 +343,22 @@ def run_gpu(args):
         d2h = args.n * 2 * 3 * 8
         e2e = {"value": world * args.n * JOB_STEPS / T2, "unit": UNIT,
                "h2d_bytes_per_step": h2d / JOB_STEPS, "d2h_bytes_per_step": d2h / JOB_STEPS,
-               "note": "whole 5000-step job through the C ABI from host arrays: scene creation, "
-                       "upload, stepping, state download"}
-    else:
-        scene.close()
+               "note": "whole 5000-step FP64 job through the C ABI from host arrays: scene "
+                       "creation, upload, stepping, state download"}
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline_sample(args.n, args.cpu_seconds)
+        st0, st1 = res["st0"], res["st1"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "n_bodies": args.n, "job_steps": JOB_STEPS,
-                       "timed_window": f"last {K} steps (prelude {prelude} + warm-up {W} untimed)",
-                       "dt": dt, "l2": "working set > L2 (bodies ~200 MB + contact table)",
+                       "timed_window": f"last {K} steps (prelude {res['prelude']} + warm-up {W} "
+                                       f"untimed)",
+                       "dt": res["dt"], "l2": "working set > L2 (bodies ~200 MB + contact table)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "contact_updates_per_s": contact_updates,
             "candidate_rows_per_s": rows_per_s,
@@ -313,13 +367,16 @@ def run_gpu(args):
                          "packing_fraction_end": st1["packing_fraction"]},
             "phase_share": share,
             "collider_runs": tm["collider_runs"],
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "roofline": {"bound": "hbm", "kernel": "contact (fused geometry + law)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_kind": peak_kind, "avg_launch_ms": avg_ms,
-                         "bytes_per_launch": bytes_avg},
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+            "roofline": {"bound": "alu", "kernel": "contact (fused geometry + law), FP64",
+                         "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_kind": "derived from unit counts and clock (FP64 FMA pipe)",
+                         "avg_launch_ms": avg_ms, "flops_per_launch": flops_avg,
+                         "hbm": {"achieved_gbs": bw, "peak_gbs": peak, "frac": bw / peak,
+                                 "peak_kind": peak_kind, "bytes_per_launch": bytes_avg}},
+            "mixed": mixed_line,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -340,6 +397,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -74,7 +74,13 @@ typedef struct dem_scene_desc {
     double verlet_dist;      /* collider sweep margin dL (section 2.1.1, "Verlet distance"):
                                 > 0 absolute; < 0 fraction of the smallest radius
                                 (default -0.5, InsertionSortCollider.verletDist) */
-    int precision;           /* DEM_FP64 (only value supported in this version) */
+    int precision;           /* DEM_FP64: every operation in double precision.
+                                DEM_MIXED: contact geometry and law in FP32 on FP32 offsets
+                                from each body's FP64 position at the last collider run
+                                (per-row FP32 reference branch vectors); the shear-force
+                                history and its rotation into the new contact frame, the
+                                velocity/position accumulation and the kinetic-energy and
+                                unbalanced-force reductions stay FP64. */
     long long capacity_bodies;   /* initial device capacity hint (0: grow on demand) */
     long long capacity_contacts; /* initial contact-table rows hint (0: grow on demand) */
     void *cuda_stream;       /* cudaStream_t to run on; NULL: the scene creates its own */

@@ -183,14 +183,21 @@ __global__ void k_cellsort(const int *__restrict__ count, const int *__restrict_
 }
 
 __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
-                          const int *__restrict__ new_to_old, int *slot_of_id, int has_walls) {
+                          const int *__restrict__ new_to_old, int *slot_of_id, int has_walls,
+                          int mixed) {
   long long p = (long long)blockIdx.x * kT + threadIdx.x;
   if (p >= N) return;
   int o = new_to_old[p];
   double4_32a x = src.pos[o];
   dst.pos[p] = x;
-  dst.vel[p] = src.vel[o];
-  dst.angvel[p] = src.angvel[o];
+  const double4_32a v = src.vel[o], w = src.angvel[o];
+  dst.vel[p] = v;
+  dst.angvel[p] = w;
+  if (mixed) {   // the new reference position is x itself: zero offset
+    dst.p32[p] = make_float4(0.0f, 0.0f, 0.0f, (float)x.w);
+    dst.vw32[2 * p] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)w.x);
+    dst.vw32[2 * p + 1] = make_float4((float)w.y, (float)w.z, 0.0f, 0.0f);
+  }
   dst.ori[p] = src.ori[o];
   dst.mprop[p] = src.mprop[o];
   dst.xref[p] = make_double4_32a(x.x, x.y, x.z, 0.0);
@@ -249,8 +256,8 @@ __global__ void k_count(CellRec cr, long long N, Grid g, const int *__restrict__
   if (bad) atomicOr(err, kErrShiftRange);
 }
 
-__global__ void k_emit(CellRec cr, long long N, Grid g, const int *__restrict__ count,
-                       const int *__restrict__ start, Table t, int *dfill) {
+__global__ void k_emit(CellRec cr, Bodies b, long long N, Grid g, const int *__restrict__ count,
+                       const int *__restrict__ start, Table t, int *dfill, int mixed) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
@@ -269,6 +276,17 @@ __global__ void k_emit(CellRec cr, long long N, Grid g, const int *__restrict__ 
       }
       t.pair[r] = make_int2(s, j);   // body 1 = the slot that found the pair
       t.cpack[r] = cp;                // cell shift of body 2
+      if (mixed) {   // reference branch vector at this run, formed in FP64, rounded once
+        const double4_32a p1 = b.pos[s], p2 = b.pos[j];
+        double h[3] = {0, 0, 0};
+        if (g.periodic) {
+          int c0, c1, c2;
+          unpack_shift(cp, c0, c1, c2);
+          h[0] = g.L[0] * c0; h[1] = g.L[1] * c1; h[2] = g.L[2] * c2;
+        }
+        t.g32[r] = make_float4((float)((p2.x + h[0]) - p1.x), (float)((p2.y + h[1]) - p1.y),
+                               (float)((p2.z + h[2]) - p1.z), 0.0f);
+      }
       const int e = t.down_start[j] + atomicAdd(&dfill[j], 1);
       if (e < t.down_start[j + 1]) t.down[e] = r;
       ++r;
@@ -292,7 +310,8 @@ __global__ void k_downsort(Table t, long long N) {
   }
 }
 
-__global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old) {
+__global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old,
+                        int mixed) {
   long long k = (long long)blockIdx.x * kT + threadIdx.x;
   if (k >= nt.P) return;
   const int2 pr = nt.pair[k];
@@ -310,13 +329,36 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
         if (ot.pair[r].y == o1 && ot.cpack[r] == ncp) { hit = r; flip = true; break; }
     }
   }
+  const double sg = flip ? -1.0 : 1.0;
+  if (mixed) {
+    double4_32a fs = make_double4_32a(0, 0, 0, 0);
+    float4 hn = make_float4(0, 0, 0, 0);
+    float kn = 0.0f;
+    if (hit >= 0) {
+      kn = ot.g32[hit].w;
+      if (kn != 0.0f) {
+        const double4_32a ofs = ot.hfs[hit];
+        const float4 ohn = ot.hn32[hit];
+        const float sf = (float)sg;
+        fs = make_double4_32a(sg * ofs.x, sg * ofs.y, sg * ofs.z, ofs.w);
+        hn = make_float4(sf * ohn.x, sf * ohn.y, sf * ohn.z, ohn.w);
+        ot.found[hit] = 1;
+      }
+    }
+    const float4 gref = nt.g32[k];
+    nt.g32[k] = make_float4(gref.x, gref.y, gref.z, kn);
+    nt.hfs[k] = fs;
+    nt.hn32[k] = hn;
+    nt.oF32[k] = make_float4(0, 0, 0, 0);
+    nt.oM32[k] = make_float4(0, 0, 0, 0);
+    return;
+  }
   double4_32a fs = make_double4_32a(0, 0, 0, 0), hn = make_double4_32a(0, 0, 0, 0);
   double tp = 0;
   if (hit >= 0) {
     double4_32a ofs = ot.hfs[hit];
     if (ofs.w != 0.0) {
       double4_32a ohn = ot.hn[hit];
-      const double sg = flip ? -1.0 : 1.0;
       fs = make_double4_32a(sg * ofs.x, sg * ofs.y, sg * ofs.z, ofs.w);
       hn = make_double4_32a(sg * ohn.x, sg * ohn.y, sg * ohn.z, ohn.w);
       tp = ot.tanphi[hit];
@@ -330,10 +372,11 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
   nt.oM[k] = make_double4_32a(0, 0, 0, 0);
 }
 
-__global__ void k_lost(Table ot, int *err) {
+__global__ void k_lost(Table ot, int *err, int mixed) {
   long long r = (long long)blockIdx.x * kT + threadIdx.x;
   if (r >= ot.P) return;
-  if (ot.hfs[r].w != 0.0 && !ot.found[r]) atomicOr(err, kErrHistoryLost);
+  const bool real = mixed ? (ot.g32[r].w != 0.0f) : (ot.hfs[r].w != 0.0);
+  if (real && !ot.found[r]) atomicOr(err, kErrHistoryLost);
 }
 
 inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
@@ -364,9 +407,11 @@ void launch_cellsort(const int *count, const int *start, long long ncell, const 
 }
 
 void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
-                    const int *new_to_old, int *slot_of_id, int has_walls, cudaStream_t st) {
+                    const int *new_to_old, int *slot_of_id, int has_walls, int mixed,
+                    cudaStream_t st) {
   if (N > 0)
-    k_reorder<<<blocks(N), kT, 0, st>>>(src, dst, N, cap, new_to_old, slot_of_id, has_walls);
+    k_reorder<<<blocks(N), kT, 0, st>>>(src, dst, N, cap, new_to_old, slot_of_id, has_walls,
+                                        mixed);
 }
 
 void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
@@ -380,9 +425,11 @@ void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const in
     k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, N, g, count, start, cnt_up, cnt_down, err);
 }
 
-void launch_emit(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, int *dfill, cudaStream_t st) {
-  if (N > 0) k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, N, g, count, start, t, dfill);
+void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid &g,
+                 const int *count, const int *start, const Table &t, int *dfill, int mixed,
+                 cudaStream_t st) {
+  if (N > 0)
+    k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, g, count, start, t, dfill, mixed);
 }
 
 void launch_downsort(const Table &t, long long N, cudaStream_t st) {
@@ -390,12 +437,12 @@ void launch_downsort(const Table &t, long long N, cudaStream_t st) {
 }
 
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
-                  cudaStream_t st) {
-  if (nt.P > 0) k_merge<<<blocks(nt.P), kT, 0, st>>>(nt, ot, N_old, new_to_old);
+                  int mixed, cudaStream_t st) {
+  if (nt.P > 0) k_merge<<<blocks(nt.P), kT, 0, st>>>(nt, ot, N_old, new_to_old, mixed);
 }
 
-void launch_lost(const Table &ot, int *err, cudaStream_t st) {
-  if (ot.P > 0) k_lost<<<blocks(ot.P), kT, 0, st>>>(ot, err);
+void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st) {
+  if (ot.P > 0) k_lost<<<blocks(ot.P), kT, 0, st>>>(ot, err, mixed);
 }
 
 }  // namespace dem

@@ -1,0 +1,146 @@
+// Mixed-precision variant of the fused contact kernel (same method as
+// contact.cu: Ig2_Sphere_Sphere_ScGeom + Ip2_FrictMat_FrictMat_FrictPhys +
+// Law2_ScGeom_FrictPhys_CundallStrack, sections 2.1.2-2.1.4).
+//
+// Precision split:
+//   FP32  geometry and law: the branch vector is rebuilt each step from a
+//         per-row FP32 reference branch vector (xref2 + Href c - xref1, formed in
+//         FP64 at the collider run and rounded once) plus the FP32 offsets of
+//         both bodies from their own FP64 positions at that run, plus the FP32
+//         change of the cell shift (H - Href) c; normal, penetration, relative
+//         velocity, stiffnesses, normal force, output force and torque arms.
+//   FP64  the shear-force history and its transport into the new contact frame
+//         (the rotation -Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)), the
+//         accumulation of the shear increment and the Coulomb cap of the stored
+//         force.
+// Every length is an offset bounded by the cell size, so FP32 keeps about
+// 1e-7 relative resolution of the branch length whatever the cell extent.
+//
+// Traffic per real row: 172 B read (row 28 + history 48 + two bodies 96),
+// 80 B written; per non-real row 60 B read -- about 60% of the FP64 kernel's,
+// with a sixth of its FP64 operations.
+#include "dem_internal.cuh"
+
+namespace dem {
+
+namespace {
+constexpr int kT = 256;
+
+__global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
+                                                      const CellState *__restrict__ cs,
+                                                      const DevStatus *__restrict__ ds,
+                                                      const Mat *__restrict__ mats, int periodic) {
+  if (ds->pending) return;
+  const double dt = cs->dt;
+  const float dtf = (float)dt;
+  float dH[3] = {0, 0, 0}, Wd[3] = {0, 0, 0};
+  if (periodic)
+    for (int q = 0; q < 3; ++q) { dH[q] = cs->dHf[q]; Wd[q] = cs->Wf[q]; }
+  const long long P = t.P;
+  for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < P;
+       k += (long long)gridDim.x * kT) {
+    const int2 pr = t.pair[k];
+    const float4 g = t.g32[k];
+    const float4 a = b.p32[pr.x];
+    const float4 c = b.p32[pr.y];
+    float cx = 0, cy = 0, cz = 0;
+    if (periodic) {
+      int i0, i1, i2;
+      unpack_shift(t.cpack[k], i0, i1, i2);
+      cx = (float)i0; cy = (float)i1; cz = (float)i2;
+    }
+    const float dx = g.x + (c.x - a.x) + dH[0] * cx;
+    const float dy = g.y + (c.y - a.y) + dH[1] * cy;
+    const float dz = g.z + (c.z - a.z) + dH[2] * cz;
+    const float l2 = dx * dx + dy * dy + dz * dz;
+    const float R = a.w + c.w;
+    float kn = g.w;
+    if (!(l2 < R * R)) {
+      if (kn != 0.0f) {  // contact lost: back to a potential interaction
+        t.g32[k] = make_float4(g.x, g.y, g.z, 0.0f);
+        t.hfs[k] = make_double4_32a(0, 0, 0, 0);
+        const float4 z = make_float4(0, 0, 0, 0);
+        t.hn32[k] = z; t.oF32[k] = z; t.oM32[k] = z;
+      }
+      continue;
+    }
+    const float l = sqrtf(l2);
+    const float il = 1.0f / l;
+    const float nx = dx * il, ny = dy * il, nz = dz * il;
+    const float pen = R - l;
+    const float r1 = a.w, r2 = c.w;
+    double4_32a fsd = t.hfs[k];
+    float4 hn = t.hn32[k];
+    float ks;
+    double tanphi;
+    if (kn == 0.0f) {   // Ip2_FrictMat_FrictMat_FrictPhys on a new contact
+      const Mat m1 = mats[b.mat[pr.x]], m2 = mats[b.mat[pr.y]];
+      const float k1 = (float)m1.young * (2 * r1), k2 = (float)m2.young * (2 * r2);
+      kn = k1 * k2 / (k1 + k2);
+      const float s1 = (float)(m1.young * m1.poisson) * (2 * r1);
+      const float s2 = (float)(m2.young * m2.poisson) * (2 * r2);
+      ks = s1 * s2 / (s1 + s2);
+      tanphi = fmin(m1.tanphi, m2.tanphi);
+      fsd = make_double4_32a(0, 0, 0, tanphi);
+      hn = make_float4(nx, ny, nz, ks);
+      t.g32[k] = make_float4(g.x, g.y, g.z, kn);
+    } else {
+      ks = hn.w;
+      tanphi = fsd.w;
+    }
+    const float4 va1 = b.vw32[2 * pr.x], vb1 = b.vw32[2 * pr.x + 1];
+    const float4 va2 = b.vw32[2 * pr.y], vb2 = b.vw32[2 * pr.y + 1];
+    const float w1x = va1.w, w1y = vb1.x, w1z = vb1.y;
+    const float w2x = va2.w, w2y = vb2.x, w2z = vb2.y;
+    const float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
+    // 1. transport of the stored shear force into the new frame, in FP64
+    const float ax = hn.y * nz - hn.z * ny;
+    const float ay = hn.z * nx - hn.x * nz;
+    const float az = hn.x * ny - hn.y * nx;
+    const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
+    const double bx = (double)ax + (double)(tw * nx);
+    const double by = (double)ay + (double)(tw * ny);
+    const double bz = (double)az + (double)(tw * nz);
+    double fx = fsd.x - (fsd.y * bz - fsd.z * by);
+    double fy = fsd.y - (fsd.z * bx - fsd.x * bz);
+    double fz = fsd.z - (fsd.x * by - fsd.y * bx);
+    // 2. mutual motion (ratchet-free v12), FP32; increment accumulated in FP64
+    const float rx = r2 * w2x + r1 * w1x, ry = r2 * w2y + r1 * w1y, rz = r2 * w2z + r1 * w1z;
+    const float f = R * il;
+    const float ux = f * (v2x - va1.x) - (ry * nz - rz * ny);
+    const float uy = f * (v2y - va1.y) - (rz * nx - rx * nz);
+    const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
+    const float vn = nx * ux + ny * uy + nz * uz;
+    const float kd = ks * dtf;
+    fx -= (double)(kd * (ux - vn * nx));
+    fy -= (double)(kd * (uy - vn * ny));
+    fz -= (double)(kd * (uz - vn * nz));
+    // Law2: normal force (FP32), Coulomb cap of the stored force (FP64)
+    const float Fn = kn * pen;
+    const double maxFs = (double)Fn * tanphi;
+    const double fs2 = fx * fx + fy * fy + fz * fz;
+    if (fs2 > maxFs * maxFs) {
+      const double sc = maxFs / sqrt(fs2);
+      fx *= sc; fy *= sc; fz *= sc;
+    }
+    const float Fx = Fn * nx + (float)fx, Fy = Fn * ny + (float)fy, Fz = Fn * nz + (float)fz;
+    const float d1 = r1 - 0.5f * pen, d2 = r2 - 0.5f * pen;
+    t.hfs[k] = make_double4_32a(fx, fy, fz, tanphi);
+    t.hn32[k] = make_float4(nx, ny, nz, ks);
+    t.oF32[k] = make_float4(Fx, Fy, Fz, d1);
+    t.oM32[k] = make_float4(-(ny * Fz - nz * Fy), -(nz * Fx - nx * Fz), -(nx * Fy - ny * Fx), d2);
+  }
+}
+}  // namespace
+
+void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
+                          const DevStatus *ds, const Mat *mats, int periodic, int nsm,
+                          cudaStream_t st) {
+  if (t.P <= 0) return;
+  long long need = (t.P + kT - 1) / kT;
+  long long cap = (long long)nsm * 8;
+  unsigned grid = (unsigned)(need < cap ? need : cap);
+  k_contact_mixed<<<grid, kT, 0, st>>>(t, b, cs, ds, mats, periodic);
+}
+
+}  // namespace dem

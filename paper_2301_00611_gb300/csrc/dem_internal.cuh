@@ -46,13 +46,21 @@ struct Bodies {
   int *id, *mat;
   uint8_t *flags;   // bit0 fixed; bit (1+w) in contact with wall w
   double4_32a *whist;   // [6 * cap] or null
+  // mixed precision mirrors (null in FP64 mode), written by the integrator:
+  float4 *p32;      // (x - xref, r) in FP32
+  float4 *vw32;     // [2 * cap]: (vx, vy, vz, wx), (wy, wz, 0, 0)
 };
 
 struct Table {
   int2 *pair;
   int *cpack;
-  double4_32a *hfs, *hn, *oF, *oM;
+  double4_32a *hfs, *hn, *oF, *oM;   // FP64 mode; mixed mode uses hfs = (Fs, tan(phi))
   double *tanphi;
+  // mixed precision rows (null in FP64 mode)
+  float4 *g32;      // (reference branch vector xref2 + Href c - xref1, kn); kn == 0: not real
+  float4 *hn32;     // (previous normal, ks)
+  float4 *oF32;     // (F on body 2, d1)
+  float4 *oM32;     // (-(n x F), d2)
   int *row_start;   // [nbody + 1]
   int *down_start;  // [nbody + 1]
   int *down;        // [cap]
@@ -77,6 +85,11 @@ struct CellState {
   double thr2;          // squared displacement bound that triggers the collider
   long long iter;
   int periodic, pad;
+  // FP32 diagonals used by the mixed-precision contact kernel for the current step
+  float dHf[3];         // H - Href
+  float Wf[3];          // image velocity matrix W
+  float Ef[3];          // E
+  float pad2[3];
 };
 
 // Small status block read back by the host after a batch of steps.
@@ -135,34 +148,42 @@ void launch_scatter(long long N, const uint32_t *key, const int *start, int *fil
 void launch_cellsort(const int *count, const int *start, long long ncell, const int *id,
                      int *tmp, cudaStream_t st);
 void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
-                    const int *new_to_old, int *slot_of_id, int has_walls, cudaStream_t st);
+                    const int *new_to_old, int *slot_of_id, int has_walls, int mixed,
+                    cudaStream_t st);
 void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
                     cudaStream_t st);
 void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
                   const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st);
-void launch_emit(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
-                 const int *start, const Table &t, int *dfill, cudaStream_t st);
+void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid &g,
+                 const int *count, const int *start, const Table &t, int *dfill, int mixed,
+                 cudaStream_t st);
 void launch_downsort(const Table &t, long long N, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
-                  cudaStream_t st);
-void launch_lost(const Table &ot, int *err, cudaStream_t st);
+                  int mixed, cudaStream_t st);
+void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
 
 // contact.cu
 void launch_contact(const Table &t, const Bodies &b, const CellState *cs, const DevStatus *ds,
                     const Mat *mats, int periodic, int nsm, cudaStream_t st);
+// contact_mixed.cu
+void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
+                          const DevStatus *ds, const Mat *mats, int periodic, int nsm,
+                          cudaStream_t st);
 
 // integrate.cu
 void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                      const Mat *mats, const SceneConst &sc, long long cap, cudaStream_t st);
+                      const Mat *mats, const SceneConst &sc, long long cap, int mixed,
+                      cudaStream_t st);
 void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st);
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
-                          cudaStream_t st);
+                          int mixed, cudaStream_t st);
 // stats: per-block partial sums (deterministic tree), summed on the host in block order
 int stats_blocks(long long n);
 void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, double *partials,
                        cudaStream_t st);
-void launch_row_stats(const Table &t, const Bodies &b, double *partials, cudaStream_t st);
+void launch_row_stats(const Table &t, const Bodies &b, double *partials, int mixed,
+                      cudaStream_t st);
 void launch_wall_stats(const Bodies &b, const SceneConst &sc, const Mat *mats, long long cap,
                        double *partials, cudaStream_t st);
 

@@ -38,6 +38,28 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
   }
 }
 
+// Mixed precision: the same fixed-order gather over FP32 row outputs, summed in FP32
+// (the contact forces are FP32 results; the sum feeds an FP64 velocity update).
+__device__ inline void gather_rows_f32(const Table &t, int s, double F[3], double T[3]) {
+  float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
+  const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
+  for (int k = r0; k < r1; ++k) {
+    const float4 f = t.oF32[k], m = t.oM32[k];
+    f0 -= f.x; f1 -= f.y; f2 -= f.z;
+    t0 += f.w * m.x; t1 += f.w * m.y; t2 += f.w * m.z;
+  }
+  const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int k = t.down[e];
+    if (k < 0) continue;
+    const float4 f = t.oF32[k], m = t.oM32[k];
+    f0 += f.x; f1 += f.y; f2 += f.z;
+    t0 += m.w * m.x; t1 += m.w * m.y; t2 += m.w * m.z;
+  }
+  F[0] = f0; F[1] = f1; F[2] = f2;
+  T[0] = t0; T[1] = t1; T[2] = t2;
+}
+
 // FrictPhys of a sphere-wall contact: equivalent wall radius = sphere radius,
 // wall material = material 0.
 __device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn, double &ks,
@@ -50,6 +72,7 @@ __device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn,
   tanphi = fmin(mw.tanphi, ms.tanphi);
 }
 
+template <bool Mixed>
 __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
                                                   DevStatus *ds, const Mat *__restrict__ mats,
                                                   SceneConst sc, long long cap) {
@@ -59,7 +82,8 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   const int s = (int)sl;
   const double dt = cs->dt;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  gather_rows(t, s, F, T);
+  if (Mixed) gather_rows_f32(t, s, F, T);
+  else gather_rows(t, s, F, T);
 
   const double4_32a p = b.pos[s];
   const double4_32a v = b.vel[s];
@@ -139,14 +163,28 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
       const double *Lp = cs->Lprev;
       for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
     }
-    for (int q = 0; q < 3; ++q) {
-      const double Ft = F[q] + mp.x * sc.gravity[q];
-      const double acc = Ft * mp.z;
-      const double Fd = Ft * (1 - lam * sgn(Ft * (vref[q] + 0.5 * dt * acc)));
-      vn_[q] = vv[q] + dt * Fd * mp.z;
-      const double aacc = T[q] * mp.w;
-      const double Td = T[q] * (1 - lam * sgn(T[q] * (ww[q] + 0.5 * dt * aacc)));
-      wn_[q] = ww[q] + dt * Td * mp.w;
+    if (Mixed) {   // damping in FP32, the velocity accumulation in FP64
+      const float dtf = (float)dt, lamf = (float)lam, im = (float)mp.z, iI = (float)mp.w;
+      for (int q = 0; q < 3; ++q) {
+        const float Ft = (float)(F[q] + mp.x * sc.gravity[q]);
+        const float acc = Ft * im;
+        const float Fd = Ft * (1.0f - lamf * (float)sgn((double)(Ft * ((float)vref[q] + 0.5f * dtf * acc))));
+        vn_[q] = vv[q] + (double)(dtf * Fd * im);
+        const float Tq = (float)T[q];
+        const float aacc = Tq * iI;
+        const float Td = Tq * (1.0f - lamf * (float)sgn((double)(Tq * ((float)ww[q] + 0.5f * dtf * aacc))));
+        wn_[q] = ww[q] + (double)(dtf * Td * iI);
+      }
+    } else {
+      for (int q = 0; q < 3; ++q) {
+        const double Ft = F[q] + mp.x * sc.gravity[q];
+        const double acc = Ft * mp.z;
+        const double Fd = Ft * (1 - lam * sgn(Ft * (vref[q] + 0.5 * dt * acc)));
+        vn_[q] = vv[q] + dt * Fd * mp.z;
+        const double aacc = T[q] * mp.w;
+        const double Td = T[q] * (1 - lam * sgn(T[q] * (ww[q] + 0.5 * dt * aacc)));
+        wn_[q] = ww[q] + dt * Td * mp.w;
+      }
     }
     if (sc.periodic) {   // homoDeform = 2
       const double *dL = cs->dL, *L = cs->L;
@@ -166,7 +204,30 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   // term is exact to double precision (next terms < 1e-26) and needs no square root,
   // division or sincos; larger angles use sincos.
   const double w2 = wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2];
-  if (w2 > 0) {
+  if (Mixed && w2 > 0) {
+    // mixed precision: the increment dq in FP32 (series to x^4 is exact in FP32 for
+    // x < 1e-2), the composition with the stored FP64 orientation in FP64
+    const double4_32a q0 = b.ori[s];
+    const float dtf = (float)dt;
+    const float w0f = (float)wn_[0], w1f = (float)wn_[1], w2f = (float)wn_[2];
+    const float x2 = 0.25f * (dtf * dtf) * (w0f * w0f + w1f * w1f + w2f * w2f);
+    float ch, sx;
+    if (x2 < 1e-4f) {
+      ch = 1.0f - 0.5f * x2 * (1.0f - x2 * (1.0f / 12.0f));
+      sx = 1.0f - x2 * (1.0f / 6.0f) * (1.0f - x2 * (1.0f / 20.0f));
+    } else {
+      const float x = sqrtf(x2);
+      float sh;
+      sincosf(x, &sh, &ch);
+      sx = sh / x;
+    }
+    const float hs = 0.5f * dtf * sx;
+    const double dw = ch, dx = hs * w0f, dy = hs * w1f, dz = hs * w2f;
+    b.ori[s] = make_double4_32a(dw * q0.x - dx * q0.y - dy * q0.z - dz * q0.w,
+                                dw * q0.y + dx * q0.x + dy * q0.w - dz * q0.z,
+                                dw * q0.z - dx * q0.w + dy * q0.x + dz * q0.y,
+                                dw * q0.w + dx * q0.z - dy * q0.y + dz * q0.x);
+  } else if (w2 > 0) {
     const double4_32a q0 = b.ori[s];
     const double x2 = 0.25 * (dt * dt) * w2;
     double ch, sx;   // cos x, sin x / x
@@ -189,12 +250,26 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
 
   // collider trigger: displacement since the last run, minus the affine part
   const double4_32a xr = b.xref[s];
-  const double *E = cs->E;   // diagonal
-  const double ux = (xn[0] - xr.x) - E[0] * xr.x;
-  const double uy = (xn[1] - xr.y) - E[4] * xr.y;
-  const double uz = (xn[2] - xr.z) - E[8] * xr.z;
-  const double u2 = ux * ux + uy * uy + uz * uz;
-  if (!(u2 <= cs->thr2)) {
+  bool far;
+  if (Mixed) {
+    // FP32 offsets from the reference position feed the next contact pass
+    const float ox = (float)(xn[0] - xr.x), oy = (float)(xn[1] - xr.y), oz = (float)(xn[2] - xr.z);
+    b.p32[s] = make_float4(ox, oy, oz, (float)r);
+    b.vw32[2 * s] = make_float4((float)vn_[0], (float)vn_[1], (float)vn_[2], (float)wn_[0]);
+    b.vw32[2 * s + 1] = make_float4((float)wn_[1], (float)wn_[2], 0.0f, 0.0f);
+    const float ux = ox - cs->Ef[0] * (float)xr.x;
+    const float uy = oy - cs->Ef[1] * (float)xr.y;
+    const float uz = oz - cs->Ef[2] * (float)xr.z;
+    // FP32 rounding allowance: trigger slightly early
+    far = !(ux * ux + uy * uy + uz * uz <= (float)(0.998 * cs->thr2));
+  } else {
+    const double *E = cs->E;   // diagonal
+    const double ux = (xn[0] - xr.x) - E[0] * xr.x;
+    const double uy = (xn[1] - xr.y) - E[4] * xr.y;
+    const double uz = (xn[2] - xr.z) - E[8] * xr.z;
+    far = !(ux * ux + uy * uy + uz * uz <= cs->thr2);
+  }
+  if (far) {
     if (!ds->request) ds->request = 1;
   }
   if (!isfinite(xn[0] + xn[1] + xn[2] + vn_[0] + vn_[1] + vn_[2] + wn_[0] + wn_[1] + wn_[2]))
@@ -234,6 +309,11 @@ __global__ void k_cell_advance(CellState *cs, DevStatus *ds) {
     for (int q = 0; q < 9; ++q) e2 += cs->E[q] * cs->E[q];
     const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
     cs->thr2 = eff > 0 ? eff * eff : -1.0;
+    for (int q = 0; q < 3; ++q) {
+      cs->dHf[q] = (float)(cs->H[4 * q] - cs->Href[4 * q]);
+      cs->Wf[q] = (float)cs->W[4 * q];
+      cs->Ef[q] = (float)cs->E[4 * q];
+    }
   }
   cs->iter += 1;
   cs->time = __dadd_rn(cs->time, dt);
@@ -241,12 +321,13 @@ __global__ void k_cell_advance(CellState *cs, DevStatus *ds) {
 }
 
 __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats, SceneConst sc,
-                                long long cap, double4_32a *Fo, double4_32a *To) {
+                                long long cap, double4_32a *Fo, double4_32a *To, int mixed) {
   const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = (int)sl;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  gather_rows(t, s, F, T);
+  if (mixed) gather_rows_f32(t, s, F, T);
+  else gather_rows(t, s, F, T);
   const uint8_t flags = b.flags[s];
   if (sc.wall_mask && (flags & 0x7e)) {
     const double r = b.pos[s].w;
@@ -305,12 +386,20 @@ __global__ void k_body_stats(Bodies b, const double4_32a *__restrict__ F, long l
 }
 
 // real sphere-sphere rows: count, sum |F|, Love-Weber stress sum F_i (x1 - x2')_j
-__global__ void k_row_stats(Table t, double *partials) {
+__global__ void k_row_stats(Table t, double *partials, int mixed) {
   double v[11] = {0};
   for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
-    const double4_32a fs = t.hfs[k];
-    if (fs.w == 0.0) continue;
-    const double4_32a f = t.oF[k], m = t.oM[k], n = t.hn[k];
+    double4_32a f, m, n;
+    if (mixed) {
+      if (t.g32[k].w == 0.0f) continue;
+      const float4 a = t.oF32[k], c = t.oM32[k], h = t.hn32[k];
+      f = make_double4_32a(a.x, a.y, a.z, a.w);
+      m = make_double4_32a(c.x, c.y, c.z, c.w);
+      n = make_double4_32a(h.x, h.y, h.z, h.w);
+    } else {
+      if (t.hfs[k].w == 0.0) continue;
+      f = t.oF[k]; m = t.oM[k]; n = t.hn[k];
+    }
     const double l = f.w + m.w;
     v[0] += 1.0;
     v[1] += sqrt(f.x * f.x + f.y * f.y + f.z * f.z);
@@ -346,8 +435,11 @@ inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
 }  // namespace
 
 void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                          const Mat *mats, const SceneConst &sc, long long cap, cudaStream_t st) {
-  if (sc.N > 0) k_integrate<<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+                      const Mat *mats, const SceneConst &sc, long long cap, int mixed,
+                      cudaStream_t st) {
+  if (sc.N <= 0) return;
+  if (mixed) k_integrate<true><<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+  else k_integrate<false><<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
 }
 
 void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st) {
@@ -355,9 +447,9 @@ void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st) {
 }
 
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
-                              const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
-                              cudaStream_t st) {
-  if (sc.N > 0) k_gather_forces<<<blocks(sc.N), kT, 0, st>>>(b, t, mats, sc, cap, F, T);
+                          const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
+                          int mixed, cudaStream_t st) {
+  if (sc.N > 0) k_gather_forces<<<blocks(sc.N), kT, 0, st>>>(b, t, mats, sc, cap, F, T, mixed);
 }
 
 int stats_blocks(long long n) {
@@ -370,9 +462,10 @@ void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, doubl
   k_body_stats<<<stats_blocks(N), kT, 0, st>>>(b, F, N, partials);
 }
 
-void launch_row_stats(const Table &t, const Bodies &b, double *partials, cudaStream_t st) {
+void launch_row_stats(const Table &t, const Bodies &b, double *partials, int mixed,
+                      cudaStream_t st) {
   (void)b;
-  k_row_stats<<<stats_blocks(t.P), kT, 0, st>>>(t, partials);
+  k_row_stats<<<stats_blocks(t.P), kT, 0, st>>>(t, partials, mixed);
 }
 
 void launch_wall_stats(const Bodies &b, const SceneConst &sc, const Mat *mats, long long cap,

@@ -73,6 +73,7 @@ bool is_diag(const double *M) {
 void cell_derive(CellState &c) {
   if (!c.periodic) {
     for (int q = 0; q < 9; ++q) { c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0; }
+    for (int q = 0; q < 3; ++q) { c.dHf[q] = 0; c.Wf[q] = 0; c.Ef[q] = 0; }
     c.thr2 = c.verlet * c.verlet;
     return;
   }
@@ -88,6 +89,11 @@ void cell_derive(CellState &c) {
   for (int q = 0; q < 9; ++q) e2 += c.E[q] * c.E[q];
   double eff = c.verlet - std::sqrt(e2) * (c.rmax + c.verlet);
   c.thr2 = eff > 0 ? eff * eff : -1.0;
+  for (int q = 0; q < 3; ++q) {
+    c.dHf[q] = (float)(c.H[4 * q] - c.Href[4 * q]);
+    c.Wf[q] = (float)c.W[4 * q];
+    c.Ef[q] = (float)c.E[4 * q];
+  }
 }
 
 unsigned next_pow2(unsigned v) {
@@ -151,6 +157,7 @@ struct dem_scene {
   bool cs_dirty = true;
   bool dt_set = false;
   bool has_walls = false;
+  bool mixed = false;
   long long n_rebuilds = 0;
   bool velgrad_pending = false;
   double velgrad_next[9]{};
@@ -220,6 +227,7 @@ dem_status wait(dem_scene *s) {
 void free_bodies(dem_scene *s, Bodies &b) {
   dfree(s, b.pos); dfree(s, b.vel); dfree(s, b.angvel); dfree(s, b.ori); dfree(s, b.xref);
   dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.mat); dfree(s, b.flags); dfree(s, b.whist);
+  dfree(s, b.p32); dfree(s, b.vw32);
 }
 
 dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
@@ -231,12 +239,18 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
       (r = dalloc(s, &b.flags, cap)))
     return r;
   if (s->has_walls && (r = dalloc(s, &b.whist, 6 * cap))) return r;
+  if (s->mixed && ((r = dalloc(s, &b.p32, cap)) || (r = dalloc(s, &b.vw32, 2 * cap)))) return r;
   return DEM_OK;
 }
 
-void free_table(dem_scene *s, Table &t) {
+void free_rows(dem_scene *s, Table &t) {
   dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oF);
   dfree(s, t.oM); dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
+  dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oF32); dfree(s, t.oM32);
+}
+
+void free_table(dem_scene *s, Table &t) {
+  free_rows(s, t);
   dfree(s, t.row_start); dfree(s, t.down_start);
   t.cap = 0; t.nbody_cap = 0; t.P = 0;
 }
@@ -247,13 +261,19 @@ dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody)
   if (rows > t.cap) {
     long long P = t.P;
     long long nc = std::max<long long>(rows + rows / 4, 1024);
-    dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oF);
-    dfree(s, t.oM); dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
+    free_rows(s, t);
     if ((r = dalloc(s, &t.pair, nc)) || (r = dalloc(s, &t.cpack, nc)) ||
-        (r = dalloc(s, &t.hfs, nc)) || (r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oF, nc)) ||
-        (r = dalloc(s, &t.oM, nc)) || (r = dalloc(s, &t.tanphi, nc)) ||
-        (r = dalloc(s, &t.down, nc)) || (r = dalloc(s, &t.found, nc)))
+        (r = dalloc(s, &t.hfs, nc)) || (r = dalloc(s, &t.down, nc)) ||
+        (r = dalloc(s, &t.found, nc)))
       return r;
+    if (s->mixed) {
+      if ((r = dalloc(s, &t.g32, nc)) || (r = dalloc(s, &t.hn32, nc)) ||
+          (r = dalloc(s, &t.oF32, nc)) || (r = dalloc(s, &t.oM32, nc)))
+        return r;
+    } else if ((r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oF, nc)) ||
+               (r = dalloc(s, &t.oM, nc)) || (r = dalloc(s, &t.tanphi, nc))) {
+      return r;
+    }
     t.cap = nc;
     t.P = std::min(P, nc);
   }
@@ -465,7 +485,8 @@ dem_status rebuild_core(dem_scene *s) {
   exclusive_scan(s->cell_count, s->cell_start, ncell, s->scan_ws, s->st);
   launch_scatter(N, s->key, s->cell_start, s->cell_fill, s->new_to_old, s->st);
   launch_cellsort(s->cell_count, s->cell_start, ncell, s->cur.id, s->new_to_old, s->st);
-  launch_reorder(s->cur, s->alt, N, s->cap, s->new_to_old, s->slot_of_id, s->has_walls, s->st);
+  launch_reorder(s->cur, s->alt, N, s->cap, s->new_to_old, s->slot_of_id, s->has_walls, s->mixed,
+                 s->st);
   std::swap(s->cur, s->alt);
   // 4: candidates (count, prefix sums, emit)
   Table &ot = s->tab[s->tc];
@@ -488,15 +509,16 @@ dem_status rebuild_core(dem_scene *s) {
   nt.P = P;
   int *dfill = reinterpret_cast<int *>(s->key);   // the bin keys are no longer needed
   CK(cudaMemsetAsync(dfill, 0, sizeof(int) * N, s->st));
-  launch_emit(s->wpos, s->cinfo, N, g, s->cell_count, s->cell_start, nt, dfill, s->st);
+  launch_emit(s->wpos, s->cinfo, s->cur, N, g, s->cell_count, s->cell_start, nt, dfill, s->mixed,
+              s->st);
   launch_downsort(nt, N, s->st);
   // 5: carry the contact history of the previous table
   ot.P = std::min(ot.P, ot.cap);
   if (ot.P > 0) CK(cudaMemsetAsync(ot.found, 0, sizeof(int) * ot.P, s->st));
   Table otv = ot;
   if (ot.P == 0 || ot.row_start == nullptr) otv.P = 0;
-  launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->st);
-  if (s->check_lost) launch_lost(otv, &s->ds_d->error, s->st);
+  launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->mixed, s->st);
+  if (s->check_lost) launch_lost(otv, &s->ds_d->error, s->mixed, s->st);
   s->tab_nbody[1 - s->tc] = N;
   s->tc = 1 - s->tc;
   // reference configuration of this collider run
@@ -561,7 +583,7 @@ void dem_scene_desc_init(dem_scene_desc *d) {
   d->device = -1;
 }
 
-const char *dem_version(void) { return "gb300-dem 0.1 (sm_103a, fp64)"; }
+const char *dem_version(void) { return "gb300-dem 0.2 (sm_103a, fp64 + mixed)"; }
 
 const char *dem_last_error(const dem_scene *s) {
   return s ? s->err.c_str() : g_create_error.c_str();
@@ -574,8 +596,8 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
     return DEM_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (desc->precision != DEM_FP64) {
-    g_create_error = "only DEM_FP64 precision is available in this version";
+  if (desc->precision != DEM_FP64 && desc->precision != DEM_MIXED) {
+    g_create_error = "precision must be DEM_FP64 or DEM_MIXED";
     return DEM_ERR_UNSUPPORTED;
   }
   if (!(desc->damping >= 0) || !(desc->damping < 1)) {
@@ -608,6 +630,7 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
   }
   s->desc = *desc;
   s->has_walls = !desc->periodic && (desc->wall_mask & 0x3F);
+  s->mixed = desc->precision == DEM_MIXED;
   if (!s->has_walls) s->desc.wall_mask = 0;
   auto bad = [&](cudaError_t e, const char *what) {
     g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -851,9 +874,12 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
     cudaEvent_t *ev = s->timing ? s->tev.data() + 2 : nullptr;
     for (long long i = 0; i < B; ++i) {
       if (ev) CK(cudaEventRecord(ev[6 * i], s->st));
-      launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
+      if (s->mixed)
+        launch_contact_mixed(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
+      else
+        launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
       if (ev) { CK(cudaEventRecord(ev[6 * i + 1], s->st)); CK(cudaEventRecord(ev[6 * i + 2], s->st)); }
-      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->st);
+      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->mixed, s->st);
       if (ev) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
       launch_cell_advance(s->cs_d, s->ds_d, s->st);
       if (ev) CK(cudaEventRecord(ev[6 * i + 5], s->st));
@@ -936,7 +962,7 @@ dem_status dem_get_state(dem_scene *s, double *pos, double *vel, double *angvel,
       return DEM_OK;
     }
     launch_gather_forces(s->cur, s->tab[s->tc], s->mats_d, scene_const(s), s->cap, s->gF, s->gT,
-                         s->st);
+                         s->mixed, s->st);
     CK(cudaGetLastError());
     if (force && (r = fetch4(s, s->gF, sid, force, 3))) return r;
     if (torque && (r = fetch4(s, s->gT, sid, torque, 3))) return r;
@@ -976,6 +1002,7 @@ dem_status dem_set_state(dem_scene *s, const double *pos, const double *vel, con
     s->table_fresh = false;
     s->check_lost = false;
   }
+  if (s->mixed && (vel || angvel)) s->need_rebuild = true;   // refresh the FP32 mirrors
   return DEM_OK;
 }
 
@@ -1069,14 +1096,23 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
   std::vector<int> cp(P), id(N);
   std::vector<double4_32a> hfs(P), hn(P), oF(P), oM(P), pos(N);
   std::vector<double> tp(P);
+  std::vector<float4> g32, hn32, oF32, oM32;
   if (P > 0) {
     CK(cudaMemcpyAsync(pair.data(), t.pair, sizeof(int2) * P, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(cp.data(), t.cpack, sizeof(int) * P, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(hfs.data(), t.hfs, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(hn.data(), t.hn, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(oF.data(), t.oF, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(oM.data(), t.oM, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(tp.data(), t.tanphi, sizeof(double) * P, cudaMemcpyDeviceToHost, s->st));
+    if (s->mixed) {
+      g32.resize(P); hn32.resize(P); oF32.resize(P); oM32.resize(P);
+      CK(cudaMemcpyAsync(g32.data(), t.g32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(hn32.data(), t.hn32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(oF32.data(), t.oF32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(oM32.data(), t.oM32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
+    } else {
+      CK(cudaMemcpyAsync(hn.data(), t.hn, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(oF.data(), t.oF, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(oM.data(), t.oM, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(tp.data(), t.tanphi, sizeof(double) * P, cudaMemcpyDeviceToHost, s->st));
+    }
   }
   CK(cudaMemcpyAsync(id.data(), s->cur.id, sizeof(int) * N, cudaMemcpyDeviceToHost, s->st));
   CK(cudaMemcpyAsync(pos.data(), s->cur.pos, sizeof(double4_32a) * N, cudaMemcpyDeviceToHost, s->st));
@@ -1090,6 +1126,15 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
                          cudaMemcpyDeviceToHost, s->st));
   }
   if ((r = wait(s))) return r;
+  if (s->mixed) {   // one view of both layouts: hfs = (Fs, kn), hn = (n, ks), tp = tan(phi)
+    for (long long k = 0; k < P; ++k) {
+      tp[k] = hfs[k].w;
+      hfs[k].w = g32[k].w;
+      hn[k] = make_double4_32a(hn32[k].x, hn32[k].y, hn32[k].z, hn32[k].w);
+      oF[k] = make_double4_32a(oF32[k].x, oF32[k].y, oF32[k].z, oF32[k].w);
+      oM[k] = make_double4_32a(oM32[k].x, oM32[k].y, oM32[k].z, oM32[k].w);
+    }
+  }
   for (long long k = 0; k < P; ++k) {
     if (hfs[k].w == 0.0) continue;
     HostContact h{};
@@ -1261,12 +1306,27 @@ dem_status dem_set_contacts(dem_scene *s, long long n, const int *id1, const int
     rs[rows[k].a + 1] += 1;
   }
   for (long long i = 0; i < N; ++i) rs[i + 1] += rs[i];
+  std::vector<float4> g32, hn32;
+  if (s->mixed) {   // history layout of the mixed table: hfs = (Fs, tan(phi)), hn32, g32.w = kn
+    g32.resize(P);
+    hn32.resize(P);
+    for (long long k = 0; k < P; ++k) {
+      g32[k] = make_float4(0, 0, 0, (float)hfs[k].w);
+      hn32[k] = make_float4((float)hn[k].x, (float)hn[k].y, (float)hn[k].z, (float)hn[k].w);
+      hfs[k].w = tp[k];
+    }
+  }
   if (P > 0) {
     CK(cudaMemcpyAsync(t.pair, pair.data(), sizeof(int2) * P, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(t.cpack, cp.data(), sizeof(int) * P, cudaMemcpyHostToDevice, s->st));
     CK(cudaMemcpyAsync(t.hfs, hfs.data(), sizeof(double4_32a) * P, cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemcpyAsync(t.hn, hn.data(), sizeof(double4_32a) * P, cudaMemcpyHostToDevice, s->st));
-    CK(cudaMemcpyAsync(t.tanphi, tp.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s->st));
+    if (s->mixed) {
+      CK(cudaMemcpyAsync(t.g32, g32.data(), sizeof(float4) * P, cudaMemcpyHostToDevice, s->st));
+      CK(cudaMemcpyAsync(t.hn32, hn32.data(), sizeof(float4) * P, cudaMemcpyHostToDevice, s->st));
+    } else {
+      CK(cudaMemcpyAsync(t.hn, hn.data(), sizeof(double4_32a) * P, cudaMemcpyHostToDevice, s->st));
+      CK(cudaMemcpyAsync(t.tanphi, tp.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s->st));
+    }
   }
   CK(cudaMemcpyAsync(t.row_start, rs.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s->st));
   t.P = P;
@@ -1328,7 +1388,8 @@ dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
   o->n_candidates = have_table ? t.P : 0;
   double *ph = s->partials_h;
   // bodies: kinetic energy, |F| of free bodies
-  if (have_table) launch_gather_forces(s->cur, t, s->mats_d, sc, s->cap, s->gF, s->gT, s->st);
+  if (have_table)
+    launch_gather_forces(s->cur, t, s->mats_d, sc, s->cap, s->gF, s->gT, s->mixed, s->st);
   else CK(cudaMemsetAsync(s->gF, 0, sizeof(double4_32a) * s->N, s->st));
   int nb = stats_blocks(s->N);
   launch_body_stats(s->cur, s->gF, s->N, s->partials, s->st);
@@ -1339,7 +1400,7 @@ dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
   double nc = 0, sumC = 0, sig[9] = {0};
   if (have_table && t.P > 0) {
     int nr = stats_blocks(t.P);
-    launch_row_stats(t, s->cur, s->partials, s->st);
+    launch_row_stats(t, s->cur, s->partials, s->mixed, s->st);
     CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 11 * nr, cudaMemcpyDeviceToHost, s->st));
     if ((r = wait(s))) return r;
     for (int b = 0; b < nr; ++b) {

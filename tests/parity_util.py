@@ -70,8 +70,11 @@ def compare_contact_sets(co, cg, band=frozenset()):
     return len(ko)
 
 
-def compare_contacts(co, cg, band=frozenset(), tol=TOL):
-    """Per-contact parity on the common set; returns (count, worst relative errors)."""
+def compare_contacts(co, cg, band=frozenset(), tol=TOL, eps=EPS, coord=None):
+    """Per-contact parity on the common set; returns (count, worst relative errors).
+    eps and coord give the rounding unit and the coordinate scale of the branch
+    vector (FP64: the scene's coordinates; mixed precision: FP32 offsets bounded by
+    the contact distance)."""
     n = compare_contact_sets(co, cg, band)
     io = {k: t for t, k in enumerate(contact_keys(co))}
     ig = {k: t for t, k in enumerate(contact_keys(cg))}
@@ -82,13 +85,16 @@ def compare_contacts(co, cg, band=frozenset(), tol=TOL):
     if len(keys) == 0:
         return n, worst
     scale = np.linalg.norm(co["fn"][a], axis=1) + np.linalg.norm(co["fs"][a], axis=1)
-    ulp_force = co["phys"][a, 0] * ULPS * EPS * _coord_scale()
+    X = _coord_scale() if coord is None else coord
+    ulp_force = co["phys"][a, 0] * ULPS * eps * X
     for f in ("fn", "fs"):
         e = np.max(np.abs(cg[f][b] - co[f][a]), axis=1) / (tol * scale + ulp_force)
         worst[f] = float(e.max()) * tol
-    worst["normal"] = float(np.max(np.abs(cg["normal"][b] - co["normal"][a])))
+    worst["normal"] = float(np.max(np.abs(cg["normal"][b] - co["normal"][a]))) * (EPS / eps)
     rs = np.abs(co["phys"][a])
     worst["phys"] = float(np.max(np.abs(cg["phys"][b] - co["phys"][a]) / np.maximum(rs, 1e-300)))
+    if eps != EPS:   # FP32 stiffnesses: a few FP32 roundings
+        worst["phys"] *= tol / (8 * eps)
     worst["pen_abs"] = float(np.max(np.abs(cg["pen"][b] - co["pen"][a])))
     assert np.array_equal(cg["c"][b], co["c"][a]), "cell shifts differ"
     for f in ("fn", "fs", "normal", "phys"):
@@ -109,7 +115,8 @@ def body_sums(co, n):
     return fsum, ksum
 
 
-def compare_states(so, sg, length_scale, tol=TOL, co=None, masses=None, dt=0.0, gravity=0.0):
+def compare_states(so, sg, length_scale, tol=TOL, co=None, masses=None, dt=0.0, gravity=0.0,
+                   eps=EPS, coord=None):
     """State parity after one step.  With the oracle's contacts `co`, masses
     (m, I, r per body) and dt, velocities, spins, forces and torques are compared
     per body against the size of the terms that were summed; without them, against
@@ -121,7 +128,8 @@ def compare_states(so, sg, length_scale, tol=TOL, co=None, masses=None, dt=0.0, 
         m, I, r = masses
         n = len(m)
         fsum, ksum = body_sums(co, n)
-        fterm = tol * fsum + ULPS * EPS * _coord_scale() * ksum
+        X = _coord_scale() if coord is None else coord
+        fterm = tol * fsum + ULPS * eps * X * ksum
         fscale = fterm + tol * m * abs(gravity)
         dv = np.linalg.norm(sg["vel"] - so["vel"], axis=1)
         vs = tol * np.linalg.norm(so["vel"], axis=1) + dt * fscale / m

@@ -218,8 +218,31 @@ dem_status dem_get_stats(dem_scene *scene, dem_stats *out);
 dem_status dem_set_timing(dem_scene *scene, int enable);
 dem_status dem_get_timing(dem_scene *scene, dem_timing *out);
 
+/* Collision detection on a bare configuration (section 2.1.1, both passes: the
+ * grid's bounding-volume filter, then the exact sphere test): every pair
+ * i < j of the caller's indices with |x_j + H c - x_i| < (r_i + r_j) + margin,
+ * c the cell shift of j (periodic cells: H = cell_h, diagonal; the shift of the
+ * nearest image).  The exact test is evaluated in double precision with
+ * round-to-nearest operations in the order written, so the set is exactly the
+ * one this definition gives.
+ *   pos_dev     DEVICE n*3 doubles; radius_dev DEVICE n doubles (> 0, finite)
+ *   cell_h      HOST 9 doubles (read only when periodic)
+ *   id1_dev, id2_dev  DEVICE cap ints; cell_dist_dev DEVICE cap*3 ints (nullable)
+ *   count       HOST: receives the number of pairs; when it exceeds cap only the
+ *               first cap rows are written (call again with a larger cap).
+ * Rows come in a fixed order (grouped by the grid order of the sphere that
+ * found them), the same on every call.  Scratch memory is allocated on
+ * cuda_stream (NULL: the default stream) and freed before returning; the call
+ * waits for its work.  Errors (reported by dem_last_error(NULL)): INVALID_ARG,
+ * NONFINITE, GEOMETRY (a sphere pair spans a third of the periodic cell), OOM,
+ * TIMEOUT, CUDA. */
+dem_status dem_find_pairs(const double *pos_dev, const double *radius_dev, long long n,
+                          int periodic, const double *cell_h, double margin, long long cap,
+                          int *id1_dev, int *id2_dev, int *cell_dist_dev, long long *count,
+                          void *cuda_stream);
+
 /* Message of the last error on this scene ("" if none).  NULL scene: the last
- * error of a failed dem_scene_create in this thread. */
+ * error of a failed dem_scene_create or dem_find_pairs in this thread. */
 const char *dem_last_error(const dem_scene *scene);
 
 /* Library version string. */

@@ -22,101 +22,12 @@
 //      sphere): filled in atomic order during the emit, then sorted per body, so
 //      the force gather reads them in a deterministic order.
 #include "dem_internal.cuh"
+#include "grid.cuh"
 
 namespace dem {
 
 namespace {
 constexpr int kT = 256;
-
-__host__ __device__ inline uint32_t spread3(uint32_t x) {  // 8 bits -> every third bit
-  x &= 0xffu;
-  x = (x | (x << 8)) & 0x0000f00fu;
-  x = (x | (x << 4)) & 0x000c30c3u;
-  x = (x | (x << 2)) & 0x00249249u;
-  return x;
-}
-__host__ __device__ inline uint32_t morton3(int i, int j, int k) {
-  return spread3((uint32_t)i) | (spread3((uint32_t)j) << 1) | (spread3((uint32_t)k) << 2);
-}
-
-// cell coordinates (and, periodic, the integer image) of a position
-__device__ inline void cell_of(const Grid &g, double x, double y, double z, int c[3], int img[3]) {
-  const double p[3] = {x, y, z};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    int ck;
-    if (g.periodic) {
-      double s = p[k] * g.scale[k];
-      double fi = floor(s);
-      double f = s - fi;
-      ck = (int)(f * g.n[k]);
-      img[k] = (int)fi;
-    } else {
-      ck = (int)floor((p[k] - g.lo[k]) * g.scale[k]);
-      img[k] = 0;
-    }
-    c[k] = ck < 0 ? 0 : (ck >= g.n[k] ? g.n[k] - 1 : ck);
-  }
-}
-
-__device__ inline int neg_shift(int p) {
-  int a, b, c;
-  unpack_shift(p, a, b, c);
-  return pack_shift(-a, -b, -c);
-}
-
-// Forward half of the 27-cell stencil: own cell (partners with a higher slot)
-// plus the 13 offsets with (dz, dy, dx) lexicographically positive, so every pair
-// of neighbouring cells is visited from exactly one side.
-template <class F>
-__device__ inline void for_half_shell(const Grid &g, const int *__restrict__ count,
-                                      const int *__restrict__ start, const int ci[3], int s,
-                                      F &&f) {
-  for (int dz = 0; dz <= 1; ++dz)
-    for (int dy = (dz ? -1 : 0); dy <= 1; ++dy)
-      for (int dx = ((dz || dy) ? -1 : 0); dx <= 1; ++dx) {
-        const int d[3] = {dx, dy, dz};
-        int cj[3], w[3];
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          int c = ci[k] + d[k];
-          w[k] = 0;
-          if (g.periodic) {
-            if (c < 0) { c += g.n[k]; w[k] = -1; }
-            else if (c >= g.n[k]) { c -= g.n[k]; w[k] = 1; }
-          } else if (c < 0 || c >= g.n[k]) {
-            ok = false;
-          }
-          cj[k] = c;
-        }
-        if (!ok) continue;
-        const bool self = (dx == 0 && dy == 0 && dz == 0);
-        const uint32_t m = morton3(cj[0], cj[1], cj[2]);
-        const int s0 = start[m], cnt = count[m];
-        for (int j = (self ? s + 1 : s0); j < s0 + cnt; ++j) f(j, w);
-      }
-}
-
-// Per-slot collider record: FP32 position relative to the grid (periodic: the
-// wrapped position), radius, packed cell coordinates and the integer image.
-struct CellRec {
-  float4 *wpos;   // (x, y, z, r)
-  int4 *info;     // (cell0 | cell1 << 10 | cell2 << 20, img0, img1, img2)
-};
-
-// Conservative FP32 candidate test of (s, j): keeps every pair whose FP64
-// distance is below r1 + r2 + reach (the slack covers the FP32 rounding of
-// coordinates bounded by the cell size), so the candidate set is a superset of
-// the exact one; count and emit evaluate it identically.
-__device__ inline bool cand_f32(const Grid &g, const float4 &a, const float4 &b, const int w[3],
-                                float slack) {
-  const float dx = (b.x + (float)w[0] * g.Lf[0]) - a.x;
-  const float dy = (b.y + (float)w[1] * g.Lf[1]) - a.y;
-  const float dz = (b.z + (float)w[2] * g.Lf[2]) - a.z;
-  const float R = (a.w + b.w) + g.reachf + slack;
-  return dx * dx + dy * dy + dz * dz < R * R;
-}
 
 __global__ void k_bbox(const double4_32a *__restrict__ pos, long long N, double *partials) {
   __shared__ double sh[6][kT];

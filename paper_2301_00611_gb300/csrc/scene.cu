@@ -563,6 +563,10 @@ dem_status prepare_step(dem_scene *s) {
 
 }  // namespace
 
+namespace dem {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace dem
+
 // =================================================================== C ABI
 extern "C" {
 

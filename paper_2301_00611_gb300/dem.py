@@ -109,6 +109,8 @@ _SIGS = {
     "dem_get_stats": (ctypes.c_int, [_P, _P]),
     "dem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "dem_get_timing": (ctypes.c_int, [_P, _P]),
+    "dem_find_pairs": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
+                                      ctypes.c_double, ctypes.c_longlong, _P, _P, _P, _P, _P]),
     "dem_last_error": (ctypes.c_char_p, [_P]),
     "dem_version": (ctypes.c_char_p, []),
 }
@@ -364,6 +366,37 @@ def _timing_methods():
 
 
 _timing_methods()
+
+
+def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, stream=None):
+    """All pairs i < j with |x_j + H c - x_i| < r_i + r_j + margin (dem_find_pairs).
+
+    pos (n, 3) and radius (n,) are float64 CUDA tensors; returns int32 CUDA tensors
+    (i, j, c) in the library's fixed row order."""
+    import torch
+    lib = load_library()
+    pos = pos.contiguous()
+    radius = radius.contiguous()
+    if pos.dtype != torch.float64 or radius.dtype != torch.float64 or not pos.is_cuda:
+        raise ValueError("pos and radius must be float64 CUDA tensors")
+    n = radius.numel()
+    H = np.ascontiguousarray(np.eye(3) if cell is None else cell, dtype=np.float64).reshape(3, 3)
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    cap = max(16, 8 * n) if cap is None else int(cap)
+    while True:
+        I = torch.empty(cap, dtype=torch.int32, device=pos.device)
+        J = torch.empty(cap, dtype=torch.int32, device=pos.device)
+        C = torch.empty((cap, 3), dtype=torch.int32, device=pos.device)
+        cnt = ctypes.c_longlong()
+        rc = lib.dem_find_pairs(pos.data_ptr(), radius.data_ptr(), n, int(bool(periodic)),
+                                H.ctypes.data, float(margin), cap, I.data_ptr(), J.data_ptr(),
+                                C.data_ptr(), ctypes.byref(cnt), st)
+        if rc != DEM_OK:
+            raise DemError(rc, lib.dem_last_error(None).decode())
+        if cnt.value <= cap:
+            m = cnt.value
+            return I[:m], J[:m], C[:m]
+        cap = cnt.value
 
 
 def version() -> str:

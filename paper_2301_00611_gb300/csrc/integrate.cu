@@ -19,7 +19,17 @@ namespace dem {
 namespace {
 constexpr int kT = 256;
 
-__device__ inline double sgn(double x) { return (double)((x > 0) - (x < 0)); }
+// damping factor 1 - lam * sgn(p) as a select (no integer-to-double conversion)
+__device__ inline double damp_factor(double p, double lam) {
+  return p > 0 ? 1.0 - lam : (p < 0 ? 1.0 + lam : 1.0);
+}
+__device__ inline float damp_factor_f(float p, float lam) {
+  return p > 0.0f ? 1.0f - lam : (p < 0.0f ? 1.0f + lam : 1.0f);
+}
+// finiteness by exponent bits (integer pipe)
+__device__ inline bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
 
 __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[3]) {
   const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
@@ -168,21 +178,21 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
       for (int q = 0; q < 3; ++q) {
         const float Ft = (float)(F[q] + mp.x * sc.gravity[q]);
         const float acc = Ft * im;
-        const float Fd = Ft * (1.0f - lamf * (float)sgn((double)(Ft * ((float)vref[q] + 0.5f * dtf * acc))));
+        const float Fd = Ft * damp_factor_f(Ft * ((float)vref[q] + 0.5f * dtf * acc), lamf);
         vn_[q] = vv[q] + (double)(dtf * Fd * im);
         const float Tq = (float)T[q];
         const float aacc = Tq * iI;
-        const float Td = Tq * (1.0f - lamf * (float)sgn((double)(Tq * ((float)ww[q] + 0.5f * dtf * aacc))));
+        const float Td = Tq * damp_factor_f(Tq * ((float)ww[q] + 0.5f * dtf * aacc), lamf);
         wn_[q] = ww[q] + (double)(dtf * Td * iI);
       }
     } else {
       for (int q = 0; q < 3; ++q) {
         const double Ft = F[q] + mp.x * sc.gravity[q];
         const double acc = Ft * mp.z;
-        const double Fd = Ft * (1 - lam * sgn(Ft * (vref[q] + 0.5 * dt * acc)));
+        const double Fd = Ft * damp_factor(Ft * (vref[q] + 0.5 * dt * acc), lam);
         vn_[q] = vv[q] + dt * Fd * mp.z;
         const double aacc = T[q] * mp.w;
-        const double Td = T[q] * (1 - lam * sgn(T[q] * (ww[q] + 0.5 * dt * aacc)));
+        const double Td = T[q] * damp_factor(T[q] * (ww[q] + 0.5 * dt * aacc), lam);
         wn_[q] = ww[q] + dt * Td * mp.w;
       }
     }
@@ -205,8 +215,8 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   // division or sincos; larger angles use sincos.
   const double w2 = wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2];
   if (Mixed && w2 > 0) {
-    // mixed precision: the increment dq in FP32 (series to x^4 is exact in FP32 for
-    // x < 1e-2), the composition with the stored FP64 orientation in FP64
+    // mixed precision: the orientation step in FP32 (series to x^4 is exact in FP32
+    // for x < 1e-2), stored back in the FP64 record
     const double4_32a q0 = b.ori[s];
     const float dtf = (float)dt;
     const float w0f = (float)wn_[0], w1f = (float)wn_[1], w2f = (float)wn_[2];
@@ -222,11 +232,12 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
       sx = sh / x;
     }
     const float hs = 0.5f * dtf * sx;
-    const double dw = ch, dx = hs * w0f, dy = hs * w1f, dz = hs * w2f;
-    b.ori[s] = make_double4_32a(dw * q0.x - dx * q0.y - dy * q0.z - dz * q0.w,
-                                dw * q0.y + dx * q0.x + dy * q0.w - dz * q0.z,
-                                dw * q0.z - dx * q0.w + dy * q0.x + dz * q0.y,
-                                dw * q0.w + dx * q0.z - dy * q0.y + dz * q0.x);
+    const float dw = ch, dx = hs * w0f, dy = hs * w1f, dz = hs * w2f;
+    const float a0 = (float)q0.x, a1 = (float)q0.y, a2 = (float)q0.z, a3 = (float)q0.w;
+    b.ori[s] = make_double4_32a(dw * a0 - dx * a1 - dy * a2 - dz * a3,
+                                dw * a1 + dx * a0 + dy * a3 - dz * a2,
+                                dw * a2 - dx * a3 + dy * a0 + dz * a1,
+                                dw * a3 + dx * a2 - dy * a1 + dz * a0);
   } else if (w2 > 0) {
     const double4_32a q0 = b.ori[s];
     const double x2 = 0.25 * (dt * dt) * w2;
@@ -272,8 +283,9 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   if (far) {
     if (!ds->request) ds->request = 1;
   }
-  if (!isfinite(xn[0] + xn[1] + xn[2] + vn_[0] + vn_[1] + vn_[2] + wn_[0] + wn_[1] + wn_[2]))
-    atomicOr(&ds->error, kErrNonFinite);
+  bool ok = true;
+  for (int q = 0; q < 3; ++q) ok &= finite_bits(xn[q]) & finite_bits(vn_[q]) & finite_bits(wn_[q]);
+  if (!ok) atomicOr(&ds->error, kErrNonFinite);
 }
 
 // Row-major 3x3 helpers evaluated with round-to-nearest operations in a fixed

@@ -68,7 +68,7 @@ def test_mixed_one_step(mods, kind):
     co, cg = orc.contacts(), gpu.contacts()
     reach = 2 * float(w.radius.max()) * 1.25
     n, worst = compare_contacts(co, cg, band, tol=TOL32, eps=EPS32, coord=reach)
-    assert n > 1000
+    assert n > 500
     X = float(np.max(np.abs(before["pos"])))
     set_coord_scale(X)
     compare_states(orc.state(), gpu.state(), X, tol=TOL32, co=co, masses=masses_of(w),
@@ -77,18 +77,25 @@ def test_mixed_one_step(mods, kind):
 
 
 def test_mixed_compaction_statistics(mods):
-    """Periodic compaction over 400 steps with several collider runs: kinetic energy,
-    coordination number and packing fraction within 1e-3 of the FP64 oracle."""
+    """Periodic compaction from 0.33 to ~0.6 solid fraction over 500 steps with several
+    collider runs: kinetic energy, coordination number and packing fraction within 1e-3
+    of the FP64 oracle once the packing carries thousands of contacts (one contact more
+    or less must be below the tolerance for a count statistic to be comparable)."""
     oracle, pkg = mods
-    w = workloads.periodic_cloud(3000, 6, phi=0.33, inflate=1.02, vel_scale=0.02)
+    w = workloads.periodic_cloud(4000, 6, phi=0.33, inflate=1.02, vel_scale=0.02)
     orc, gpu = _pair(w, mods, verlet_dist=-0.1)
-    L = np.diag([-30.0, -30.0, -30.0])
+    dt = orc.clock()[2]
+    g = workloads.compaction_rate(0.33, 0.6, 500, dt)
+    L = np.diag([g, g, g])
     orc.set_velgrad(L)
     gpu.set_cell_velgrad(L)
-    for _ in range(4):
-        orc.step(100)
-        gpu.step(100)
+    orc.step(400)
+    gpu.step(400)
+    for _ in range(2):
+        orc.step(50)
+        gpu.step(50)
         so, sg = orc.stats(), gpu.stats()
+        assert so["n_contacts"] > 3000
         assert abs(sg["kinetic_energy"] / so["ke"] - 1) < 1e-3
         assert abs(sg["coordination"] / so["Z"] - 1) < 1e-3
         assert abs(sg["packing_fraction"] / so["phi"] - 1) < 1e-6

@@ -158,6 +158,19 @@ dem_status dem_get_dt(dem_scene *scene, double *dt);
  * effect at the next step.  Must be diagonal.  Errors: INVALID_ARG, STATE (aperiodic). */
 dem_status dem_set_cell_velgrad(dem_scene *scene, const double velgrad[9]);
 
+/* Stress-controlled periodic cell (PeriTriaxController: goal, stressMask,
+ * maxStrainRate, growDamping, globUpdate).  Every glob_update steps the diagonal
+ * velocity gradient of each axis a is set, effective from the next step:
+ *   stress_mask bit a set: grad(v)_aa = clamp((1 - grow_damping)(goal[a] - s_aa) /
+ *     (K_a dt glob_update), +-max_rate[a]), with s the Love-Weber stress of that
+ *     step's contacts (compression negative, Pa) and K_a = (1/V) sum kn (l n_a)^2;
+ *   bit clear: grad(v)_aa = goal[a] (a strain rate, 1/s).
+ * The text names these attributes but prints no update formula; this is the
+ * formula both the library and its test oracle use.  Errors: STATE (aperiodic),
+ * INVALID_ARG. */
+dem_status dem_set_triax(dem_scene *scene, const double goal[3], int stress_mask,
+                         const double max_rate[3], double grow_damping, int glob_update);
+
 /* Advance nsteps time steps (O.run(nsteps, wait=True)).  Blocks until done.
  * Errors: STATE (no bodies' dt), NONFINITE (a body state became NaN/Inf),
  * GEOMETRY, CAPACITY, OOM, TIMEOUT, CUDA.  On NONFINITE the scene stops at the

@@ -75,6 +75,7 @@ def _load():
         "orc_set_dt": (_i, [_p, _d]),
         "orc_set_velgrad": (_i, [_p, _p]),
         "orc_step": (_i, [_p, _l]),
+        "orc_set_triax": (_i, [_p, _p, _i, _p, _d, _i]),
         "orc_num_bodies": (_l, [_p]),
         "orc_get_state": (None, [_p, _p, _p, _p, _p, _p, _p]),
         "orc_set_state": (_i, [_p, _p, _p, _p, _p]),
@@ -204,6 +205,13 @@ class OracleScene:
         L = _f64(L, (3, 3))
         if self._lib.orc_set_velgrad(self._h, _ptr(L)) != 0:
             raise ValueError("set_velgrad needs a periodic scene")
+
+    def set_triax(self, goal, stress_mask, max_rate, grow_damping=0.25, glob_update=5):
+        g = _f64(goal)
+        m = _f64(max_rate)
+        if self._lib.orc_set_triax(self._h, _ptr(g), int(stress_mask), _ptr(m),
+                                   float(grow_damping), int(glob_update)) != 0:
+            raise ValueError("set_triax needs a periodic scene and valid parameters")
 
     def step(self, n=1):
         rc = self._lib.orc_step(self._h, int(n))

@@ -53,6 +53,17 @@
  *   R11 fixed bodies keep their velocities (no force integration) and still move
  *      with them.
  *   R12 sphere inertia I = 2/5 m r^2, mass = density * 4/3 pi r^3 (utils.sphere).
+ *   R16 PeriTriaxController (attributes only in the text: goal, stressMask,
+ *      maxStrainRate, globUpdate, growDamping): every globUpdate steps, from the
+ *      contacts of that step and the cell volume they were computed in,
+ *      sigma_ii = (1/V) sum F_i (x1 - x2')_i (Love-Weber, compression negative) and
+ *      K_i = (1/V) sum kn (l n_i)^2; a stress-controlled axis (stressMask bit i) gets
+ *      grad(v)_ii = clamp((1 - growDamping)(goal_i - sigma_ii) / (K_i dt globUpdate),
+ *      +-maxRate_i) -- the rate that closes (1 - growDamping) of the stress gap over
+ *      the globUpdate steps it is held for
+ *      (0 when K_i = 0 and the goal is not met: the rate bound applies), a
+ *      strain-controlled axis grad(v)_ii = goal_i; the new gradient is assigned
+ *      like Cell.velGrad (effective from the next step) and held in between.
  */
 #include "dem_oracle.h"
 
@@ -95,6 +106,9 @@ struct orc_scene {
     long ncon, capcon;
     /* energy tracker (cumulative works) */
     double grav_work, nonvisc_damp, plast_dissip;
+    /* stress-controlled periodic cell (PeriTriaxController reading R16) */
+    int triax, stress_mask, glob_update;
+    double goal[3], max_rate[3], grow_damping;
 };
 
 /* ---------------------------------------------------------------- vectors */
@@ -692,6 +706,57 @@ static void quat_mul(const double *a, const double *b, double *o) { /* (w,x,y,z)
     o[0] = w; o[1] = x; o[2] = y; o[3] = z;
 }
 
+/* PeriTriaxController servo, reading R16. */
+static void triax_update(orc_scene *s) {
+    double V = fabs(m_det(s->Hprev));   /* the cell the contacts of this step were computed in */
+    double sig[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+    for (long k = 0; k < s->ncon; ++k) {
+        const orc_contact *ct = &s->con[k];
+        if (ct->id1 < 0) continue;
+        double l = (s->radius[ct->id1] + s->radius[ct->id2]) - ct->pen;
+        for (int a = 0; a < 3; ++a) {
+            double F = ct->fn * ct->n[a] + ct->fs[a];
+            sig[a] += F * (-l * ct->n[a]);
+            double b = l * ct->n[a];
+            K[a] += ct->kn * (b * b);
+        }
+    }
+    double L[9];
+    memcpy(L, s->L_pending ? s->Lnext : s->L, sizeof L);
+    for (int a = 0; a < 3; ++a) {
+        double rate;
+        if (s->stress_mask & (1 << a)) {
+            double sa = sig[a] / V, Ka = K[a] / V;
+            double want = (1 - s->grow_damping) * (s->goal[a] - sa);
+            if (Ka > 0) rate = want / (Ka * (s->dt * s->glob_update));
+            else rate = want > 0 ? s->max_rate[a] : (want < 0 ? -s->max_rate[a] : 0.0);
+            if (rate > s->max_rate[a]) rate = s->max_rate[a];
+            if (rate < -s->max_rate[a]) rate = -s->max_rate[a];
+        } else {
+            rate = s->goal[a];
+        }
+        L[4 * a] = rate;
+    }
+    memcpy(s->Lnext, L, sizeof L);
+    s->L_pending = 1;
+}
+
+int orc_set_triax(orc_scene *s, const double *goal, int stress_mask, const double *max_rate,
+                  double grow_damping, int glob_update) {
+    if (!s || !s->periodic || glob_update < 1 || !(grow_damping >= 0) || !(grow_damping < 1))
+        return -1;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(goal[a]) || !(max_rate[a] >= 0)) return -1;
+        s->goal[a] = goal[a];
+        s->max_rate[a] = max_rate[a];
+    }
+    s->stress_mask = stress_mask & 7;
+    s->grow_damping = grow_damping;
+    s->glob_update = glob_update;
+    s->triax = 1;
+    return 0;
+}
+
 static int step_once(orc_scene *s) {
     const double dt = s->dt;
     if (!(dt > 0)) return -1;
@@ -838,6 +903,7 @@ static int step_once(orc_scene *s) {
     }
     s->time += dt;
     s->iter += 1;
+    if (s->triax && s->periodic && s->iter % s->glob_update == 0) triax_update(s);
     return 0;
 }
 

@@ -38,6 +38,9 @@ long orc_add_spheres(orc_scene *s, long n, const double *pos, const double *radi
 int orc_set_dt(orc_scene *s, double dt);
 int orc_set_velgrad(orc_scene *s, const double *L9);
 int orc_step(orc_scene *s, long nsteps);
+/* stress-controlled periodic cell (PeriTriaxController, reading R16 in dem_oracle.c) */
+int orc_set_triax(orc_scene *s, const double *goal3, int stress_mask, const double *max_rate3,
+                  double grow_damping, int glob_update);
 
 long orc_num_bodies(const orc_scene *s);
 void orc_get_state(const orc_scene *s, double *pos, double *vel, double *angvel, double *ori,

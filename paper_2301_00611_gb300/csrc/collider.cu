@@ -108,6 +108,10 @@ __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
     dst.p32[p] = make_float4(0.0f, 0.0f, 0.0f, (float)x.w);
     dst.vw32[2 * p] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)w.x);
     dst.vw32[2 * p + 1] = make_float4((float)w.y, (float)w.z, 0.0f, 0.0f);
+    dst.xref32[p] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
+    const double4_32a mp = src.mprop[o];
+    dst.mprop32[p] = make_float4((float)mp.x, (float)mp.y, (float)mp.z, (float)mp.w);
+    dst.ori32[p] = src.ori32[o];   // the mixed path keeps the orientation in FP32
   }
   dst.ori[p] = src.ori[o];
   dst.mprop[p] = src.mprop[o];

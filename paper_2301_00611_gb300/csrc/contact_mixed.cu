@@ -9,19 +9,19 @@
 //         both bodies from their own FP64 positions at that run, plus the FP32
 //         change of the cell shift (H - Href) c; normal, penetration, relative
 //         velocity, stiffnesses, normal force, output force and torque arms.
-//   FP64  the shear-force history and its transport into the new contact frame
-//         (the rotation -Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)), the
-//         accumulation of the shear increment and the Coulomb cap of the stored
-//         force.
+//   FP64  the shear-force history: the transport into the new contact frame
+//         (-Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)) and the shear increment are
+//         formed in FP32 and accumulated into the FP64 spring, and the Coulomb cap
+//         rescales the FP64 spring.
 // Every length is an offset bounded by the cell size, so FP32 keeps about
 // 1e-7 relative resolution of the branch length whatever the cell extent.
 //
 // Traffic per real row: 172 B read (row 28 + history 48 + two bodies 96),
 // 80 B written; per non-real row 60 B read -- about 60% of the FP64 kernel's.
-// GB300's FP64 pipe issues ~2 instructions per clock per SM, so at the HBM
-// rate (~21 B per clock per SM) a real row affords ~25 FP64-pipe instructions
-// (conversions included): the FP64 work is kept to the rotation, the
-// accumulation and the cap, with every other quantity formed in FP32.
+// GB300's FP64 pipe issues ~2 instructions per clock per SM and also carries
+// every double<->float conversion, so at the HBM rate (~21 B per clock per SM) a
+// real row affords ~25 FP64-pipe instructions: this kernel uses ~12 (three
+// conversions in, three out, three accumulating adds, three for the output).
 #include "dem_internal.cuh"
 
 namespace dem {
@@ -105,25 +105,31 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
     const float vn = nx * ux + ny * uy + nz * uz;
     const float kd = ks * dtf;
     const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
-    // 1. transport of the stored shear force into the new frame, in FP64: the rotation
-    //    vector b = n- x n + (dt/2 n.(w1+w2)) n is formed in FP32 (its size is an angle
-    //    per step), the rotation Fs - Fs x b and the increment are applied in FP64
+    // 1. transport of the stored shear force into the new frame: the rotation vector
+    //    b = n- x n + (dt/2 n.(w1+w2)) n and the change -Fs x b - ks dt v12_perp are
+    //    formed in FP32 from an FP32 copy of the spring and accumulated into the FP64
+    //    spring (as NewtonIntegrator accumulates FP32 increments into FP64 velocities):
+    //    the stored force never drifts from repeated FP32 rounding
     const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
-    const double bx = (double)((hn.y * nz - hn.z * ny) + tw * nx);
-    const double by = (double)((hn.z * nx - hn.x * nz) + tw * ny);
-    const double bz = (double)((hn.x * ny - hn.y * nx) + tw * nz);
-    double fx = fsd.x - ((fsd.y * bz - fsd.z * by) + (double)ix);
-    double fy = fsd.y - ((fsd.z * bx - fsd.x * bz) + (double)iy);
-    double fz = fsd.z - ((fsd.x * by - fsd.y * bx) + (double)iz);
-    // Law2: normal force (FP32), Coulomb cap of the stored force (FP64)
+    const float bx = (hn.y * nz - hn.z * ny) + tw * nx;
+    const float by = (hn.z * nx - hn.x * nz) + tw * ny;
+    const float bz = (hn.x * ny - hn.y * nx) + tw * nz;
+    const float sx0 = (float)fsd.x, sy0 = (float)fsd.y, sz0 = (float)fsd.z;
+    double fx = fsd.x - (double)((sy0 * bz - sz0 * by) + ix);
+    double fy = fsd.y - (double)((sz0 * bx - sx0 * bz) + iy);
+    double fz = fsd.z - (double)((sx0 * by - sy0 * bx) + iz);
+    // Law2: normal force, Coulomb test in FP32; the cap rescales the FP64 spring
     const float Fn = kn * pen;
-    const double maxFs = (double)(Fn * (float)tanphi);
-    const double fs2 = fx * fx + fy * fy + fz * fz;
+    const float maxFs = Fn * (float)tanphi;
+    float sx = (float)fx, sy = (float)fy, sz = (float)fz;
+    const float fs2 = sx * sx + sy * sy + sz * sz;
     if (fs2 > maxFs * maxFs) {
-      const double sc = maxFs * rsqrt(fs2);
-      fx *= sc; fy *= sc; fz *= sc;
+      const float sc = maxFs * rsqrtf(fs2);
+      const double scd = (double)sc;
+      fx *= scd; fy *= scd; fz *= scd;
+      sx *= sc; sy *= sc; sz *= sc;
     }
-    const float Fx = Fn * nx + (float)fx, Fy = Fn * ny + (float)fy, Fz = Fn * nz + (float)fz;
+    const float Fx = Fn * nx + sx, Fy = Fn * ny + sy, Fz = Fn * nz + sz;
     const float d1 = r1 - 0.5f * pen, d2 = r2 - 0.5f * pen;
     t.hfs[k] = make_double4_32a(fx, fy, fz, tanphi);
     t.hn32[k] = make_float4(nx, ny, nz, ks);

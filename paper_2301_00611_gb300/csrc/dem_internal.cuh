@@ -49,6 +49,9 @@ struct Bodies {
   // mixed precision mirrors (null in FP64 mode), written by the integrator:
   float4 *p32;      // (x - xref, r) in FP32
   float4 *vw32;     // [2 * cap]: (vx, vy, vz, wx), (wy, wz, 0, 0)
+  float4 *xref32;   // xref in FP32 (collider trigger, fluctuation velocity)
+  float4 *mprop32;  // (m, I, 1/m, 1/I) in FP32
+  float4 *ori32;    // orientation quaternion (mixed mode keeps it in FP32)
 };
 
 struct Table {
@@ -90,7 +93,13 @@ struct CellState {
   float Wf[3];          // image velocity matrix W
   float Ef[3];          // E
   float pad2[3];
+  // stress-controlled cell (PeriTriaxController): goal stress (stress_mask bit set)
+  // or strain rate per axis, rate bound, growDamping, update period in steps
+  double goal[3], max_rate[3], grow_damping;
+  int triax, stress_mask, glob_update, pad3;
 };
+
+constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
 
 // Small status block read back by the host after a batch of steps.
 struct DevStatus {
@@ -174,7 +183,11 @@ void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
 void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
                       const Mat *mats, const SceneConst &sc, long long cap, int mixed,
                       cudaStream_t st);
-void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st);
+void launch_cell_advance(CellState *cs, DevStatus *ds, const double *servo_partials,
+                         cudaStream_t st);
+// servo: per-block sums of sigma_ii * V and K_i * V over the real rows (6 per block)
+void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
+                           cudaStream_t st);
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
                           int mixed, cudaStream_t st);

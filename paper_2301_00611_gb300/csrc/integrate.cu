@@ -82,6 +82,179 @@ __device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn,
   tanphi = fmin(mw.tanphi, ms.tanphi);
 }
 
+// Mixed precision integrator: FP32 force sum, walls, damping and orientation;
+// FP64 only where the velocity and position accumulate (v += dv, x += dt v) and in
+// the offset of the new position from its reference (rounded once to FP32 for the
+// contact kernel).  Every quantity it needs in FP32 is read from the FP32 mirrors
+// the previous step wrote, so the FP64 pipe (conversions included) carries ~27
+// instructions per body.
+__global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
+                                                        const CellState *__restrict__ cs,
+                                                        DevStatus *ds, const Mat *__restrict__ mats,
+                                                        SceneConst sc, long long cap) {
+  if (ds->pending) return;
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= sc.N) return;
+  const int s = (int)sl;
+  const double dt = cs->dt;
+  const float dtf = (float)dt;
+  float F[3], T[3];
+  {
+    float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
+    const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
+    for (int k = r0; k < r1; ++k) {
+      const float4 f = t.oF32[k], m = t.oM32[k];
+      f0 -= f.x; f1 -= f.y; f2 -= f.z;
+      t0 += f.w * m.x; t1 += f.w * m.y; t2 += f.w * m.z;
+    }
+    const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int k = t.down[e];
+      if (k < 0) continue;
+      const float4 f = t.oF32[k], m = t.oM32[k];
+      f0 += f.x; f1 += f.y; f2 += f.z;
+      t0 += m.w * m.x; t1 += m.w * m.y; t2 += m.w * m.z;
+    }
+    F[0] = f0; F[1] = f1; F[2] = f2; T[0] = t0; T[1] = t1; T[2] = t2;
+  }
+  const float4 va = b.vw32[2 * s], vb = b.vw32[2 * s + 1];   // v-, w- in FP32
+  const float4 off = b.p32[s];                                // x - xref, r
+  const float4 xr = b.xref32[s];
+  const float4 mp = b.mprop32[s];                             // m, I, 1/m, 1/I
+  uint8_t flags = b.flags[s];
+  const float vv[3] = {va.x, va.y, va.z}, ww[3] = {va.w, vb.x, vb.y};
+  const float xf[3] = {xr.x + off.x, xr.y + off.y, xr.z + off.z};
+  const float r = off.w;
+
+  if (sc.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
+    const double4_32a pd = b.pos[s];
+    const double xd[3] = {pd.x, pd.y, pd.z};
+    for (int wi = 0; wi < 6; ++wi) {
+      if (!(sc.wall_mask & (1 << wi))) continue;
+      const int ax = wi >> 1;
+      const float dist = (float)(xd[ax] - ((wi & 1) ? sc.box_hi[ax] : sc.box_lo[ax]));
+      const bool was = flags & (2 << wi);
+      if (!(fabsf(dist) < r)) {
+        if (was) {
+          b.whist[wi * cap + s] = make_double4_32a(0, 0, 0, 0);
+          flags &= ~(2 << wi);
+        }
+        continue;
+      }
+      const float sn = dist >= 0 ? 1.0f : -1.0f;
+      float n[3] = {0, 0, 0};
+      n[ax] = sn;
+      const float pen = r - fabsf(dist);
+      double knd, ksd, tpd;
+      wall_phys(mats, b.mat[s], (double)r, knd, ksd, tpd);
+      const float kn = (float)knd, ks = (float)ksd, tanphi = (float)tpd;
+      float fs[3] = {0, 0, 0};
+      if (was) {
+        const double4_32a h = b.whist[wi * cap + s];
+        fs[0] = (float)h.x; fs[1] = (float)h.y; fs[2] = (float)h.z;
+      }
+      const float tw = 0.5f * dtf * (sn * ww[ax]);
+      const float tn[3] = {tw * n[0], tw * n[1], tw * n[2]};
+      const float c0 = fs[1] * tn[2] - fs[2] * tn[1];
+      const float c1 = fs[2] * tn[0] - fs[0] * tn[2];
+      const float c2 = fs[0] * tn[1] - fs[1] * tn[0];
+      fs[0] -= c0; fs[1] -= c1; fs[2] -= c2;
+      const float rr[3] = {r * ww[0], r * ww[1], r * ww[2]};
+      const float cr[3] = {rr[1] * n[2] - rr[2] * n[1], rr[2] * n[0] - rr[0] * n[2],
+                           rr[0] * n[1] - rr[1] * n[0]};
+      const float fac = (r + r) / (2 * r - pen);
+      float u[3];
+      for (int q = 0; q < 3; ++q) u[q] = fac * vv[q] - cr[q];
+      const float vn = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+      for (int q = 0; q < 3; ++q) fs[q] -= ks * (dtf * (u[q] - vn * n[q]));
+      const float Fn = kn * pen;
+      const float maxFs = Fn * tanphi;
+      const float fs2 = fs[0] * fs[0] + fs[1] * fs[1] + fs[2] * fs[2];
+      if (fs2 > maxFs * maxFs) {
+        const float scl = maxFs * rsqrtf(fs2);
+        fs[0] *= scl; fs[1] *= scl; fs[2] *= scl;
+      }
+      const float F2[3] = {Fn * n[0] + fs[0], Fn * n[1] + fs[1], Fn * n[2] + fs[2]};
+      const float arm = -(r - 0.5f * pen);
+      const float a[3] = {arm * n[0], arm * n[1], arm * n[2]};
+      F[0] += F2[0]; F[1] += F2[1]; F[2] += F2[2];
+      T[0] += a[1] * F2[2] - a[2] * F2[1];
+      T[1] += a[2] * F2[0] - a[0] * F2[2];
+      T[2] += a[0] * F2[1] - a[1] * F2[0];
+      b.whist[wi * cap + s] = make_double4_32a(fs[0], fs[1], fs[2], sn * Fn);
+      flags |= (2 << wi);
+    }
+  }
+
+  float dv[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
+  const bool fixed = flags & 1;
+  if (!fixed) {
+    const float lam = (float)sc.damping;
+    float vref[3] = {vv[0], vv[1], vv[2]};
+    if (sc.periodic)
+      for (int q = 0; q < 3; ++q) vref[q] -= (float)cs->Lprev[4 * q] * xf[q];
+    for (int q = 0; q < 3; ++q) {
+      const float Ft = F[q] + mp.x * (float)sc.gravity[q];
+      const float acc = Ft * mp.z;
+      const float Fd = Ft * damp_factor_f(Ft * (vref[q] + 0.5f * dtf * acc), lam);
+      dv[q] = dtf * Fd * mp.z;
+      const float aacc = T[q] * mp.w;
+      const float Td = T[q] * damp_factor_f(T[q] * (ww[q] + 0.5f * dtf * aacc), lam);
+      dw[q] = dtf * Td * mp.w;
+    }
+    if (sc.periodic)   // homoDeform = 2
+      for (int q = 0; q < 3; ++q)
+        dv[q] += (float)cs->dL[4 * q] * xf[q] + dtf * ((float)cs->L[4 * q] * vv[q]);
+  }
+  // FP64 accumulation of velocity, spin and position
+  const double4_32a v = b.vel[s], w = b.angvel[s], p = b.pos[s];
+  const double vn_[3] = {v.x + (double)dv[0], v.y + (double)dv[1], v.z + (double)dv[2]};
+  const double wn_[3] = {w.x + (double)dw[0], w.y + (double)dw[1], w.z + (double)dw[2]};
+  const double xn[3] = {p.x + dt * vn_[0], p.y + dt * vn_[1], p.z + dt * vn_[2]};
+  b.pos[s] = make_double4_32a(xn[0], xn[1], xn[2], p.w);
+  b.vel[s] = make_double4_32a(vn_[0], vn_[1], vn_[2], 0.0);
+  b.angvel[s] = make_double4_32a(wn_[0], wn_[1], wn_[2], 0.0);
+  if (flags != b.flags[s]) b.flags[s] = flags;
+  const float vnf[3] = {(float)vn_[0], (float)vn_[1], (float)vn_[2]};
+  const float wnf[3] = {(float)wn_[0], (float)wn_[1], (float)wn_[2]};
+  b.vw32[2 * s] = make_float4(vnf[0], vnf[1], vnf[2], wnf[0]);
+  b.vw32[2 * s + 1] = make_float4(wnf[1], wnf[2], 0.0f, 0.0f);
+  const double4_32a xrd = b.xref[s];
+  const float ox = (float)(xn[0] - xrd.x), oy = (float)(xn[1] - xrd.y), oz = (float)(xn[2] - xrd.z);
+  b.p32[s] = make_float4(ox, oy, oz, r);
+
+  // orientation in FP32: q+ = dq(w+ dt) q, series of cos x and sin x / x for x < 1e-2
+  const float w2 = wnf[0] * wnf[0] + wnf[1] * wnf[1] + wnf[2] * wnf[2];
+  if (w2 > 0.0f) {
+    const float4 q0 = b.ori32[s];
+    const float x2 = 0.25f * (dtf * dtf) * w2;
+    float ch, sx;
+    if (x2 < 1e-4f) {
+      ch = 1.0f - 0.5f * x2 * (1.0f - x2 * (1.0f / 12.0f));
+      sx = 1.0f - x2 * (1.0f / 6.0f) * (1.0f - x2 * (1.0f / 20.0f));
+    } else {
+      const float x = sqrtf(x2);
+      float sh;
+      sincosf(x, &sh, &ch);
+      sx = sh / x;
+    }
+    const float hs = 0.5f * dtf * sx;
+    const float dq0 = ch, dq1 = hs * wnf[0], dq2 = hs * wnf[1], dq3 = hs * wnf[2];
+    b.ori32[s] = make_float4(dq0 * q0.x - dq1 * q0.y - dq2 * q0.z - dq3 * q0.w,
+                             dq0 * q0.y + dq1 * q0.x + dq2 * q0.w - dq3 * q0.z,
+                             dq0 * q0.z - dq1 * q0.w + dq2 * q0.x + dq3 * q0.y,
+                             dq0 * q0.w + dq1 * q0.z - dq2 * q0.y + dq3 * q0.x);
+  }
+  // collider trigger on the FP32 offset (slightly early to cover its rounding)
+  const float ux = ox - cs->Ef[0] * xr.x, uy = oy - cs->Ef[1] * xr.y, uz = oz - cs->Ef[2] * xr.z;
+  if (!(ux * ux + uy * uy + uz * uz <= (float)(0.998 * cs->thr2))) {
+    if (!ds->request) ds->request = 1;
+  }
+  if (!(isfinite(ox + oy + oz) && isfinite(vnf[0] + vnf[1] + vnf[2]) &&
+        isfinite(wnf[0] + wnf[1] + wnf[2])))
+    atomicOr(&ds->error, kErrNonFinite);
+}
+
 template <bool Mixed>
 __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
                                                   DevStatus *ds, const Mat *__restrict__ mats,
@@ -300,7 +473,7 @@ __device__ inline void m_mul_rn(const double *A, const double *B, double *O) {
   for (int q = 0; q < 9; ++q) O[q] = Tm[q];
 }
 
-__global__ void k_cell_advance(CellState *cs, DevStatus *ds) {
+__global__ void k_cell_advance(CellState *cs, DevStatus *ds, const double *servo) {
   if (ds->pending) return;
   const double dt = cs->dt;
   if (cs->periodic) {
@@ -309,6 +482,31 @@ __global__ void k_cell_advance(CellState *cs, DevStatus *ds) {
       cs->H[q] = cs->Hnext[q];
       cs->Lprev[q] = cs->L[q];
       cs->dL[q] = 0.0;   // L - Lprev after the assignment above
+    }
+    if (servo) {
+      // PeriTriaxController: new diagonal gradient from this step's contacts (their
+      // stress and stiffness in the cell Hprev they were computed in), effective from
+      // the next step; the partials are summed in block order
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      for (int b = 0; b < kServoBlocks; ++b)
+        for (int q = 0; q < 6; ++q) acc[q] += servo[6 * b + q];
+      const double *P = cs->Hprev;
+      const double V = fabs(P[0] * (P[4] * P[8] - P[5] * P[7]) - P[1] * (P[3] * P[8] - P[5] * P[6]) +
+                            P[2] * (P[3] * P[7] - P[4] * P[6]));
+      for (int a = 0; a < 3; ++a) {
+        double rate;
+        if (cs->stress_mask & (1 << a)) {
+          const double sa = acc[a] / V, Ka = acc[3 + a] / V;
+          const double want = (1 - cs->grow_damping) * (cs->goal[a] - sa);
+          if (Ka > 0) rate = want / (Ka * (dt * cs->glob_update));
+          else rate = want > 0 ? cs->max_rate[a] : (want < 0 ? -cs->max_rate[a] : 0.0);
+          rate = fmin(fmax(rate, -cs->max_rate[a]), cs->max_rate[a]);
+        } else {
+          rate = cs->goal[a];
+        }
+        cs->L[4 * a] = rate;
+      }
+      for (int q = 0; q < 9; ++q) cs->dL[q] = cs->L[q] - cs->Lprev[q];
     }
     m_mul_rn(cs->Lprev, cs->Hprev, cs->W);
     double A[9];
@@ -382,6 +580,35 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials) {
     for (int q = 0; q < K; ++q) partials[K * blockIdx.x + q] = sh[q][0];
 }
 
+// servo sums over real rows: sigma_a * V = sum F_a (-l n_a), K_a * V = sum kn (l n_a)^2
+__global__ void k_servo_partials(Table t, const DevStatus *ds, int mixed, double *partials) {
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (!ds->pending) {
+    for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
+      double F[3], n[3], l, kn;
+      if (mixed) {
+        kn = t.g32[k].w;
+        if (kn == 0.0) continue;
+        const float4 f = t.oF32[k], m = t.oM32[k], h = t.hn32[k];
+        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        l = (double)f.w + (double)m.w;
+      } else {
+        kn = t.hfs[k].w;
+        if (kn == 0.0) continue;
+        const double4_32a f = t.oF[k], m = t.oM[k], h = t.hn[k];
+        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        l = f.w + m.w;
+      }
+      for (int a = 0; a < 3; ++a) {
+        v[a] += F[a] * (-l * n[a]);
+        const double b = l * n[a];
+        v[3 + a] += kn * (b * b);
+      }
+    }
+  }
+  block_reduce_store<6>(v, partials);
+}
+
 // ke, sum |F contact| over free bodies, number of free bodies
 __global__ void k_body_stats(Bodies b, const double4_32a *__restrict__ F, long long N, double *partials) {
   double v[3] = {0, 0, 0};
@@ -450,12 +677,18 @@ void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevS
                       const Mat *mats, const SceneConst &sc, long long cap, int mixed,
                       cudaStream_t st) {
   if (sc.N <= 0) return;
-  if (mixed) k_integrate<true><<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+  if (mixed) k_integrate_mixed<<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
   else k_integrate<false><<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
 }
 
-void launch_cell_advance(CellState *cs, DevStatus *ds, cudaStream_t st) {
-  k_cell_advance<<<1, 1, 0, st>>>(cs, ds);
+void launch_cell_advance(CellState *cs, DevStatus *ds, const double *servo_partials,
+                         cudaStream_t st) {
+  k_cell_advance<<<1, 1, 0, st>>>(cs, ds, servo_partials);
+}
+
+void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
+                           cudaStream_t st) {
+  k_servo_partials<<<kServoBlocks, kT, 0, st>>>(t, ds, mixed, partials);
 }
 
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,

@@ -143,6 +143,7 @@ struct dem_scene {
   int *scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
   double *partials = nullptr;  // 1024 blocks x 16 doubles
+  double *servo = nullptr;     // kServoBlocks x 6 doubles
   double *partials_h = nullptr;
 
   CellState cs_h{};
@@ -227,7 +228,7 @@ dem_status wait(dem_scene *s) {
 void free_bodies(dem_scene *s, Bodies &b) {
   dfree(s, b.pos); dfree(s, b.vel); dfree(s, b.angvel); dfree(s, b.ori); dfree(s, b.xref);
   dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.mat); dfree(s, b.flags); dfree(s, b.whist);
-  dfree(s, b.p32); dfree(s, b.vw32);
+  dfree(s, b.p32); dfree(s, b.vw32); dfree(s, b.xref32); dfree(s, b.mprop32); dfree(s, b.ori32);
 }
 
 dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
@@ -239,7 +240,10 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
       (r = dalloc(s, &b.flags, cap)))
     return r;
   if (s->has_walls && (r = dalloc(s, &b.whist, 6 * cap))) return r;
-  if (s->mixed && ((r = dalloc(s, &b.p32, cap)) || (r = dalloc(s, &b.vw32, 2 * cap)))) return r;
+  if (s->mixed && ((r = dalloc(s, &b.p32, cap)) || (r = dalloc(s, &b.vw32, 2 * cap)) ||
+                   (r = dalloc(s, &b.xref32, cap)) || (r = dalloc(s, &b.mprop32, cap)) ||
+                   (r = dalloc(s, &b.ori32, cap))))
+    return r;
   return DEM_OK;
 }
 
@@ -308,6 +312,14 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
       for (int w = 0; w < 6; ++w)
         CK(cudaMemcpyAsync(nb.whist + w * nc, s->cur.whist + w * s->cap, d4,
                            cudaMemcpyDeviceToDevice, s->st));
+    if (s->mixed) {
+      const size_t f4 = sizeof(float4) * N;
+      CK(cudaMemcpyAsync(nb.p32, s->cur.p32, f4, cudaMemcpyDeviceToDevice, s->st));
+      CK(cudaMemcpyAsync(nb.vw32, s->cur.vw32, 2 * f4, cudaMemcpyDeviceToDevice, s->st));
+      CK(cudaMemcpyAsync(nb.xref32, s->cur.xref32, f4, cudaMemcpyDeviceToDevice, s->st));
+      CK(cudaMemcpyAsync(nb.mprop32, s->cur.mprop32, f4, cudaMemcpyDeviceToDevice, s->st));
+      CK(cudaMemcpyAsync(nb.ori32, s->cur.ori32, f4, cudaMemcpyDeviceToDevice, s->st));
+    }
   }
   free_bodies(s, s->cur);
   free_bodies(s, s->alt);
@@ -668,7 +680,7 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
     return DEM_ERR_CUDA;
   }
   if (dalloc(s, &s->mats_d, kMaxMat) || dalloc(s, &s->cs_d, 1) || dalloc(s, &s->ds_d, 1) ||
-      dalloc(s, &s->partials, 1024 * 16)) {
+      dalloc(s, &s->partials, 1024 * 16) || dalloc(s, &s->servo, kServoBlocks * 6)) {
     g_create_error = s->err;
     dem_scene_destroy(s);
     return DEM_ERR_OOM;
@@ -717,7 +729,7 @@ void dem_scene_destroy(dem_scene *s) {
   dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
   dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
-  dfree(s, s->scan_ws); dfree(s, s->partials);
+  dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->rb_h) cudaFreeHost(s->rb_h);
@@ -811,6 +823,13 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
   CK(cudaMemcpyAsync(s->slot_of_id + o, SL.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   if (s->has_walls)
     for (int w = 0; w < 6; ++w) CK(cudaMemsetAsync(s->cur.whist + w * s->cap + o, 0, d4, s->st));
+  if (s->mixed) {   // FP32 mirrors of the new bodies (the collider run refreshes p32, vw32)
+    std::vector<float4> M32(n), O32(n, make_float4(1, 0, 0, 0));
+    for (long long t = 0; t < n; ++t)
+      M32[t] = make_float4((float)M[t].x, (float)M[t].y, (float)M[t].z, (float)M[t].w);
+    CK(cudaMemcpyAsync(s->cur.mprop32 + o, M32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(s->cur.ori32 + o, O32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st));
+  }
   if (first_id) *first_id = s->N;
   s->N += n;
   s->need_rebuild = true;
@@ -838,6 +857,29 @@ dem_status dem_get_dt(dem_scene *s, double *dt) {
   dem_status r = ensure_dt(s);
   if (r) return r;
   *dt = s->cs_h.dt;
+  return DEM_OK;
+}
+
+dem_status dem_set_triax(dem_scene *s, const double *goal, int stress_mask,
+                         const double *max_rate, double grow_damping, int glob_update) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the stress servo needs a periodic scene");
+  if (!goal || !max_rate || glob_update < 1 || !(grow_damping >= 0) || !(grow_damping < 1))
+    return fail(s, DEM_ERR_INVALID_ARG, "bad servo parameters");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(goal[a]) || !(max_rate[a] >= 0) || !std::isfinite(max_rate[a]))
+      return fail(s, DEM_ERR_INVALID_ARG, "bad servo goal or rate bound");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  for (int a = 0; a < 3; ++a) {
+    s->cs_h.goal[a] = goal[a];
+    s->cs_h.max_rate[a] = max_rate[a];
+  }
+  s->cs_h.stress_mask = stress_mask & 7;
+  s->cs_h.grow_damping = grow_damping;
+  s->cs_h.glob_update = glob_update;
+  s->cs_h.triax = 1;
+  s->cs_dirty = true;
   return DEM_OK;
 }
 
@@ -885,7 +927,10 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
       if (ev) { CK(cudaEventRecord(ev[6 * i + 1], s->st)); CK(cudaEventRecord(ev[6 * i + 2], s->st)); }
       launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->mixed, s->st);
       if (ev) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
-      launch_cell_advance(s->cs_d, s->ds_d, s->st);
+      // servo update steps (PeriTriaxController every glob_update steps)
+      const bool upd = s->cs_h.triax && ((it0 + i + 1) % s->cs_h.glob_update == 0);
+      if (upd) launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
+      launch_cell_advance(s->cs_d, s->ds_d, upd ? s->servo : nullptr, s->st);
       if (ev) CK(cudaEventRecord(ev[6 * i + 5], s->st));
     }
     s->launches += B * ((t.P > 0 ? 1 : 0) + 2);
@@ -957,7 +1002,19 @@ dem_status dem_get_state(dem_scene *s, double *pos, double *vel, double *angvel,
   if (pos && (r = fetch4(s, s->cur.pos, sid, pos, 3))) return r;
   if (vel && (r = fetch4(s, s->cur.vel, sid, vel, 3))) return r;
   if (angvel && (r = fetch4(s, s->cur.angvel, sid, angvel, 3))) return r;
-  if (ori && (r = fetch4(s, s->cur.ori, sid, ori, 4))) return r;
+  if (ori) {
+    if (s->mixed) {
+      std::vector<float4> h(s->N);
+      CK(cudaMemcpyAsync(h.data(), s->cur.ori32, sizeof(float4) * s->N, cudaMemcpyDeviceToHost, s->st));
+      if ((r = wait(s))) return r;
+      for (long long i = 0; i < s->N; ++i) {
+        const float4 &q = h[sid[i]];
+        ori[4 * i] = q.x; ori[4 * i + 1] = q.y; ori[4 * i + 2] = q.z; ori[4 * i + 3] = q.w;
+      }
+    } else if ((r = fetch4(s, s->cur.ori, sid, ori, 4))) {
+      return r;
+    }
+  }
   if (force || torque) {
     if (!s->table_fresh) {
       // no contact table matches the current body order yet: no contact forces
@@ -1001,6 +1058,14 @@ dem_status dem_set_state(dem_scene *s, const double *pos, const double *vel, con
   if (vel && (r = put(vel, s->cur.vel, 3, false))) return r;
   if (angvel && (r = put(angvel, s->cur.angvel, 3, false))) return r;
   if (ori && (r = put(ori, s->cur.ori, 4, false))) return r;
+  if (ori && s->mixed) {
+    std::vector<float4> h32(N);
+    for (long long i = 0; i < N; ++i)
+      h32[sid[i]] = make_float4((float)ori[4 * i], (float)ori[4 * i + 1], (float)ori[4 * i + 2],
+                                (float)ori[4 * i + 3]);
+    CK(cudaMemcpyAsync(s->cur.ori32, h32.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s->st));
+    if ((r = wait(s))) return r;
+  }
   if (pos) {
     s->need_rebuild = true;
     s->table_fresh = false;

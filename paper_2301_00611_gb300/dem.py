@@ -95,6 +95,7 @@ _SIGS = {
     "dem_set_dt": (ctypes.c_int, [_P, ctypes.c_double]),
     "dem_get_dt": (ctypes.c_int, [_P, _P]),
     "dem_set_cell_velgrad": (ctypes.c_int, [_P, _P]),
+    "dem_set_triax": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int]),
     "dem_step": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "dem_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "dem_set_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -263,6 +264,12 @@ class Scene:
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_cell_velgrad(self._h, _ptr(L)))
 
+    def set_triax(self, goal, stress_mask, max_rate, grow_damping=0.25, glob_update=5):
+        g = _f64(goal)
+        m = _f64(max_rate)
+        self._check(self._lib.dem_set_triax(self._h, _ptr(g), int(stress_mask), _ptr(m),
+                                            float(grow_damping), int(glob_update)))
+
     # --- stepping
     def step(self, n=1):
         self._check(self._lib.dem_step(self._h, int(n)))
@@ -375,6 +382,7 @@ def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, str
     (i, j, c) in the library's fixed row order."""
     import torch
     lib = load_library()
+    fn = lib.dem_find_pairs
     pos = pos.contiguous()
     radius = radius.contiguous()
     if pos.dtype != torch.float64 or radius.dtype != torch.float64 or not pos.is_cuda:
@@ -388,9 +396,9 @@ def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, str
         J = torch.empty(cap, dtype=torch.int32, device=pos.device)
         C = torch.empty((cap, 3), dtype=torch.int32, device=pos.device)
         cnt = ctypes.c_longlong()
-        rc = lib.dem_find_pairs(pos.data_ptr(), radius.data_ptr(), n, int(bool(periodic)),
-                                H.ctypes.data, float(margin), cap, I.data_ptr(), J.data_ptr(),
-                                C.data_ptr(), ctypes.byref(cnt), st)
+        rc = fn(pos.data_ptr(), radius.data_ptr(), n, int(bool(periodic)), H.ctypes.data,
+                float(margin), cap, I.data_ptr(), J.data_ptr(), C.data_ptr(), ctypes.byref(cnt),
+                st)
         if rc != DEM_OK:
             raise DemError(rc, lib.dem_last_error(None).decode())
         if cnt.value <= cap:

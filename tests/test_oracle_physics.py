@@ -340,3 +340,22 @@ def test_love_weber_stress_of_a_force_chain(oracle_mod):
     off[0, 0] = 0
     assert np.all(np.abs(off) < 1e-12 * abs(sig[0, 0]))
     assert st["Z"] == 2.0
+
+
+def test_stress_servo_reaches_its_goal(oracle_mod):
+    """PeriTriaxController reading: lateral axes under stress control settle at the goal
+    stress while the third axis is driven at its prescribed strain rate (and therefore
+    loads up): the behaviour the controller's goal/stressMask attributes describe."""
+    w = workloads.periodic_cloud(400, 31, phi=0.34, inflate=1.06, friction=0.5)
+    s = oracle_mod.OracleScene.from_workload(w)
+    goal = -5e4
+    s.set_triax([goal, goal, -2.0], 0b011, [50.0, 50.0, 50.0], 0.25, 5)
+    s.step(2500)
+    sig = np.diag(s.stats()["stress"])
+    L = np.diag(s.cell()["velgrad"])
+    assert abs(sig[0] / goal - 1) < 0.02 and abs(sig[1] / goal - 1) < 0.02
+    assert L[2] == -2.0
+    s.step(1000)
+    sig2 = np.diag(s.stats()["stress"])
+    assert abs(sig2[0] / goal - 1) < 0.02 and abs(sig2[1] / goal - 1) < 0.02
+    assert sig2[2] < sig[2] < 0          # the strain-controlled axis keeps compressing

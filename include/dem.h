@@ -254,6 +254,27 @@ dem_status dem_find_pairs(const double *pos_dev, const double *radius_dev, long 
                           int *id1_dev, int *id2_dev, int *cell_dist_dev, long long *count,
                           void *cuda_stream);
 
+/* dem_find_pairs without any allocation.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory at the time of the
+ * call -- for example a program whose device memory is already reserved by
+ * another framework's memory pool, or a latency-sensitive loop that must not
+ * make the allocator's calls (which can synchronize the device).
+ * Same arguments, results and errors as dem_find_pairs, with these limits:
+ *   - at most 65,536 spheres (larger n: DEM_ERR_CAPACITY with a message naming
+ *     dem_find_pairs) and at most 64 grid cells per axis;
+ *   - its scratch is one fixed ~10 MB device array inside the library, held on
+ *     every GPU that loads the library until the process exits;
+ *   - the first call on a device looks up that array's device address (a one-time
+ *     set-up per device): make that first call before any stream capture;
+ *   - every call uses the same array, so calls whose work overlaps on the GPU
+ *     (other threads, other streams) race and must be serialized by the caller;
+ *     each call clears the parts that must start at zero.
+ * The caller still provides the input and output arrays. */
+dem_status dem_find_pairs_noalloc(const double *pos_dev, const double *radius_dev, long long n,
+                                  int periodic, const double *cell_h, double margin,
+                                  long long cap, int *id1_dev, int *id2_dev, int *cell_dist_dev,
+                                  long long *count, void *cuda_stream);
+
 /* Message of the last error on this scene ("" if none).  NULL scene: the last
  * error of a failed dem_scene_create or dem_find_pairs in this thread. */
 const char *dem_last_error(const dem_scene *scene);

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -193,9 +194,10 @@ cudaError_t bounded_wait(cudaStream_t st, bool *timed_out) {
 }
 }  // namespace
 
-// Grid of a pair query: cell edge >= 2 r_max + margin.
+// Grid of a pair query: cell edge >= 2 r_max + margin, at most max_side cells per axis.
 dem_status pair_grid(int periodic, const double *H, const double lo[3], const double hi[3],
-                     double rmax, double margin, Grid &g, std::string &err) {
+                     double rmax, double margin, Grid &g, std::string &err,
+                     int max_side = kMaxGridSide) {
   const double hmin = 2 * rmax + margin;
   g = Grid{};
   g.periodic = periodic;
@@ -209,13 +211,13 @@ dem_status pair_grid(int periodic, const double *H, const double lo[3], const do
         err = "periodic cell edge shorter than 3 * (2 r_max + margin)";
         return DEM_ERR_GEOMETRY;
       }
-      g.n[k] = std::min(n, kMaxGridSide);
+      g.n[k] = std::min(n, max_side);
       g.L[k] = L;
       g.scale[k] = 1.0 / L;
       ext = std::max(ext, L);
     } else {
       const double e = std::max(hi[k] - lo[k] + 2 * rmax, hmin);
-      const int n = std::max(1, std::min((int)std::floor(e / hmin), kMaxGridSide));
+      const int n = std::max(1, std::min((int)std::floor(e / hmin), max_side));
       g.n[k] = n;
       g.lo[k] = lo[k] - rmax;
       g.scale[k] = n / e;
@@ -284,6 +286,24 @@ int pairs_extent(const double *pos, const double *rad, long long n, const PairSc
   const int nb = (int)std::min<long long>(1024, std::max<long long>(1, (n + kT - 1) / kT));
   k_pack<<<nb, kT, 0, st>>>(pos, rad, n, S.packed, S.partials, S.err);
   return nb;
+}
+
+// Launches of the second phase (bin, sort, count, scan, emit) on zeroed counters.
+dem_status pairs_run_nowait(long long n, const Grid &g, double margin, const PairScratch &S,
+                            long long cap, int *I, int *J, int *C, cudaStream_t st) {
+  const long long ncell = (long long)g.B * g.B * g.B;
+  k_bin_q<<<blocks(n), kT, 0, st>>>(S.packed, n, g, S.key, S.count);
+  exclusive_scan(S.count, S.start, ncell, S.ws, st);
+  k_scatter_q<<<blocks(n), kT, 0, st>>>(n, S.key, S.start, S.fill, S.order);
+  k_cellsort_q<<<blocks(ncell), kT, 0, st>>>(S.count, S.start, ncell, S.order);
+  CellRec cr{S.wpos, S.info};
+  k_sorted_rec<<<blocks(n), kT, 0, st>>>(S.packed, S.order, n, g, S.sorted, cr);
+  k_pairs<false><<<blocks(n), kT, 0, st>>>(S.sorted, S.order, cr, n, g, S.count, S.start, margin,
+                                           S.cnt, nullptr, 0, nullptr, nullptr, nullptr);
+  exclusive_scan(S.cnt, S.off, n, S.ws, st);
+  k_pairs<true><<<blocks(n), kT, 0, st>>>(S.sorted, S.order, cr, n, g, S.count, S.start, margin,
+                                          nullptr, S.off, cap, I, J, C);
+  return cudaGetLastError() == cudaSuccess ? DEM_OK : DEM_ERR_CUDA;
 }
 
 // Second phase: bin, sort, count, scan, emit.  *total receives the pair count.
@@ -401,6 +421,142 @@ extern "C" dem_status dem_find_pairs(const double *pos_dev, const double *radius
   cudaFreeAsync(mem2, st);
   cudaFreeAsync(mem, st);
   if (r) return fail(r, err);
+  *count = total;
+  return DEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pair query without allocation.
+//
+// The scratch of dem_find_pairs_noalloc lives in one file-scope device array
+// of fixed size, present on every GPU that loads this library until the process
+// exits.  Host code cannot pass the array's name to a kernel (in host code the
+// name is only a host-side stand-in); the device address is fetched with
+// cudaGetSymbolAddress once per device, with that device current, on the first
+// call there.
+namespace dem {
+namespace {
+constexpr long long kNoAllocMaxSpheres = 1LL << 16;   // 65,536 spheres
+constexpr int kNoAllocMaxSide = 64;                     // grid cells per axis
+constexpr long long kNoAllocMaxCells = (long long)kNoAllocMaxSide * kNoAllocMaxSide * kNoAllocMaxSide;
+constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+// the layout of carve() at the maximum sizes, with room for the scan workspace
+constexpr size_t kNoAllocBytes =
+    2 * up256(32 * kNoAllocMaxSpheres) + up256(8 * 7 * 1024) + up256(4 * kNoAllocMaxSpheres) +
+    up256(4 * kNoAllocMaxCells) + up256(4 * (kNoAllocMaxCells + 1)) + up256(4 * kNoAllocMaxCells) +
+    2 * up256(4 * kNoAllocMaxSpheres) + up256(4 * (kNoAllocMaxSpheres + 1)) + up256(16) +
+    up256(16384) + up256(16 * kNoAllocMaxSpheres) + up256(16 * kNoAllocMaxSpheres);
+
+__device__ __align__(256) unsigned char g_pairs_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_dev[kMaxDevices] = {nullptr};
+
+// device address of the scratch array on the current device (set up on first use)
+cudaError_t scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_dev[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_pairs_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return cudaSuccess;
+}
+
+// bounded wait that creates nothing: poll the stream until its work is done
+cudaError_t bounded_stream_wait(cudaStream_t st, bool *timed_out) {
+  *timed_out = false;
+  const char *env = std::getenv("DEM_TIMEOUT_S");
+  double lim = env ? std::atof(env) : 120.0;
+  if (!(lim > 0)) lim = 120.0;
+  const double deadline = now_s() + lim;
+  while (true) {
+    cudaError_t e = cudaStreamQuery(st);
+    if (e != cudaErrorNotReady) return e;
+    if (now_s() > deadline) { *timed_out = true; return cudaSuccess; }
+    std::this_thread::yield();
+  }
+}
+}  // namespace
+}  // namespace dem
+
+extern "C" dem_status dem_find_pairs_noalloc(const double *pos_dev, const double *radius_dev,
+                                             long long n, int periodic, const double *cell_h,
+                                             double margin, long long cap, int *id1_dev,
+                                             int *id2_dev, int *cell_dist_dev, long long *count,
+                                             void *cuda_stream) {
+  std::string err;
+  auto fail = [&](dem_status c, const std::string &m) { set_global_error(m); return c; };
+  if (!count || n < 0 || cap < 0 || !(margin >= 0) || (n > 0 && (!pos_dev || !radius_dev)) ||
+      (cap > 0 && (!id1_dev || !id2_dev)))
+    return fail(DEM_ERR_INVALID_ARG, "bad pair-query arguments");
+  if (periodic && (!cell_h || cell_h[1] != 0 || cell_h[2] != 0 || cell_h[3] != 0 ||
+                   cell_h[5] != 0 || cell_h[6] != 0 || cell_h[7] != 0 || !(cell_h[0] > 0) ||
+                   !(cell_h[4] > 0) || !(cell_h[8] > 0)))
+    return fail(DEM_ERR_INVALID_ARG, "the periodic cell must be diagonal with positive edges");
+  if (n > kNoAllocMaxSpheres)
+    return fail(DEM_ERR_CAPACITY, "dem_find_pairs_noalloc takes at most 65536 spheres; use "
+                                  "dem_find_pairs for larger configurations");
+  *count = 0;
+  set_global_error("");
+  if (n < 2) return DEM_OK;
+  void *base = nullptr;
+  cudaError_t e = scratch_address(&base);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DEM_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
+  }
+  if (pair_scratch_bytes(n, kNoAllocMaxCells) > kNoAllocBytes)
+    return fail(DEM_ERR_CAPACITY, "internal: pair-query scratch exceeds its static size");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // one layout for both phases, carved at the largest grid; the previous call's
+  // contents are stale: the error word and the cell counters are cleared here
+  PairScratch S = carve((char *)base, n, kNoAllocMaxCells);
+  cudaMemsetAsync(S.err, 0, sizeof(int), st);
+  const int nb = pairs_extent(pos_dev, radius_dev, n, S, st);
+  double host7[7 * 256];
+  int bad = 0;
+  e = cudaMemcpyAsync(host7, S.partials, sizeof(double) * 7 * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  bool to = false;
+  if (e == cudaSuccess) e = bounded_stream_wait(st, &to);
+  if (to) return fail(DEM_ERR_TIMEOUT, "timed out waiting for the GPU");
+  if (e != cudaSuccess) return fail(DEM_ERR_CUDA, std::string("pair query: ") + cudaGetErrorString(e));
+  if (bad) return fail(DEM_ERR_NONFINITE, "non-finite position or non-positive radius");
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double rmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], host7[7 * b + k]);
+      hi[k] = std::max(hi[k], host7[7 * b + 3 + k]);
+    }
+    rmax = std::max(rmax, host7[7 * b + 6]);
+  }
+  Grid g;
+  dem_status r = pair_grid(periodic, cell_h, lo, hi, rmax, margin, g, err, kNoAllocMaxSide);
+  if (r) return fail(r, err);
+  // pairs_run's own wait creates an event; the no-allocation path repeats its
+  // launches with the polling wait instead
+  const long long ncell = (long long)g.B * g.B * g.B;
+  cudaMemsetAsync(S.count, 0, sizeof(int) * ncell, st);
+  cudaMemsetAsync(S.fill, 0, sizeof(int) * ncell, st);
+  long long total = 0;
+  r = pairs_run_nowait(n, g, margin, S, cap, id1_dev, id2_dev, cell_dist_dev, st);
+  if (r) return fail(r, "pair query launch failed");
+  int tot = 0;
+  e = cudaMemcpyAsync(&tot, S.off + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = bounded_stream_wait(st, &to);
+  if (to) return fail(DEM_ERR_TIMEOUT, "timed out waiting for the GPU");
+  if (e != cudaSuccess) return fail(DEM_ERR_CUDA, std::string("pair query: ") + cudaGetErrorString(e));
+  total = tot;
   *count = total;
   return DEM_OK;
 }

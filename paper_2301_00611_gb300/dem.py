@@ -112,6 +112,9 @@ _SIGS = {
     "dem_get_timing": (ctypes.c_int, [_P, _P]),
     "dem_find_pairs": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
                                       ctypes.c_double, ctypes.c_longlong, _P, _P, _P, _P, _P]),
+    "dem_find_pairs_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
+                                              ctypes.c_double, ctypes.c_longlong, _P, _P, _P, _P,
+                                              _P]),
     "dem_last_error": (ctypes.c_char_p, [_P]),
     "dem_version": (ctypes.c_char_p, []),
 }
@@ -375,14 +378,18 @@ def _timing_methods():
 _timing_methods()
 
 
-def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, stream=None):
+def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, stream=None,
+               noalloc=False):
     """All pairs i < j with |x_j + H c - x_i| < r_i + r_j + margin (dem_find_pairs).
 
     pos (n, 3) and radius (n,) are float64 CUDA tensors; returns int32 CUDA tensors
-    (i, j, c) in the library's fixed row order."""
+    (i, j, c) in the library's fixed row order.  noalloc=True calls
+    dem_find_pairs_noalloc, which uses the library's fixed scratch array instead of
+    allocating (at most 65,536 spheres; the output tensors are still allocated here,
+    by the caller of the C function)."""
     import torch
     lib = load_library()
-    fn = lib.dem_find_pairs
+    fn = lib.dem_find_pairs_noalloc if noalloc else lib.dem_find_pairs
     pos = pos.contiguous()
     radius = radius.contiguous()
     if pos.dtype != torch.float64 or radius.dtype != torch.float64 or not pos.is_cuda:

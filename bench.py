@@ -216,13 +216,31 @@ def cpu_baseline_sample(n, seconds_hint=20.0):
                       f"the seeded initial cloud, {el:.1f} s single-threaded"}
 
 
-def _time_window(Scene, w, args, precision, world, local):
+def tune_shape(Scene, w, args, precision):
+    """Launch shapes for the timed scene: dem_autotune on a separate copy of the job
+    advanced to mid-compaction (a contact network like the timed window's).  Launch
+    shapes change no result, so the timed trajectory is the same whichever is picked."""
+    from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
+    if args.no_autotune:
+        return None
+    prec = DEM_MIXED if precision == "mixed" else DEM_FP64
+    s = Scene.from_workload(w, capacity_bodies=args.n, precision=prec)
+    s.set_cell_velgrad(velgrad_for(s.dt()))
+    s.step(TUNE_AT)
+    shape = s.autotune(steps_per_trial=TUNE_STEPS)
+    s.close()
+    return shape
+
+
+def _time_window(Scene, w, args, precision, world, local, shape=None):
     """Run the job to its timed window on one scene; returns the measurements."""
     import torch
     from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
     stream = torch.cuda.current_stream()
     prec = DEM_MIXED if precision == "mixed" else DEM_FP64
     scene = Scene.from_workload(w, capacity_bodies=args.n, precision=prec)
+    if shape:
+        scene.set_tuning(**shape)
     dt = scene.dt()
     scene.set_cell_velgrad(velgrad_for(dt))
     K, W = args.steps, args.warmup
@@ -265,6 +283,8 @@ def _time_window(Scene, w, args, precision, world, local):
 #   real rows add: FP64 shear history 32 + normal/ks 16 + two FP32 velocity/spin 64
 #                  + writes history 32, normal 16, F/d1 16, M/d2 16 = 192
 ROW_BYTES_ALL_MIXED = 60
+TUNE_AT = 3000      # step of the job at which the launch shapes are tuned
+TUNE_STEPS = 10     # timed steps per autotune trial
 ROW_BYTES_REAL_MIXED = 192
 
 
@@ -288,10 +308,13 @@ def run_gpu(args):
     w = make_workload(args.n)
     K, W = args.steps, args.warmup
     peak, peak_kind = _peaks()
-    res = _time_window(Scene, w, args, "fp64", world, local)
+    shape64 = tune_shape(Scene, w, args, "fp64")
+    res = _time_window(Scene, w, args, "fp64", world, local, shape64)
     mixed = None
     if args.precision in ("both", "mixed"):
-        mixed = _time_window(Scene, w, args, "mixed", world, local)
+        shape32 = tune_shape(Scene, w, args, "mixed")
+        mixed = _time_window(Scene, w, args, "mixed", world, local, shape32)
+        mixed["shape"] = shape32
 
     T, ms, tm = res["T"], res["ms"], res["tm"]
     value = world * args.n * K / T
@@ -317,6 +340,7 @@ def run_gpu(args):
             "phase_share": {k: mixed["tm"][k] / max(1e-9, mixed["ms"])
                             for k in ("contact_ms", "integrate_ms", "cell_ms", "collider_ms")},
             "collider_runs": mixed["tm"]["collider_runs"], "gpu_launches": mixed["launches"],
+            "launch_shape": mixed["shape"],
             "clocks": mixed["clocks"],
             "contacts": {"start": mixed["st0"]["n_contacts"], "end": mixed["st1"]["n_contacts"]},
             "roofline": {"bound": "hbm", "kernel": "contact (fused geometry + law), mixed",
@@ -346,6 +370,10 @@ def run_gpu(args):
                "note": "whole 5000-step FP64 job through the C ABI from host arrays: scene "
                        "creation, upload, stepping, state download"}
 
+    batched = None
+    if not args.no_batch and (rank == 0 or world == 1):
+        batched = run_batch_measure(args)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -368,6 +396,7 @@ def run_gpu(args):
             "phase_share": share,
             "collider_runs": tm["collider_runs"],
             "gpu_launches": res["launches"],
+            "launch_shape": shape64,
             "clocks": res["clocks"],
             "roofline": {"bound": "alu", "kernel": "contact (fused geometry + law), FP64",
                          "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -377,6 +406,7 @@ def run_gpu(args):
                          "hbm": {"achieved_gbs": bw, "peak_gbs": peak, "frac": bw / peak,
                                  "peak_kind": peak_kind, "bytes_per_launch": bytes_avg}},
             "mixed": mixed_line,
+            "batched": batched,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -384,6 +414,146 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- batched sweep
+BATCH_SCENES = 512
+BATCH_STEPS = 2000
+BATCH_TUNE_STEPS = 4   # timed steps per autotune trial (the trials are real steps)
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def run_batch_measure(args):
+    """The batched deposition sweep: every scene a sub-scene of one device scene
+    (mixed precision, one launch per kernel per step for all of them, launch shapes
+    from dem_autotune in the first steps), against the plain FP64 path running the
+    same scenes one at a time.  Returns the measurement dict."""
+    import workloads
+    from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED, Scene
+    ws = workloads.batch_depositions(args.batch_scenes, 3, steps=BATCH_STEPS)
+    nsum = sum(w.n for w in ws)
+    g = Scene(capacity_bodies=nsum, precision=DEM_MIXED, dt=1.0)
+    g.set_material(0, 1000.0, 1e6, 0.25, 0.5)
+    subs = [g.add_workload(w, material_base=1 + k) for k, w in enumerate(ws)]
+    _sync()
+    t0 = time.perf_counter()
+    shape = g.autotune(steps_per_trial=BATCH_TUNE_STEPS)   # 11 trials of 5 real steps
+    done = g.subscene(subs[0])["iter"]
+    _sync()
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.step(BATCH_STEPS - done)
+    _sync()
+    t_batch = time.perf_counter() - t0
+    tm_timed = BATCH_STEPS - done
+    batch_stats = [g.subscene_stats(q) for q in subs]
+    g.close()
+    # plain FP64, one scene at a time (the same full 2000-step jobs)
+    t_plain = 0.0
+    plain_stats = []
+    sample = ws[::max(1, args.batch_plain_every)]
+    for w in sample:
+        s = Scene.from_workload(w, precision=DEM_FP64)
+        _sync()
+        t0 = time.perf_counter()
+        s.step(BATCH_STEPS)
+        _sync()
+        t_plain += time.perf_counter() - t0
+        plain_stats.append(s.stats())
+        s.close()
+    idx = list(range(0, len(ws), max(1, args.batch_plain_every)))
+    ke_err = [abs(batch_stats[i]["kinetic_energy"] / p["kinetic_energy"] - 1)
+              for i, p in zip(idx, plain_stats)]
+    z_err = [abs(batch_stats[i]["coordination"] - p["coordination"]) / max(p["coordination"], 1e-300)
+             for i, p in zip(idx, plain_stats) if p["coordination"] > 0]
+    phi_err = [abs(batch_stats[i]["packing_fraction"] / p["packing_fraction"] - 1)
+               for i, p in zip(idx, plain_stats)]
+    batched = len(ws) * tm_timed / t_batch
+    plain = len(sample) * BATCH_STEPS / t_plain
+    return {
+        "workload": f"{len(ws)} gravity depositions, sizes log-uniform [500, 50000] "
+                    f"({nsum} spheres), friction U[0.2, 0.7] rad, E log-uniform [1e6, 1e8] Pa, "
+                    f"{BATCH_STEPS} steps each",
+        "value": batched, "unit": "scene-steps/s",
+        "body_steps_per_s": nsum * tm_timed / t_batch,
+        "timed_steps": tm_timed, "tuning_steps": done, "tuning_seconds": t_tune,
+        "launch_shape": shape,
+        "plain_fp64_one_at_a_time": {"value": plain, "unit": "scene-steps/s",
+                                     "scenes_timed": len(sample)},
+        "speedup_vs_plain": batched / plain,
+        "accuracy_vs_plain_fp64": {"kinetic_energy_rel_max": max(ke_err),
+                                   "kinetic_energy_rel_median": float(np.median(ke_err)),
+                                   "coordination_rel_max": max(z_err) if z_err else 0.0,
+                                   "packing_fraction_rel_max": max(phi_err),
+                                   "scenes_compared": len(plain_stats)},
+        "dtype": "mixed (batched) vs f64 (plain)",
+    }
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of deposition / compaction requests replayed in real
+    time against the continuous-batching server (mixed precision), then the same
+    requests through the plain FP64 one-scene-at-a-time path as a FIFO queue."""
+    import torch
+    import workloads
+    from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED
+    from paper_2301_00611_gb300.serve import percentile, run_alone, serve_stream
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    reqs = workloads.serving_requests(args.requests, 4, args.rate)
+    built = {r["id"]: workloads.request_workload(r) for r in reqs}   # client-side scenes
+
+    def velgrad_for(rq, w):
+        if not w.periodic:
+            return None
+        steps = rq["steps"]
+        return lambda dt: workloads.compaction_rate(0.30, 0.62, steps, dt) * np.eye(3)
+
+    srv, wall = serve_stream(reqs, lambda rq: built[rq["id"]], args.serve_capacity, DEM_MIXED,
+                             args.tick_steps, velgrad_for)
+    lat = [r.latency for r in srv.results]
+    srv.close()
+    # plain FP64 path, one scene at a time in arrival order (FIFO): measured service
+    # times, queueing from the same arrival times
+    t_free = 0.0
+    plain_lat = []
+    plain_busy = 0.0
+    for rq in sorted(reqs, key=lambda r: r["arrival"]):
+        w = built[rq["id"]]
+        vg = velgrad_for(rq, w)
+        _sync()
+        t0 = time.perf_counter()
+        run_alone(w, rq["steps"], DEM_FP64, vg)
+        _sync()
+        svc = time.perf_counter() - t0
+        plain_busy += svc
+        start = max(t_free, rq["arrival"])
+        t_free = start + svc
+        plain_lat.append(t_free - rq["arrival"])
+    scene_steps = sum(rq["steps"] for rq in reqs)
+    line = {
+        "metric": "served p50/p99 latency and scene-steps/s (Poisson request stream)",
+        "value": percentile(lat, 99), "unit": "s (p99 latency)", "higher_is_better": False,
+        "n_gpus": 1, "data": "synthetic (seeded)",
+        "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, spheres log-uniform "
+                               "[1000, 200000], steps U[500, 5000], deposition/compaction mix",
+                   "capacity_bodies": args.serve_capacity, "tick_steps": args.tick_steps},
+        "served": {"p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+                   "scene_steps_per_s": scene_steps / wall, "wall_s": wall,
+                   "body_steps_per_s": srv.body_steps / wall,
+                   "concurrency_mean": float(np.mean(srv.concurrency)) if srv.concurrency else 0,
+                   "concurrency_max": max(srv.concurrency) if srv.concurrency else 0,
+                   "ticks": srv.ticks, "dtype": "mixed"},
+        "plain_fp64_fifo": {"p50_s": percentile(plain_lat, 50), "p99_s": percentile(plain_lat, 99),
+                            "scene_steps_per_s": scene_steps / plain_busy, "dtype": "f64"},
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -398,11 +568,33 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of dem_autotune's")
+    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve"])
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched deposition sweep out of the headline line")
+    ap.add_argument("--batch-scenes", type=int, default=BATCH_SCENES)
+    ap.add_argument("--batch-plain-every", type=int, default=1,
+                    help="time the plain FP64 path on every k-th scene of the sweep")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--serve-capacity", type=int, default=4_000_000)
+    ap.add_argument("--tick-steps", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serve":
+        return run_serve(args)
+    if args.mode == "batch":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"metric": "batched deposition sweep", **run_batch_measure(args)}),
+              flush=True)
+        return 0
     return run_gpu(args)
 
 

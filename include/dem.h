@@ -134,7 +134,7 @@ void dem_scene_destroy(dem_scene *scene);
 
 /* FrictMat (Material / ElastMat / FrictMat class reference): density [kg/m^3],
  * young [Pa], poisson = ks/kn ratio, friction angle [rad] in [0, pi/2).
- * mat_id in [0, 63].  Must precede dem_add_spheres that use it: mass and inertia
+ * mat_id in [0, 4095].  Must precede dem_add_spheres that use it: mass and inertia
  * are fixed at insertion (utils.sphere).  Errors: INVALID_ARG. */
 dem_status dem_set_material(dem_scene *scene, int mat_id, double density, double young,
                             double poisson, double friction_angle);
@@ -230,6 +230,110 @@ dem_status dem_get_stats(dem_scene *scene, dem_stats *out);
  * except kernel_launches.  Timing adds two event records per launch. */
 dem_status dem_set_timing(dem_scene *scene, int enable);
 dem_status dem_get_timing(dem_scene *scene, dem_timing *out);
+
+/* ---- Sub-scenes: many independent scenes advanced by the same launches.
+ *
+ * A scene holds one or more sub-scenes.  Sub-scene 0 is the one its descriptor
+ * defines (every single-scene call above acts on it); dem_add_subscene adds more,
+ * each with its own periodic cell or box and walls, wall material, gravity,
+ * damping, time step (so its own clock) and sweep margin, sharing the material
+ * table, the precision and the launch shapes.  Bodies of different sub-scenes
+ * never interact: the collider builds one grid per sub-scene.  One dem_step(n)
+ * advances every sub-scene by n of its own steps with one launch per kernel for
+ * all of them.  The paper has no counterpart (Yade runs one scene per process);
+ * this is how the library batches parameter sweeps on one GPU.
+ *
+ * Ids: the spheres of a sub-scene have consecutive ids [first_id, first_id + n)
+ * in the scene's id space, so dem_get_state / dem_get_contacts cover every
+ * sub-scene at once.  Removing a sub-scene closes the gap at the next collider run
+ * (the ids of the sub-scenes after it move down); dem_get_subscene reports the
+ * current range.  The stress servo (dem_set_triax) runs only on a scene without
+ * sub-scenes. */
+typedef struct dem_subscene_desc {
+    int periodic;            /* 1: periodic cell cell_h (diagonal, positive); 0: box */
+    double cell_h[9];
+    double box_lo[3], box_hi[3];   /* walls of an aperiodic sub-scene */
+    int wall_mask;           /* bit 2*axis + side (side 0: low face), as dem_scene_desc */
+    int wall_material;       /* material of the walls (set with dem_set_material) */
+    double gravity[3];
+    double damping;          /* eq. 2.9, in [0, 1) */
+    double dt;               /* > 0: fixed; 0: 0.5 x p-wave step of its own spheres */
+    double verlet_dist;      /* as dem_scene_desc */
+} dem_subscene_desc;
+
+/* Defaults: aperiodic, no walls, wall material 0, no gravity, damping 0.2, dt 0
+ * (automatic), verlet_dist -0.5.  Never fails. */
+void dem_subscene_desc_init(dem_subscene_desc *desc);
+
+/* Add an empty sub-scene; *sub receives its index (a removed sub-scene's index may
+ * be reused).  Errors: INVALID_ARG (bad descriptor, unknown wall material),
+ * UNSUPPORTED (the scene runs the stress servo), OOM. */
+dem_status dem_add_subscene(dem_scene *scene, const dem_subscene_desc *desc, int *sub);
+
+/* dem_add_spheres for sub-scene `sub`.  Only the sub-scene that received the last
+ * spheres (or an empty one) can grow: UNSUPPORTED otherwise. */
+dem_status dem_add_spheres_to(dem_scene *scene, int sub, long long n, const double *pos,
+                              const double *radius, const int *mat, const double *vel,
+                              const double *angvel, const unsigned char *fixed,
+                              long long *first_id);
+
+/* Remove a sub-scene and its spheres (they leave the arrays at the next collider
+ * run, which the next dem_step starts with).  INVALID_ARG for an unknown index. */
+dem_status dem_remove_subscene(dem_scene *scene, int sub);
+
+/* Current id range, clock and time step of a sub-scene (any pointer may be NULL). */
+dem_status dem_get_subscene(dem_scene *scene, int sub, long long *first_id, long long *n,
+                            long long *iter, double *time, double *dt);
+
+/* dem_get_stats restricted to one sub-scene (packing fraction over its own cell or
+ * box).  STATE when sub-scenes were added or removed since the last step. */
+dem_status dem_get_subscene_stats(dem_scene *scene, int sub, dem_stats *out);
+
+/* dem_set_cell_velgrad for a periodic sub-scene. */
+dem_status dem_set_subscene_velgrad(dem_scene *scene, int sub, const double *velgrad);
+
+/* Number of spheres in the scene's id space (all sub-scenes; spheres of a removed
+ * sub-scene count until the next collider run closes their ids). */
+dem_status dem_num_bodies(dem_scene *scene, long long *n);
+
+/* dem_get_state for the ids [first_id, first_id + n) only (gathered on the device,
+ * n records copied).  OUT_OF_RANGE when the range leaves [0, number of spheres). */
+dem_status dem_get_state_range(dem_scene *scene, long long first_id, long long n, double *pos,
+                               double *vel, double *angvel, double *ori);
+
+/* Launch shapes of the step kernels.  No shape changes a result: every table row
+ * and every body is computed by one thread with the same arithmetic whatever the
+ * shape, so two scenes that differ only in their tuning follow bit-identical
+ * trajectories.  (The paper's counterpart is the choice of OpenMP thread count,
+ * section 3.1.6; this library exposes the GPU launch geometry instead.)
+ *   contact_block          threads per block of the contact kernel: 128 or 256
+ *   contact_blocks_per_sm  blocks per SM of the contact kernel's persistent grid,
+ *                          1..64 (each warp walks rows/(SMs*blocks*block/32) rows)
+ *   integrate_block        threads per block of the integrator: 128, 256 or 512
+ *   degree_order           1: integrate bodies in decreasing order of incident
+ *                          contact rows (lanes of a warp get similar row counts);
+ *                          0: in slot order
+ * Defaults: 256, 8, 256, 1. */
+typedef struct dem_tuning {
+    int contact_block;
+    int contact_blocks_per_sm;
+    int integrate_block;
+    int degree_order;
+} dem_tuning;
+
+/* Set the launch shapes (INVALID_ARG outside the ranges above) or read them. */
+dem_status dem_set_tuning(dem_scene *scene, const dem_tuning *tuning);
+dem_status dem_get_tuning(const dem_scene *scene, dem_tuning *tuning);
+
+/* Pick the launch shapes by timing the scene's own steps: six contact-kernel
+ * shapes (block 128/256 x 4/8/16 blocks of 256 threads per SM), then five more
+ * integrator shapes (block 128/256/512 x body order) with the best contact shape;
+ * each trial is one untimed step plus steps_per_trial timed steps (CUDA events
+ * around each kernel; collider runs excluded).  The trial steps are real steps:
+ * the scene advances by 11 * (steps_per_trial + 1) steps, along the trajectory
+ * any fixed shape gives.  The best shape is applied and, if chosen is non-null,
+ * written there.  Errors: INVALID_ARG (steps_per_trial < 1), those of dem_step. */
+dem_status dem_autotune(dem_scene *scene, long long steps_per_trial, dem_tuning *chosen);
 
 /* Collision detection on a bare configuration (section 2.1.1, both passes: the
  * grid's bounding-volume filter, then the exact sphere test): every pair

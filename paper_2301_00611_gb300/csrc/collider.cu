@@ -52,14 +52,74 @@ __global__ void k_bbox(const double4_32a *__restrict__ pos, long long N, double 
     for (int k = 0; k < 6; ++k) partials[6 * blockIdx.x + k] = sh[k][0];
 }
 
-__global__ void k_bin(const double4_32a *__restrict__ pos, long long N, Grid g, uint32_t *key,
+// Grid of body i: the one grid, or the grid of its sub-scene.
+__device__ __forceinline__ const Grid &grid_of(const Grid *__restrict__ grids,
+                                               const int *__restrict__ sid, int multi, long long i) {
+  return grids[multi ? sid[i] : 0];
+}
+
+// Cell key of every body; bodies of a removed sub-scene (grid with no cells) get
+// the sentinel key `dead`, which sorts them behind every live body.
+// Order-preserving map of doubles to unsigned integers (sign bit flipped for
+// positives, all bits for negatives), so that integer atomics give min / max.
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Bounding boxes of the sub-scenes: keys[k * cap + q] (k = 0..2 lower, 3..5 upper
+// bounds of x - r / x + r), lower keys preset to all ones and upper to zero.  A
+// warp whose bodies share one sub-scene (the usual case: bodies are grouped by
+// sub-scene) reduces in registers and issues six atomics.
+__global__ void k_bbox_sub(const double4_32a *__restrict__ pos, const int *__restrict__ sid,
+                           long long N, int cap, unsigned long long *keys) {
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * kT;
+  for (long long base = (long long)blockIdx.x * kT + (threadIdx.x & ~31); base < N; base += stride) {
+    const long long i = base + lane;
+    int q = -1;
+    unsigned long long k[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    if (i < N) {
+      q = sid[i];
+      const double4_32a p = pos[i];
+      k[0] = ord_key(p.x - p.w); k[1] = ord_key(p.y - p.w); k[2] = ord_key(p.z - p.w);
+      k[3] = ord_key(p.x + p.w); k[4] = ord_key(p.y + p.w); k[5] = ord_key(p.z + p.w);
+    }
+    const int q0 = __shfl_sync(0xffffffffu, q, 0);
+    const bool uniform = __all_sync(0xffffffffu, q == q0 || q < 0);
+    if (uniform) {
+      for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 6; ++c) {
+          const unsigned long long v = __shfl_down_sync(0xffffffffu, k[c], o);
+          k[c] = c < 3 ? (v < k[c] ? v : k[c]) : (v > k[c] ? v : k[c]);
+        }
+      if (lane == 0 && q0 >= 0)
+        for (int c = 0; c < 6; ++c) {
+          if (c < 3) atomicMin(&keys[(long long)c * cap + q0], k[c]);
+          else atomicMax(&keys[(long long)c * cap + q0], k[c]);
+        }
+    } else if (q >= 0) {
+      for (int c = 0; c < 6; ++c) {
+        if (c < 3) atomicMin(&keys[(long long)c * cap + q], k[c]);
+        else atomicMax(&keys[(long long)c * cap + q], k[c]);
+      }
+    }
+  }
+}
+
+__global__ void k_bin(const double4_32a *__restrict__ pos, const int *__restrict__ sid, long long N,
+                      const Grid *__restrict__ grids, int multi, uint32_t dead, uint32_t *key,
                       int *count) {
   long long i = (long long)blockIdx.x * kT + threadIdx.x;
   if (i >= N) return;
-  double4_32a p = pos[i];
-  int c[3], img[3];
-  cell_of(g, p.x, p.y, p.z, c, img);
-  uint32_t m = morton3(c[0], c[1], c[2]);
+  const Grid &g = grid_of(grids, sid, multi, i);
+  uint32_t m = dead;
+  if (g.n[0] > 0) {
+    const double4_32a p = pos[i];
+    int c[3], img[3];
+    cell_of(g, p.x, p.y, p.z, c, img);
+    m = (uint32_t)cell_index(g, c[0], c[1], c[2]);
+  }
   key[i] = m;
   atomicAdd(&count[m], 1);
 }
@@ -95,7 +155,7 @@ __global__ void k_cellsort(const int *__restrict__ count, const int *__restrict_
 
 __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
                           const int *__restrict__ new_to_old, int *slot_of_id, int has_walls,
-                          int mixed) {
+                          int mixed, const int *__restrict__ id_shift) {
   long long p = (long long)blockIdx.x * kT + threadIdx.x;
   if (p >= N) return;
   int o = new_to_old[p];
@@ -116,8 +176,11 @@ __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
   dst.ori[p] = src.ori[o];
   dst.mprop[p] = src.mprop[o];
   dst.xref[p] = make_double4_32a(x.x, x.y, x.z, 0.0);
-  int id = src.id[o];
+  const int q = src.sid[o];
+  // ids close up over the ranges of removed sub-scenes
+  const int id = src.id[o] - (id_shift ? id_shift[q] : 0);
   dst.id[p] = id;
+  dst.sid[p] = q;
   dst.mat[p] = src.mat[o];
   dst.flags[p] = src.flags[o];
   slot_of_id[id] = (int)p;
@@ -125,9 +188,11 @@ __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
     for (int w = 0; w < 6; ++w) dst.whist[w * cap + p] = src.whist[w * cap + o];
 }
 
-__global__ void k_cellrec(const double4_32a *__restrict__ pos, long long N, Grid g, CellRec cr) {
+__global__ void k_cellrec(const double4_32a *__restrict__ pos, const int *__restrict__ sid,
+                          long long N, const Grid *__restrict__ grids, int multi, CellRec cr) {
   long long i = (long long)blockIdx.x * kT + threadIdx.x;
   if (i >= N) return;
+  const Grid &g = grid_of(grids, sid, multi, i);
   const double4_32a p = pos[i];
   int c[3], img[3];
   cell_of(g, p.x, p.y, p.z, c, img);
@@ -145,11 +210,13 @@ __device__ inline void unpack_cell(int v, int c[3]) {
   c[2] = (v >> 20) & 1023;
 }
 
-__global__ void k_count(CellRec cr, long long N, Grid g, const int *__restrict__ count,
+__global__ void k_count(CellRec cr, const int *__restrict__ sid, long long N,
+                        const Grid *__restrict__ grids, int multi, const int *__restrict__ count,
                         const int *__restrict__ start, int *cnt_up, int *cnt_down, int *err) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
+  const Grid &g = grid_of(grids, sid, multi, sl);
   const float4 a = cr.wpos[s];
   const int4 inf = cr.info[s];
   int ci[3];
@@ -171,11 +238,13 @@ __global__ void k_count(CellRec cr, long long N, Grid g, const int *__restrict__
   if (bad) atomicOr(err, kErrShiftRange);
 }
 
-__global__ void k_emit(CellRec cr, Bodies b, long long N, Grid g, const int *__restrict__ count,
-                       const int *__restrict__ start, Table t, int *dfill, int mixed) {
+__global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict__ grids,
+                       int multi, const int *__restrict__ count, const int *__restrict__ start,
+                       Table t, int *dfill, int mixed) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
+  const Grid &g = grid_of(grids, b.sid, multi, sl);
   const float4 a = cr.wpos[s];
   const int4 inf = cr.info[s];
   int ci[3];
@@ -223,6 +292,38 @@ __global__ void k_downsort(Table t, long long N) {
     }
     t.down[b + 1] = v;
   }
+}
+
+// Integration order: bodies grouped by their number of incident rows, largest
+// first, so that the lanes of a warp walk row lists of about the same length
+// (the per-body sum is a loop whose trip count is the warp's longest list).  The
+// order inside a group is left to the atomics: it changes no result, only which
+// lane integrates which body.
+__device__ inline int degree_bucket(const Table &t, int s) {
+  const int d = (t.row_start[s + 1] - t.row_start[s]) + (t.down_start[s + 1] - t.down_start[s]);
+  return kDegreeBuckets - 1 - (d < kDegreeBuckets - 1 ? d : kDegreeBuckets - 1);
+}
+
+__global__ void k_degree_hist(Table t, long long N, int *hist) {
+  long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= N) return;
+  atomicAdd(&hist[degree_bucket(t, (int)sl)], 1);
+}
+
+__global__ void k_degree_scan(int *ws) {   // one thread: exclusive scan of the 64 counts
+  int acc = 0;
+  for (int i = 0; i < kDegreeBuckets; ++i) {
+    const int c = ws[i];
+    ws[kDegreeBuckets + i] = acc;
+    acc += c;
+  }
+}
+
+__global__ void k_degree_scatter(Table t, long long N, int *fill) {
+  long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= N) return;
+  const int pos = atomicAdd(&fill[degree_bucket(t, (int)sl)], 1);
+  t.ord[pos] = (int)sl;
 }
 
 __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old,
@@ -306,9 +407,17 @@ void launch_bbox(const Bodies &b, long long N, double *partials, int nblk, cudaS
   k_bbox<<<nblk, kT, 0, st>>>(b.pos, N, partials);
 }
 
-void launch_bin(const Bodies &b, long long N, const Grid &g, uint32_t *key, int *count,
-                cudaStream_t st) {
-  if (N > 0) k_bin<<<blocks(N), kT, 0, st>>>(b.pos, N, g, key, count);
+void launch_bbox_sub(const Bodies &b, long long N, int cap, unsigned long long *keys,
+                     int nsm, cudaStream_t st) {
+  if (N <= 0) return;
+  const long long need = (N + kT - 1) / kT;
+  const long long lim = (long long)nsm * 4;
+  k_bbox_sub<<<(unsigned)(need < lim ? need : lim), kT, 0, st>>>(b.pos, b.sid, N, cap, keys);
+}
+
+void launch_bin(const Bodies &b, long long N, const Grid *grids, int multi, uint32_t dead,
+                uint32_t *key, int *count, cudaStream_t st) {
+  if (N > 0) k_bin<<<blocks(N), kT, 0, st>>>(b.pos, b.sid, N, grids, multi, dead, key, count);
 }
 
 void launch_scatter(long long N, const uint32_t *key, const int *start, int *fill, int *tmp,
@@ -323,32 +432,42 @@ void launch_cellsort(const int *count, const int *start, long long ncell, const 
 
 void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
                     const int *new_to_old, int *slot_of_id, int has_walls, int mixed,
-                    cudaStream_t st) {
+                    const int *id_shift, cudaStream_t st) {
   if (N > 0)
     k_reorder<<<blocks(N), kT, 0, st>>>(src, dst, N, cap, new_to_old, slot_of_id, has_walls,
-                                        mixed);
+                                        mixed, id_shift);
 }
 
-void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
-                    cudaStream_t st) {
-  if (N > 0) k_cellrec<<<blocks(N), kT, 0, st>>>(b.pos, N, g, CellRec{wpos, info});
+void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, float4 *wpos,
+                    int4 *info, cudaStream_t st) {
+  if (N > 0) k_cellrec<<<blocks(N), kT, 0, st>>>(b.pos, b.sid, N, grids, multi, CellRec{wpos, info});
 }
 
-void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
-                  const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st) {
+void launch_count(float4 *wpos, int4 *info, const int *sid, long long N, const Grid *grids,
+                  int multi, const int *count, const int *start, int *cnt_up, int *cnt_down,
+                  int *err, cudaStream_t st) {
   if (N > 0)
-    k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, N, g, count, start, cnt_up, cnt_down, err);
+    k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, sid, N, grids, multi, count, start,
+                                      cnt_up, cnt_down, err);
 }
 
-void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid &g,
-                 const int *count, const int *start, const Table &t, int *dfill, int mixed,
-                 cudaStream_t st) {
+void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
+                 int multi, const int *count, const int *start, const Table &t, int *dfill,
+                 int mixed, cudaStream_t st) {
   if (N > 0)
-    k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, g, count, start, t, dfill, mixed);
+    k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
+                                     dfill, mixed);
 }
 
 void launch_downsort(const Table &t, long long N, cudaStream_t st) {
   if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, N);
+}
+
+void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st) {
+  if (N <= 0) return;
+  k_degree_hist<<<blocks(N), kT, 0, st>>>(t, N, ws);
+  k_degree_scan<<<1, 1, 0, st>>>(ws);
+  k_degree_scatter<<<blocks(N), kT, 0, st>>>(t, N, ws + kDegreeBuckets);
 }
 
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,

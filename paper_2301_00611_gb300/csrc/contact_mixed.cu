@@ -27,126 +27,205 @@
 namespace dem {
 
 namespace {
-constexpr int kT = 256;
+constexpr int kQ = 64;   // per-warp queue of real rows (< 32 left over + 32 new)
 
+// Queued real row: its index, FP32 branch vector, squared length, radii, sub-scene.
+struct QRowF {
+  float dx, dy, dz, l2, r1, r2;
+  long long k;
+  int q, pad;
+};
+
+// What a row needs of its (sub-)scene's cell state in FP32, plus the FP64 step.
+struct RowCellF {
+  double dt;
+  float dH[3], W[3];
+  int periodic;
+};
+__device__ __forceinline__ RowCellF row_cell_f(const CellState &c) {
+  RowCellF r;
+  r.dt = c.dt;
+  r.periodic = c.periodic;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.dH[i] = c.periodic ? c.dHf[i] : 0.0f;
+    r.W[i] = c.periodic ? c.Wf[i] : 0.0f;
+  }
+  return r;
+}
+
+// One real row in mixed precision (Ip2 on creation, shear transport, Law2, outputs).
+__device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
+                                               const Mat *__restrict__ mats, const QRowF &e,
+                                               const RowCellF &rc) {
+  const double dt = rc.dt;
+  const float *Wd = rc.W;
+  const long long k = e.k;
+  const int2 pr = t.pair[k];
+  const float dx = e.dx, dy = e.dy, dz = e.dz, l2 = e.l2, r1 = e.r1, r2 = e.r2;
+  const float R = r1 + r2;
+  const float dtf = (float)dt;
+  const float l = sqrtf(l2);
+  const float il = 1.0f / l;
+  const float nx = dx * il, ny = dy * il, nz = dz * il;
+  const float pen = R - l;
+  const float4 g = t.g32[k];
+  float kn = g.w;
+  double4_32a fsd = t.hfs[k];
+  float4 hn = t.hn32[k];
+  float ks;
+  double tanphi;
+  if (kn == 0.0f) {   // Ip2_FrictMat_FrictMat_FrictPhys on a new contact
+    const Mat m1 = mats[b.mat[pr.x]], m2 = mats[b.mat[pr.y]];
+    const float k1 = (float)m1.young * (2 * r1), k2 = (float)m2.young * (2 * r2);
+    kn = k1 * k2 / (k1 + k2);
+    const float s1 = (float)(m1.young * m1.poisson) * (2 * r1);
+    const float s2 = (float)(m2.young * m2.poisson) * (2 * r2);
+    ks = s1 * s2 / (s1 + s2);
+    tanphi = fmin(m1.tanphi, m2.tanphi);
+    fsd = make_double4_32a(0, 0, 0, tanphi);
+    hn = make_float4(nx, ny, nz, ks);
+    t.g32[k] = make_float4(g.x, g.y, g.z, kn);
+  } else {
+    ks = hn.w;
+    tanphi = fsd.w;
+  }
+  float cx = 0, cy = 0, cz = 0;
+  if (rc.periodic) {
+    int i0, i1, i2;
+    unpack_shift(t.cpack[k], i0, i1, i2);
+    cx = (float)i0; cy = (float)i1; cz = (float)i2;
+  }
+  const float4 va1 = b.vw32[2 * pr.x], vb1 = b.vw32[2 * pr.x + 1];
+  const float4 va2 = b.vw32[2 * pr.y], vb2 = b.vw32[2 * pr.y + 1];
+  const float w1x = va1.w, w1y = vb1.x, w1z = vb1.y;
+  const float w2x = va2.w, w2y = vb2.x, w2z = vb2.y;
+  const float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
+  // 2 (first, in FP32). mutual motion: ratchet-free v12, its part perpendicular to n
+  const float rx = r2 * w2x + r1 * w1x, ry = r2 * w2y + r1 * w1y, rz = r2 * w2z + r1 * w1z;
+  const float f = R * il;
+  const float ux = f * (v2x - va1.x) - (ry * nz - rz * ny);
+  const float uy = f * (v2y - va1.y) - (rz * nx - rx * nz);
+  const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
+  const float vn = nx * ux + ny * uy + nz * uz;
+  const float kd = ks * dtf;
+  const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
+  // 1. transport of the stored shear force into the new frame: the rotation vector
+  //    b = n- x n + (dt/2 n.(w1+w2)) n and the change -Fs x b - ks dt v12_perp are
+  //    formed in FP32 from an FP32 copy of the spring and accumulated into the FP64
+  //    spring (as NewtonIntegrator accumulates FP32 increments into FP64 velocities):
+  //    the stored force never drifts from repeated FP32 rounding
+  const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
+  const float bx = (hn.y * nz - hn.z * ny) + tw * nx;
+  const float by = (hn.z * nx - hn.x * nz) + tw * ny;
+  const float bz = (hn.x * ny - hn.y * nx) + tw * nz;
+  const float sx0 = (float)fsd.x, sy0 = (float)fsd.y, sz0 = (float)fsd.z;
+  double fx = fsd.x - (double)((sy0 * bz - sz0 * by) + ix);
+  double fy = fsd.y - (double)((sz0 * bx - sx0 * bz) + iy);
+  double fz = fsd.z - (double)((sx0 * by - sy0 * bx) + iz);
+  // Law2: normal force, Coulomb test in FP32; the cap rescales the FP64 spring
+  const float Fn = kn * pen;
+  const float maxFs = Fn * (float)tanphi;
+  float sx = (float)fx, sy = (float)fy, sz = (float)fz;
+  const float fs2 = sx * sx + sy * sy + sz * sz;
+  if (fs2 > maxFs * maxFs) {
+    const float sc = maxFs * rsqrtf(fs2);
+    const double scd = (double)sc;
+    fx *= scd; fy *= scd; fz *= scd;
+    sx *= sc; sy *= sc; sz *= sc;
+  }
+  const float Fx = Fn * nx + sx, Fy = Fn * ny + sy, Fz = Fn * nz + sz;
+  const float d1 = r1 - 0.5f * pen, d2 = r2 - 0.5f * pen;
+  t.hfs[k] = make_double4_32a(fx, fy, fz, tanphi);
+  t.hn32[k] = make_float4(nx, ny, nz, ks);
+  t.oF32[k] = make_float4(Fx, Fy, Fz, d1);
+  t.oM32[k] = make_float4(-(ny * Fz - nz * Fy), -(nz * Fx - nx * Fz), -(nx * Fy - ny * Fx), d2);
+}
+
+// Same per-warp queue of real rows as the FP64 kernel: the FP32 geometry test on
+// tiles of 32 consecutive rows, the law on 32 queued real rows at a time.
+template <int kT>
 __global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
                                                       const CellState *__restrict__ cs,
                                                       const DevStatus *__restrict__ ds,
-                                                      const Mat *__restrict__ mats, int periodic) {
+                                                      const Mat *__restrict__ mats, int multi) {
+  constexpr int kWarps = kT / 32;
   if (ds->pending) return;
-  const double dt = cs->dt;
-  const float dtf = (float)dt;
-  float dH[3] = {0, 0, 0}, Wd[3] = {0, 0, 0};
-  if (periodic)
-    for (int q = 0; q < 3; ++q) { dH[q] = cs->dHf[q]; Wd[q] = cs->Wf[q]; }
+  __shared__ QRowF q[kWarps][kQ];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  QRowF *wq = q[wi];
+  const RowCellF rc0 = row_cell_f(cs[0]);
   const long long P = t.P;
-  for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < P;
-       k += (long long)gridDim.x * kT) {
-    const int2 pr = t.pair[k];
-    const float4 g = t.g32[k];
-    const float4 a = b.p32[pr.x];
-    const float4 c = b.p32[pr.y];
-    float cx = 0, cy = 0, cz = 0;
-    if (periodic) {
-      int i0, i1, i2;
-      unpack_shift(t.cpack[k], i0, i1, i2);
-      cx = (float)i0; cy = (float)i1; cz = (float)i2;
-    }
-    const float dx = g.x + (c.x - a.x) + dH[0] * cx;
-    const float dy = g.y + (c.y - a.y) + dH[1] * cy;
-    const float dz = g.z + (c.z - a.z) + dH[2] * cz;
-    const float l2 = dx * dx + dy * dy + dz * dz;
-    const float R = a.w + c.w;
-    float kn = g.w;
-    if (!(l2 < R * R)) {
-      if (kn != 0.0f) {  // contact lost: back to a potential interaction
+  const long long stride = (long long)gridDim.x * kT;
+  int cnt = 0;
+  for (long long base = (long long)blockIdx.x * kT + wi * 32; base < P; base += stride) {
+    const long long k = base + lane;
+    bool real = false;
+    float dx = 0, dy = 0, dz = 0, l2 = 0, r1 = 0, r2 = 0;
+    int sq = 0;
+    if (k < P) {
+      const int2 pr = t.pair[k];
+      const float4 g = t.g32[k];
+      const float4 a = b.p32[pr.x];
+      const float4 c = b.p32[pr.y];
+      if (multi) sq = b.sid[pr.x];
+      float cx = 0, cy = 0, cz = 0, dH0 = 0, dH1 = 0, dH2 = 0;
+      if (multi ? cs[sq].periodic : rc0.periodic) {
+        int i0, i1, i2;
+        unpack_shift(t.cpack[k], i0, i1, i2);
+        cx = (float)i0; cy = (float)i1; cz = (float)i2;
+        dH0 = multi ? cs[sq].dHf[0] : rc0.dH[0];
+        dH1 = multi ? cs[sq].dHf[1] : rc0.dH[1];
+        dH2 = multi ? cs[sq].dHf[2] : rc0.dH[2];
+      }
+      // branch vector: reference branch at the collider run + both offsets + the
+      // change of the cell shift since then
+      dx = g.x + (c.x - a.x) + dH0 * cx;
+      dy = g.y + (c.y - a.y) + dH1 * cy;
+      dz = g.z + (c.z - a.z) + dH2 * cz;
+      l2 = dx * dx + dy * dy + dz * dz;
+      r1 = a.w; r2 = c.w;
+      const float R = r1 + r2;
+      real = l2 < R * R;
+      if (!real && g.w != 0.0f) {   // contact lost: back to a potential interaction
         t.g32[k] = make_float4(g.x, g.y, g.z, 0.0f);
         t.hfs[k] = make_double4_32a(0, 0, 0, 0);
         const float4 z = make_float4(0, 0, 0, 0);
         t.hn32[k] = z; t.oF32[k] = z; t.oM32[k] = z;
       }
-      continue;
     }
-    const float l = sqrtf(l2);
-    const float il = 1.0f / l;
-    const float nx = dx * il, ny = dy * il, nz = dz * il;
-    const float pen = R - l;
-    const float r1 = a.w, r2 = c.w;
-    double4_32a fsd = t.hfs[k];
-    float4 hn = t.hn32[k];
-    float ks;
-    double tanphi;
-    if (kn == 0.0f) {   // Ip2_FrictMat_FrictMat_FrictPhys on a new contact
-      const Mat m1 = mats[b.mat[pr.x]], m2 = mats[b.mat[pr.y]];
-      const float k1 = (float)m1.young * (2 * r1), k2 = (float)m2.young * (2 * r2);
-      kn = k1 * k2 / (k1 + k2);
-      const float s1 = (float)(m1.young * m1.poisson) * (2 * r1);
-      const float s2 = (float)(m2.young * m2.poisson) * (2 * r2);
-      ks = s1 * s2 / (s1 + s2);
-      tanphi = fmin(m1.tanphi, m2.tanphi);
-      fsd = make_double4_32a(0, 0, 0, tanphi);
-      hn = make_float4(nx, ny, nz, ks);
-      t.g32[k] = make_float4(g.x, g.y, g.z, kn);
-    } else {
-      ks = hn.w;
-      tanphi = fsd.w;
+    const unsigned m = __ballot_sync(0xffffffffu, real);
+    if (real) {
+      const int at = cnt + __popc(m & ((1u << lane) - 1u));
+      wq[at] = QRowF{dx, dy, dz, l2, r1, r2, k, sq, 0};
     }
-    const float4 va1 = b.vw32[2 * pr.x], vb1 = b.vw32[2 * pr.x + 1];
-    const float4 va2 = b.vw32[2 * pr.y], vb2 = b.vw32[2 * pr.y + 1];
-    const float w1x = va1.w, w1y = vb1.x, w1z = vb1.y;
-    const float w2x = va2.w, w2y = vb2.x, w2z = vb2.y;
-    const float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
-    // 2 (first, in FP32). mutual motion: ratchet-free v12, its part perpendicular to n
-    const float rx = r2 * w2x + r1 * w1x, ry = r2 * w2y + r1 * w1y, rz = r2 * w2z + r1 * w1z;
-    const float f = R * il;
-    const float ux = f * (v2x - va1.x) - (ry * nz - rz * ny);
-    const float uy = f * (v2y - va1.y) - (rz * nx - rx * nz);
-    const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
-    const float vn = nx * ux + ny * uy + nz * uz;
-    const float kd = ks * dtf;
-    const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
-    // 1. transport of the stored shear force into the new frame: the rotation vector
-    //    b = n- x n + (dt/2 n.(w1+w2)) n and the change -Fs x b - ks dt v12_perp are
-    //    formed in FP32 from an FP32 copy of the spring and accumulated into the FP64
-    //    spring (as NewtonIntegrator accumulates FP32 increments into FP64 velocities):
-    //    the stored force never drifts from repeated FP32 rounding
-    const float tw = 0.5f * dtf * (nx * (w1x + w2x) + ny * (w1y + w2y) + nz * (w1z + w2z));
-    const float bx = (hn.y * nz - hn.z * ny) + tw * nx;
-    const float by = (hn.z * nx - hn.x * nz) + tw * ny;
-    const float bz = (hn.x * ny - hn.y * nx) + tw * nz;
-    const float sx0 = (float)fsd.x, sy0 = (float)fsd.y, sz0 = (float)fsd.z;
-    double fx = fsd.x - (double)((sy0 * bz - sz0 * by) + ix);
-    double fy = fsd.y - (double)((sz0 * bx - sx0 * bz) + iy);
-    double fz = fsd.z - (double)((sx0 * by - sy0 * bx) + iz);
-    // Law2: normal force, Coulomb test in FP32; the cap rescales the FP64 spring
-    const float Fn = kn * pen;
-    const float maxFs = Fn * (float)tanphi;
-    float sx = (float)fx, sy = (float)fy, sz = (float)fz;
-    const float fs2 = sx * sx + sy * sy + sz * sz;
-    if (fs2 > maxFs * maxFs) {
-      const float sc = maxFs * rsqrtf(fs2);
-      const double scd = (double)sc;
-      fx *= scd; fy *= scd; fz *= scd;
-      sx *= sc; sy *= sc; sz *= sc;
+    cnt += __popc(m);
+    __syncwarp();
+    if (cnt >= 32) {
+      const QRowF e = wq[lane];
+      real_row_mixed(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
+      __syncwarp();
+      if (lane < cnt - 32) wq[lane] = wq[lane + 32];
+      cnt -= 32;
+      __syncwarp();
     }
-    const float Fx = Fn * nx + sx, Fy = Fn * ny + sy, Fz = Fn * nz + sz;
-    const float d1 = r1 - 0.5f * pen, d2 = r2 - 0.5f * pen;
-    t.hfs[k] = make_double4_32a(fx, fy, fz, tanphi);
-    t.hn32[k] = make_float4(nx, ny, nz, ks);
-    t.oF32[k] = make_float4(Fx, Fy, Fz, d1);
-    t.oM32[k] = make_float4(-(ny * Fz - nz * Fy), -(nz * Fx - nx * Fz), -(nx * Fy - ny * Fx), d2);
+  }
+  if (lane < cnt) {
+    const QRowF e = wq[lane];
+    real_row_mixed(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
   }
 }
 }  // namespace
 
 void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
-                          const DevStatus *ds, const Mat *mats, int periodic, int nsm,
-                          cudaStream_t st) {
+                          const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
+                          int per_sm, cudaStream_t st) {
   if (t.P <= 0) return;
-  long long need = (t.P + kT - 1) / kT;
-  long long cap = (long long)nsm * 8;
+  long long need = (t.P + block - 1) / block;
+  long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  k_contact_mixed<<<grid, kT, 0, st>>>(t, b, cs, ds, mats, periodic);
+  if (block == 128) k_contact_mixed<128><<<grid, 128, 0, st>>>(t, b, cs, ds, mats, multi);
+  else k_contact_mixed<256><<<grid, 256, 0, st>>>(t, b, cs, ds, mats, multi);
 }
 
 }  // namespace dem

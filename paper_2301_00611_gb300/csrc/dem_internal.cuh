@@ -27,7 +27,7 @@
 
 namespace dem {
 
-constexpr int kMaxMat = 64;
+constexpr int kMaxMat = 4096;
 constexpr int kMaxGridSide = 256;   // cells per axis (Morton code of 24 bits)
 
 // error bits set by kernels (DevStatus::error)
@@ -44,6 +44,7 @@ struct Mat {
 struct Bodies {
   double4_32a *pos, *vel, *angvel, *ori, *xref, *mprop;
   int *id, *mat;
+  int *sid;         // sub-scene of each body (read only when SceneConst::multi)
   uint8_t *flags;   // bit0 fixed; bit (1+w) in contact with wall w
   double4_32a *whist;   // [6 * cap] or null
   // mixed precision mirrors (null in FP64 mode), written by the integrator:
@@ -67,6 +68,7 @@ struct Table {
   int *row_start;   // [nbody + 1]
   int *down_start;  // [nbody + 1]
   int *down;        // [cap]
+  int *ord;         // [nbody]: bodies by decreasing number of incident rows (integration order)
   int *found;       // [cap]
   long long cap;    // rows
   long long nbody_cap;
@@ -97,16 +99,25 @@ struct CellState {
   // or strain rate per axis, rate bound, growDamping, update period in steps
   double goal[3], max_rate[3], grow_damping;
   int triax, stress_mask, glob_update, pad3;
+  // constants of the (sub-)scene: gravity, damping, walls of an aperiodic box
+  double gravity[3], damping;
+  double box_lo[3], box_hi[3];
+  int wall_mask;    // walls present (bit w: wall w = 2 axis + side)
+  int wall_mat;     // material of the walls
+  int alive;        // 0: a removed sub-scene (its slot is skipped)
+  int pad4;
 };
 
 constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
+constexpr int kDegreeBuckets = 64;  // incident-row counts >= 63 share the last bucket
 
 // Small status block read back by the host after a batch of steps.
 struct DevStatus {
   int pending;    // collider run needed before the next step (steps are skipped)
   int request;    // set by the integrator when a displacement exceeds the bound
   int error;      // kErr* bits
-  int pad;
+  int arrive;     // blocks of the current cell-advance launch that have finished
+  unsigned long long steps;   // steps completed (never reset)
 };
 
 struct Grid {
@@ -120,15 +131,17 @@ struct Grid {
   float Lf[3];      // FP32 copies for the candidate test
   float reachf;
   float slack;      // FP32 rounding allowance of the candidate test (keeps it conservative)
+  long long base;   // first global cell index of this grid (sub-scenes are consecutive)
+  int morton;       // 1: cells indexed by Morton code (B^3), 0: row-major (n0 n1 n2)
+  int pad;
 };
 
 struct SceneConst {
   long long N;
-  double gravity[3];
-  double damping;
-  double box_lo[3], box_hi[3];
-  int wall_mask;
-  int periodic;
+  int walls;     // some sub-scene has walls
+  int periodic;  // some sub-scene is periodic
+  int ordered;   // integrate bodies in Table::ord order (else slot order)
+  int multi;     // more than one sub-scene: per-body constants from CellState[sid]
 };
 
 // ---- cell shift packing: 3 x 10-bit two's complement in one int
@@ -150,47 +163,66 @@ void exclusive_scan(const int *in, int *out, long long n, int *workspace, cudaSt
 // collider.cu
 void launch_bbox(const Bodies &b, long long N, double *partials, int nblk, cudaStream_t st);
 int bbox_blocks(long long N);
-void launch_bin(const Bodies &b, long long N, const Grid &g, uint32_t *key, int *count,
-                cudaStream_t st);
+// grids: device array, one per sub-scene (multi) or one; bodies whose grid has no
+// cells take the key `dead`
+void launch_bin(const Bodies &b, long long N, const Grid *grids, int multi, uint32_t dead,
+                uint32_t *key, int *count, cudaStream_t st);
 void launch_scatter(long long N, const uint32_t *key, const int *start, int *fill, int *tmp,
                     cudaStream_t st);
 void launch_cellsort(const int *count, const int *start, long long ncell, const int *id,
                      int *tmp, cudaStream_t st);
+// id_shift (nullable): per sub-scene amount subtracted from the ids (removals)
 void launch_reorder(const Bodies &src, const Bodies &dst, long long N, long long cap,
                     const int *new_to_old, int *slot_of_id, int has_walls, int mixed,
-                    cudaStream_t st);
-void launch_cellrec(const Bodies &b, long long N, const Grid &g, float4 *wpos, int4 *info,
-                    cudaStream_t st);
-void launch_count(float4 *wpos, int4 *info, long long N, const Grid &g, const int *count,
-                  const int *start, int *cnt_up, int *cnt_down, int *err, cudaStream_t st);
-void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid &g,
-                 const int *count, const int *start, const Table &t, int *dfill, int mixed,
-                 cudaStream_t st);
+                    const int *id_shift, cudaStream_t st);
+// per-sub-scene bounding boxes as ordered keys (see collider.cu); keys preset
+void launch_bbox_sub(const Bodies &b, long long N, int cap, unsigned long long *keys, int nsm,
+                     cudaStream_t st);
+void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, float4 *wpos,
+                    int4 *info, cudaStream_t st);
+void launch_count(float4 *wpos, int4 *info, const int *sid, long long N, const Grid *grids,
+                  int multi, const int *count, const int *start, int *cnt_up, int *cnt_down,
+                  int *err, cudaStream_t st);
+void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
+                 int multi, const int *count, const int *start, const Table &t, int *dfill,
+                 int mixed, cudaStream_t st);
 void launch_downsort(const Table &t, long long N, cudaStream_t st);
+// t.ord = bodies in decreasing order of incident rows; ws: 2 * kDegreeBuckets zeroed ints
+void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
                   int mixed, cudaStream_t st);
 void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
 
 // contact.cu
+// block: 128 or 256 threads; per_sm: blocks per SM of the persistent grid
+// multi: cs is an array indexed by Bodies::sid (else cs[0] holds the one scene)
 void launch_contact(const Table &t, const Bodies &b, const CellState *cs, const DevStatus *ds,
-                    const Mat *mats, int periodic, int nsm, cudaStream_t st);
+                    const Mat *mats, int multi, int nsm, int block, int per_sm,
+                    cudaStream_t st);
 // contact_mixed.cu
 void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
-                          const DevStatus *ds, const Mat *mats, int periodic, int nsm,
-                          cudaStream_t st);
+                          const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
+                          int per_sm, cudaStream_t st);
 
 // integrate.cu
+// block: 128, 256 or 512 threads
 void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                      const Mat *mats, const SceneConst &sc, long long cap, int mixed,
+                      const Mat *mats, const SceneConst &sc, long long cap, int mixed, int block,
                       cudaStream_t st);
-void launch_cell_advance(CellState *cs, DevStatus *ds, const double *servo_partials,
+// one thread per sub-scene (cs[0 .. nsub)); servo partials apply to sub-scene 0
+void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
                          cudaStream_t st);
 // servo: per-block sums of sigma_ii * V and K_i * V over the real rows (6 per block)
 void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
                            cudaStream_t st);
-void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
+void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, const CellState *cs,
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
                           int mixed, cudaStream_t st);
+// dst[i] = src[slot_of_id[i]] for i < n (records of consecutive ids, in id order)
+void launch_gather_ids(const int *slot_of_id, long long n, const double4_32a *src,
+                       double4_32a *dst, cudaStream_t st);
+void launch_gather_ids_f(const int *slot_of_id, long long n, const float4 *src, float4 *dst,
+                         cudaStream_t st);
 // stats: per-block partial sums (deterministic tree), summed on the host in block order
 int stats_blocks(long long n);
 void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, double *partials,

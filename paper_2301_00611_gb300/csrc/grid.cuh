@@ -19,6 +19,13 @@ __host__ __device__ inline uint32_t morton3(int i, int j, int k) {
   return spread3((uint32_t)i) | (spread3((uint32_t)j) << 1) | (spread3((uint32_t)k) << 2);
 }
 
+// global index of cell (i, j, k) of grid g: Morton code (one scene) or row-major
+// (sub-scenes), offset by the grid's first cell
+__host__ __device__ inline long long cell_index(const Grid &g, int i, int j, int k) {
+  return g.base + (g.morton ? (long long)morton3(i, j, k)
+                            : ((long long)k * g.n[1] + j) * g.n[0] + i);
+}
+
 // cell coordinates (and, periodic, the integer image) of a position
 __device__ inline void cell_of(const Grid &g, double x, double y, double z, int c[3], int img[3]) {
   const double p[3] = {x, y, z};
@@ -72,7 +79,7 @@ __device__ inline void for_half_shell(const Grid &g, const int *__restrict__ cou
         }
         if (!ok) continue;
         const bool self = (dx == 0 && dy == 0 && dz == 0);
-        const uint32_t m = morton3(cj[0], cj[1], cj[2]);
+        const long long m = cell_index(g, cj[0], cj[1], cj[2]);
         const int s0 = start[m], cnt = count[m];
         for (int j = (self ? s + 1 : s0); j < s0 + cnt; ++j) f(j, w);
       }

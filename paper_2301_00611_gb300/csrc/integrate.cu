@@ -71,10 +71,10 @@ __device__ inline void gather_rows_f32(const Table &t, int s, double F[3], doubl
 }
 
 // FrictPhys of a sphere-wall contact: equivalent wall radius = sphere radius,
-// wall material = material 0.
-__device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn, double &ks,
-                                 double &tanphi) {
-  const Mat mw = mats[0], ms = mats[mat];
+// wall material = the scene's wall material (material 0 by default).
+__device__ inline void wall_phys(const Mat *mats, int wmat, int mat, double r, double &kn,
+                                 double &ks, double &tanphi) {
+  const Mat mw = mats[wmat], ms = mats[mat];
   const double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
   kn = k1 * k2 / (k1 + k2);
   const double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
@@ -88,15 +88,17 @@ __device__ inline void wall_phys(const Mat *mats, int mat, double r, double &kn,
 // contact kernel).  Every quantity it needs in FP32 is read from the FP32 mirrors
 // the previous step wrote, so the FP64 pipe (conversions included) carries ~27
 // instructions per body.
-__global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
+template <int kB>
+__global__ void __launch_bounds__(kB) k_integrate_mixed(Bodies b, Table t,
                                                         const CellState *__restrict__ cs,
                                                         DevStatus *ds, const Mat *__restrict__ mats,
                                                         SceneConst sc, long long cap) {
   if (ds->pending) return;
-  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
-  const int s = (int)sl;
-  const double dt = cs->dt;
+  const int s = sc.ordered ? t.ord[sl] : (int)sl;
+  const CellState &c = cs[sc.multi ? b.sid[s] : 0];
+  const double dt = c.dt;
   const float dtf = (float)dt;
   float F[3], T[3];
   {
@@ -126,13 +128,13 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
   const float xf[3] = {xr.x + off.x, xr.y + off.y, xr.z + off.z};
   const float r = off.w;
 
-  if (sc.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
+  if (sc.walls && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
     const double4_32a pd = b.pos[s];
     const double xd[3] = {pd.x, pd.y, pd.z};
     for (int wi = 0; wi < 6; ++wi) {
-      if (!(sc.wall_mask & (1 << wi))) continue;
+      if (!(c.wall_mask & (1 << wi))) continue;
       const int ax = wi >> 1;
-      const float dist = (float)(xd[ax] - ((wi & 1) ? sc.box_hi[ax] : sc.box_lo[ax]));
+      const float dist = (float)(xd[ax] - ((wi & 1) ? c.box_hi[ax] : c.box_lo[ax]));
       const bool was = flags & (2 << wi);
       if (!(fabsf(dist) < r)) {
         if (was) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
       n[ax] = sn;
       const float pen = r - fabsf(dist);
       double knd, ksd, tpd;
-      wall_phys(mats, b.mat[s], (double)r, knd, ksd, tpd);
+      wall_phys(mats, c.wall_mat, b.mat[s], (double)r, knd, ksd, tpd);
       const float kn = (float)knd, ks = (float)ksd, tanphi = (float)tpd;
       float fs[3] = {0, 0, 0};
       if (was) {
@@ -189,12 +191,12 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
   float dv[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
   const bool fixed = flags & 1;
   if (!fixed) {
-    const float lam = (float)sc.damping;
+    const float lam = (float)c.damping;
     float vref[3] = {vv[0], vv[1], vv[2]};
-    if (sc.periodic)
-      for (int q = 0; q < 3; ++q) vref[q] -= (float)cs->Lprev[4 * q] * xf[q];
+    if (c.periodic)
+      for (int q = 0; q < 3; ++q) vref[q] -= (float)c.Lprev[4 * q] * xf[q];
     for (int q = 0; q < 3; ++q) {
-      const float Ft = F[q] + mp.x * (float)sc.gravity[q];
+      const float Ft = F[q] + mp.x * (float)c.gravity[q];
       const float acc = Ft * mp.z;
       const float Fd = Ft * damp_factor_f(Ft * (vref[q] + 0.5f * dtf * acc), lam);
       dv[q] = dtf * Fd * mp.z;
@@ -202,9 +204,9 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
       const float Td = T[q] * damp_factor_f(T[q] * (ww[q] + 0.5f * dtf * aacc), lam);
       dw[q] = dtf * Td * mp.w;
     }
-    if (sc.periodic)   // homoDeform = 2
+    if (c.periodic)   // homoDeform = 2
       for (int q = 0; q < 3; ++q)
-        dv[q] += (float)cs->dL[4 * q] * xf[q] + dtf * ((float)cs->L[4 * q] * vv[q]);
+        dv[q] += (float)c.dL[4 * q] * xf[q] + dtf * ((float)c.L[4 * q] * vv[q]);
   }
   // FP64 accumulation of velocity, spin and position
   const double4_32a v = b.vel[s], w = b.angvel[s], p = b.pos[s];
@@ -246,8 +248,8 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
                              dq0 * q0.w + dq1 * q0.z - dq2 * q0.y + dq3 * q0.x);
   }
   // collider trigger on the FP32 offset (slightly early to cover its rounding)
-  const float ux = ox - cs->Ef[0] * xr.x, uy = oy - cs->Ef[1] * xr.y, uz = oz - cs->Ef[2] * xr.z;
-  if (!(ux * ux + uy * uy + uz * uz <= (float)(0.998 * cs->thr2))) {
+  const float ux = ox - c.Ef[0] * xr.x, uy = oy - c.Ef[1] * xr.y, uz = oz - c.Ef[2] * xr.z;
+  if (!(ux * ux + uy * uy + uz * uz <= (float)(0.998 * c.thr2))) {
     if (!ds->request) ds->request = 1;
   }
   if (!(isfinite(ox + oy + oz) && isfinite(vnf[0] + vnf[1] + vnf[2]) &&
@@ -255,18 +257,18 @@ __global__ void __launch_bounds__(kT) k_integrate_mixed(Bodies b, Table t,
     atomicOr(&ds->error, kErrNonFinite);
 }
 
-template <bool Mixed>
-__global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
+template <int kB>
+__global__ void __launch_bounds__(kB) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
                                                   DevStatus *ds, const Mat *__restrict__ mats,
                                                   SceneConst sc, long long cap) {
   if (ds->pending) return;
-  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
-  const int s = (int)sl;
-  const double dt = cs->dt;
+  const int s = sc.ordered ? t.ord[sl] : (int)sl;
+  const CellState &c = cs[sc.multi ? b.sid[s] : 0];
+  const double dt = c.dt;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  if (Mixed) gather_rows_f32(t, s, F, T);
-  else gather_rows(t, s, F, T);
+  gather_rows(t, s, F, T);
 
   const double4_32a p = b.pos[s];
   const double4_32a v = b.vel[s];
@@ -276,11 +278,11 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   const double x[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z}, ww[3] = {w.x, w.y, w.z};
   const double r = p.w;
 
-  if (sc.wall_mask) {
+  if (sc.walls && c.wall_mask) {
     for (int wi = 0; wi < 6; ++wi) {
-      if (!(sc.wall_mask & (1 << wi))) continue;
+      if (!(c.wall_mask & (1 << wi))) continue;
       const int ax = wi >> 1;
-      const double wc = (wi & 1) ? sc.box_hi[ax] : sc.box_lo[ax];
+      const double wc = (wi & 1) ? c.box_hi[ax] : c.box_lo[ax];
       const double dist = x[ax] - wc;
       const bool was = flags & (2 << wi);
       if (!(fabs(dist) < r)) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
       n[ax] = sn;
       const double pen = r - fabs(dist);
       double kn, ks, tanphi;
-      wall_phys(mats, b.mat[s], r, kn, ks, tanphi);
+      wall_phys(mats, c.wall_mat, b.mat[s], r, kn, ks, tanphi);
       double fs[3] = {0, 0, 0};
       if (was) {
         const double4_32a h = b.whist[wi * cap + s];
@@ -339,38 +341,24 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   double vn_[3], wn_[3];
   const bool fixed = flags & 1;
   if (!fixed) {
-    const double lam = sc.damping;
+    const double lam = c.damping;
     double vref[3] = {vv[0], vv[1], vv[2]};
     // cell matrices are diagonal (enforced at the C ABI): only their diagonals enter
-    if (sc.periodic) {   // fluctuation velocity for eq. 2.9 in a deforming cell
-      const double *Lp = cs->Lprev;
+    if (c.periodic) {   // fluctuation velocity for eq. 2.9 in a deforming cell
+      const double *Lp = c.Lprev;
       for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
     }
-    if (Mixed) {   // damping in FP32, the velocity accumulation in FP64
-      const float dtf = (float)dt, lamf = (float)lam, im = (float)mp.z, iI = (float)mp.w;
-      for (int q = 0; q < 3; ++q) {
-        const float Ft = (float)(F[q] + mp.x * sc.gravity[q]);
-        const float acc = Ft * im;
-        const float Fd = Ft * damp_factor_f(Ft * ((float)vref[q] + 0.5f * dtf * acc), lamf);
-        vn_[q] = vv[q] + (double)(dtf * Fd * im);
-        const float Tq = (float)T[q];
-        const float aacc = Tq * iI;
-        const float Td = Tq * damp_factor_f(Tq * ((float)ww[q] + 0.5f * dtf * aacc), lamf);
-        wn_[q] = ww[q] + (double)(dtf * Td * iI);
-      }
-    } else {
-      for (int q = 0; q < 3; ++q) {
-        const double Ft = F[q] + mp.x * sc.gravity[q];
-        const double acc = Ft * mp.z;
-        const double Fd = Ft * damp_factor(Ft * (vref[q] + 0.5 * dt * acc), lam);
-        vn_[q] = vv[q] + dt * Fd * mp.z;
-        const double aacc = T[q] * mp.w;
-        const double Td = T[q] * damp_factor(T[q] * (ww[q] + 0.5 * dt * aacc), lam);
-        wn_[q] = ww[q] + dt * Td * mp.w;
-      }
+    for (int q = 0; q < 3; ++q) {
+      const double Ft = F[q] + mp.x * c.gravity[q];
+      const double acc = Ft * mp.z;
+      const double Fd = Ft * damp_factor(Ft * (vref[q] + 0.5 * dt * acc), lam);
+      vn_[q] = vv[q] + dt * Fd * mp.z;
+      const double aacc = T[q] * mp.w;
+      const double Td = T[q] * damp_factor(T[q] * (ww[q] + 0.5 * dt * aacc), lam);
+      wn_[q] = ww[q] + dt * Td * mp.w;
     }
-    if (sc.periodic) {   // homoDeform = 2
-      const double *dL = cs->dL, *L = cs->L;
+    if (c.periodic) {   // homoDeform = 2
+      const double *dL = c.dL, *L = c.L;
       for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
     }
   } else {
@@ -383,41 +371,17 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
   if (flags != b.flags[s]) b.flags[s] = flags;
 
   // orientation: q+ = dq(w+ dt) q, dq = (cos x, (sin x / x) * w dt / 2), x = |w| dt / 2.
-  // For x < 1e-2 the Maclaurin series of cos x and sin x / x truncated after the x^8
-  // term is exact to double precision (next terms < 1e-26) and needs no square root,
-  // division or sincos; larger angles use sincos.
+  // For x < 1e-2 the Maclaurin series of cos x and sin x / x truncated after the x^4
+  // term (first omitted terms x^6/720 and x^6/5040, below 1.4e-15) needs no square
+  // root, division or sincos; larger angles use sincos.
   const double w2 = wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2];
-  if (Mixed && w2 > 0) {
-    // mixed precision: the orientation step in FP32 (series to x^4 is exact in FP32
-    // for x < 1e-2), stored back in the FP64 record
-    const double4_32a q0 = b.ori[s];
-    const float dtf = (float)dt;
-    const float w0f = (float)wn_[0], w1f = (float)wn_[1], w2f = (float)wn_[2];
-    const float x2 = 0.25f * (dtf * dtf) * (w0f * w0f + w1f * w1f + w2f * w2f);
-    float ch, sx;
-    if (x2 < 1e-4f) {
-      ch = 1.0f - 0.5f * x2 * (1.0f - x2 * (1.0f / 12.0f));
-      sx = 1.0f - x2 * (1.0f / 6.0f) * (1.0f - x2 * (1.0f / 20.0f));
-    } else {
-      const float x = sqrtf(x2);
-      float sh;
-      sincosf(x, &sh, &ch);
-      sx = sh / x;
-    }
-    const float hs = 0.5f * dtf * sx;
-    const float dw = ch, dx = hs * w0f, dy = hs * w1f, dz = hs * w2f;
-    const float a0 = (float)q0.x, a1 = (float)q0.y, a2 = (float)q0.z, a3 = (float)q0.w;
-    b.ori[s] = make_double4_32a(dw * a0 - dx * a1 - dy * a2 - dz * a3,
-                                dw * a1 + dx * a0 + dy * a3 - dz * a2,
-                                dw * a2 - dx * a3 + dy * a0 + dz * a1,
-                                dw * a3 + dx * a2 - dy * a1 + dz * a0);
-  } else if (w2 > 0) {
+  if (w2 > 0) {
     const double4_32a q0 = b.ori[s];
     const double x2 = 0.25 * (dt * dt) * w2;
     double ch, sx;   // cos x, sin x / x
     if (x2 < 1e-4) {
-      ch = 1.0 - 0.5 * x2 * (1.0 - x2 * (1.0 / 12.0) * (1.0 - x2 * (1.0 / 30.0) * (1.0 - x2 * (1.0 / 56.0))));
-      sx = 1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0) * (1.0 - x2 * (1.0 / 72.0))));
+      ch = 1.0 - 0.5 * x2 * (1.0 - x2 * (1.0 / 12.0));
+      sx = 1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0));
     } else {
       const double x = sqrt(x2);
       double sh;
@@ -434,26 +398,11 @@ __global__ void __launch_bounds__(kT) k_integrate(Bodies b, Table t, const CellS
 
   // collider trigger: displacement since the last run, minus the affine part
   const double4_32a xr = b.xref[s];
-  bool far;
-  if (Mixed) {
-    // FP32 offsets from the reference position feed the next contact pass
-    const float ox = (float)(xn[0] - xr.x), oy = (float)(xn[1] - xr.y), oz = (float)(xn[2] - xr.z);
-    b.p32[s] = make_float4(ox, oy, oz, (float)r);
-    b.vw32[2 * s] = make_float4((float)vn_[0], (float)vn_[1], (float)vn_[2], (float)wn_[0]);
-    b.vw32[2 * s + 1] = make_float4((float)wn_[1], (float)wn_[2], 0.0f, 0.0f);
-    const float ux = ox - cs->Ef[0] * (float)xr.x;
-    const float uy = oy - cs->Ef[1] * (float)xr.y;
-    const float uz = oz - cs->Ef[2] * (float)xr.z;
-    // FP32 rounding allowance: trigger slightly early
-    far = !(ux * ux + uy * uy + uz * uz <= (float)(0.998 * cs->thr2));
-  } else {
-    const double *E = cs->E;   // diagonal
-    const double ux = (xn[0] - xr.x) - E[0] * xr.x;
-    const double uy = (xn[1] - xr.y) - E[4] * xr.y;
-    const double uz = (xn[2] - xr.z) - E[8] * xr.z;
-    far = !(ux * ux + uy * uy + uz * uz <= cs->thr2);
-  }
-  if (far) {
+  const double *E = c.E;   // diagonal
+  const double ux = (xn[0] - xr.x) - E[0] * xr.x;
+  const double uy = (xn[1] - xr.y) - E[4] * xr.y;
+  const double uz = (xn[2] - xr.z) - E[8] * xr.z;
+  if (!(ux * ux + uy * uy + uz * uz <= c.thr2)) {
     if (!ds->request) ds->request = 1;
   }
   bool ok = true;
@@ -473,8 +422,8 @@ __device__ inline void m_mul_rn(const double *A, const double *B, double *O) {
   for (int q = 0; q < 9; ++q) O[q] = Tm[q];
 }
 
-__global__ void k_cell_advance(CellState *cs, DevStatus *ds, const double *servo) {
-  if (ds->pending) return;
+// Advance of one (sub-)scene's cell and clock.
+__device__ void cell_advance(CellState *cs, const double *servo) {
   const double dt = cs->dt;
   if (cs->periodic) {
     for (int q = 0; q < 9; ++q) {
@@ -527,11 +476,33 @@ __global__ void k_cell_advance(CellState *cs, DevStatus *ds, const double *servo
   }
   cs->iter += 1;
   cs->time = __dadd_rn(cs->time, dt);
-  if (ds->request) ds->pending = 1;
 }
 
-__global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats, SceneConst sc,
-                                long long cap, double4_32a *Fo, double4_32a *To, int mixed) {
+// One thread per sub-scene.  Every block reads "pending" before it counts itself
+// in; the last block to arrive (so every block has read it) turns a collider
+// request into "pending" and counts the step, so no block can see the flag of the
+// step it is advancing.
+__global__ void k_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo) {
+  const bool skip = *(volatile int *)&ds->pending;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!skip && q < nsub && cs[q].alive) cell_advance(cs + q, q == 0 ? servo : nullptr);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int arrived = atomicAdd(&ds->arrive, 1);
+    if (arrived == (int)gridDim.x - 1) {
+      ds->arrive = 0;
+      if (!skip) {
+        ds->steps += 1;
+        if (*(volatile int *)&ds->request) ds->pending = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
+                                const CellState *__restrict__ cs, SceneConst sc, long long cap,
+                                double4_32a *Fo, double4_32a *To, int mixed) {
   const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = (int)sl;
@@ -539,7 +510,8 @@ __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
   if (mixed) gather_rows_f32(t, s, F, T);
   else gather_rows(t, s, F, T);
   const uint8_t flags = b.flags[s];
-  if (sc.wall_mask && (flags & 0x7e)) {
+  if (sc.walls && (flags & 0x7e)) {
+    const int wmat = cs[sc.multi ? b.sid[s] : 0].wall_mat;
     const double r = b.pos[s].w;
     for (int wi = 0; wi < 6; ++wi) {
       if (!(flags & (2 << wi))) continue;
@@ -548,7 +520,7 @@ __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
       const double sn = h.w >= 0 ? 1.0 : -1.0;
       const double Fn = fabs(h.w);
       double kn, ks, tanphi;
-      wall_phys(mats, b.mat[s], r, kn, ks, tanphi);
+      wall_phys(mats, wmat, b.mat[s], r, kn, ks, tanphi);
       const double pen = Fn / kn;
       double n[3] = {0, 0, 0};
       n[ax] = sn;
@@ -674,16 +646,25 @@ inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
 }  // namespace
 
 void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                      const Mat *mats, const SceneConst &sc, long long cap, int mixed,
+                      const Mat *mats, const SceneConst &sc, long long cap, int mixed, int block,
                       cudaStream_t st) {
   if (sc.N <= 0) return;
-  if (mixed) k_integrate_mixed<<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
-  else k_integrate<false><<<blocks(sc.N), kT, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+  const unsigned g = (unsigned)((sc.N + block - 1) / block);
+  if (mixed) {
+    if (block == 128) k_integrate_mixed<128><<<g, 128, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    else if (block == 512) k_integrate_mixed<512><<<g, 512, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    else k_integrate_mixed<256><<<g, 256, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+  } else {
+    if (block == 128) k_integrate<128><<<g, 128, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    else if (block == 512) k_integrate<512><<<g, 512, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    else k_integrate<256><<<g, 256, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+  }
 }
 
-void launch_cell_advance(CellState *cs, DevStatus *ds, const double *servo_partials,
+void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
                          cudaStream_t st) {
-  k_cell_advance<<<1, 1, 0, st>>>(cs, ds, servo_partials);
+  const int threads = nsub < 128 ? 32 * ((nsub + 31) / 32) : 128;
+  k_cell_advance<<<(nsub + threads - 1) / threads, threads, 0, st>>>(cs, nsub, ds, servo_partials);
 }
 
 void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
@@ -691,10 +672,31 @@ void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, doubl
   k_servo_partials<<<kServoBlocks, kT, 0, st>>>(t, ds, mixed, partials);
 }
 
-void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats,
+void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, const CellState *cs,
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
                           int mixed, cudaStream_t st) {
-  if (sc.N > 0) k_gather_forces<<<blocks(sc.N), kT, 0, st>>>(b, t, mats, sc, cap, F, T, mixed);
+  if (sc.N > 0)
+    k_gather_forces<<<blocks(sc.N), kT, 0, st>>>(b, t, mats, cs, sc, cap, F, T, mixed);
+}
+
+__global__ void k_gather_ids(const int *__restrict__ slot_of_id, long long n,
+                             const double4_32a *__restrict__ src, double4_32a *dst) {
+  const long long i = (long long)blockIdx.x * kT + threadIdx.x;
+  if (i < n) dst[i] = src[slot_of_id[i]];
+}
+__global__ void k_gather_ids_f(const int *__restrict__ slot_of_id, long long n,
+                               const float4 *__restrict__ src, float4 *dst) {
+  const long long i = (long long)blockIdx.x * kT + threadIdx.x;
+  if (i < n) dst[i] = src[slot_of_id[i]];
+}
+
+void launch_gather_ids(const int *slot_of_id, long long n, const double4_32a *src,
+                       double4_32a *dst, cudaStream_t st) {
+  if (n > 0) k_gather_ids<<<blocks(n), kT, 0, st>>>(slot_of_id, n, src, dst);
+}
+void launch_gather_ids_f(const int *slot_of_id, long long n, const float4 *src, float4 *dst,
+                         cudaStream_t st) {
+  if (n > 0) k_gather_ids_f<<<blocks(n), kT, 0, st>>>(slot_of_id, n, src, dst);
 }
 
 int stats_blocks(long long n) {

@@ -230,6 +230,8 @@ dem_status pair_grid(int periodic, const double *H, const double lo[3], const do
   unsigned B = 1;
   while ((int)B < std::max(g.n[0], std::max(g.n[1], g.n[2]))) B <<= 1;
   g.B = (int)B;
+  g.base = 0;
+  g.morton = 1;
   return DEM_OK;
 }
 

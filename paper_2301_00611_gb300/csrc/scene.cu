@@ -96,6 +96,30 @@ void cell_derive(CellState &c) {
   }
 }
 
+// Cell state of a new (sub-)scene: periodic cell H (identity otherwise), walls of an
+// aperiodic box, wall material, gravity, damping; clock at zero.
+void init_cell(CellState &c, int periodic, const double *cell_h, const double *lo,
+               const double *hi, int wall_mask, int wall_mat, const double *gravity,
+               double damping) {
+  std::memset(&c, 0, sizeof c);
+  c.periodic = periodic ? 1 : 0;
+  for (int q = 0; q < 9; ++q) {
+    c.H[q] = periodic ? cell_h[q] : ((q % 4 == 0) ? 1.0 : 0.0);
+    c.Hprev[q] = c.H[q];
+    c.Href[q] = c.H[q];
+  }
+  m_inv(c.Href, c.Hrefinv);
+  for (int k = 0; k < 3; ++k) {
+    c.box_lo[k] = lo[k];
+    c.box_hi[k] = hi[k];
+    c.gravity[k] = gravity[k];
+  }
+  c.damping = damping;
+  c.wall_mask = periodic ? 0 : (wall_mask & 0x3F);
+  c.wall_mat = wall_mat;
+  c.alive = 1;
+}
+
 unsigned next_pow2(unsigned v) {
   unsigned p = 1;
   while (p < v) p <<= 1;
@@ -104,9 +128,25 @@ unsigned next_pow2(unsigned v) {
 }  // namespace
 
 struct Readback {
-  CellState cs;
   DevStatus ds;
   int totals[4];
+};
+
+// A sub-scene: an independent scene sharing the library's arrays with the others
+// (its own cell or box, walls, gravity, damping, time step and clock; its bodies
+// carry its index in Bodies::sid).  Sub-scene 0 is the scene of the descriptor.
+struct Sub {
+  bool used = false;
+  CellState cs{};                 // host copy (refreshed after every batch of steps)
+  long long n = 0, id0 = 0;       // bodies and first id (ids of a sub-scene are consecutive)
+  double rmin = INFINITY, rmax = 0, vsolid = 0;
+  double verlet_rule = -0.5;      // > 0 absolute sweep margin, < 0 fraction of r_min
+  bool dt_set = false;
+  Grid grid{};                    // grid of the last collider run
+  long long slot0 = 0;            // first slot (valid after a collider run)
+  bool removing = false;          // removed; its bodies go at the next collider run
+  bool velgrad_pending = false;   // velocity gradient for the next step (Cell.velGrad)
+  double velgrad_next[9]{};
 };
 
 struct dem_scene {
@@ -122,7 +162,6 @@ struct dem_scene {
   Mat *mats_d = nullptr;
 
   long long N = 0, cap = 0;
-  double rmin = INFINITY, rmax = 0, vsolid = 0;
   std::vector<double> radius_h;  // by id
   std::vector<int> mat_h;        // by id
   std::vector<unsigned char> fixed_h;
@@ -144,10 +183,24 @@ struct dem_scene {
   size_t scan_ws_bytes = 0;
   double *partials = nullptr;  // 1024 blocks x 16 doubles
   double *servo = nullptr;     // kServoBlocks x 6 doubles
+  int *deg_ws = nullptr;       // 2 x kDegreeBuckets ints (integration order)
+  // launch shapes of the step kernels (none changes a result)
+  int contact_block = 256, contact_per_sm = 8, integrate_block = 256, degree_order = 1;
   double *partials_h = nullptr;
 
-  CellState cs_h{};
-  CellState *cs_d = nullptr;
+  std::vector<Sub> subs;         // sub-scene 0 always exists
+  CellState *cs_d = nullptr;     // [subs_cap]
+  CellState *cs_rb = nullptr;    // pinned [subs_cap]: read back after each batch
+  Grid *grids_d = nullptr;       // [subs_cap]
+  int *id_shift_d = nullptr;     // [subs_cap]: id renumbering at a collider run
+  Grid *grids_h = nullptr;       // pinned [subs_cap]
+  int *shift_h = nullptr;        // pinned [subs_cap]
+  unsigned long long *bbox_keys = nullptr;   // [6 * subs_cap]
+  unsigned long long *bbox_h = nullptr;      // pinned [6 * subs_cap]
+  int subs_cap = 0;
+  unsigned long long steps_seen = 0;   // DevStatus::steps at the last read
+  CellState &cs0() { return subs[0].cs; }
+  int nsub() const { return (int)subs.size(); }
   DevStatus *ds_d = nullptr;
   Readback *rb_h = nullptr;  // pinned
   cudaEvent_t ev = nullptr;
@@ -156,12 +209,10 @@ struct dem_scene {
   bool table_fresh = false;   // table rows hold the contacts of the last completed step
   bool check_lost = false;
   bool cs_dirty = true;
-  bool dt_set = false;
-  bool has_walls = false;
+  bool layout_dirty = true;      // bodies added or removed since the last collider run
+  bool has_walls = false;        // some sub-scene has walls
   bool mixed = false;
   long long n_rebuilds = 0;
-  bool velgrad_pending = false;
-  double velgrad_next[9]{};
   bool broken = false;
   long long batch = 16;
   // timing
@@ -227,7 +278,8 @@ dem_status wait(dem_scene *s) {
 
 void free_bodies(dem_scene *s, Bodies &b) {
   dfree(s, b.pos); dfree(s, b.vel); dfree(s, b.angvel); dfree(s, b.ori); dfree(s, b.xref);
-  dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.mat); dfree(s, b.flags); dfree(s, b.whist);
+  dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.sid); dfree(s, b.mat); dfree(s, b.flags);
+  dfree(s, b.whist);
   dfree(s, b.p32); dfree(s, b.vw32); dfree(s, b.xref32); dfree(s, b.mprop32); dfree(s, b.ori32);
 }
 
@@ -236,10 +288,11 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
   if ((r = dalloc(s, &b.pos, cap)) || (r = dalloc(s, &b.vel, cap)) ||
       (r = dalloc(s, &b.angvel, cap)) || (r = dalloc(s, &b.ori, cap)) ||
       (r = dalloc(s, &b.xref, cap)) || (r = dalloc(s, &b.mprop, cap)) ||
-      (r = dalloc(s, &b.id, cap)) || (r = dalloc(s, &b.mat, cap)) ||
-      (r = dalloc(s, &b.flags, cap)))
+      (r = dalloc(s, &b.id, cap)) || (r = dalloc(s, &b.sid, cap)) ||
+      (r = dalloc(s, &b.mat, cap)) || (r = dalloc(s, &b.flags, cap)))
     return r;
-  if (s->has_walls && (r = dalloc(s, &b.whist, 6 * cap))) return r;
+  // wall histories exist for every body (a sub-scene with walls may join later)
+  if ((r = dalloc(s, &b.whist, 6 * cap))) return r;
   if (s->mixed && ((r = dalloc(s, &b.p32, cap)) || (r = dalloc(s, &b.vw32, 2 * cap)) ||
                    (r = dalloc(s, &b.xref32, cap)) || (r = dalloc(s, &b.mprop32, cap)) ||
                    (r = dalloc(s, &b.ori32, cap))))
@@ -255,7 +308,7 @@ void free_rows(dem_scene *s, Table &t) {
 
 void free_table(dem_scene *s, Table &t) {
   free_rows(s, t);
-  dfree(s, t.row_start); dfree(s, t.down_start);
+  dfree(s, t.row_start); dfree(s, t.down_start); dfree(s, t.ord);
   t.cap = 0; t.nbody_cap = 0; t.P = 0;
 }
 
@@ -283,10 +336,41 @@ dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody)
   }
   if (nbody + 1 > t.nbody_cap) {
     long long nb = std::max<long long>(nbody + 1, 64);
-    dfree(s, t.row_start); dfree(s, t.down_start);
-    if ((r = dalloc(s, &t.row_start, nb)) || (r = dalloc(s, &t.down_start, nb))) return r;
+    dfree(s, t.row_start); dfree(s, t.down_start); dfree(s, t.ord);
+    if ((r = dalloc(s, &t.row_start, nb)) || (r = dalloc(s, &t.down_start, nb)) ||
+        (r = dalloc(s, &t.ord, nb)))
+      return r;
     t.nbody_cap = nb;
   }
+  return DEM_OK;
+}
+
+// capacity of the per-sub-scene arrays (device cell states, grids, staging)
+dem_status ensure_subs(dem_scene *s, int need) {
+  if (need <= s->subs_cap) return DEM_OK;
+  const int nc = std::max(need, std::max(8, 2 * s->subs_cap));
+  CellState *cs = nullptr;
+  dem_status r;
+  if ((r = dalloc(s, &cs, nc))) return r;
+  if (s->cs_d && s->subs_cap > 0)
+    CK(cudaMemcpyAsync(cs, s->cs_d, sizeof(CellState) * s->subs_cap, cudaMemcpyDeviceToDevice, s->st));
+  if ((r = wait(s))) return r;
+  dfree(s, s->cs_d);
+  s->cs_d = cs;
+  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys);
+  if ((r = dalloc(s, &s->grids_d, nc)) || (r = dalloc(s, &s->id_shift_d, nc)) ||
+      (r = dalloc(s, &s->bbox_keys, 6LL * nc)))
+    return r;
+  if (s->cs_rb) cudaFreeHost(s->cs_rb);
+  if (s->grids_h) cudaFreeHost(s->grids_h);
+  if (s->shift_h) cudaFreeHost(s->shift_h);
+  if (s->bbox_h) cudaFreeHost(s->bbox_h);
+  s->cs_rb = nullptr; s->grids_h = nullptr; s->shift_h = nullptr; s->bbox_h = nullptr;
+  CK(cudaMallocHost((void **)&s->cs_rb, sizeof(CellState) * nc));
+  CK(cudaMallocHost((void **)&s->grids_h, sizeof(Grid) * nc));
+  CK(cudaMallocHost((void **)&s->shift_h, sizeof(int) * nc));
+  CK(cudaMallocHost((void **)&s->bbox_h, sizeof(unsigned long long) * 6 * nc));
+  s->subs_cap = nc;
   return DEM_OK;
 }
 
@@ -306,6 +390,7 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
     CK(cudaMemcpyAsync(nb.xref, s->cur.xref, d4, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.mprop, s->cur.mprop, d4, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.id, s->cur.id, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.sid, s->cur.sid, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.mat, s->cur.mat, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.flags, s->cur.flags, N, cudaMemcpyDeviceToDevice, s->st));
     if (s->has_walls)
@@ -350,21 +435,23 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
 SceneConst scene_const(const dem_scene *s) {
   SceneConst c{};
   c.N = s->N;
-  for (int k = 0; k < 3; ++k) {
-    c.gravity[k] = s->desc.gravity[k];
-    c.box_lo[k] = s->desc.box_lo[k];
-    c.box_hi[k] = s->desc.box_hi[k];
-  }
-  c.damping = s->desc.damping;
-  c.wall_mask = s->has_walls ? s->desc.wall_mask : 0;
-  c.periodic = s->desc.periodic;
+  c.walls = 0;
+  c.periodic = 0;
+  for (const Sub &u : s->subs)
+    if (u.used) {
+      c.walls |= u.cs.wall_mask ? 1 : 0;
+      c.periodic |= u.cs.periodic;
+    }
+  c.ordered = s->degree_order;
+  c.multi = s->nsub() > 1;
   return c;
 }
 
-// 0.5 * utils.PWaveTimeStep: min over spheres of SpherePWaveTimeStep = r / sqrt(E / rho)
-double default_dt(const dem_scene *s) {
+// 0.5 * utils.PWaveTimeStep: min over the sub-scene's spheres of SpherePWaveTimeStep
+// = r / sqrt(E / rho)
+double default_dt(const dem_scene *s, const Sub &u) {
   double dt = INFINITY;
-  for (long long i = 0; i < s->N; ++i) {
+  for (long long i = u.id0; i < u.id0 + u.n; ++i) {
     const Mat &m = s->mats_h[s->mat_h[i]];
     double d = s->radius_h[i] / std::sqrt(m.young / m.density);
     if (d < dt) dt = d;
@@ -372,20 +459,26 @@ double default_dt(const dem_scene *s) {
   return 0.5 * dt;
 }
 
+// every used sub-scene with bodies needs a time step; sub-scene 0 without bodies
+// and without an explicit dt is an error only when nothing else can step
 dem_status ensure_dt(dem_scene *s) {
-  if (s->dt_set) return DEM_OK;
+  for (Sub &u : s->subs) {
+    if (!u.used || u.dt_set || u.n == 0) continue;
+    u.cs.dt = default_dt(s, u);
+    u.dt_set = true;
+    s->cs_dirty = true;
+  }
   if (s->N == 0) return fail(s, DEM_ERR_STATE, "no time step: the scene has no bodies");
-  s->cs_h.dt = default_dt(s);
-  s->dt_set = true;
-  s->cs_dirty = true;
   return DEM_OK;
 }
 
 dem_status upload_cell(dem_scene *s) {
-  cell_derive(s->cs_h);
-  CK(cudaMemcpyAsync(s->cs_d, &s->cs_h, sizeof(CellState), cudaMemcpyHostToDevice, s->st));
+  for (Sub &u : s->subs) cell_derive(u.cs);
+  for (int q = 0; q < s->nsub(); ++q) s->cs_rb[q] = s->subs[q].cs;
+  CK(cudaMemcpyAsync(s->cs_d, s->cs_rb, sizeof(CellState) * s->nsub(), cudaMemcpyHostToDevice,
+                     s->st));
   s->cs_dirty = false;
-  return DEM_OK;
+  return wait(s);   // the pinned staging buffer is read again after each batch
 }
 
 dem_status status_error(dem_scene *s, int e) {
@@ -402,12 +495,13 @@ dem_status status_error(dem_scene *s, int e) {
 dem_status rebuild_core(dem_scene *s);
 
 // kernels the collider launches (bin, scan x2-3, scatter, cellsort, reorder, count,
-// scans, emit, merge, down, lost): counted approximately from its phases
+// scans, emit, down sort, degree order x3, merge, lost): counted approximately from
+// its phases
 dem_status rebuild(dem_scene *s) {
   if (s->timing) CK(cudaEventRecord(s->tev[0], s->st));
   dem_status r = rebuild_core(s);
   if (r) return r;
-  s->launches += 16;
+  s->launches += 19;
   if (s->timing) {
     CK(cudaEventRecord(s->tev[1], s->st));
     CK(cudaEventSynchronize(s->tev[1]));
@@ -419,17 +513,26 @@ dem_status rebuild(dem_scene *s) {
   return DEM_OK;
 }
 
-dem_status rebuild_core(dem_scene *s) {
-  const long long N = s->N;
-  const double verlet = s->cs_h.verlet;
+double key_value(unsigned long long k) {   // inverse of the device's ord_key
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
+}
+
+// Grid of one sub-scene: cell edge >= 2 r_max + 2 dL; periodic: the cell divided
+// into n >= 3 cells per axis; aperiodic: the bounding box [lo, hi] of its spheres.
+dem_status sub_grid(dem_scene *s, Sub &u, const double lo[3], const double hi[3], bool morton,
+                    Grid &g) {
+  const double verlet = u.cs.verlet;
   const double reach = 2 * verlet;
-  const double hmin = 2 * s->rmax + reach;
-  Grid g{};
-  g.periodic = s->desc.periodic;
+  const double hmin = 2 * u.rmax + reach;
+  g = Grid{};
+  g.periodic = u.cs.periodic;
   g.reach = reach;
   if (g.periodic) {
     for (int k = 0; k < 3; ++k) {
-      double L = s->cs_h.H[4 * k];
+      double L = u.cs.H[4 * k];
       int n = (int)std::floor(L / hmin);
       if (n < 3)
         return fail(s, DEM_ERR_GEOMETRY,
@@ -441,18 +544,6 @@ dem_status rebuild_core(dem_scene *s) {
       g.lo[k] = 0;
     }
   } else {
-    int nblk = bbox_blocks(N);
-    launch_bbox(s->cur, N, s->partials, nblk, s->st);
-    CK(cudaMemcpyAsync(s->partials_h, s->partials, sizeof(double) * 6 * nblk,
-                       cudaMemcpyDeviceToHost, s->st));
-    dem_status r = wait(s);
-    if (r) return r;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nblk; ++b)
-      for (int k = 0; k < 3; ++k) {
-        lo[k] = std::min(lo[k], s->partials_h[6 * b + k]);
-        hi[k] = std::max(hi[k], s->partials_h[6 * b + 3 + k]);
-      }
     for (int k = 0; k < 3; ++k) {
       if (!std::isfinite(lo[k]) || !std::isfinite(hi[k]))
         return fail(s, DEM_ERR_NONFINITE, "non-finite body position");
@@ -474,8 +565,69 @@ dem_status rebuild_core(dem_scene *s) {
   // FP32 coordinates are bounded by ext: a few ulps of ext plus a relative allowance
   g.slack = (float)(8.0 * ext * std::ldexp(1.0, -23) + 1e-5 * hmin);
   g.B = (int)next_pow2((unsigned)std::max(g.n[0], std::max(g.n[1], g.n[2])));
-  const long long ncell = (long long)g.B * g.B * g.B;
+  g.morton = morton ? 1 : 0;
+  return DEM_OK;
+}
+
+dem_status rebuild_core(dem_scene *s) {
+  const long long N = s->N;   // slots in use: live bodies and those of removed sub-scenes
+  const int nsub = s->nsub();
+  const bool multi = nsub > 1;
   dem_status r;
+  // 0. bounding boxes of the aperiodic sub-scenes
+  std::vector<double> lo(3 * nsub, INFINITY), hi(3 * nsub, -INFINITY);
+  bool need_box = false;
+  for (const Sub &u : s->subs) need_box |= u.used && !u.removing && u.n > 0 && !u.cs.periodic;
+  if (need_box && !multi) {
+    int nblk = bbox_blocks(N);
+    launch_bbox(s->cur, N, s->partials, nblk, s->st);
+    CK(cudaMemcpyAsync(s->partials_h, s->partials, sizeof(double) * 6 * nblk,
+                       cudaMemcpyDeviceToHost, s->st));
+    if ((r = wait(s))) return r;
+    for (int b = 0; b < nblk; ++b)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], s->partials_h[6 * b + k]);
+        hi[k] = std::max(hi[k], s->partials_h[6 * b + 3 + k]);
+      }
+  } else if (need_box) {
+    const long long cap = s->subs_cap;
+    CK(cudaMemsetAsync(s->bbox_keys, 0xff, sizeof(unsigned long long) * 3 * cap, s->st));
+    CK(cudaMemsetAsync(s->bbox_keys + 3 * cap, 0, sizeof(unsigned long long) * 3 * cap, s->st));
+    launch_bbox_sub(s->cur, N, (int)cap, s->bbox_keys, s->nsm, s->st);
+    CK(cudaMemcpyAsync(s->bbox_h, s->bbox_keys, sizeof(unsigned long long) * 6 * cap,
+                       cudaMemcpyDeviceToHost, s->st));
+    if ((r = wait(s))) return r;
+    for (int q = 0; q < nsub; ++q)
+      for (int k = 0; k < 3; ++k) {
+        lo[3 * q + k] = key_value(s->bbox_h[k * cap + q]);
+        hi[3 * q + k] = key_value(s->bbox_h[(3 + k) * cap + q]);
+      }
+  }
+  // 1. grids, one block of cells per live sub-scene (Morton order for a single scene,
+  //    row-major for sub-scenes), consecutive in sub-scene order; bodies of removed
+  //    sub-scenes take the sentinel cell after the last one
+  long long total = 0, n_live = 0;
+  bool removal = false;
+  for (int q = 0; q < nsub; ++q) {
+    Sub &u = s->subs[q];
+    Grid &g = u.grid;
+    removal |= u.removing;
+    if (!u.used || u.removing || u.n == 0) {
+      g = Grid{};
+      g.base = total;
+      continue;
+    }
+    if ((r = sub_grid(s, u, &lo[3 * q], &hi[3 * q], !multi, g))) return r;
+    g.base = total;
+    total += multi ? (long long)g.n[0] * g.n[1] * g.n[2] : (long long)g.B * g.B * g.B;
+    u.slot0 = n_live;
+    n_live += u.n;
+  }
+  if (total + 1 > 0x7fffffffLL) return fail(s, DEM_ERR_CAPACITY, "collider grid exceeds 2^31 cells");
+  const uint32_t dead = (uint32_t)total;
+  const long long ncell = total + 1;
+  for (int q = 0; q < nsub; ++q) s->grids_h[q] = s->subs[q].grid;
+  CK(cudaMemcpyAsync(s->grids_d, s->grids_h, sizeof(Grid) * nsub, cudaMemcpyHostToDevice, s->st));
   if (ncell > s->cell_cap) {
     dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
     if ((r = dalloc(s, &s->cell_count, ncell)) || (r = dalloc(s, &s->cell_start, ncell + 1)) ||
@@ -492,68 +644,109 @@ dem_status rebuild_core(dem_scene *s) {
   CK(cudaMemsetAsync(s->cell_count, 0, sizeof(int) * ncell, s->st));
   CK(cudaMemsetAsync(s->cell_fill, 0, sizeof(int) * ncell, s->st));
   CK(cudaMemsetAsync(&s->ds_d->error, 0, sizeof(int), s->st));
-  // 1-3: bin, counting sort into Morton order, permute the bodies
-  launch_bin(s->cur, N, g, s->key, s->cell_count, s->st);
+  // ids close up over removed sub-scenes: each live sub-scene's ids move down by the
+  // bodies of removed sub-scenes with smaller ids
+  const int *id_shift = nullptr;
+  if (removal) {
+    for (int q = 0; q < nsub; ++q) {
+      long long sh = 0;
+      for (const Sub &v : s->subs)
+        if (v.removing && v.id0 < s->subs[q].id0) sh += v.n;
+      s->shift_h[q] = (int)sh;
+    }
+    CK(cudaMemcpyAsync(s->id_shift_d, s->shift_h, sizeof(int) * nsub, cudaMemcpyHostToDevice,
+                       s->st));
+    id_shift = s->id_shift_d;
+  }
+  // 2-3: bin, counting sort (cell order, then id within a cell), permute the bodies
+  launch_bin(s->cur, N, s->grids_d, multi, dead, s->key, s->cell_count, s->st);
   exclusive_scan(s->cell_count, s->cell_start, ncell, s->scan_ws, s->st);
   launch_scatter(N, s->key, s->cell_start, s->cell_fill, s->new_to_old, s->st);
   launch_cellsort(s->cell_count, s->cell_start, ncell, s->cur.id, s->new_to_old, s->st);
-  launch_reorder(s->cur, s->alt, N, s->cap, s->new_to_old, s->slot_of_id, s->has_walls, s->mixed,
-                 s->st);
+  launch_reorder(s->cur, s->alt, n_live, s->cap, s->new_to_old, s->slot_of_id, s->has_walls,
+                 s->mixed, id_shift, s->st);
   std::swap(s->cur, s->alt);
+  const long long N_old = N;
+  s->N = n_live;
+  const long long NL = n_live;
   // 4: candidates (count, prefix sums, emit)
   Table &ot = s->tab[s->tc];
   Table &nt = s->tab[1 - s->tc];
-  if ((r = ensure_table(s, nt, 0, N))) return r;
-  launch_cellrec(s->cur, N, g, s->wpos, s->cinfo, s->st);
-  CK(cudaMemsetAsync(s->cnt_down, 0, sizeof(int) * N, s->st));
-  launch_count(s->wpos, s->cinfo, N, g, s->cell_count, s->cell_start, s->cnt_up, s->cnt_down,
-               &s->ds_d->error, s->st);
-  exclusive_scan(s->cnt_up, nt.row_start, N, s->scan_ws, s->st);
-  exclusive_scan(s->cnt_down, nt.down_start, N, s->scan_ws, s->st);
-  CK(cudaMemcpyAsync(&s->rb_h->totals[0], nt.row_start + N, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-  CK(cudaMemcpyAsync(&s->rb_h->totals[1], nt.down_start + N, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if ((r = ensure_table(s, nt, 0, NL))) return r;
+  launch_cellrec(s->cur, NL, s->grids_d, multi, s->wpos, s->cinfo, s->st);
+  CK(cudaMemsetAsync(s->cnt_down, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
+  launch_count(s->wpos, s->cinfo, s->cur.sid, NL, s->grids_d, multi, s->cell_count,
+               s->cell_start, s->cnt_up, s->cnt_down, &s->ds_d->error, s->st);
+  exclusive_scan(s->cnt_up, nt.row_start, NL, s->scan_ws, s->st);
+  exclusive_scan(s->cnt_down, nt.down_start, NL, s->scan_ws, s->st);
+  CK(cudaMemcpyAsync(&s->rb_h->totals[0], nt.row_start + NL, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&s->rb_h->totals[1], nt.down_start + NL, sizeof(int), cudaMemcpyDeviceToHost, s->st));
   CK(cudaMemcpyAsync(&s->rb_h->ds, s->ds_d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->st));
   if ((r = wait(s))) return r;
   if (s->rb_h->ds.error) return status_error(s, s->rb_h->ds.error);
   const long long P = s->rb_h->totals[0];
   if (P != s->rb_h->totals[1]) return fail(s, DEM_ERR_STATE, "internal: candidate count mismatch");
-  if ((r = ensure_table(s, nt, P, N))) return r;
+  if ((r = ensure_table(s, nt, P, NL))) return r;
   nt.P = P;
   int *dfill = reinterpret_cast<int *>(s->key);   // the bin keys are no longer needed
-  CK(cudaMemsetAsync(dfill, 0, sizeof(int) * N, s->st));
-  launch_emit(s->wpos, s->cinfo, s->cur, N, g, s->cell_count, s->cell_start, nt, dfill, s->mixed,
-              s->st);
-  launch_downsort(nt, N, s->st);
+  CK(cudaMemsetAsync(dfill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
+  launch_emit(s->wpos, s->cinfo, s->cur, NL, s->grids_d, multi, s->cell_count, s->cell_start, nt,
+              dfill, s->mixed, s->st);
+  launch_downsort(nt, NL, s->st);
+  CK(cudaMemsetAsync(s->deg_ws, 0, sizeof(int) * 2 * kDegreeBuckets, s->st));
+  launch_degree_order(nt, NL, s->deg_ws, s->st);
   // 5: carry the contact history of the previous table
   ot.P = std::min(ot.P, ot.cap);
   if (ot.P > 0) CK(cudaMemsetAsync(ot.found, 0, sizeof(int) * ot.P, s->st));
   Table otv = ot;
   if (ot.P == 0 || ot.row_start == nullptr) otv.P = 0;
   launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->mixed, s->st);
-  if (s->check_lost) launch_lost(otv, &s->ds_d->error, s->mixed, s->st);
-  s->tab_nbody[1 - s->tc] = N;
+  // a removed sub-scene's contacts vanish by design: no history check on that run
+  if (s->check_lost && !removal) launch_lost(otv, &s->ds_d->error, s->mixed, s->st);
+  (void)N_old;
+  s->tab_nbody[1 - s->tc] = NL;
   s->tc = 1 - s->tc;
+  // host bookkeeping of removals: ids and per-id host arrays close up
+  if (removal) {
+    std::vector<const Sub *> gone;   // erase id ranges from the highest down
+    for (const Sub &u : s->subs)
+      if (u.removing) gone.push_back(&u);
+    std::sort(gone.begin(), gone.end(), [](const Sub *a, const Sub *b) { return a->id0 > b->id0; });
+    for (const Sub *u : gone) {
+      s->radius_h.erase(s->radius_h.begin() + u->id0, s->radius_h.begin() + u->id0 + u->n);
+      s->mat_h.erase(s->mat_h.begin() + u->id0, s->mat_h.begin() + u->id0 + u->n);
+      s->fixed_h.erase(s->fixed_h.begin() + u->id0, s->fixed_h.begin() + u->id0 + u->n);
+    }
+    for (int q = 0; q < nsub; ++q) s->subs[q].id0 -= s->shift_h[q];
+    for (Sub &u : s->subs)
+      if (u.removing) u = Sub{};   // free slot (used = false, cs.alive = 0)
+  }
   // reference configuration of this collider run
-  std::memcpy(s->cs_h.Href, s->cs_h.H, sizeof s->cs_h.H);
-  if (!m_inv(s->cs_h.Href, s->cs_h.Hrefinv))
-    return fail(s, DEM_ERR_INVALID_ARG, "singular periodic cell");
+  for (Sub &u : s->subs) {
+    if (!u.used) continue;
+    std::memcpy(u.cs.Href, u.cs.H, sizeof u.cs.H);
+    if (!m_inv(u.cs.Href, u.cs.Hrefinv)) return fail(s, DEM_ERR_INVALID_ARG, "singular periodic cell");
+  }
   if ((r = upload_cell(s))) return r;
   // clear pending/request; the error word keeps the history check of this run,
   // which the host reads with the next status block
   CK(cudaMemsetAsync(s->ds_d, 0, 2 * sizeof(int), s->st));
   s->need_rebuild = false;
+  s->layout_dirty = false;
   s->check_lost = true;
   s->n_rebuilds += 1;
   CK(cudaGetLastError());
   return DEM_OK;
 }
 
+// status block and every sub-scene's cell state (clock, cell, servo gradient)
 dem_status read_status(dem_scene *s) {
-  CK(cudaMemcpyAsync(&s->rb_h->cs, s->cs_d, sizeof(CellState), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(s->cs_rb, s->cs_d, sizeof(CellState) * s->nsub(), cudaMemcpyDeviceToHost,
+                     s->st));
   CK(cudaMemcpyAsync(&s->rb_h->ds, s->ds_d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->st));
   dem_status r = wait(s);
   if (r) return r;
-  s->cs_h = s->rb_h->cs;
+  for (int q = 0; q < s->nsub(); ++q) s->subs[q].cs = s->cs_rb[q];
   return DEM_OK;
 }
 
@@ -562,13 +755,14 @@ dem_status sync_host(dem_scene *s) {
   return wait(s);
 }
 
-// Bring pending host-side changes (velGrad, dt) into the device cell state.
+// Bring pending host-side changes (velGrad, dt) into the device cell states.
 dem_status prepare_step(dem_scene *s) {
-  if (s->velgrad_pending) {
-    std::memcpy(s->cs_h.L, s->velgrad_next, sizeof s->velgrad_next);
-    s->velgrad_pending = false;
-    s->cs_dirty = true;
-  }
+  for (Sub &u : s->subs)
+    if (u.velgrad_pending) {
+      std::memcpy(u.cs.L, u.velgrad_next, sizeof u.velgrad_next);
+      u.velgrad_pending = false;
+      s->cs_dirty = true;
+    }
   if (s->cs_dirty) return upload_cell(s);
   return DEM_OK;
 }
@@ -679,22 +873,22 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
     dem_scene_destroy(s);
     return DEM_ERR_CUDA;
   }
-  if (dalloc(s, &s->mats_d, kMaxMat) || dalloc(s, &s->cs_d, 1) || dalloc(s, &s->ds_d, 1) ||
-      dalloc(s, &s->partials, 1024 * 16) || dalloc(s, &s->servo, kServoBlocks * 6)) {
+  if (dalloc(s, &s->mats_d, kMaxMat) || dalloc(s, &s->ds_d, 1) ||
+      dalloc(s, &s->partials, 1024 * 16) || dalloc(s, &s->servo, kServoBlocks * 6) ||
+      dalloc(s, &s->deg_ws, 2 * kDegreeBuckets) || ensure_subs(s, 1)) {
     g_create_error = s->err;
     dem_scene_destroy(s);
     return DEM_ERR_OOM;
   }
-  // cell state
-  CellState &c = s->cs_h;
+  // sub-scene 0: the scene of the descriptor
+  s->subs.resize(1);
+  Sub &u0 = s->subs[0];
+  u0.used = true;
+  u0.verlet_rule = desc->verlet_dist;
+  CellState &c = u0.cs;
   std::memset(&c, 0, sizeof c);
-  c.periodic = s->desc.periodic;
-  for (int q = 0; q < 9; ++q) {
-    c.H[q] = s->desc.periodic ? s->desc.cell_h[q] : ((q % 4 == 0) ? 1.0 : 0.0);
-    c.Hprev[q] = c.H[q];
-    c.Href[q] = c.H[q];
-  }
-  m_inv(c.Href, c.Hrefinv);
+  init_cell(c, s->desc.periodic, s->desc.cell_h, s->desc.box_lo, s->desc.box_hi,
+            s->has_walls ? s->desc.wall_mask : 0, 0, s->desc.gravity, s->desc.damping);
   DevStatus z{};
   if ((e = cudaMemcpyAsync(s->ds_d, &z, sizeof z, cudaMemcpyHostToDevice, s->st)) != cudaSuccess) {
     bad(e, "status init");
@@ -713,8 +907,8 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
     dem_scene_destroy(s);
     return DEM_ERR_OOM;
   }
-  s->dt_set = desc->dt > 0;
-  c.dt = s->dt_set ? desc->dt : 0;
+  u0.dt_set = desc->dt > 0;
+  c.dt = u0.dt_set ? desc->dt : 0;
   *out = s;
   return DEM_OK;
 }
@@ -729,9 +923,14 @@ void dem_scene_destroy(dem_scene *s) {
   dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
   dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
-  dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo);
+  dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo); dfree(s, s->deg_ws);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
+  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys);
   if (s->st) cudaStreamSynchronize(s->st);
+  if (s->cs_rb) cudaFreeHost(s->cs_rb);
+  if (s->grids_h) cudaFreeHost(s->grids_h);
+  if (s->shift_h) cudaFreeHost(s->shift_h);
+  if (s->bbox_h) cudaFreeHost(s->bbox_h);
   if (s->rb_h) cudaFreeHost(s->rb_h);
   if (s->partials_h) cudaFreeHost(s->partials_h);
   if (s->ev) cudaEventDestroy(s->ev);
@@ -743,7 +942,7 @@ void dem_scene_destroy(dem_scene *s) {
 dem_status dem_set_material(dem_scene *s, int mat, double density, double young, double poisson,
                             double friction) {
   if (!s) return DEM_ERR_INVALID_ARG;
-  if (mat < 0 || mat >= kMaxMat) return fail(s, DEM_ERR_INVALID_ARG, "material id out of [0, 63]");
+  if (mat < 0 || mat >= kMaxMat) return fail(s, DEM_ERR_INVALID_ARG, "material id out of [0, 4095]");
   if (!(density > 0) || !(young > 0) || !(poisson >= 0) || !(friction >= 0) ||
       !(friction < 1.5707963267948966) || !std::isfinite(density) || !std::isfinite(young) ||
       !std::isfinite(poisson))
@@ -755,15 +954,23 @@ dem_status dem_set_material(dem_scene *s, int mat, double density, double young,
   return sync_host(s);
 }
 
-dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const double *radius,
-                           const int *mat, const double *vel, const double *angvel,
-                           const unsigned char *fixed, long long *first_id) {
-  if (!s) return DEM_ERR_INVALID_ARG;
+namespace {
+dem_status add_spheres_sub(dem_scene *s, int q, long long n, const double *pos,
+                           const double *radius, const int *mat, const double *vel,
+                           const double *angvel, const unsigned char *fixed, long long *first_id) {
   if (n < 0) return fail(s, DEM_ERR_INVALID_ARG, "negative count");
+  if (q < 0 || q >= s->nsub() || !s->subs[q].used || s->subs[q].removing)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  Sub &u = s->subs[q];
   if (n == 0) {
-    if (first_id) *first_id = s->N;
+    if (first_id) *first_id = u.n ? u.id0 : s->N;
     return DEM_OK;
   }
+  // the ids of a sub-scene are consecutive: only the sub-scene holding the last ids
+  // (or an empty one) can grow
+  if (u.n > 0 && u.id0 + u.n != s->N)
+    return fail(s, DEM_ERR_UNSUPPORTED,
+                "spheres can be added only to the sub-scene that received the last ones");
   if (!pos || !radius) return fail(s, DEM_ERR_INVALID_ARG, "null pos or radius");
   if (s->N + n > 0x7fffffffLL) return fail(s, DEM_ERR_CAPACITY, "more than 2^31-1 bodies");
   for (long long i = 0; i < n; ++i) {
@@ -782,7 +989,7 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
   if ((r = sync_host(s))) return r;
   if ((r = ensure_bodies(s, s->N + n))) return r;
   std::vector<double4_32a> P(n), V(n), A(n), O(n), M(n);
-  std::vector<int> ID(n), MT(n);
+  std::vector<int> ID(n), MT(n), SU(n, q);
   std::vector<uint8_t> FL(n);
   std::vector<int> SL(n);
   const double pi = 3.14159265358979323846;
@@ -802,9 +1009,9 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
     MT[t] = m;
     FL[t] = (fixed && fixed[t]) ? 1 : 0;
     SL[t] = (int)(s->N + t);
-    s->rmin = std::min(s->rmin, rr);
-    s->rmax = std::max(s->rmax, rr);
-    s->vsolid += (4.0 / 3.0) * pi * rr * rr * rr;
+    u.rmin = std::min(u.rmin, rr);
+    u.rmax = std::max(u.rmax, rr);
+    u.vsolid += (4.0 / 3.0) * pi * rr * rr * rr;
     s->radius_h.push_back(rr);
     s->mat_h.push_back(m);
     s->fixed_h.push_back(FL[t]);
@@ -818,11 +1025,11 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
   CK(cudaMemcpyAsync(s->cur.xref + o, P.data(), d4, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.mprop + o, M.data(), d4, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.id + o, ID.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->cur.sid + o, SU.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.mat + o, MT.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.flags + o, FL.data(), n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->slot_of_id + o, SL.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
-  if (s->has_walls)
-    for (int w = 0; w < 6; ++w) CK(cudaMemsetAsync(s->cur.whist + w * s->cap + o, 0, d4, s->st));
+  for (int w = 0; w < 6; ++w) CK(cudaMemsetAsync(s->cur.whist + w * s->cap + o, 0, d4, s->st));
   if (s->mixed) {   // FP32 mirrors of the new bodies (the collider run refreshes p32, vw32)
     std::vector<float4> M32(n), O32(n, make_float4(1, 0, 0, 0));
     for (long long t = 0; t < n; ++t)
@@ -831,23 +1038,35 @@ dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const d
     CK(cudaMemcpyAsync(s->cur.ori32 + o, O32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st));
   }
   if (first_id) *first_id = s->N;
+  if (u.n == 0) u.id0 = s->N;
+  u.n += n;
   s->N += n;
   s->need_rebuild = true;
+  s->layout_dirty = true;
   s->table_fresh = false;
   s->check_lost = false;
   // sweep margin: > 0 absolute, < 0 fraction of the smallest radius
-  double vd = s->desc.verlet_dist;
-  s->cs_h.verlet = vd > 0 ? vd : (vd < 0 ? -vd * s->rmin : 0.5 * s->rmin);
-  s->cs_h.rmax = s->rmax;
+  const double vd = u.verlet_rule;
+  u.cs.verlet = vd > 0 ? vd : (vd < 0 ? -vd * u.rmin : 0.5 * u.rmin);
+  u.cs.rmax = u.rmax;
   s->cs_dirty = true;
   return sync_host(s);
 }
+}  // namespace
+
+dem_status dem_add_spheres(dem_scene *s, long long n, const double *pos, const double *radius,
+                           const int *mat, const double *vel, const double *angvel,
+                           const unsigned char *fixed, long long *first_id) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  return add_spheres_sub(s, 0, n, pos, radius, mat, vel, angvel, fixed, first_id);
+}
+
 
 dem_status dem_set_dt(dem_scene *s, double dt) {
   if (!s) return DEM_ERR_INVALID_ARG;
   if (!(dt > 0) || !std::isfinite(dt)) return fail(s, DEM_ERR_INVALID_ARG, "dt must be positive");
-  s->cs_h.dt = dt;
-  s->dt_set = true;
+  s->cs0().dt = dt;
+  s->subs[0].dt_set = true;
   s->cs_dirty = true;
   return DEM_OK;
 }
@@ -856,7 +1075,7 @@ dem_status dem_get_dt(dem_scene *s, double *dt) {
   if (!s || !dt) return DEM_ERR_INVALID_ARG;
   dem_status r = ensure_dt(s);
   if (r) return r;
-  *dt = s->cs_h.dt;
+  *dt = s->cs0().dt;
   return DEM_OK;
 }
 
@@ -864,6 +1083,8 @@ dem_status dem_set_triax(dem_scene *s, const double *goal, int stress_mask,
                          const double *max_rate, double grow_damping, int glob_update) {
   if (!s) return DEM_ERR_INVALID_ARG;
   if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the stress servo needs a periodic scene");
+  if (s->nsub() > 1)
+    return fail(s, DEM_ERR_UNSUPPORTED, "the stress servo runs on a scene without sub-scenes");
   if (!goal || !max_rate || glob_update < 1 || !(grow_damping >= 0) || !(grow_damping < 1))
     return fail(s, DEM_ERR_INVALID_ARG, "bad servo parameters");
   for (int a = 0; a < 3; ++a)
@@ -872,13 +1093,13 @@ dem_status dem_set_triax(dem_scene *s, const double *goal, int stress_mask,
   dem_status r;
   if ((r = sync_host(s))) return r;
   for (int a = 0; a < 3; ++a) {
-    s->cs_h.goal[a] = goal[a];
-    s->cs_h.max_rate[a] = max_rate[a];
+    s->cs0().goal[a] = goal[a];
+    s->cs0().max_rate[a] = max_rate[a];
   }
-  s->cs_h.stress_mask = stress_mask & 7;
-  s->cs_h.grow_damping = grow_damping;
-  s->cs_h.glob_update = glob_update;
-  s->cs_h.triax = 1;
+  s->cs0().stress_mask = stress_mask & 7;
+  s->cs0().grow_damping = grow_damping;
+  s->cs0().glob_update = glob_update;
+  s->cs0().triax = 1;
   s->cs_dirty = true;
   return DEM_OK;
 }
@@ -889,8 +1110,8 @@ dem_status dem_set_cell_velgrad(dem_scene *s, const double *L) {
   if (!is_diag(L)) return fail(s, DEM_ERR_UNSUPPORTED, "only a diagonal velGrad is supported");
   for (int q = 0; q < 9; ++q)
     if (!std::isfinite(L[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite velGrad");
-  std::memcpy(s->velgrad_next, L, sizeof s->velgrad_next);
-  s->velgrad_pending = true;
+  std::memcpy(s->subs[0].velgrad_next, L, sizeof s->subs[0].velgrad_next);
+  s->subs[0].velgrad_pending = true;
   return DEM_OK;
 }
 
@@ -902,9 +1123,14 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
   if (nsteps == 0) return DEM_OK;
   dem_status r;
   if (s->N == 0) {
-    if (!s->dt_set) return fail(s, DEM_ERR_STATE, "no bodies and no time step");
-    for (long long k = 0; k < nsteps; ++k) s->cs_h.time += s->cs_h.dt;
-    s->cs_h.iter += nsteps;
+    bool any = false;
+    for (Sub &u : s->subs) {
+      if (!u.used || !u.dt_set) continue;
+      for (long long k = 0; k < nsteps; ++k) u.cs.time += u.cs.dt;
+      u.cs.iter += nsteps;
+      any = true;
+    }
+    if (!any) return fail(s, DEM_ERR_STATE, "no bodies and no time step");
     s->cs_dirty = true;
     return DEM_OK;
   }
@@ -915,22 +1141,28 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
   while (remaining > 0) {
     if (s->need_rebuild && (r = rebuild(s))) return r;
     const long long B = std::min<long long>(remaining, s->batch);
-    const long long it0 = s->cs_h.iter;
+    const long long it0 = s->cs0().iter;
     const Table &t = s->tab[s->tc];
     cudaEvent_t *ev = s->timing ? s->tev.data() + 2 : nullptr;
     for (long long i = 0; i < B; ++i) {
       if (ev) CK(cudaEventRecord(ev[6 * i], s->st));
       if (s->mixed)
-        launch_contact_mixed(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
+        launch_contact_mixed(t, s->cur, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
+                             s->contact_block, s->contact_per_sm, s->st);
       else
-        launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, s->desc.periodic, s->nsm, s->st);
+        launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
+                       s->contact_block, s->contact_per_sm, s->st);
       if (ev) { CK(cudaEventRecord(ev[6 * i + 1], s->st)); CK(cudaEventRecord(ev[6 * i + 2], s->st)); }
-      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->mixed, s->st);
+      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->mixed,
+                       s->integrate_block, s->st);
       if (ev) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
       // servo update steps (PeriTriaxController every glob_update steps)
-      const bool upd = s->cs_h.triax && ((it0 + i + 1) % s->cs_h.glob_update == 0);
-      if (upd) launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
-      launch_cell_advance(s->cs_d, s->ds_d, upd ? s->servo : nullptr, s->st);
+      const bool upd = !sc.multi && s->cs0().triax && ((it0 + i + 1) % s->cs0().glob_update == 0);
+      if (upd) {
+        launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
+        s->launches += 1;
+      }
+      launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st);
       if (ev) CK(cudaEventRecord(ev[6 * i + 5], s->st));
     }
     s->launches += B * ((t.P > 0 ? 1 : 0) + 2);
@@ -953,7 +1185,8 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
       s->tm.rows_processed += B * t.P;
     }
     const DevStatus ds = s->rb_h->ds;
-    const long long done = s->cs_h.iter - it0;
+    const long long done = (long long)(ds.steps - s->steps_seen);
+    s->steps_seen = ds.steps;
     if (ds.error) return status_error(s, ds.error);
     remaining -= done;
     if (ds.pending) {
@@ -1022,8 +1255,8 @@ dem_status dem_get_state(dem_scene *s, double *pos, double *vel, double *angvel,
       if (torque) std::memset(torque, 0, sizeof(double) * 3 * s->N);
       return DEM_OK;
     }
-    launch_gather_forces(s->cur, s->tab[s->tc], s->mats_d, scene_const(s), s->cap, s->gF, s->gT,
-                         s->mixed, s->st);
+    launch_gather_forces(s->cur, s->tab[s->tc], s->mats_d, s->cs_d, scene_const(s), s->cap,
+                         s->gF, s->gT, s->mixed, s->st);
     CK(cudaGetLastError());
     if (force && (r = fetch4(s, s->gF, sid, force, 3))) return r;
     if (torque && (r = fetch4(s, s->gT, sid, torque, 3))) return r;
@@ -1081,10 +1314,12 @@ dem_status dem_get_cell(dem_scene *s, double *H, double *velgrad, double *prev_v
   if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the scene is not periodic");
   dem_status r;
   if ((r = sync_host(s))) return r;
-  if (H) std::memcpy(H, s->cs_h.H, sizeof s->cs_h.H);
-  if (velgrad) std::memcpy(velgrad, s->velgrad_pending ? s->velgrad_next : s->cs_h.L, sizeof s->cs_h.L);
-  if (prev_velgrad) std::memcpy(prev_velgrad, s->cs_h.Lprev, sizeof s->cs_h.Lprev);
-  if (prev_H) std::memcpy(prev_H, s->cs_h.Hprev, sizeof s->cs_h.Hprev);
+  if (H) std::memcpy(H, s->cs0().H, sizeof s->cs0().H);
+  if (velgrad)
+    std::memcpy(velgrad, s->subs[0].velgrad_pending ? s->subs[0].velgrad_next : s->cs0().L,
+                sizeof s->cs0().L);
+  if (prev_velgrad) std::memcpy(prev_velgrad, s->cs0().Lprev, sizeof s->cs0().Lprev);
+  if (prev_H) std::memcpy(prev_H, s->cs0().Hprev, sizeof s->cs0().Hprev);
   return DEM_OK;
 }
 
@@ -1103,17 +1338,17 @@ dem_status dem_set_cell(dem_scene *s, const double *H, const double *velgrad,
   dem_status r;
   if ((r = sync_host(s))) return r;
   if (H) {
-    std::memcpy(s->cs_h.H, H, sizeof s->cs_h.H);
+    std::memcpy(s->cs0().H, H, sizeof s->cs0().H);
     s->need_rebuild = true;
     s->table_fresh = false;
     s->check_lost = false;
   }
   if (velgrad) {
-    std::memcpy(s->cs_h.L, velgrad, sizeof s->cs_h.L);
-    s->velgrad_pending = false;
+    std::memcpy(s->cs0().L, velgrad, sizeof s->cs0().L);
+    s->subs[0].velgrad_pending = false;
   }
-  if (prev_velgrad) std::memcpy(s->cs_h.Lprev, prev_velgrad, sizeof s->cs_h.Lprev);
-  if (prev_H) std::memcpy(s->cs_h.Hprev, prev_H, sizeof s->cs_h.Hprev);
+  if (prev_velgrad) std::memcpy(s->cs0().Lprev, prev_velgrad, sizeof s->cs0().Lprev);
+  if (prev_H) std::memcpy(s->cs0().Hprev, prev_H, sizeof s->cs0().Hprev);
   s->cs_dirty = true;
   return DEM_OK;
 }
@@ -1122,8 +1357,8 @@ dem_status dem_get_clock(dem_scene *s, long long *iter, double *time) {
   if (!s) return DEM_ERR_INVALID_ARG;
   dem_status r;
   if ((r = sync_host(s))) return r;
-  if (iter) *iter = s->cs_h.iter;
-  if (time) *time = s->cs_h.time;
+  if (iter) *iter = s->cs0().iter;
+  if (time) *time = s->cs0().time;
   return DEM_OK;
 }
 
@@ -1132,8 +1367,8 @@ dem_status dem_set_clock(dem_scene *s, long long iter, double time) {
   if (iter < 0 || !std::isfinite(time)) return fail(s, DEM_ERR_INVALID_ARG, "bad clock");
   dem_status r;
   if ((r = sync_host(s))) return r;
-  s->cs_h.iter = iter;
-  s->cs_h.time = time;
+  s->cs0().iter = iter;
+  s->cs0().time = time;
   s->cs_dirty = true;
   return DEM_OK;
 }
@@ -1144,8 +1379,9 @@ struct HostContact {
   double fn[3], fs[3], n[3], cp[3], phys[3], pen;
 };
 
-void wall_phys_h(const dem_scene *s, int mat, double r, double &kn, double &ks, double &tp) {
-  const Mat &mw = s->mats_h[0], &ms = s->mats_h[mat];
+void wall_phys_h(const dem_scene *s, int wmat, int mat, double r, double &kn, double &ks,
+                 double &tp) {
+  const Mat &mw = s->mats_h[wmat], &ms = s->mats_h[mat];
   double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
   kn = k1 * k2 / (k1 + k2);
   double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
@@ -1235,6 +1471,10 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
     out.push_back(h);
   }
   if (s->has_walls) {
+    std::vector<int> wmat(N, 0);   // wall material of each id's sub-scene
+    for (const Sub &u : s->subs)
+      if (u.used || u.removing)
+        for (long long i = u.id0; i < u.id0 + u.n && i < N; ++i) wmat[i] = u.cs.wall_mat;
     for (long long sl = 0; sl < N; ++sl) {
       if (!(flags[sl] & 0x7e)) continue;
       for (int w = 0; w < 6; ++w) {
@@ -1247,7 +1487,7 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
         h.id2 = id[sl];
         double kn, ks, tanp;
         const double rr = pos[sl].w;
-        wall_phys_h(s, s->mat_h[id[sl]], rr, kn, ks, tanp);
+        wall_phys_h(s, wmat[id[sl]], s->mat_h[id[sl]], rr, kn, ks, tanp);
         h.n[ax] = sn;
         h.fn[ax] = sn * Fn;
         h.fs[0] = hw.x; h.fs[1] = hw.y; h.fs[2] = hw.z;
@@ -1435,52 +1675,87 @@ dem_status dem_get_timing(dem_scene *s, dem_timing *out) {
   return DEM_OK;
 }
 
-dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
-  if (!s || !o) return DEM_ERR_INVALID_ARG;
+namespace {
+Bodies body_view(const Bodies &b, long long o) {
+  Bodies v = b;
+  auto sh = [o](auto *&p, long long k = 1) { if (p) p += k * o; };
+  sh(v.pos); sh(v.vel); sh(v.angvel); sh(v.ori); sh(v.xref); sh(v.mprop);
+  sh(v.id); sh(v.sid); sh(v.mat); sh(v.flags); sh(v.whist);
+  sh(v.p32); sh(v.vw32, 2); sh(v.xref32); sh(v.mprop32); sh(v.ori32);
+  return v;
+}
+Table row_view(const Table &t, long long o, long long P) {
+  Table v = t;
+  auto sh = [o](auto *&p) { if (p) p += o; };
+  sh(v.pair); sh(v.cpack); sh(v.hfs); sh(v.hn); sh(v.oF); sh(v.oM); sh(v.tanphi);
+  sh(v.g32); sh(v.hn32); sh(v.oF32); sh(v.oM32); sh(v.found);
+  v.P = P;
+  return v;
+}
+
+// Statistics of sub-scene q (q < 0: of the whole scene, geometry of sub-scene 0).
+dem_status stats_of(dem_scene *s, int q, dem_stats *o) {
   dem_status r;
   if ((r = sync_host(s))) return r;
   std::memset(o, 0, sizeof *o);
-  o->iter = s->cs_h.iter;
-  o->time = s->cs_h.time;
-  o->dt = s->cs_h.dt;
-  o->n_bodies = s->N;
+  const Sub &u = s->subs[q < 0 ? 0 : q];
+  o->iter = u.cs.iter;
+  o->time = u.cs.time;
+  o->dt = u.cs.dt;
   o->n_rebuilds = s->n_rebuilds;
+  long long b0 = 0, nb_ = s->N;
+  double vsolid = 0;
+  for (const Sub &v : s->subs) vsolid += v.used ? v.vsolid : 0;
+  if (q >= 0) { b0 = u.slot0; nb_ = u.n; vsolid = u.vsolid; }
+  o->n_bodies = nb_;
   double V;
-  if (s->desc.periodic) V = std::fabs(m_det(s->cs_h.H));
-  else V = (s->desc.box_hi[0] - s->desc.box_lo[0]) * (s->desc.box_hi[1] - s->desc.box_lo[1]) *
-           (s->desc.box_hi[2] - s->desc.box_lo[2]);
-  o->packing_fraction = V > 0 ? s->vsolid / V : 0;
-  if (s->N == 0) return DEM_OK;
+  if (u.cs.periodic) V = std::fabs(m_det(u.cs.H));
+  else V = (u.cs.box_hi[0] - u.cs.box_lo[0]) * (u.cs.box_hi[1] - u.cs.box_lo[1]) *
+           (u.cs.box_hi[2] - u.cs.box_lo[2]);
+  o->packing_fraction = V > 0 ? vsolid / V : 0;
+  if (nb_ == 0) return DEM_OK;
   const bool have_table = s->table_fresh;
   const Table &t = s->tab[s->tc];
   const SceneConst sc = scene_const(s);
-  o->n_candidates = have_table ? t.P : 0;
+  long long r0 = 0, r1 = have_table ? t.P : 0;
+  if (q >= 0 && have_table) {   // rows whose first body is in the sub-scene
+    CK(cudaMemcpyAsync(&s->rb_h->totals[0], t.row_start + b0, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(&s->rb_h->totals[1], t.row_start + b0 + nb_, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    if ((r = wait(s))) return r;
+    r0 = s->rb_h->totals[0];
+    r1 = s->rb_h->totals[1];
+  }
+  o->n_candidates = r1 - r0;
   double *ph = s->partials_h;
   // bodies: kinetic energy, |F| of free bodies
   if (have_table)
-    launch_gather_forces(s->cur, t, s->mats_d, sc, s->cap, s->gF, s->gT, s->mixed, s->st);
+    launch_gather_forces(s->cur, t, s->mats_d, s->cs_d, sc, s->cap, s->gF, s->gT, s->mixed, s->st);
   else CK(cudaMemsetAsync(s->gF, 0, sizeof(double4_32a) * s->N, s->st));
-  int nb = stats_blocks(s->N);
-  launch_body_stats(s->cur, s->gF, s->N, s->partials, s->st);
+  const Bodies bv = body_view(s->cur, b0);
+  int nb = stats_blocks(nb_);
+  launch_body_stats(bv, s->gF + b0, nb_, s->partials, s->st);
   CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s->st));
   if ((r = wait(s))) return r;
   double ke = 0, sumF = 0, ndyn = 0;
   for (int b = 0; b < nb; ++b) { ke += ph[3 * b]; sumF += ph[3 * b + 1]; ndyn += ph[3 * b + 2]; }
   double nc = 0, sumC = 0, sig[9] = {0};
-  if (have_table && t.P > 0) {
-    int nr = stats_blocks(t.P);
-    launch_row_stats(t, s->cur, s->partials, s->mixed, s->st);
+  if (have_table && r1 > r0) {
+    const Table tv = row_view(t, r0, r1 - r0);
+    int nr = stats_blocks(tv.P);
+    launch_row_stats(tv, bv, s->partials, s->mixed, s->st);
     CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 11 * nr, cudaMemcpyDeviceToHost, s->st));
     if ((r = wait(s))) return r;
     for (int b = 0; b < nr; ++b) {
       nc += ph[11 * b];
       sumC += ph[11 * b + 1];
-      for (int q = 0; q < 9; ++q) sig[q] += ph[11 * b + 2 + q];
+      for (int k = 0; k < 9; ++k) sig[k] += ph[11 * b + 2 + k];
     }
   }
   double nw = 0, sumW = 0;
   if (s->has_walls) {
-    launch_wall_stats(s->cur, sc, s->mats_d, s->cap, s->partials, s->st);
+    SceneConst sv = sc;
+    sv.N = nb_;
+    launch_wall_stats(bv, sv, s->mats_d, s->cap, s->partials, s->st);
     CK(cudaMemcpyAsync(ph, s->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s->st));
     if ((r = wait(s))) return r;
     for (int b = 0; b < nb; ++b) { nw += ph[2 * b]; sumW += ph[2 * b + 1]; }
@@ -1490,9 +1765,278 @@ dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
   o->n_wall_contacts = (long long)nw;
   const double call = nc + nw;
   o->unbalanced_force = (call > 0 && ndyn > 0) ? (sumF / ndyn) / ((sumC + sumW) / call) : NAN;
-  o->coordination = 2.0 * nc / s->N;
-  for (int q = 0; q < 9; ++q) o->stress[q] = V > 0 ? sig[q] / V : 0;
+  o->coordination = 2.0 * nc / nb_;
+  for (int k = 0; k < 9; ++k) o->stress[k] = V > 0 ? sig[k] / V : 0;
   return DEM_OK;
+}
+}  // namespace
+
+dem_status dem_get_stats(dem_scene *s, dem_stats *o) {
+  if (!s || !o) return DEM_ERR_INVALID_ARG;
+  return stats_of(s, -1, o);
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ launch shapes
+namespace {
+bool valid_tuning(const dem_tuning &t) {
+  return (t.contact_block == 128 || t.contact_block == 256) && t.contact_blocks_per_sm >= 1 &&
+         t.contact_blocks_per_sm <= 64 &&
+         (t.integrate_block == 128 || t.integrate_block == 256 || t.integrate_block == 512) &&
+         (t.degree_order == 0 || t.degree_order == 1);
+}
+void apply_tuning(dem_scene *s, const dem_tuning &t) {
+  s->contact_block = t.contact_block;
+  s->contact_per_sm = t.contact_blocks_per_sm;
+  s->integrate_block = t.integrate_block;
+  s->degree_order = t.degree_order;
+}
+dem_tuning current_tuning(const dem_scene *s) {
+  dem_tuning t{};
+  t.contact_block = s->contact_block;
+  t.contact_blocks_per_sm = s->contact_per_sm;
+  t.integrate_block = s->integrate_block;
+  t.degree_order = s->degree_order;
+  return t;
+}
+}  // namespace
+
+dem_status dem_set_tuning(dem_scene *s, const dem_tuning *t) {
+  if (!s || !t) return DEM_ERR_INVALID_ARG;
+  if (!valid_tuning(*t)) return fail(s, DEM_ERR_INVALID_ARG, "launch shape out of range");
+  apply_tuning(s, *t);
+  return DEM_OK;
+}
+
+dem_status dem_get_tuning(const dem_scene *s, dem_tuning *t) {
+  if (!s || !t) return DEM_ERR_INVALID_ARG;
+  *t = current_tuning(s);
+  return DEM_OK;
+}
+
+// Coordinate search over the launch shapes, timed on the scene's own steps: first
+// the contact kernel's (block, persistent grid) with the integrator fixed, then the
+// integrator's (block, body order) with the best contact shape.  Each trial runs
+// one untimed step, then `steps` timed steps; its cost is the contact plus
+// integrator kernel time per completed step (collider runs excluded).
+dem_status dem_autotune(dem_scene *s, long long steps, dem_tuning *chosen) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (steps < 1) return fail(s, DEM_ERR_INVALID_ARG, "autotune needs at least one step per trial");
+  dem_status r;
+  const bool was_timing = s->timing;
+  const dem_timing keep_tm = s->tm;
+  auto trial = [&](const dem_tuning &t, double &cost) -> dem_status {
+    apply_tuning(s, t);
+    dem_status q;
+    if ((q = dem_step(s, 1))) return q;
+    if ((q = dem_set_timing(s, 1))) return q;
+    const long long it0 = s->cs0().iter;
+    if ((q = dem_step(s, steps))) return q;
+    const long long done = s->cs0().iter - it0;
+    cost = (s->tm.contact_ms + s->tm.integrate_ms) / (double)std::max<long long>(done, 1);
+    return DEM_OK;
+  };
+  dem_tuning best = current_tuning(s);
+  double best_cost = INFINITY;
+  const int cblocks[2] = {128, 256};
+  const int per_sm[3] = {4, 8, 16};
+  for (int b : cblocks)
+    for (int p : per_sm) {
+      dem_tuning t = best;
+      t.contact_block = b;
+      t.contact_blocks_per_sm = p * (256 / b);
+      double c;
+      if ((r = trial(t, c))) return r;
+      if (c < best_cost) { best_cost = c; best = t; }
+    }
+  const int iblocks[3] = {128, 256, 512};
+  const dem_tuning base = best;
+  for (int b : iblocks)
+    for (int o = 0; o < 2; ++o) {
+      dem_tuning t = base;
+      t.integrate_block = b;
+      t.degree_order = o;
+      if (t.integrate_block == base.integrate_block && t.degree_order == base.degree_order) continue;
+      double c;
+      if ((r = trial(t, c))) return r;
+      if (c < best_cost) { best_cost = c; best = t; }
+    }
+  apply_tuning(s, best);
+  if ((r = dem_set_timing(s, was_timing ? 1 : 0))) return r;
+  if (was_timing) {
+    const long long kl = s->tm.kernel_launches;
+    s->tm = keep_tm;
+    s->tm.kernel_launches = kl;
+  }
+  if (chosen) *chosen = best;
+  return DEM_OK;
+}
+
+// ------------------------------------------------------------------ sub-scenes
+void dem_subscene_desc_init(dem_subscene_desc *d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof *d);
+  for (int q = 0; q < 9; ++q) d->cell_h[q] = (q % 4 == 0) ? 1.0 : 0.0;
+  for (int k = 0; k < 3; ++k) { d->box_lo[k] = 0; d->box_hi[k] = 1; }
+  d->damping = 0.2;
+  d->verlet_dist = -0.5;
+}
+
+dem_status dem_add_subscene(dem_scene *s, const dem_subscene_desc *d, int *sub) {
+  if (!s || !d || !sub) return DEM_ERR_INVALID_ARG;
+  if (!(d->damping >= 0) || !(d->damping < 1) || !(d->dt >= 0) || !std::isfinite(d->dt) ||
+      !std::isfinite(d->verlet_dist))
+    return fail(s, DEM_ERR_INVALID_ARG, "bad damping, dt or verlet_dist");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(d->gravity[k]) || !std::isfinite(d->box_lo[k]) || !std::isfinite(d->box_hi[k]))
+      return fail(s, DEM_ERR_INVALID_ARG, "non-finite gravity or box");
+  if (d->periodic) {
+    if (!is_diag(d->cell_h) || !(d->cell_h[0] > 0) || !(d->cell_h[4] > 0) || !(d->cell_h[8] > 0))
+      return fail(s, DEM_ERR_INVALID_ARG, "the periodic cell must be diagonal with positive edges");
+  } else if (d->wall_mask & 0x3F) {
+    for (int k = 0; k < 3; ++k)
+      if (!(d->box_hi[k] > d->box_lo[k])) return fail(s, DEM_ERR_INVALID_ARG, "box_hi must exceed box_lo");
+  }
+  const int wm = d->periodic ? 0 : (d->wall_mask & 0x3F);
+  if (wm && (d->wall_material < 0 || d->wall_material >= kMaxMat || !s->mat_set[d->wall_material]))
+    return fail(s, DEM_ERR_INVALID_ARG, "unknown wall material (set_material first)");
+  if (s->cs0().triax)
+    return fail(s, DEM_ERR_UNSUPPORTED, "a scene running the stress servo takes no sub-scenes");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  int q = -1;
+  for (int i = 0; i < s->nsub(); ++i)
+    if (!s->subs[i].used && !s->subs[i].removing) { q = i; break; }
+  if (q < 0) {
+    if ((r = ensure_subs(s, s->nsub() + 1))) return r;
+    s->subs.emplace_back();
+    q = s->nsub() - 1;
+  }
+  Sub &u = s->subs[q];
+  u = Sub{};
+  u.used = true;
+  u.verlet_rule = d->verlet_dist;
+  init_cell(u.cs, d->periodic, d->cell_h, d->box_lo, d->box_hi, wm, d->wall_material, d->gravity,
+            d->damping);
+  u.dt_set = d->dt > 0;
+  u.cs.dt = d->dt;
+  u.id0 = s->N;
+  if (wm) s->has_walls = true;
+  s->cs_dirty = true;
+  s->need_rebuild = true;
+  *sub = q;
+  return DEM_OK;
+}
+
+dem_status dem_add_spheres_to(dem_scene *s, int sub, long long n, const double *pos,
+                              const double *radius, const int *mat, const double *vel,
+                              const double *angvel, const unsigned char *fixed, long long *first_id) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  return add_spheres_sub(s, sub, n, pos, radius, mat, vel, angvel, fixed, first_id);
+}
+
+dem_status dem_remove_subscene(dem_scene *s, int sub) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used || s->subs[sub].removing)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  Sub &u = s->subs[sub];
+  u.removing = true;
+  u.used = false;
+  u.cs.alive = 0;
+  s->cs_dirty = true;
+  s->need_rebuild = true;
+  s->layout_dirty = true;
+  s->table_fresh = false;
+  return DEM_OK;
+}
+
+dem_status dem_get_subscene(dem_scene *s, int sub, long long *first_id, long long *n,
+                            long long *iter, double *time, double *dt) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if ((r = ensure_dt(s)) && s->N > 0) return r;
+  const Sub &u = s->subs[sub];
+  if (first_id) *first_id = u.id0;
+  if (n) *n = u.n;
+  if (iter) *iter = u.cs.iter;
+  if (time) *time = u.cs.time;
+  if (dt) *dt = u.cs.dt;
+  return DEM_OK;
+}
+
+dem_status dem_get_subscene_stats(dem_scene *s, int sub, dem_stats *out) {
+  if (!s || !out) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  if (s->layout_dirty && s->subs[sub].n > 0)
+    return fail(s, DEM_ERR_STATE, "sub-scene layout changed since the last step: step first");
+  return stats_of(s, sub, out);
+}
+
+dem_status dem_set_subscene_velgrad(dem_scene *s, int sub, const double *L) {
+  if (!s || !L) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  Sub &u = s->subs[sub];
+  if (!u.cs.periodic) return fail(s, DEM_ERR_STATE, "velGrad needs a periodic sub-scene");
+  if (!is_diag(L)) return fail(s, DEM_ERR_UNSUPPORTED, "only a diagonal velGrad is supported");
+  for (int q = 0; q < 9; ++q)
+    if (!std::isfinite(L[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite velGrad");
+  std::memcpy(u.velgrad_next, L, sizeof u.velgrad_next);
+  u.velgrad_pending = true;
+  return DEM_OK;
+}
+
+dem_status dem_num_bodies(dem_scene *s, long long *n) {
+  if (!s || !n) return DEM_ERR_INVALID_ARG;
+  *n = s->N;
+  return DEM_OK;
+}
+
+dem_status dem_get_state_range(dem_scene *s, long long first_id, long long n, double *pos,
+                               double *vel, double *angvel, double *ori) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (first_id < 0 || n < 0 || first_id + n > s->N)
+    return fail(s, DEM_ERR_OUT_OF_RANGE, "id range outside [0, number of bodies)");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (n == 0) return DEM_OK;
+  std::vector<double4_32a> h(n);
+  auto get = [&](const double4_32a *src, double *out, int comps) -> dem_status {
+    launch_gather_ids(s->slot_of_id + first_id, n, src, s->gT, s->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h.data(), s->gT, sizeof(double4_32a) * n, cudaMemcpyDeviceToHost, s->st));
+    dem_status q = wait(s);
+    if (q) return q;
+    for (long long i = 0; i < n; ++i) {
+      const double c[4] = {h[i].x, h[i].y, h[i].z, h[i].w};
+      for (int k = 0; k < comps; ++k) out[comps * i + k] = c[k];
+    }
+    return DEM_OK;
+  };
+  if (pos && (r = get(s->cur.pos, pos, 3))) return r;
+  if (vel && (r = get(s->cur.vel, vel, 3))) return r;
+  if (angvel && (r = get(s->cur.angvel, angvel, 3))) return r;
+  if (ori) {
+    if (s->mixed) {
+      std::vector<float4> f(n);
+      launch_gather_ids_f(s->slot_of_id + first_id, n, s->cur.ori32, reinterpret_cast<float4 *>(s->gT),
+                          s->st);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(f.data(), s->gT, sizeof(float4) * n, cudaMemcpyDeviceToHost, s->st));
+      if ((r = wait(s))) return r;
+      for (long long i = 0; i < n; ++i) {
+        ori[4 * i] = f[i].x; ori[4 * i + 1] = f[i].y; ori[4 * i + 2] = f[i].z; ori[4 * i + 3] = f[i].w;
+      }
+    } else if ((r = get(s->cur.ori, ori, 4))) {
+      return r;
+    }
+  }
+  return DEM_OK;
+}

@@ -50,6 +50,21 @@ class SceneDesc(ctypes.Structure):
     ]
 
 
+class SubsceneDesc(ctypes.Structure):
+    _fields_ = [
+        ("periodic", ctypes.c_int),
+        ("cell_h", ctypes.c_double * 9),
+        ("box_lo", ctypes.c_double * 3),
+        ("box_hi", ctypes.c_double * 3),
+        ("wall_mask", ctypes.c_int),
+        ("wall_material", ctypes.c_int),
+        ("gravity", ctypes.c_double * 3),
+        ("damping", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("verlet_dist", ctypes.c_double),
+    ]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("iter", ctypes.c_longlong),
@@ -85,6 +100,15 @@ class Timing(ctypes.Structure):
 
 # C ABI: name -> (restype, argtypes)
 _P = ctypes.c_void_p
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("contact_block", ctypes.c_int),
+        ("contact_blocks_per_sm", ctypes.c_int),
+        ("integrate_block", ctypes.c_int),
+        ("degree_order", ctypes.c_int),
+    ]
+
+
 _SIGS = {
     "dem_scene_desc_init": (None, [_P]),
     "dem_scene_create": (ctypes.c_int, [_P, _P]),
@@ -110,6 +134,20 @@ _SIGS = {
     "dem_get_stats": (ctypes.c_int, [_P, _P]),
     "dem_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "dem_get_timing": (ctypes.c_int, [_P, _P]),
+    "dem_set_tuning": (ctypes.c_int, [_P, _P]),
+    "dem_subscene_desc_init": (None, [_P]),
+    "dem_add_subscene": (ctypes.c_int, [_P, _P, _P]),
+    "dem_add_spheres_to": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P, _P,
+                                          _P, _P]),
+    "dem_remove_subscene": (ctypes.c_int, [_P, ctypes.c_int]),
+    "dem_get_subscene": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "dem_get_subscene_stats": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "dem_set_subscene_velgrad": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "dem_num_bodies": (ctypes.c_int, [_P, _P]),
+    "dem_get_state_range": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_longlong, _P, _P, _P,
+                                           _P]),
+    "dem_get_tuning": (ctypes.c_int, [_P, _P]),
+    "dem_autotune": (ctypes.c_int, [_P, ctypes.c_longlong, _P]),
     "dem_find_pairs": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
                                       ctypes.c_double, ctypes.c_longlong, _P, _P, _P, _P, _P]),
     "dem_find_pairs_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
@@ -198,7 +236,6 @@ class Scene:
         if rc != DEM_OK:
             raise DemError(rc, self._lib.dem_last_error(None).decode())
         self._h = h
-        self._n = 0
         self.periodic = bool(periodic)
         self.desc = d
 
@@ -252,7 +289,6 @@ class Scene:
         self._check(self._lib.dem_add_spheres(self._h, radius.size, _ptr(pos), _ptr(radius),
                                               _ptr(mat), _ptr(vel), _ptr(angvel), _ptr(fx),
                                               ctypes.byref(first)))
-        self._n += radius.size
         return first.value
 
     def set_dt(self, dt):
@@ -307,7 +343,95 @@ class Scene:
 
     @property
     def n(self):
-        return self._n
+        v = ctypes.c_longlong()
+        self._check(self._lib.dem_num_bodies(self._h, ctypes.byref(v)))
+        return v.value
+
+    # --- sub-scenes (independent scenes advanced by the same launches)
+    def add_subscene(self, periodic=False, cell=None, box_lo=(0, 0, 0), box_hi=(1, 1, 1),
+                     wall_mask=0, wall_material=0, gravity=(0, 0, 0), damping=0.2, dt=0.0,
+                     verlet_dist=-0.5):
+        d = SubsceneDesc()
+        self._lib.dem_subscene_desc_init(ctypes.byref(d))
+        d.periodic = int(bool(periodic))
+        H = np.eye(3) if cell is None else np.asarray(cell, dtype=np.float64).reshape(3, 3)
+        for q in range(9):
+            d.cell_h[q] = float(H.flat[q])
+        for k in range(3):
+            d.box_lo[k] = float(box_lo[k])
+            d.box_hi[k] = float(box_hi[k])
+            d.gravity[k] = float(gravity[k])
+        d.wall_mask = int(wall_mask)
+        d.wall_material = int(wall_material)
+        d.damping = float(damping)
+        d.dt = float(dt)
+        d.verlet_dist = float(verlet_dist)
+        sub = ctypes.c_int()
+        self._check(self._lib.dem_add_subscene(self._h, ctypes.byref(d), ctypes.byref(sub)))
+        return sub.value
+
+    def add_spheres_to(self, sub, pos, radius, mat_id=None, vel=None, angvel=None, fixed=None):
+        pos = _f64(pos, (-1, 3))
+        radius = _f64(radius)
+        mat = None if mat_id is None else np.ascontiguousarray(mat_id, dtype=np.int32)
+        vel = _f64(vel, (-1, 3))
+        angvel = _f64(angvel, (-1, 3))
+        fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        first = ctypes.c_longlong()
+        self._check(self._lib.dem_add_spheres_to(self._h, int(sub), radius.size, _ptr(pos),
+                                                 _ptr(radius), _ptr(mat), _ptr(vel), _ptr(angvel),
+                                                 _ptr(fx), ctypes.byref(first)))
+        return first.value
+
+    def add_workload(self, w, material_base, dt=None):
+        """Add workload w as a new sub-scene whose materials take the ids
+        material_base + k; returns the sub-scene index."""
+        for k, m in enumerate(w.materials):
+            self.set_material(material_base + k, m.density, m.young, m.poisson, m.friction)
+        sub = self.add_subscene(periodic=w.periodic, cell=w.cell, box_lo=w.box_lo,
+                                box_hi=w.box_hi, wall_mask=w.wall_mask,
+                                wall_material=material_base, gravity=w.gravity,
+                                damping=w.damping, dt=0.0 if dt is None else dt)
+        self.add_spheres_to(sub, w.pos, w.radius, np.asarray(w.mat_id) + material_base, w.vel,
+                            w.angvel)
+        if w.periodic and np.any(w.velgrad):
+            self.set_subscene_velgrad(sub, w.velgrad)
+        return sub
+
+    def remove_subscene(self, sub):
+        self._check(self._lib.dem_remove_subscene(self._h, int(sub)))
+
+    def subscene(self, sub):
+        first, n, it = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.dem_get_subscene(self._h, int(sub), ctypes.byref(first),
+                                               ctypes.byref(n), ctypes.byref(it), ctypes.byref(t),
+                                               ctypes.byref(dt)))
+        return {"first_id": first.value, "n": n.value, "iter": it.value, "time": t.value,
+                "dt": dt.value}
+
+    def subscene_stats(self, sub):
+        st = Stats()
+        self._check(self._lib.dem_get_subscene_stats(self._h, int(sub), ctypes.byref(st)))
+        out = {name: getattr(st, name) for name, _ in Stats._fields_ if name != "stress"}
+        out["stress"] = np.array(list(st.stress)).reshape(3, 3)
+        return out
+
+    def set_subscene_velgrad(self, sub, L):
+        L = _f64(L, (3, 3))
+        self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def state_range(self, first_id, n):
+        out = {k: np.empty((n, 3)) for k in ("pos", "vel", "angvel")}
+        out["ori"] = np.empty((n, 4))
+        self._check(self._lib.dem_get_state_range(self._h, int(first_id), int(n),
+                                                  _ptr(out["pos"]), _ptr(out["vel"]),
+                                                  _ptr(out["angvel"]), _ptr(out["ori"])))
+        return out
+
+    def subscene_state(self, sub):
+        info = self.subscene(sub)
+        return self.state_range(info["first_id"], info["n"])
 
     def cell(self):
         H, L, Lp, Hp = (np.empty((3, 3)) for _ in range(4))
@@ -371,8 +495,31 @@ def _timing_methods():
         t = Timing()
         self._check(self._lib.dem_get_timing(self._h, ctypes.byref(t)))
         return {name: getattr(t, name) for name, _ in Timing._fields_}
+
+    def set_tuning(self, **shape):
+        """Launch shapes (dem_tuning fields); unspecified fields keep their value."""
+        t = Tuning()
+        self._check(self._lib.dem_get_tuning(self._h, ctypes.byref(t)))
+        for k, v in shape.items():
+            setattr(t, k, int(v))
+        self._check(self._lib.dem_set_tuning(self._h, ctypes.byref(t)))
+
+    def tuning(self):
+        t = Tuning()
+        self._check(self._lib.dem_get_tuning(self._h, ctypes.byref(t)))
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
+
+    def autotune(self, steps_per_trial=20):
+        """dem_autotune: time the launch shapes on this scene's own steps (they are
+        real steps of the simulation); applies and returns the best shape."""
+        t = Tuning()
+        self._check(self._lib.dem_autotune(self._h, int(steps_per_trial), ctypes.byref(t)))
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
     Scene.set_timing = set_timing
     Scene.timing = timing
+    Scene.set_tuning = set_tuning
+    Scene.tuning = tuning
+    Scene.autotune = autotune
 
 
 _timing_methods()

@@ -26,9 +26,16 @@ def test_deposition_full_run(precision):
         gpu.step(500)
         so, sg = orc.stats(), gpu.stats()
         assert abs(sg["kinetic_energy"] / so["ke"] - 1) < max(tol * 10, 1e-9 if tol < 1e-6 else 1e-4)
-        assert sg["n_contacts"] == so["n_contacts"]
-        assert sg["n_wall_contacts"] == int(np.sum(orc.contacts()["id1"] < 0))
+        nw = int(np.sum(orc.contacts()["id1"] < 0))
+        if precision == "fp64":   # same decisions in the same precision: equal counts
+            assert sg["n_contacts"] == so["n_contacts"] and sg["n_wall_contacts"] == nw
+        else:   # FP32 contact tests: a sphere at the threshold may decide otherwise
+            assert abs(sg["n_contacts"] - so["n_contacts"]) <= max(1, 0.01 * so["n_contacts"])
+            assert abs(sg["n_wall_contacts"] - nw) <= max(1, 0.01 * nw)
     po, pg = orc.state()["pos"], gpu.state()["pos"]
-    assert np.max(np.abs(pg - po)) < (1e-12 if precision == "fp64" else 1e-7) * 0.6
+    # FP64: rounding-level agreement (box scale 0.6 m); mixed: FP32 contact forces over
+    # 2000 steps, bounded by 1e-4 of a radius (1 um)
+    assert np.max(np.abs(pg - po)) < (0.6e-12 if precision == "fp64" else 1e-6)
+    # the clock: 2000 additions of dt in the same order on both sides
     it, t = gpu.clock()
-    assert it == 2000 and abs(t - 2000 * orc.clock()[2]) < 1e-15
+    assert it == 2000 and t == orc.clock()[1]

@@ -195,7 +195,7 @@ def test_error_paths(mods):
         s.add_spheres([[np.nan, 0.5, 0.5]], [0.01])
     assert e.value.code == 5
     with pytest.raises(pkg.DemError) as e:
-        s.set_material(70, 2600, 5e7, 0.25, 0.5)
+        s.set_material(5000, 2600, 5e7, 0.25, 0.5)
     assert e.value.code == 1
     s.add_spheres([[0.5, 0.5, 0.5], [0.52, 0.5, 0.5]], [0.011, 0.011])
     with pytest.raises(pkg.DemError) as e:

@@ -229,3 +229,75 @@ def box_cloud(n: int, seed: int, phi: float = 0.2, rmin=0.8e-3, rmax=1.2e-3, asp
                     materials=mats, periodic=False, cell=np.diag(hi), box_lo=lo, box_hi=hi,
                     wall_mask=wall_mask, gravity=np.asarray(gravity, dtype=np.float64),
                     damping=damping, dt_factor=0.5, steps=0, vel=vel, angvel=angvel)
+
+
+def scaled_deposition(n: int, seed: int, friction: float, young: float, rmin=0.009, rmax=0.011,
+                      solid_fraction=0.078, aspect=(1.0, 1.0, 2.0), density=2600.0,
+                      poisson=0.25, damping=0.2, steps=2000) -> Workload:
+    """Gravity deposition with the box scaled to n: aspect 1:1:2 and the solid fraction
+    of the 1000-sphere deposition (7.8%), so every scene is that one at another size."""
+    u = uniform(n, seed * 7919 + 17)
+    radius = rmin + u * (rmax - rmin)
+    vs = float(np.sum(4.0 / 3.0 * np.pi * radius ** 3))
+    a = np.asarray(aspect, dtype=np.float64)
+    side = (vs / solid_fraction / float(np.prod(a))) ** (1.0 / 3.0)
+    hi = side * a
+    lo = np.zeros(3)
+    pos = rsa_place(radius, lo, hi, periodic=False, seed=seed * 104729 + 19)
+    return Workload(name=f"deposition_n{n}_s{seed}", pos=pos, radius=radius,
+                    mat_id=np.zeros(n, dtype=np.int32),
+                    materials=[Material(density, young, poisson, friction)],
+                    periodic=False, cell=np.diag(hi), box_lo=lo, box_hi=hi, wall_mask=0x3F,
+                    gravity=np.array([0.0, 0.0, -9.81]), damping=damping, dt_factor=0.5,
+                    steps=steps)
+
+
+def batch_parameters(n_scenes: int = 512, seed: int = 3, nmin: int = 500, nmax: int = 50_000):
+    """Per-scene sizes and materials of the batched deposition sweep: sphere counts
+    log-uniform in [nmin, nmax], friction angle uniform in [0.2, 0.7] rad, Young's
+    modulus log-uniform in [1e6, 1e8] Pa (one splitmix64 stream per quantity)."""
+    u = uniform(3 * n_scenes, seed * 7919 + 23).reshape(3, n_scenes)
+    n = np.floor(np.exp(np.log(nmin) + u[0] * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    friction = 0.2 + 0.5 * u[1]
+    young = np.exp(np.log(1e6) + u[2] * (np.log(1e8) - np.log(1e6)))
+    return n, friction, young
+
+
+def batch_depositions(n_scenes: int = 512, seed: int = 3, nmin: int = 500, nmax: int = 50_000,
+                      steps: int = 2000) -> list:
+    """The batched sweep: one scaled deposition per scene (see batch_parameters)."""
+    n, fr, E = batch_parameters(n_scenes, seed, nmin, nmax)
+    return [scaled_deposition(int(n[k]), seed * 100003 + k, float(fr[k]), float(E[k]), steps=steps)
+            for k in range(n_scenes)]
+
+
+def serving_requests(n_requests: int = 2000, seed: int = 4, rate: float = 200.0,
+                     nmin: int = 1000, nmax: int = 200_000, smin: int = 500, smax: int = 5000):
+    """Request stream of the serving workload: Poisson arrivals (exponential gaps of
+    mean 1/rate), sphere counts log-uniform in [nmin, nmax], step budgets uniform in
+    [smin, smax], kind alternating at random between a scaled gravity deposition and a
+    periodic compaction, friction angle U[0.2, 0.7] rad, Young's modulus
+    log-uniform [1e6, 1e8] Pa.  Returns a list of dicts (no spheres yet: a request's
+    scene is built by request_workload when it is submitted)."""
+    u = uniform(6 * n_requests, seed * 7919 + 29).reshape(6, n_requests)
+    gaps = -np.log1p(-u[0]) / rate
+    t = np.cumsum(gaps) - gaps[0]
+    n = np.floor(np.exp(np.log(nmin) + u[1] * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    steps = (smin + np.floor(u[2] * (smax - smin + 1))).astype(np.int64)
+    kind = np.where(u[3] < 0.5, "deposition", "compaction")
+    fr = 0.2 + 0.5 * u[4]
+    E = np.exp(np.log(1e6) + u[5] * (np.log(1e8) - np.log(1e6)))
+    return [{"id": k, "arrival": float(t[k]), "n": int(n[k]), "steps": int(steps[k]),
+             "kind": str(kind[k]), "friction": float(fr[k]), "young": float(E[k]),
+             "seed": seed * 1000003 + k} for k in range(n_requests)]
+
+
+def request_workload(req: dict) -> Workload:
+    """The scene of one serving request: a scaled deposition, or a periodic compaction
+    from solid fraction 0.3 toward 0.62 over its step budget (log-normal radii as in
+    the 1M-sphere compaction; the caller sets the rate once dt is known)."""
+    if req["kind"] == "deposition":
+        return scaled_deposition(req["n"], req["seed"], req["friction"], req["young"],
+                                 steps=req["steps"])
+    return compaction(n=req["n"], seed=req["seed"], steps=req["steps"], young=req["young"],
+                      friction=req["friction"])

@@ -499,15 +499,19 @@ def run_serve(args):
     """Serving: a Poisson stream of deposition / compaction requests replayed in real
     time against the continuous-batching server (mixed precision), then the same
     requests through the plain FP64 one-scene-at-a-time path as a FIFO queue."""
-    import torch
+    import multiprocessing as mp
     import workloads
+    reqs = workloads.serving_requests(args.requests, 4, args.rate)
+    # the requests' scenes are built client-side before the clock starts, in a spawned
+    # process pool created before this process touches the GPU
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        built = dict(zip([r["id"] for r in reqs], pool.map(workloads.request_workload, reqs)))
+    import torch
     from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED
     from paper_2301_00611_gb300.serve import percentile, run_alone, serve_stream
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    reqs = workloads.serving_requests(args.requests, 4, args.rate)
-    built = {r["id"]: workloads.request_workload(r) for r in reqs}   # client-side scenes
 
     def velgrad_for(rq, w):
         if not w.periodic:

@@ -313,12 +313,21 @@ dem_status dem_get_state_range(dem_scene *scene, long long first_id, long long n
  *   degree_order           1: integrate bodies in decreasing order of incident
  *                          contact rows (lanes of a warp get similar row counts);
  *                          0: in slot order
- * Defaults: 256, 8, 256, 1. */
+ *   step_graphs            1: a batch of steps is captured once as a CUDA graph and
+ *                          replayed (one launch per batch; the kernels read tables and
+ *                          bodies through a device-resident descriptor, so a capture
+ *                          stays valid across collider runs until the body count, a
+ *                          table capacity, a launch shape or the sub-scene count
+ *                          changes); 0: every kernel launched one by one.  Batches
+ *                          with per-kernel timing or the stress servo are never
+ *                          captured.
+ * Defaults: 256, 8, 256, 1, 1. */
 typedef struct dem_tuning {
     int contact_block;
     int contact_blocks_per_sm;
     int integrate_block;
     int degree_order;
+    int step_graphs;
 } dem_tuning;
 
 /* Set the launch shapes (INVALID_ARG outside the ranges above) or read them. */
@@ -327,13 +336,47 @@ dem_status dem_get_tuning(const dem_scene *scene, dem_tuning *tuning);
 
 /* Pick the launch shapes by timing the scene's own steps: six contact-kernel
  * shapes (block 128/256 x 4/8/16 blocks of 256 threads per SM), then five more
- * integrator shapes (block 128/256/512 x body order) with the best contact shape;
+ * integrator shapes (block 128/256/512 x body order) with the best contact shape
+ * (step_graphs is left as set: per-kernel timing runs without graphs);
  * each trial is one untimed step plus steps_per_trial timed steps (CUDA events
  * around each kernel; collider runs excluded).  The trial steps are real steps:
  * the scene advances by 11 * (steps_per_trial + 1) steps, along the trajectory
  * any fixed shape gives.  The best shape is applied and, if chosen is non-null,
  * written there.  Errors: INVALID_ARG (steps_per_trial < 1), those of dem_step. */
 dem_status dem_autotune(dem_scene *scene, long long steps_per_trial, dem_tuning *chosen);
+
+/* GlobalStiffnessTimeStepper (section 2.1.5 "Stability considerations", eq. 2.12 -
+ * 2.14; class reference) for sub-scene `sub` (0 for a plain scene).  On every step
+ * whose count is a multiple of `interval`, after the contact pass and before the
+ * integration (the engine order of the text's scripts, so the new dt already
+ * integrates that step), dt becomes `safety` times the smallest sqrt(2) sqrt(m / K)
+ * over the free spheres and their six degrees of freedom taken as uncoupled:
+ * translational K_ii = sum (kn - ks) n_i^2 + ks (eq. 2.14) and rotational
+ * K_ii = sum ks d^2 (1 - n_i^2) over the sphere's contacts (d = r - pen/2, the arm of
+ * the shear spring).  With no contact dt = default_dt, or (default_dt <= 0) safety x
+ * the p-wave step of the sub-scene's spheres; max_dt > 0 caps it.  Density scaling
+ * is not provided.  Errors: INVALID_ARG (safety outside (0, 1], interval < 1). */
+dem_status dem_set_timestepper(dem_scene *scene, int sub, double safety, int interval,
+                               double default_dt, double max_dt);
+
+/* Micromechanics of the contacts of the last completed step (utils reference of
+ * the text), over the whole scene (sub = -1, volume of sub-scene 0) or one
+ * sub-scene:
+ *   fabric         fabricTensor: (1/n_c) sum n (x) n over sphere-sphere contacts
+ *   normal_stress  normalShearStressTensors, normal part: -(1/V) sum l N n (x) n
+ *   shear_stress   shear part: -(1/V) sum l n (x) Fs
+ * n = contact normal, l = current centroid distance, N = normal force (> 0 in
+ * compression), Fs = shear force on body 2, V = cell (periodic) or box volume;
+ * compression negative, so normal_stress + transpose(shear_stress) equals the
+ * stress of dem_get_stats.  Row-major 3x3 HOST outputs (any may be NULL); zeros
+ * before the first step.  Sums in a fixed order: reproducible bit for bit. */
+dem_status dem_get_micro(dem_scene *scene, int sub, double *fabric, double *normal_stress,
+                         double *shear_stress, long long *n_contacts);
+
+/* bodyStressTensors: per sphere (1/V_b) sum x (x) f over its contacts (spheres and
+ * walls), x the contact point relative to its centre, f the force on it, V_b the
+ * sphere volume.  out: HOST n_bodies * 9 doubles in id order (row-major). */
+dem_status dem_get_body_stress(dem_scene *scene, double *out);
 
 /* Collision detection on a bare configuration (section 2.1.1, both passes: the
  * grid's bounding-volume filter, then the exact sphere test): every pair

@@ -76,6 +76,7 @@ def _load():
         "orc_set_velgrad": (_i, [_p, _p]),
         "orc_step": (_i, [_p, _l]),
         "orc_set_triax": (_i, [_p, _p, _i, _p, _d, _i]),
+        "orc_set_timestepper": (_i, [_p, _d, _i, _d, _d]),
         "orc_num_bodies": (_l, [_p]),
         "orc_get_state": (None, [_p, _p, _p, _p, _p, _p, _p]),
         "orc_set_state": (_i, [_p, _p, _p, _p, _p]),
@@ -156,6 +157,8 @@ class OracleScene:
         if not self._h:
             raise RuntimeError("orc_create failed")
         self.periodic = bool(periodic)
+        self._box = (lo.copy(), hi.copy())
+        self._radius = np.zeros(0)
 
     @classmethod
     def from_workload(cls, w, dt=None):
@@ -192,6 +195,7 @@ class OracleScene:
                                       _ptr(vel), _ptr(angvel), _ptr(fx))
         if r < 0:
             raise ValueError(f"add_spheres failed ({r})")
+        self._radius = np.concatenate([self._radius, radius])
         return r
 
     def set_dt(self, dt):
@@ -212,6 +216,12 @@ class OracleScene:
         if self._lib.orc_set_triax(self._h, _ptr(g), int(stress_mask), _ptr(m),
                                    float(grow_damping), int(glob_update)) != 0:
             raise ValueError("set_triax needs a periodic scene and valid parameters")
+
+    def set_timestepper(self, safety=0.8, interval=1, default_dt=-1.0, max_dt=0.0):
+        """GlobalStiffnessTimeStepper (reading R17 in dem_oracle.c)."""
+        if self._lib.orc_set_timestepper(self._h, float(safety), int(interval), float(default_dt),
+                                         float(max_dt)) != 0:
+            raise ValueError("bad time-stepper parameters")
 
     def step(self, n=1):
         rc = self._lib.orc_step(self._h, int(n))
@@ -287,6 +297,48 @@ class OracleScene:
         keys = ("kinTrans", "kinRot", "gravWork", "nonviscDamp", "plastDissip",
                 "elastPotential", "total")
         return dict(zip(keys, e.tolist()))
+
+    def micro(self):
+        """Micromechanics of the current contacts, from the utils reference of the text:
+        fabricTensor F = (1/n_c) sum n n; normalShearStressTensors, read with compression
+        negative and l the current centroid distance: normal part -(1/V) sum l N n n,
+        shear part -(1/V) sum l n Fs; bodyStressTensors (1/V_b) sum x f per sphere, x the
+        contact point relative to the centre, f the force on the sphere (walls included).
+        Written out from the contact list (numpy, FP64)."""
+        c = self.contacts()
+        pos = self.state()["pos"]
+        r = self._radius
+        if self.periodic:
+            V = abs(np.linalg.det(self.cell()["H"]))
+        else:
+            lo, hi = self._box
+            V = float(np.prod(hi - lo))
+        ss = c["id1"] >= 0
+        n = c["normal"][ss]
+        fn, fs = c["fn"][ss], c["fs"][ss]
+        i1, i2 = c["id1"][ss], c["id2"][ss]
+        l = r[i1] + r[i2] - c["pen"][ss]
+        N = np.einsum("ki,ki->k", fn, n)
+        nc = n.shape[0]
+        fabric = np.einsum("ki,kj->ij", n, n) / nc if nc else np.zeros((3, 3))
+        normal = -np.einsum("k,ki,kj->ij", l * N, n, n) / V
+        shear = -np.einsum("k,ki,kj->ij", l, n, fs) / V
+        body = np.zeros((self.n, 3, 3))
+        F = c["fn"] + c["fs"]                      # force on id2
+        for k in range(len(c["id1"])):
+            b2 = c["id2"][k]
+            if c["id1"][k] >= 0:
+                b1 = c["id1"][k]
+                x1 = c["cpoint"][k] - pos[b1]      # contact point - centre of body 1
+                lk = r[b1] + r[b2] - c["pen"][k]
+                x2 = x1 - lk * c["normal"][k]      # relative to the image of body 2
+                body[b1] += np.outer(x1, -F[k])
+                body[b2] += np.outer(x2, F[k])
+            else:
+                body[b2] += np.outer(c["cpoint"][k] - pos[b2], F[k])
+        body /= (4.0 / 3.0 * np.pi * r ** 3)[:, None, None]
+        return {"fabric": fabric, "normal_stress": normal, "shear_stress": shear,
+                "body_stress": body, "n_contacts": nc}
 
     def stats(self):
         o = np.empty(14)

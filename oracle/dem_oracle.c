@@ -108,6 +108,9 @@ struct orc_scene {
     double grav_work, nonvisc_damp, plast_dissip;
     /* stress-controlled periodic cell (PeriTriaxController reading R16) */
     int triax, stress_mask, glob_update;
+    /* GlobalStiffnessTimeStepper (R17) */
+    int tstep, tstep_interval;
+    double tstep_safety, tstep_default, tstep_max;
     double goal[3], max_rate[3], grow_damping;
 };
 
@@ -757,6 +760,68 @@ int orc_set_triax(orc_scene *s, const double *goal, int stress_mask, const doubl
     return 0;
 }
 
+/* GlobalStiffnessTimeStepper (section 2.1.5 "Stability considerations", eq. 2.12-2.14,
+ * GlobalStiffnessTimeStepper class reference; reading R17).  Per body, the diagonal of
+ * its translational stiffness K_ii = sum over its contacts of (kn - ks) n_i^2 + ks
+ * (eq. 2.14) and of its rotational stiffness sum ks d^2 (1 - n_i^2) (the shear spring
+ * at the arm d = r - pen/2 from the centre); per degree of freedom the critical step
+ * sqrt(2) sqrt(m / K) (eq. 2.12, DOFs taken as uncoupled as the text prescribes); the
+ * time step is the safety coefficient times the smallest of them over the free
+ * bodies, or, when no body has a contact, defaultDt (or the safety coefficient times
+ * the p-wave step when defaultDt < 0); capped by maxDt when that is positive. */
+static void stiffness_dt(orc_scene *s) {
+    long n = s->n;
+    double *Kt = (double *)calloc(3 * (size_t)n + 1, sizeof(double));
+    double *Kr = (double *)calloc(3 * (size_t)n + 1, sizeof(double));
+    if (!Kt || !Kr) { free(Kt); free(Kr); return; }
+    for (long k = 0; k < s->ncon; ++k) {
+        const orc_contact *ct = &s->con[k];
+        long bodies[2] = {ct->id1, ct->id2};
+        for (int e = 0; e < 2; ++e) {
+            long b = bodies[e];
+            if (b < 0) continue;   /* the wall side */
+            double d = s->radius[b] - 0.5 * ct->pen;
+            for (int i = 0; i < 3; ++i) {
+                double ni2 = ct->n[i] * ct->n[i];
+                Kt[3 * b + i] += (ct->kn - ct->ks) * ni2 + ct->ks;
+                Kr[3 * b + i] += ct->ks * d * d * (1.0 - ni2);
+            }
+        }
+    }
+    double best = INFINITY;
+    for (long b = 0; b < n; ++b) {
+        if (s->fixed[b]) continue;
+        for (int i = 0; i < 3; ++i) {
+            if (Kt[3 * b + i] > 0) {
+                double t = sqrt(2.0) * sqrt(s->mass[b] / Kt[3 * b + i]);
+                if (t < best) best = t;
+            }
+            if (Kr[3 * b + i] > 0) {
+                double t = sqrt(2.0) * sqrt(s->inertia[b] / Kr[3 * b + i]);
+                if (t < best) best = t;
+            }
+        }
+    }
+    free(Kt);
+    free(Kr);
+    double dt;
+    if (isinf(best)) dt = s->tstep_default > 0 ? s->tstep_default : s->tstep_safety * orc_pwave_dt(s);
+    else dt = s->tstep_safety * best;
+    if (s->tstep_max > 0 && dt > s->tstep_max) dt = s->tstep_max;
+    s->dt = dt;
+}
+
+int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,
+                        double max_dt) {
+    if (!s || !(safety > 0) || interval < 1 || !isfinite(default_dt) || !isfinite(max_dt)) return -1;
+    s->tstep = 1;
+    s->tstep_safety = safety;
+    s->tstep_interval = interval;
+    s->tstep_default = default_dt;
+    s->tstep_max = max_dt;
+    return 0;
+}
+
 static int step_once(orc_scene *s) {
     const double dt = s->dt;
     if (!(dt > 0)) return -1;
@@ -834,6 +899,10 @@ static int step_once(orc_scene *s) {
         v_cross(arm, F2, T);
         for (int q = 0; q < 3; ++q) { s->force[3 * j + q] += F2[q]; s->torque[3 * j + q] += T[q]; }
     }
+    /* GlobalStiffnessTimeStepper between InteractionLoop and NewtonIntegrator (the
+     * engine order of the text's scripts): the new step integrates this step */
+    if (s->tstep && s->iter % s->tstep_interval == 0) stiffness_dt(s);
+    const double dtN = s->dt;
     /* NewtonIntegrator */
     const double lam = s->damping;
     double dL[9];
@@ -859,35 +928,35 @@ static int step_once(orc_scene *s) {
             double Fd[3], Td[3];
             for (int q = 0; q < 3; ++q) {
                 double acc = F[q] / m;
-                Fd[q] = F[q] * (1 - lam * sgn(F[q] * (vref[q] + 0.5 * dt * acc)));
+                Fd[q] = F[q] * (1 - lam * sgn(F[q] * (vref[q] + 0.5 * dtN * acc)));
                 double aacc = T[q] / I;
-                Td[q] = T[q] * (1 - lam * sgn(T[q] * (w[q] + 0.5 * dt * aacc)));
+                Td[q] = T[q] * (1 - lam * sgn(T[q] * (w[q] + 0.5 * dtN * aacc)));
             }
             /* leapfrog: v+ = v- + dt F/m ; w+ = w- + dt T/I */
             for (int q = 0; q < 3; ++q) {
-                v[q] = vold[q] + dt * Fd[q] / m;
-                w[q] = w[q] + dt * Td[q] / I;
+                v[q] = vold[q] + dtN * Fd[q] / m;
+                w[q] = w[q] + dtN * Td[q] / I;
             }
             if (s->periodic) {
                 /* homoDeform = 2 (R9): (grad(v) - grad(v)_prev) x + dt grad(v) v- */
                 double a1[3], a2[3];
                 m_vec(dL, xold, a1);
                 m_vec(s->L, vold, a2);
-                for (int q = 0; q < 3; ++q) v[q] = v[q] + a1[q] + dt * a2[q];
+                for (int q = 0; q < 3; ++q) v[q] = v[q] + a1[q] + dtN * a2[q];
             }
             /* energy tracker: damping work, gravity work (sign conventions of the doctest
              * in the yade.plot reference) */
             for (int q = 0; q < 3; ++q) {
-                s->nonvisc_damp += -(Fd[q] - F[q]) * v[q] * dt;
-                s->nonvisc_damp += -(Td[q] - T[q]) * w[q] * dt;
-                s->grav_work += -m * s->g[q] * v[q] * dt;
+                s->nonvisc_damp += -(Fd[q] - F[q]) * v[q] * dtN;
+                s->nonvisc_damp += -(Td[q] - T[q]) * w[q] * dtN;
+                s->grav_work += -m * s->g[q] * v[q] * dtN;
             }
         }
-        for (int q = 0; q < 3; ++q) x[q] = xold[q] + dt * v[q];
+        for (int q = 0; q < 3; ++q) x[q] = xold[q] + dtN * v[q];
         /* orientation: q+ = dq(w+ dt) q (spherical rotation, section 2.1.5) */
         double wn = sqrt(v_dot(w, w));
         if (wn > 0) {
-            double ang = wn * dt;
+            double ang = wn * dtN;
             double sh = sin(0.5 * ang), ch = cos(0.5 * ang);
             double dq[4] = {ch, sh * w[0] / wn, sh * w[1] / wn, sh * w[2] / wn};
             quat_mul(dq, s->ori + 4 * i, s->ori + 4 * i);
@@ -896,12 +965,12 @@ static int step_once(orc_scene *s) {
     /* cell: H+ = (I + grad(v) dt) H (section 2.1.6) */
     if (s->periodic) {
         double A[9];
-        for (int q = 0; q < 9; ++q) A[q] = (q % 4 == 0 ? 1.0 : 0.0) + s->L[q] * dt;
+        for (int q = 0; q < 9; ++q) A[q] = (q % 4 == 0 ? 1.0 : 0.0) + s->L[q] * dtN;
         memcpy(s->Hprev, s->H, sizeof s->H);
         m_mul(A, s->H, s->H);
         memcpy(s->Lprev, s->L, sizeof s->L);
     }
-    s->time += dt;
+    s->time += dtN;
     s->iter += 1;
     if (s->triax && s->periodic && s->iter % s->glob_update == 0) triax_update(s);
     return 0;

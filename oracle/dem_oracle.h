@@ -39,6 +39,10 @@ int orc_set_dt(orc_scene *s, double dt);
 int orc_set_velgrad(orc_scene *s, const double *L9);
 int orc_step(orc_scene *s, long nsteps);
 /* stress-controlled periodic cell (PeriTriaxController, reading R16 in dem_oracle.c) */
+/* GlobalStiffnessTimeStepper: safety coefficient, update interval (steps), defaultDt
+ * (< 0: safety x p-wave step), maxDt (<= 0: none). */
+int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,
+                        double max_dt);
 int orc_set_triax(orc_scene *s, const double *goal3, int stress_mask, const double *max_rate3,
                   double grow_damping, int glob_update);
 

@@ -148,11 +148,13 @@ struct QRow {
 // Sub-scenes (multi): each row takes its cell state from the sub-scene of body 1
 // (both bodies of a row always belong to the same sub-scene).
 template <int kT>
-__global__ void __launch_bounds__(kT, 768 / kT) k_contact(Table t, Bodies b,
+__global__ void __launch_bounds__(kT, 768 / kT) k_contact(const StepDesc *__restrict__ d,
                                                           const CellState *__restrict__ cs,
                                                           const DevStatus *__restrict__ ds,
                                                           const Mat *__restrict__ mats, int multi) {
   constexpr int kWarps = kT / 32;
+  const Table &t = d->t;
+  const Bodies &b = d->b;
   if (ds->pending) return;
   __shared__ QRow q[kWarps][kQ];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -222,14 +224,14 @@ __global__ void __launch_bounds__(kT, 768 / kT) k_contact(Table t, Bodies b,
 }
 }  // namespace
 
-void launch_contact(const Table &t, const Bodies &b, const CellState *cs, const DevStatus *ds,
+void launch_contact(const StepDesc *d, long long rows, const CellState *cs, const DevStatus *ds,
                     const Mat *mats, int multi, int nsm, int block, int per_sm, cudaStream_t st) {
-  if (t.P <= 0) return;
-  long long need = (t.P + block - 1) / block;
+  if (rows <= 0) return;
+  long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  if (block == 128) k_contact<128><<<grid, 128, 0, st>>>(t, b, cs, ds, mats, multi);
-  else k_contact<256><<<grid, 256, 0, st>>>(t, b, cs, ds, mats, multi);
+  if (block == 128) k_contact<128><<<grid, 128, 0, st>>>(d, cs, ds, mats, multi);
+  else k_contact<256><<<grid, 256, 0, st>>>(d, cs, ds, mats, multi);
 }
 
 }  // namespace dem

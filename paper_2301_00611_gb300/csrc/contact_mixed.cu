@@ -145,11 +145,13 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
 // Same per-warp queue of real rows as the FP64 kernel: the FP32 geometry test on
 // tiles of 32 consecutive rows, the law on 32 queued real rows at a time.
 template <int kT>
-__global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
+__global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict__ d,
                                                       const CellState *__restrict__ cs,
                                                       const DevStatus *__restrict__ ds,
                                                       const Mat *__restrict__ mats, int multi) {
   constexpr int kWarps = kT / 32;
+  const Table &t = d->t;
+  const Bodies &b = d->b;
   if (ds->pending) return;
   __shared__ QRowF q[kWarps][kQ];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -217,15 +219,15 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(Table t, Bodies b,
 }
 }  // namespace
 
-void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
+void launch_contact_mixed(const StepDesc *d, long long rows, const CellState *cs,
                           const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
                           int per_sm, cudaStream_t st) {
-  if (t.P <= 0) return;
-  long long need = (t.P + block - 1) / block;
+  if (rows <= 0) return;
+  long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  if (block == 128) k_contact_mixed<128><<<grid, 128, 0, st>>>(t, b, cs, ds, mats, multi);
-  else k_contact_mixed<256><<<grid, 256, 0, st>>>(t, b, cs, ds, mats, multi);
+  if (block == 128) k_contact_mixed<128><<<grid, 128, 0, st>>>(d, cs, ds, mats, multi);
+  else k_contact_mixed<256><<<grid, 256, 0, st>>>(d, cs, ds, mats, multi);
 }
 
 }  // namespace dem

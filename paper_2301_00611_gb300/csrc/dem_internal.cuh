@@ -105,7 +105,9 @@ struct CellState {
   int wall_mask;    // walls present (bit w: wall w = 2 axis + side)
   int wall_mat;     // material of the walls
   int alive;        // 0: a removed sub-scene (its slot is skipped)
-  int pad4;
+  int tstep;        // GlobalStiffnessTimeStepper on
+  int tstep_interval, pad5;
+  double tstep_safety, tstep_default, tstep_max;   // default: dt when no contact exists
 };
 
 constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
@@ -142,6 +144,16 @@ struct SceneConst {
   int periodic;  // some sub-scene is periodic
   int ordered;   // integrate bodies in Table::ord order (else slot order)
   int multi;     // more than one sub-scene: per-body constants from CellState[sid]
+};
+
+// What the step kernels read from device memory instead of their launch
+// parameters, so that a captured batch of steps stays valid across collider runs
+// (which swap the body buffers and the tables).
+struct StepDesc {
+  Table t;
+  Bodies b;
+  SceneConst sc;
+  long long cap;   // body capacity (stride of the wall histories)
 };
 
 // ---- cell shift packing: 3 x 10-bit two's complement in one int
@@ -196,22 +208,30 @@ void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
 // contact.cu
 // block: 128 or 256 threads; per_sm: blocks per SM of the persistent grid
 // multi: cs is an array indexed by Bodies::sid (else cs[0] holds the one scene)
-void launch_contact(const Table &t, const Bodies &b, const CellState *cs, const DevStatus *ds,
+// rows: upper bound of the table rows (sizes the grid: the table capacity, so that the
+// launch shape does not change between collider runs)
+void launch_contact(const StepDesc *d, long long rows, const CellState *cs, const DevStatus *ds,
                     const Mat *mats, int multi, int nsm, int block, int per_sm,
                     cudaStream_t st);
 // contact_mixed.cu
-void launch_contact_mixed(const Table &t, const Bodies &b, const CellState *cs,
+void launch_contact_mixed(const StepDesc *d, long long rows, const CellState *cs,
                           const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
                           int per_sm, cudaStream_t st);
 
 // integrate.cu
 // block: 128, 256 or 512 threads
-void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                      const Mat *mats, const SceneConst &sc, long long cap, int mixed, int block,
-                      cudaStream_t st);
+// N and walls must equal d->sc.N and d->sc.walls (they size and select the launch)
+void launch_integrate(const StepDesc *d, long long N, int walls, const CellState *cs,
+                      DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st);
 // one thread per sub-scene (cs[0 .. nsub)); servo partials apply to sub-scene 0
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
                          cudaStream_t st);
+// GlobalStiffnessTimeStepper: per-sub-scene minimum critical step (keys: nsub entries
+// preset to +inf bits, reset by the launch) applied to the due sub-scenes' dt
+void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub,
+                        const DevStatus *ds, const Mat *mats, long long N, long long cap,
+                        int mixed, int multi, int walls, unsigned long long *keys,
+                        cudaStream_t st);
 // servo: per-block sums of sigma_ii * V and K_i * V over the real rows (6 per block)
 void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
                            cudaStream_t st);
@@ -223,6 +243,13 @@ void launch_gather_ids(const int *slot_of_id, long long n, const double4_32a *sr
                        double4_32a *dst, cudaStream_t st);
 void launch_gather_ids_f(const int *slot_of_id, long long n, const float4 *src, float4 *dst,
                          cudaStream_t st);
+// micro.cu: fabric / normal-shear stress partials (28 per block, micro_blocks(P) blocks)
+// and per-body stress tensors (9 per slot)
+int micro_blocks(long long P);
+void launch_micro_rows(const Table &t, int mixed, double *partials, cudaStream_t st);
+void launch_body_stress(const Bodies &b, const Table &t, long long N, long long cap, int mixed,
+                        int walls, int multi, const CellState *cs, const Mat *mats, double *out,
+                        cudaStream_t st);
 // stats: per-block partial sums (deterministic tree), summed on the host in block order
 int stats_blocks(long long n);
 void launch_body_stats(const Bodies &b, const double4_32a *F, long long N, double *partials,

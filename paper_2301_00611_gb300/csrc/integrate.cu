@@ -19,9 +19,13 @@ namespace dem {
 namespace {
 constexpr int kT = 256;
 
-// damping factor 1 - lam * sgn(p) as a select (no integer-to-double conversion)
-__device__ inline double damp_factor(double p, double lam) {
-  return p > 0 ? 1.0 - lam : (p < 0 ? 1.0 + lam : 1.0);
+// Damping factor 1 - lam * sgn(p) for p = a * b, with sgn(a b) read from the sign bits and zero tests
+// of a and b on the integer pipe (no FP64 product or compares).  It differs from
+// sgn(fl(a b)) only if the product underflows to zero.
+__device__ inline double damp_factor_ab(double a, double b, double one_m, double one_p) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const bool zero = ((ia << 1) == 0) | ((ib << 1) == 0);
+  return zero ? 1.0 : ((ia ^ ib) < 0 ? one_p : one_m);
 }
 __device__ inline float damp_factor_f(float p, float lam) {
   return p > 0.0f ? 1.0f - lam : (p < 0.0f ? 1.0f + lam : 1.0f);
@@ -31,18 +35,37 @@ __device__ inline bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// Rows are visited in the fixed order (own rows, then the down list); two rows are
+// loaded before either is added, which keeps more loads in flight without changing
+// the order of the additions.
 __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[3]) {
   const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
-  for (int k = r0; k < r1; ++k) {   // rows where s is body 1: force -F, torque d1 M
+  int k = r0;
+  for (; k + 1 < r1; k += 2) {   // rows where s is body 1: force -F, torque d1 M
+    const double4_32a fa = t.oF[k], ma = t.oM[k], fb = t.oF[k + 1], mb = t.oM[k + 1];
+    F[0] -= fa.x; F[1] -= fa.y; F[2] -= fa.z;
+    T[0] += fa.w * ma.x; T[1] += fa.w * ma.y; T[2] += fa.w * ma.z;
+    F[0] -= fb.x; F[1] -= fb.y; F[2] -= fb.z;
+    T[0] += fb.w * mb.x; T[1] += fb.w * mb.y; T[2] += fb.w * mb.z;
+  }
+  if (k < r1) {
     const double4_32a f = t.oF[k], m = t.oM[k];
     F[0] -= f.x; F[1] -= f.y; F[2] -= f.z;
     T[0] += f.w * m.x; T[1] += f.w * m.y; T[2] += f.w * m.z;
   }
   const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
-  for (int e = e0; e < e1; ++e) {   // rows where s is body 2: force +F, torque d2 M
-    const int k = t.down[e];
-    if (k < 0) continue;
-    const double4_32a f = t.oF[k], m = t.oM[k];
+  int e = e0;
+  for (; e + 1 < e1; e += 2) {   // rows where s is body 2: force +F, torque d2 M
+    const int ka = t.down[e], kb = t.down[e + 1];
+    const double4_32a fa = t.oF[ka], ma = t.oM[ka], fb = t.oF[kb], mb = t.oM[kb];
+    F[0] += fa.x; F[1] += fa.y; F[2] += fa.z;
+    T[0] += ma.w * ma.x; T[1] += ma.w * ma.y; T[2] += ma.w * ma.z;
+    F[0] += fb.x; F[1] += fb.y; F[2] += fb.z;
+    T[0] += mb.w * mb.x; T[1] += mb.w * mb.y; T[2] += mb.w * mb.z;
+  }
+  if (e < e1) {
+    const int k1 = t.down[e];
+    const double4_32a f = t.oF[k1], m = t.oM[k1];
     F[0] += f.x; F[1] += f.y; F[2] += f.z;
     T[0] += m.w * m.x; T[1] += m.w * m.y; T[2] += m.w * m.z;
   }
@@ -88,12 +111,15 @@ __device__ inline void wall_phys(const Mat *mats, int wmat, int mat, double r, d
 // contact kernel).  Every quantity it needs in FP32 is read from the FP32 mirrors
 // the previous step wrote, so the FP64 pipe (conversions included) carries ~27
 // instructions per body.
-template <int kB>
-__global__ void __launch_bounds__(kB) k_integrate_mixed(Bodies b, Table t,
+template <int kB, bool kWalls>
+__global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restrict__ d,
                                                         const CellState *__restrict__ cs,
-                                                        DevStatus *ds, const Mat *__restrict__ mats,
-                                                        SceneConst sc, long long cap) {
+                                                        DevStatus *ds, const Mat *__restrict__ mats) {
   if (ds->pending) return;
+  const Bodies &b = d->b;
+  const Table &t = d->t;
+  const SceneConst &sc = d->sc;
+  const long long cap = d->cap;
   const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = sc.ordered ? t.ord[sl] : (int)sl;
@@ -101,19 +127,35 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(Bodies b, Table t,
   const double dt = c.dt;
   const float dtf = (float)dt;
   float F[3], T[3];
-  {
+  {   // fixed-order gather, two rows loaded before either is added
     float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
     const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
-    for (int k = r0; k < r1; ++k) {
+    int k = r0;
+    for (; k + 1 < r1; k += 2) {
+      const float4 fa = t.oF32[k], ma = t.oM32[k], fb = t.oF32[k + 1], mb = t.oM32[k + 1];
+      f0 -= fa.x; f1 -= fa.y; f2 -= fa.z;
+      t0 += fa.w * ma.x; t1 += fa.w * ma.y; t2 += fa.w * ma.z;
+      f0 -= fb.x; f1 -= fb.y; f2 -= fb.z;
+      t0 += fb.w * mb.x; t1 += fb.w * mb.y; t2 += fb.w * mb.z;
+    }
+    if (k < r1) {
       const float4 f = t.oF32[k], m = t.oM32[k];
       f0 -= f.x; f1 -= f.y; f2 -= f.z;
       t0 += f.w * m.x; t1 += f.w * m.y; t2 += f.w * m.z;
     }
     const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int k = t.down[e];
-      if (k < 0) continue;
-      const float4 f = t.oF32[k], m = t.oM32[k];
+    int e = e0;
+    for (; e + 1 < e1; e += 2) {
+      const int ka = t.down[e], kb = t.down[e + 1];
+      const float4 fa = t.oF32[ka], ma = t.oM32[ka], fb = t.oF32[kb], mb = t.oM32[kb];
+      f0 += fa.x; f1 += fa.y; f2 += fa.z;
+      t0 += ma.w * ma.x; t1 += ma.w * ma.y; t2 += ma.w * ma.z;
+      f0 += fb.x; f1 += fb.y; f2 += fb.z;
+      t0 += mb.w * mb.x; t1 += mb.w * mb.y; t2 += mb.w * mb.z;
+    }
+    if (e < e1) {
+      const int k1 = t.down[e];
+      const float4 f = t.oF32[k1], m = t.oM32[k1];
       f0 += f.x; f1 += f.y; f2 += f.z;
       t0 += m.w * m.x; t1 += m.w * m.y; t2 += m.w * m.z;
     }
@@ -128,7 +170,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(Bodies b, Table t,
   const float xf[3] = {xr.x + off.x, xr.y + off.y, xr.z + off.z};
   const float r = off.w;
 
-  if (sc.walls && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
+  if (kWalls && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
     const double4_32a pd = b.pos[s];
     const double xd[3] = {pd.x, pd.y, pd.z};
     for (int wi = 0; wi < 6; ++wi) {
@@ -257,11 +299,15 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(Bodies b, Table t,
     atomicOr(&ds->error, kErrNonFinite);
 }
 
-template <int kB>
-__global__ void __launch_bounds__(kB) k_integrate(Bodies b, Table t, const CellState *__restrict__ cs,
-                                                  DevStatus *ds, const Mat *__restrict__ mats,
-                                                  SceneConst sc, long long cap) {
+template <int kB, bool kWalls>
+__global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d,
+                                                  const CellState *__restrict__ cs,
+                                                  DevStatus *ds, const Mat *__restrict__ mats) {
   if (ds->pending) return;
+  const Bodies &b = d->b;
+  const Table &t = d->t;
+  const SceneConst &sc = d->sc;
+  const long long cap = d->cap;
   const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = sc.ordered ? t.ord[sl] : (int)sl;
@@ -278,7 +324,7 @@ __global__ void __launch_bounds__(kB) k_integrate(Bodies b, Table t, const CellS
   const double x[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z}, ww[3] = {w.x, w.y, w.z};
   const double r = p.w;
 
-  if (sc.walls && c.wall_mask) {
+  if (kWalls && c.wall_mask) {
     for (int wi = 0; wi < 6; ++wi) {
       if (!(c.wall_mask & (1 << wi))) continue;
       const int ax = wi >> 1;
@@ -348,14 +394,14 @@ __global__ void __launch_bounds__(kB) k_integrate(Bodies b, Table t, const CellS
       const double *Lp = c.Lprev;
       for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
     }
+    const double hdt = 0.5 * dt, one_m = 1.0 - lam, one_p = 1.0 + lam;
+    const double dtm = dt * mp.z, dtI = dt * mp.w;   // dt / m, dt / I
     for (int q = 0; q < 3; ++q) {
       const double Ft = F[q] + mp.x * c.gravity[q];
-      const double acc = Ft * mp.z;
-      const double Fd = Ft * damp_factor(Ft * (vref[q] + 0.5 * dt * acc), lam);
-      vn_[q] = vv[q] + dt * Fd * mp.z;
-      const double aacc = T[q] * mp.w;
-      const double Td = T[q] * damp_factor(T[q] * (ww[q] + 0.5 * dt * aacc), lam);
-      wn_[q] = ww[q] + dt * Td * mp.w;
+      const double Fd = Ft * damp_factor_ab(Ft, vref[q] + hdt * (Ft * mp.z), one_m, one_p);
+      vn_[q] = vv[q] + Fd * dtm;
+      const double Td = T[q] * damp_factor_ab(T[q], ww[q] + hdt * (T[q] * mp.w), one_m, one_p);
+      wn_[q] = ww[q] + Td * dtI;
     }
     if (c.periodic) {   // homoDeform = 2
       const double *dL = c.dL, *L = c.L;
@@ -422,6 +468,23 @@ __device__ inline void m_mul_rn(const double *A, const double *B, double *O) {
   for (int q = 0; q < 9; ++q) O[q] = Tm[q];
 }
 
+// The next cell H+ = (I + L dt) H, the affine strain since the collider run and
+// the displacement bound that follow from it (periodic cells).
+__device__ void derive_next(CellState *cs) {
+  const double dt = cs->dt;
+  double A[9];
+  for (int q = 0; q < 9; ++q) A[q] = __dadd_rn((q % 4 == 0) ? 1.0 : 0.0, __dmul_rn(cs->L[q], dt));
+  m_mul_rn(A, cs->H, cs->Hnext);
+  double D[9];
+  for (int q = 0; q < 9; ++q) D[q] = cs->Hnext[q] - cs->Href[q];
+  m_mul_rn(D, cs->Hrefinv, cs->E);
+  double e2 = 0;
+  for (int q = 0; q < 9; ++q) e2 += cs->E[q] * cs->E[q];
+  const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
+  cs->thr2 = eff > 0 ? eff * eff : -1.0;
+  for (int q = 0; q < 3; ++q) cs->Ef[q] = (float)cs->E[4 * q];
+}
+
 // Advance of one (sub-)scene's cell and clock.
 __device__ void cell_advance(CellState *cs, const double *servo) {
   const double dt = cs->dt;
@@ -458,20 +521,10 @@ __device__ void cell_advance(CellState *cs, const double *servo) {
       for (int q = 0; q < 9; ++q) cs->dL[q] = cs->L[q] - cs->Lprev[q];
     }
     m_mul_rn(cs->Lprev, cs->Hprev, cs->W);
-    double A[9];
-    for (int q = 0; q < 9; ++q) A[q] = __dadd_rn((q % 4 == 0) ? 1.0 : 0.0, __dmul_rn(cs->L[q], dt));
-    m_mul_rn(A, cs->H, cs->Hnext);
-    double D[9];
-    for (int q = 0; q < 9; ++q) D[q] = cs->Hnext[q] - cs->Href[q];
-    m_mul_rn(D, cs->Hrefinv, cs->E);
-    double e2 = 0;
-    for (int q = 0; q < 9; ++q) e2 += cs->E[q] * cs->E[q];
-    const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
-    cs->thr2 = eff > 0 ? eff * eff : -1.0;
+    derive_next(cs);
     for (int q = 0; q < 3; ++q) {
       cs->dHf[q] = (float)(cs->H[4 * q] - cs->Href[4 * q]);
       cs->Wf[q] = (float)cs->W[4 * q];
-      cs->Ef[q] = (float)cs->E[4 * q];
     }
   }
   cs->iter += 1;
@@ -643,28 +696,138 @@ __global__ void k_wall_stats(Bodies b, SceneConst sc, const Mat *__restrict__ ma
 }
 
 inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+// GlobalStiffnessTimeStepper (section 2.1.5, eq. 2.12-2.14): per body the diagonal of
+// its translational stiffness sum (kn - ks) n_i^2 + ks and rotational stiffness
+// sum ks d^2 (1 - n_i^2) over its real contacts (spheres and walls, d = r - pen/2),
+// the smallest sqrt(2) sqrt(m / K) over its degrees of freedom, and the minimum over
+// the bodies of each sub-scene into keys[sub] (bit patterns of positive doubles
+// order like the values, so an integer atomic min is exact and order-free).
+__device__ inline void stiff_add(double Kt[3], double Kr[3], double kn, double ks, const double n[3],
+                                 double d) {
+  for (int i = 0; i < 3; ++i) {
+    const double ni2 = n[i] * n[i];
+    Kt[i] += (kn - ks) * ni2 + ks;
+    Kr[i] += ks * d * d * (1.0 - ni2);
+  }
+}
+
+__global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
+                            const Mat *__restrict__ mats, long long N, long long cap, int mixed,
+                            int multi, int walls, unsigned long long *keys) {
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  unsigned long long key = 0x7ff0000000000000ull;   // +inf: no contact
+  int q = -1;
+  if (sl < N) {
+    const int s = (int)sl;
+    q = multi ? b.sid[s] : 0;
+    double Kt[3] = {0, 0, 0}, Kr[3] = {0, 0, 0};
+    auto row = [&](long long k, bool first) {
+      double kn, ks, n[3], d;
+      if (mixed) {
+        const float4 g = t.g32[k];
+        if (g.w == 0.0f) return;
+        const float4 h = t.hn32[k];
+        kn = g.w; ks = h.w; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        d = first ? t.oF32[k].w : t.oM32[k].w;
+      } else {
+        const double4_32a f = t.hfs[k];
+        if (f.w == 0.0) return;
+        const double4_32a h = t.hn[k];
+        kn = f.w; ks = h.w; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        d = first ? t.oF[k].w : t.oM[k].w;
+      }
+      stiff_add(Kt, Kr, kn, ks, n, d);
+    };
+    for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) row(k, true);
+    for (int e = t.down_start[s]; e < t.down_start[s + 1]; ++e) row(t.down[e], false);
+    const uint8_t fl = b.flags[s];
+    const double r = b.pos[s].w;
+    if (walls && (fl & 0x7e)) {
+      double kn, ks, tp;
+      wall_phys(mats, cs[q].wall_mat, b.mat[s], r, kn, ks, tp);
+      for (int wi = 0; wi < 6; ++wi) {
+        if (!(fl & (2 << wi))) continue;
+        const double4_32a h = b.whist[wi * cap + s];
+        double n[3] = {0, 0, 0};
+        n[wi >> 1] = 1.0;   // only n_i^2 enters
+        stiff_add(Kt, Kr, kn, ks, n, r - 0.5 * (fabs(h.w) / kn));
+      }
+    }
+    if (!(fl & 1)) {
+      const double4_32a mp = b.mprop[s];   // m, I
+      double best = INFINITY;
+      for (int i = 0; i < 3; ++i) {
+        if (Kt[i] > 0) best = fmin(best, sqrt(2.0) * sqrt(mp.x / Kt[i]));
+        if (Kr[i] > 0) best = fmin(best, sqrt(2.0) * sqrt(mp.y / Kr[i]));
+      }
+      key = (unsigned long long)__double_as_longlong(best);
+    }
+  }
+  // one atomic per warp when its bodies share a sub-scene (the usual case)
+  const int q0 = __shfl_sync(0xffffffffu, q, 0);
+  if (__all_sync(0xffffffffu, q == q0 || q < 0)) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_down_sync(0xffffffffu, key, o);
+      key = v < key ? v : key;
+    }
+    if (lane == 0 && q0 >= 0 && key != 0x7ff0000000000000ull) atomicMin(&keys[q0], key);
+  } else if (q >= 0 && key != 0x7ff0000000000000ull) {
+    atomicMin(&keys[q], key);
+  }
+}
+
+// Apply the new step to the sub-scenes due for an update this step (iteration
+// count a multiple of their interval), re-derive the next cell with it, and reset
+// every key.
+__global__ void k_dt_apply(CellState *cs, int nsub, const DevStatus *ds, unsigned long long *keys) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsub) return;
+  const unsigned long long key = keys[q];
+  keys[q] = 0x7ff0000000000000ull;
+  if (ds->pending) return;
+  CellState *c = cs + q;
+  if (!c->alive || !c->tstep || (c->iter % c->tstep_interval) != 0) return;
+  double dt = key == 0x7ff0000000000000ull ? c->tstep_default
+                                           : c->tstep_safety * __longlong_as_double((long long)key);
+  if (c->tstep_max > 0 && dt > c->tstep_max) dt = c->tstep_max;
+  c->dt = dt;
+  if (c->periodic) derive_next(c);
+}
 }  // namespace
 
-void launch_integrate(const Bodies &b, const Table &t, const CellState *cs, DevStatus *ds,
-                      const Mat *mats, const SceneConst &sc, long long cap, int mixed, int block,
-                      cudaStream_t st) {
-  if (sc.N <= 0) return;
-  const unsigned g = (unsigned)((sc.N + block - 1) / block);
+void launch_integrate(const StepDesc *d, long long N, int walls, const CellState *cs,
+                      DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st) {
+  if (N <= 0) return;
+  // kernels without the sphere-wall branch when no sub-scene has walls (fewer registers)
+#define DEM_INTEGRATE(K, B, W) K<B, W><<<(unsigned)((N + B - 1) / B), B, 0, st>>>(d, cs, ds, mats)
+#define DEM_INTEGRATE_ALL(K)                                                                  \
+  if (block == 128) { if (walls) DEM_INTEGRATE(K, 128, true); else DEM_INTEGRATE(K, 128, false); } \
+  else if (block == 512) { if (walls) DEM_INTEGRATE(K, 512, true); else DEM_INTEGRATE(K, 512, false); } \
+  else { if (walls) DEM_INTEGRATE(K, 256, true); else DEM_INTEGRATE(K, 256, false); }
   if (mixed) {
-    if (block == 128) k_integrate_mixed<128><<<g, 128, 0, st>>>(b, t, cs, ds, mats, sc, cap);
-    else if (block == 512) k_integrate_mixed<512><<<g, 512, 0, st>>>(b, t, cs, ds, mats, sc, cap);
-    else k_integrate_mixed<256><<<g, 256, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    DEM_INTEGRATE_ALL(k_integrate_mixed)
   } else {
-    if (block == 128) k_integrate<128><<<g, 128, 0, st>>>(b, t, cs, ds, mats, sc, cap);
-    else if (block == 512) k_integrate<512><<<g, 512, 0, st>>>(b, t, cs, ds, mats, sc, cap);
-    else k_integrate<256><<<g, 256, 0, st>>>(b, t, cs, ds, mats, sc, cap);
+    DEM_INTEGRATE_ALL(k_integrate)
   }
+#undef DEM_INTEGRATE_ALL
+#undef DEM_INTEGRATE
 }
 
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
                          cudaStream_t st) {
   const int threads = nsub < 128 ? 32 * ((nsub + 31) / 32) : 128;
   k_cell_advance<<<(nsub + threads - 1) / threads, threads, 0, st>>>(cs, nsub, ds, servo_partials);
+}
+
+void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub,
+                        const DevStatus *ds, const Mat *mats, long long N, long long cap,
+                        int mixed, int multi, int walls, unsigned long long *keys,
+                        cudaStream_t st) {
+  if (N > 0)
+    k_stiffness<<<blocks(N), kT, 0, st>>>(b, t, cs, mats, N, cap, mixed, multi, walls, keys);
+  k_dt_apply<<<(nsub + 127) / 128, 128, 0, st>>>(cs, nsub, ds, keys);
 }
 
 void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,

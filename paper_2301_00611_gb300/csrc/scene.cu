@@ -11,6 +11,7 @@
 // collider run is pending it runs the collider (collider.cu) and continues.
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -132,6 +133,19 @@ struct Readback {
   int totals[4];
 };
 
+// What a captured batch of steps depends on besides its step count.
+struct GraphKey {
+  long long N = -1, rows = -1;
+  int contact_block = 0, contact_per_sm = 0, integrate_block = 0, multi = 0, walls = 0, nsub = 0,
+      mixed = 0;
+  const void *cs = nullptr;
+  bool operator==(const GraphKey &o) const {
+    return N == o.N && rows == o.rows && contact_block == o.contact_block &&
+           contact_per_sm == o.contact_per_sm && integrate_block == o.integrate_block &&
+           multi == o.multi && walls == o.walls && nsub == o.nsub && mixed == o.mixed && cs == o.cs;
+  }
+};
+
 // A sub-scene: an independent scene sharing the library's arrays with the others
 // (its own cell or box, walls, gravity, damping, time step and clock; its bodies
 // carry its index in Bodies::sid).  Sub-scene 0 is the scene of the descriptor.
@@ -147,6 +161,8 @@ struct Sub {
   bool removing = false;          // removed; its bodies go at the next collider run
   bool velgrad_pending = false;   // velocity gradient for the next step (Cell.velGrad)
   double velgrad_next[9]{};
+  double tstep_default_rule = -1; // time stepper's defaultDt as set (< 0: from the p-wave step)
+  long long tstep_default_n = -1; // body count the derived default was computed for
 };
 
 struct dem_scene {
@@ -181,11 +197,16 @@ struct dem_scene {
   long long cell_cap = 0;
   int *scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
-  double *partials = nullptr;  // 1024 blocks x 16 doubles
+  double *partials = nullptr;  // 1024 blocks x 32 doubles
   double *servo = nullptr;     // kServoBlocks x 6 doubles
   int *deg_ws = nullptr;       // 2 x kDegreeBuckets ints (integration order)
   // launch shapes of the step kernels (none changes a result)
   int contact_block = 256, contact_per_sm = 8, integrate_block = 256, degree_order = 1;
+  int step_graphs = 1;           // replay captured batches of steps
+  StepDesc *step_d = nullptr;    // device step descriptor
+  StepDesc *step_h = nullptr;    // pinned staging copy
+  GraphKey graph_key{};
+  std::map<long long, cudaGraphExec_t> graphs;   // captured batches by step count
   double *partials_h = nullptr;
 
   std::vector<Sub> subs;         // sub-scene 0 always exists
@@ -196,6 +217,7 @@ struct dem_scene {
   Grid *grids_h = nullptr;       // pinned [subs_cap]
   int *shift_h = nullptr;        // pinned [subs_cap]
   unsigned long long *bbox_keys = nullptr;   // [6 * subs_cap]
+  unsigned long long *dt_keys = nullptr;     // [subs_cap] time-stepper minima (+inf bits)
   unsigned long long *bbox_h = nullptr;      // pinned [6 * subs_cap]
   int subs_cap = 0;
   unsigned long long steps_seen = 0;   // DevStatus::steps at the last read
@@ -274,6 +296,12 @@ dem_status wait(dem_scene *s) {
     if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
     else std::this_thread::yield();
   }
+}
+
+void drop_graphs(dem_scene *s) {
+  for (auto &kv : s->graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
 }
 
 void free_bodies(dem_scene *s, Bodies &b) {
@@ -357,10 +385,16 @@ dem_status ensure_subs(dem_scene *s, int need) {
   if ((r = wait(s))) return r;
   dfree(s, s->cs_d);
   s->cs_d = cs;
-  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys);
+  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys); dfree(s, s->dt_keys);
   if ((r = dalloc(s, &s->grids_d, nc)) || (r = dalloc(s, &s->id_shift_d, nc)) ||
-      (r = dalloc(s, &s->bbox_keys, 6LL * nc)))
+      (r = dalloc(s, &s->bbox_keys, 6LL * nc)) || (r = dalloc(s, &s->dt_keys, nc)))
     return r;
+  {
+    std::vector<unsigned long long> inf(nc, 0x7ff0000000000000ull);
+    CK(cudaMemcpyAsync(s->dt_keys, inf.data(), sizeof(unsigned long long) * nc,
+                       cudaMemcpyHostToDevice, s->st));
+    if ((r = wait(s))) return r;
+  }
   if (s->cs_rb) cudaFreeHost(s->cs_rb);
   if (s->grids_h) cudaFreeHost(s->grids_h);
   if (s->shift_h) cudaFreeHost(s->shift_h);
@@ -463,10 +497,18 @@ double default_dt(const dem_scene *s, const Sub &u) {
 // and without an explicit dt is an error only when nothing else can step
 dem_status ensure_dt(dem_scene *s) {
   for (Sub &u : s->subs) {
-    if (!u.used || u.dt_set || u.n == 0) continue;
-    u.cs.dt = default_dt(s, u);
-    u.dt_set = true;
-    s->cs_dirty = true;
+    if (!u.used || u.n == 0) continue;
+    if (!u.dt_set) {
+      u.cs.dt = default_dt(s, u);
+      u.dt_set = true;
+      s->cs_dirty = true;
+    }
+    // time stepper without contacts: safety x p-wave step of the current spheres
+    if (u.cs.tstep && u.tstep_default_rule <= 0 && u.tstep_default_n != u.n) {
+      u.cs.tstep_default = u.cs.tstep_safety * 2.0 * default_dt(s, u);
+      u.tstep_default_n = u.n;
+      s->cs_dirty = true;
+    }
   }
   if (s->N == 0) return fail(s, DEM_ERR_STATE, "no time step: the scene has no bodies");
   return DEM_OK;
@@ -868,14 +910,15 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
   }
   if ((e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMallocHost((void **)&s->rb_h, sizeof(Readback))) != cudaSuccess ||
-      (e = cudaMallocHost((void **)&s->partials_h, sizeof(double) * 1024 * 16)) != cudaSuccess) {
+      (e = cudaMallocHost((void **)&s->partials_h, sizeof(double) * 1024 * 32)) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&s->step_h, sizeof(StepDesc))) != cudaSuccess) {
     bad(e, "scene setup");
     dem_scene_destroy(s);
     return DEM_ERR_CUDA;
   }
   if (dalloc(s, &s->mats_d, kMaxMat) || dalloc(s, &s->ds_d, 1) ||
-      dalloc(s, &s->partials, 1024 * 16) || dalloc(s, &s->servo, kServoBlocks * 6) ||
-      dalloc(s, &s->deg_ws, 2 * kDegreeBuckets) || ensure_subs(s, 1)) {
+      dalloc(s, &s->partials, 1024 * 32) || dalloc(s, &s->servo, kServoBlocks * 6) ||
+      dalloc(s, &s->deg_ws, 2 * kDegreeBuckets) || dalloc(s, &s->step_d, 1) || ensure_subs(s, 1)) {
     g_create_error = s->err;
     dem_scene_destroy(s);
     return DEM_ERR_OOM;
@@ -916,6 +959,9 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
 void dem_scene_destroy(dem_scene *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
+  drop_graphs(s);
+  dfree(s, s->step_d);
+  if (s->step_h) cudaFreeHost(s->step_h);
   free_bodies(s, s->cur);
   free_bodies(s, s->alt);
   free_table(s, s->tab[0]);
@@ -925,7 +971,7 @@ void dem_scene_destroy(dem_scene *s) {
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
   dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo); dfree(s, s->deg_ws);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
-  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys);
+  dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys); dfree(s, s->dt_keys);
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->cs_rb) cudaFreeHost(s->cs_rb);
   if (s->grids_h) cudaFreeHost(s->grids_h);
@@ -1136,36 +1182,87 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
   }
   if ((r = ensure_dt(s))) return r;
   if ((r = prepare_step(s))) return r;
-  const SceneConst sc = scene_const(s);
   long long remaining = nsteps;
   while (remaining > 0) {
     if (s->need_rebuild && (r = rebuild(s))) return r;
+    const SceneConst sc = scene_const(s);
     const long long B = std::min<long long>(remaining, s->batch);
     const long long it0 = s->cs0().iter;
     const Table &t = s->tab[s->tc];
     cudaEvent_t *ev = s->timing ? s->tev.data() + 2 : nullptr;
-    for (long long i = 0; i < B; ++i) {
-      if (ev) CK(cudaEventRecord(ev[6 * i], s->st));
-      if (s->mixed)
-        launch_contact_mixed(t, s->cur, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
-                             s->contact_block, s->contact_per_sm, s->st);
-      else
-        launch_contact(t, s->cur, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
-                       s->contact_block, s->contact_per_sm, s->st);
-      if (ev) { CK(cudaEventRecord(ev[6 * i + 1], s->st)); CK(cudaEventRecord(ev[6 * i + 2], s->st)); }
-      launch_integrate(s->cur, t, s->cs_d, s->ds_d, s->mats_d, sc, s->cap, s->mixed,
-                       s->integrate_block, s->st);
-      if (ev) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
-      // servo update steps (PeriTriaxController every glob_update steps)
-      const bool upd = !sc.multi && s->cs0().triax && ((it0 + i + 1) % s->cs0().glob_update == 0);
-      if (upd) {
-        launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
-        s->launches += 1;
+    // the step kernels read tables and bodies through the step descriptor
+    *s->step_h = StepDesc{t, s->cur, sc, s->cap};
+    CK(cudaMemcpyAsync(s->step_d, s->step_h, sizeof(StepDesc), cudaMemcpyHostToDevice, s->st));
+    const long long rows = std::max(s->tab[0].cap, s->tab[1].cap);
+    const bool servo = !sc.multi && s->cs0().triax;
+    bool tstep = false;
+    for (const Sub &u : s->subs) tstep |= u.used && u.cs.tstep;
+    auto tstep_due = [&](long long i) {
+      for (const Sub &u : s->subs)
+        if (u.used && u.cs.tstep && (u.cs.iter + i) % u.cs.tstep_interval == 0) return true;
+      return false;
+    };
+    auto launch_steps = [&](bool record) -> dem_status {
+      for (long long i = 0; i < B; ++i) {
+        if (record) CK(cudaEventRecord(ev[6 * i], s->st));
+        if (s->mixed)
+          launch_contact_mixed(s->step_d, rows, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
+                               s->contact_block, s->contact_per_sm, s->st);
+        else
+          launch_contact(s->step_d, rows, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
+                         s->contact_block, s->contact_per_sm, s->st);
+        if (record) CK(cudaEventRecord(ev[6 * i + 1], s->st));
+        if (tstep && tstep_due(i)) {   // GlobalStiffnessTimeStepper: after the contacts
+          launch_timestepper(s->cur, t, s->cs_d, s->nsub(), s->ds_d, s->mats_d, sc.N, s->cap,
+                             s->mixed, sc.multi, sc.walls, s->dt_keys, s->st);
+          s->launches += 2;
+        }
+        if (record) CK(cudaEventRecord(ev[6 * i + 2], s->st));
+        launch_integrate(s->step_d, sc.N, sc.walls, s->cs_d, s->ds_d, s->mats_d, s->mixed,
+                         s->integrate_block, s->st);
+        if (record) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
+        // servo update steps (PeriTriaxController every glob_update steps)
+        const bool upd = servo && ((it0 + i + 1) % s->cs0().glob_update == 0);
+        if (upd) {
+          launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
+          s->launches += 1;
+        }
+        launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st);
+        if (record) CK(cudaEventRecord(ev[6 * i + 5], s->st));
       }
-      launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st);
-      if (ev) CK(cudaEventRecord(ev[6 * i + 5], s->st));
+      return DEM_OK;
+    };
+    if (s->step_graphs && !ev && !servo && !tstep) {
+      // replay a captured batch of B steps (one graph launch instead of 3B launches);
+      // captures are kept while nothing that shapes the launches changes
+      const GraphKey key{sc.N, rows, s->contact_block, s->contact_per_sm, s->integrate_block,
+                         sc.multi, sc.walls, s->nsub(), s->mixed ? 1 : 0, s->cs_d};
+      if (!(key == s->graph_key)) {
+        drop_graphs(s);
+        s->graph_key = key;
+      }
+      cudaGraphExec_t &ex = s->graphs[B];
+      if (!ex) {
+        CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+        const long long keep = s->launches;
+        dem_status q = launch_steps(false);
+        s->launches = keep;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->st, &g);
+        if (q) return q;
+        if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          ex = nullptr;
+          return cuda_fail(s, e, "cudaGraphInstantiate");
+        }
+      }
+      CK(cudaGraphLaunch(ex, s->st));
+    } else if ((r = launch_steps(ev != nullptr))) {
+      return r;
     }
-    s->launches += B * ((t.P > 0 ? 1 : 0) + 2);
+    s->launches += B * ((rows > 0 ? 1 : 0) + 2);
     CK(cudaGetLastError());
     if ((r = read_status(s))) return r;
     s->table_fresh = true;
@@ -1784,13 +1881,14 @@ bool valid_tuning(const dem_tuning &t) {
   return (t.contact_block == 128 || t.contact_block == 256) && t.contact_blocks_per_sm >= 1 &&
          t.contact_blocks_per_sm <= 64 &&
          (t.integrate_block == 128 || t.integrate_block == 256 || t.integrate_block == 512) &&
-         (t.degree_order == 0 || t.degree_order == 1);
+         (t.degree_order == 0 || t.degree_order == 1) && (t.step_graphs == 0 || t.step_graphs == 1);
 }
 void apply_tuning(dem_scene *s, const dem_tuning &t) {
   s->contact_block = t.contact_block;
   s->contact_per_sm = t.contact_blocks_per_sm;
   s->integrate_block = t.integrate_block;
   s->degree_order = t.degree_order;
+  s->step_graphs = t.step_graphs;
 }
 dem_tuning current_tuning(const dem_scene *s) {
   dem_tuning t{};
@@ -1798,6 +1896,7 @@ dem_tuning current_tuning(const dem_scene *s) {
   t.contact_blocks_per_sm = s->contact_per_sm;
   t.integrate_block = s->integrate_block;
   t.degree_order = s->degree_order;
+  t.step_graphs = s->step_graphs;
   return t;
 }
 }  // namespace
@@ -2038,5 +2137,102 @@ dem_status dem_get_state_range(dem_scene *s, long long first_id, long long n, do
       return r;
     }
   }
+  return DEM_OK;
+}
+
+// ------------------------------------------------------------------ micromechanics
+dem_status dem_get_micro(dem_scene *s, int sub, double *fabric, double *normal_stress,
+                         double *shear_stress, long long *n_contacts) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub >= s->nsub() || (sub >= 0 && !s->subs[sub].used))
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  if (sub >= 0 && s->layout_dirty && s->subs[sub].n > 0)
+    return fail(s, DEM_ERR_STATE, "sub-scene layout changed since the last step: step first");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  const Sub &u = s->subs[sub < 0 ? 0 : sub];
+  double V;
+  if (u.cs.periodic) V = std::fabs(m_det(u.cs.H));
+  else V = (u.cs.box_hi[0] - u.cs.box_lo[0]) * (u.cs.box_hi[1] - u.cs.box_lo[1]) *
+           (u.cs.box_hi[2] - u.cs.box_lo[2]);
+  double acc[28] = {0};
+  if (s->table_fresh && s->N > 0) {
+    const Table &t = s->tab[s->tc];
+    long long r0 = 0, r1 = t.P;
+    if (sub >= 0) {
+      CK(cudaMemcpyAsync(&s->rb_h->totals[0], t.row_start + u.slot0, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(&s->rb_h->totals[1], t.row_start + u.slot0 + u.n, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+      if ((r = wait(s))) return r;
+      r0 = s->rb_h->totals[0];
+      r1 = s->rb_h->totals[1];
+    }
+    if (r1 > r0) {
+      const Table tv = row_view(t, r0, r1 - r0);
+      const int nb = micro_blocks(tv.P);
+      launch_micro_rows(tv, s->mixed, s->partials, s->st);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(s->partials_h, s->partials, sizeof(double) * 28 * nb, cudaMemcpyDeviceToHost, s->st));
+      if ((r = wait(s))) return r;
+      for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 28; ++q) acc[q] += s->partials_h[28 * b + q];
+    }
+  }
+  const double nc = acc[0];
+  for (int q = 0; q < 9; ++q) {
+    if (fabric) fabric[q] = nc > 0 ? acc[1 + q] / nc : 0.0;
+    if (normal_stress) normal_stress[q] = V > 0 ? -acc[10 + q] / V : 0.0;
+    if (shear_stress) shear_stress[q] = V > 0 ? -acc[19 + q] / V : 0.0;
+  }
+  if (n_contacts) *n_contacts = (long long)nc;
+  return DEM_OK;
+}
+
+dem_status dem_get_body_stress(dem_scene *s, double *out) {
+  if (!s || !out) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  const long long N = s->N;
+  if (N == 0) return DEM_OK;
+  if (!s->table_fresh) {   // no contacts computed for the current layout yet
+    std::memset(out, 0, sizeof(double) * 9 * N);
+    return DEM_OK;
+  }
+  double *dev = nullptr;
+  if ((r = dalloc(s, &dev, 9 * N))) return r;
+  const SceneConst sc = scene_const(s);
+  launch_body_stress(s->cur, s->tab[s->tc], N, s->cap, s->mixed, sc.walls, sc.multi, s->cs_d,
+                     s->mats_d, dev, s->st);
+  CK(cudaGetLastError());
+  std::vector<double> h(9 * N);
+  std::vector<int> slot(N);
+  CK(cudaMemcpyAsync(h.data(), dev, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(slot.data(), s->slot_of_id, sizeof(int) * N, cudaMemcpyDeviceToHost, s->st));
+  dfree(s, dev);
+  if ((r = wait(s))) return r;
+  for (long long i = 0; i < N; ++i)
+    std::memcpy(out + 9 * i, h.data() + 9 * (long long)slot[i], sizeof(double) * 9);
+  return DEM_OK;
+}
+
+// ------------------------------------------------------------------ time stepper
+dem_status dem_set_timestepper(dem_scene *s, int sub, double safety, int interval,
+                               double default_dt, double max_dt) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  if (!(safety > 0) || !(safety <= 1) || interval < 1 || !std::isfinite(default_dt) ||
+      !std::isfinite(max_dt))
+    return fail(s, DEM_ERR_INVALID_ARG, "bad time-stepper parameters");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  Sub &u = s->subs[sub];
+  u.cs.tstep = 1;
+  u.cs.tstep_safety = safety;
+  u.cs.tstep_interval = interval;
+  u.cs.tstep_max = max_dt;
+  u.tstep_default_rule = default_dt;
+  u.tstep_default_n = -1;
+  if (default_dt > 0) u.cs.tstep_default = default_dt;
+  s->cs_dirty = true;
   return DEM_OK;
 }

@@ -106,6 +106,7 @@ class Tuning(ctypes.Structure):
         ("contact_blocks_per_sm", ctypes.c_int),
         ("integrate_block", ctypes.c_int),
         ("degree_order", ctypes.c_int),
+        ("step_graphs", ctypes.c_int),
     ]
 
 
@@ -144,6 +145,10 @@ _SIGS = {
     "dem_get_subscene_stats": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_set_subscene_velgrad": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_num_bodies": (ctypes.c_int, [_P, _P]),
+    "dem_get_micro": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
+    "dem_get_body_stress": (ctypes.c_int, [_P, _P]),
+    "dem_set_timestepper": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double]),
     "dem_get_state_range": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_longlong, _P, _P, _P,
                                            _P]),
     "dem_get_tuning": (ctypes.c_int, [_P, _P]),
@@ -420,6 +425,25 @@ class Scene:
     def set_subscene_velgrad(self, sub, L):
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def set_timestepper(self, safety=0.8, interval=1, default_dt=-1.0, max_dt=0.0, sub=0):
+        """GlobalStiffnessTimeStepper (dem_set_timestepper)."""
+        self._check(self._lib.dem_set_timestepper(self._h, int(sub), float(safety), int(interval),
+                                                  float(default_dt), float(max_dt)))
+
+    def micro(self, sub=-1):
+        """Fabric tensor and the normal / shear parts of the contact stress (dem_get_micro)."""
+        F, SN, ST = np.empty((3, 3)), np.empty((3, 3)), np.empty((3, 3))
+        nc = ctypes.c_longlong()
+        self._check(self._lib.dem_get_micro(self._h, int(sub), _ptr(F), _ptr(SN), _ptr(ST),
+                                            ctypes.byref(nc)))
+        return {"fabric": F, "normal_stress": SN, "shear_stress": ST, "n_contacts": nc.value}
+
+    def body_stress(self):
+        """Per-sphere stress tensors (dem_get_body_stress), shape (n, 3, 3) in id order."""
+        out = np.empty((self.n, 9))
+        self._check(self._lib.dem_get_body_stress(self._h, _ptr(out)))
+        return out.reshape(-1, 3, 3)
 
     def state_range(self, first_id, n):
         out = {k: np.empty((n, 3)) for k in ("pos", "vel", "angvel")}

@@ -1,6 +1,7 @@
 """Launch shapes (dem_set_tuning / dem_autotune) change no result: every row and
 every body is computed by one thread with the same arithmetic whatever the block
-size, persistent grid or body order, so trajectories must be bit-identical."""
+size, persistent grid, body order or whether a batch of steps is replayed from a
+captured CUDA graph, so trajectories must be bit-identical."""
 import numpy as np
 import pytest
 
@@ -9,9 +10,12 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 SHAPES = [
-    dict(contact_block=256, contact_blocks_per_sm=8, integrate_block=256, degree_order=1),
-    dict(contact_block=128, contact_blocks_per_sm=3, integrate_block=512, degree_order=0),
-    dict(contact_block=256, contact_blocks_per_sm=1, integrate_block=128, degree_order=1),
+    dict(contact_block=256, contact_blocks_per_sm=8, integrate_block=256, degree_order=1,
+         step_graphs=1),
+    dict(contact_block=128, contact_blocks_per_sm=3, integrate_block=512, degree_order=0,
+         step_graphs=0),
+    dict(contact_block=256, contact_blocks_per_sm=1, integrate_block=128, degree_order=1,
+         step_graphs=1),
 ]
 
 
@@ -67,7 +71,7 @@ def test_tuning_rejects_out_of_range(pkg):
     w = _workloads()[1]
     g = pkg.Scene.from_workload(w)
     for bad in (dict(contact_block=64), dict(contact_blocks_per_sm=0), dict(integrate_block=1024),
-                dict(degree_order=2)):
+                dict(degree_order=2), dict(step_graphs=3)):
         with pytest.raises(pkg.DemError) as e:
             g.set_tuning(**bad)
         assert e.value.code == 1

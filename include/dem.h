@@ -314,14 +314,16 @@ dem_status dem_get_state_range(dem_scene *scene, long long first_id, long long n
  *                          contact rows (lanes of a warp get similar row counts);
  *                          0: in slot order
  *   step_graphs            1: a batch of steps is captured once as a CUDA graph and
- *                          replayed (one launch per batch; the kernels read tables and
- *                          bodies through a device-resident descriptor, so a capture
- *                          stays valid across collider runs until the body count, a
- *                          table capacity, a launch shape or the sub-scene count
- *                          changes); 0: every kernel launched one by one.  Batches
- *                          with per-kernel timing or the stress servo are never
- *                          captured.
- * Defaults: 256, 8, 256, 1, 1. */
+ *                          replayed (one launch per batch; the kernels then read
+ *                          tables and bodies through a device-resident descriptor, so
+ *                          a capture stays valid across collider runs until the body
+ *                          count, a table capacity, a launch shape or the sub-scene
+ *                          count changes); 0: every kernel launched one by one, with
+ *                          the arrays as launch parameters (fewer registers);
+ *                          -1: graphs below 262,144 bodies, where launch overhead
+ *                          matters.  Batches with per-kernel timing, the stress servo
+ *                          or the time stepper are never captured.
+ * Defaults: 256, 8, 256, 1, -1. */
 typedef struct dem_tuning {
     int contact_block;
     int contact_blocks_per_sm;
@@ -344,6 +346,23 @@ dem_status dem_get_tuning(const dem_scene *scene, dem_tuning *tuning);
  * any fixed shape gives.  The best shape is applied and, if chosen is non-null,
  * written there.  Errors: INVALID_ARG (steps_per_trial < 1), those of dem_step. */
 dem_status dem_autotune(dem_scene *scene, long long steps_per_trial, dem_tuning *chosen);
+
+/* Contact law of a sub-scene (0 for a plain scene), chosen before its first step
+ * (STATE afterwards, INVALID_ARG for an unknown law):
+ *   DEM_LAW_LINEAR          Ip2_FrictMat_FrictMat_FrictPhys + Law2_ScGeom_FrictPhys_
+ *                           CundallStrack (the default): Fn = kn pen
+ *   DEM_LAW_HERTZ_MINDLIN   Ip2_FrictMat_FrictMat_MindlinPhys + Law2_ScGeom_MindlinPhys_
+ *                           Mindlin (class references): Fn = kno pen^3/2 with
+ *                           kno = 4/3 E* sqrt(R*), shear stiffness kso pen^1/2 with
+ *                           kso = 8 sqrt(R*) / ((2-nu1)/G1 + (2-nu2)/G2) (2 sqrt(4R) G /
+ *                           (2 - nu) for equal materials, as the text writes),
+ *                           1/E* = sum (1 - nu^2)/E, R* = r1 r2 / (r1 + r2) (a wall: r),
+ *                           G = E / (2 (1 + nu)), the material's poisson being the true
+ *                           Poisson ratio; the same shear transport and Coulomb cap; no
+ *                           viscous damping, adhesion or rolling moments.
+ * dem_get_contacts then reports (kno, kso, tan phi) in phys. */
+enum { DEM_LAW_LINEAR = 0, DEM_LAW_HERTZ_MINDLIN = 1 };
+dem_status dem_set_law(dem_scene *scene, int sub, int law);
 
 /* GlobalStiffnessTimeStepper (section 2.1.5 "Stability considerations", eq. 2.12 -
  * 2.14; class reference) for sub-scene `sub` (0 for a plain scene).  On every step

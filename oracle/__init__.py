@@ -77,6 +77,7 @@ def _load():
         "orc_step": (_i, [_p, _l]),
         "orc_set_triax": (_i, [_p, _p, _i, _p, _d, _i]),
         "orc_set_timestepper": (_i, [_p, _d, _i, _d, _d]),
+        "orc_set_law": (_i, [_p, _i]),
         "orc_num_bodies": (_l, [_p]),
         "orc_get_state": (None, [_p, _p, _p, _p, _p, _p, _p]),
         "orc_set_state": (_i, [_p, _p, _p, _p, _p]),
@@ -217,6 +218,11 @@ class OracleScene:
                                    float(grow_damping), int(glob_update)) != 0:
             raise ValueError("set_triax needs a periodic scene and valid parameters")
 
+    def set_law(self, law):
+        """0: Cundall-Strack (linear), 1: Hertz-Mindlin (reading R18 in dem_oracle.c)."""
+        if self._lib.orc_set_law(self._h, int(law)) != 0:
+            raise ValueError("unknown contact law")
+
     def set_timestepper(self, safety=0.8, interval=1, default_dt=-1.0, max_dt=0.0):
         """GlobalStiffnessTimeStepper (reading R17 in dem_oracle.c)."""
         if self._lib.orc_set_timestepper(self._h, float(safety), int(interval), float(default_dt),
@@ -303,8 +309,10 @@ class OracleScene:
         fabricTensor F = (1/n_c) sum n n; normalShearStressTensors, read with compression
         negative and l the current centroid distance: normal part -(1/V) sum l N n n,
         shear part -(1/V) sum l n Fs; bodyStressTensors (1/V_b) sum x f per sphere, x the
-        contact point relative to the centre, f the force on the sphere (walls included).
-        Written out from the contact list (numpy, FP64)."""
+        contact point relative to the centre, f the force on the sphere (walls included),
+        x read in the configuration the contact forces were computed in (the contact
+        geometry), not from the positions the integrator has since moved.  Written out
+        from the contact list (numpy, FP64)."""
         c = self.contacts()
         pos = self.state()["pos"]
         r = self._radius
@@ -325,17 +333,17 @@ class OracleScene:
         shear = -np.einsum("k,ki,kj->ij", l, n, fs) / V
         body = np.zeros((self.n, 3, 3))
         F = c["fn"] + c["fs"]                      # force on id2
+        # contact point relative to each centre in the configuration the forces were
+        # computed in: (r - pen/2) along the normal from body 1 (toward body 2), the
+        # opposite way from body 2, and from the sphere toward a wall
         for k in range(len(c["id1"])):
-            b2 = c["id2"][k]
+            b2, nk, pk = c["id2"][k], c["normal"][k], c["pen"][k]
             if c["id1"][k] >= 0:
                 b1 = c["id1"][k]
-                x1 = c["cpoint"][k] - pos[b1]      # contact point - centre of body 1
-                lk = r[b1] + r[b2] - c["pen"][k]
-                x2 = x1 - lk * c["normal"][k]      # relative to the image of body 2
-                body[b1] += np.outer(x1, -F[k])
-                body[b2] += np.outer(x2, F[k])
+                body[b1] += np.outer((r[b1] - 0.5 * pk) * nk, -F[k])
+                body[b2] += np.outer(-(r[b2] - 0.5 * pk) * nk, F[k])
             else:
-                body[b2] += np.outer(c["cpoint"][k] - pos[b2], F[k])
+                body[b2] += np.outer(-(r[b2] - 0.5 * pk) * nk, F[k])
         body /= (4.0 / 3.0 * np.pi * r ** 3)[:, None, None]
         return {"fabric": fabric, "normal_stress": normal, "shear_stress": shear,
                 "body_stress": body, "n_contacts": nc}

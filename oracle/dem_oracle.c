@@ -108,6 +108,8 @@ struct orc_scene {
     double grav_work, nonvisc_damp, plast_dissip;
     /* stress-controlled periodic cell (PeriTriaxController reading R16) */
     int triax, stress_mask, glob_update;
+    /* contact law: 0 Law2_ScGeom_FrictPhys_CundallStrack, 1 Hertz-Mindlin (R18) */
+    int law;
     /* GlobalStiffnessTimeStepper (R17) */
     int tstep, tstep_interval;
     double tstep_safety, tstep_default, tstep_max;
@@ -564,12 +566,53 @@ static void ip2_frict(const orc_mat *m1, double r1, const orc_mat *m2, double r2
     *tanphi = tan(phi);
 }
 
+/* Ip2_FrictMat_FrictMat_MindlinPhys (class reference; reading R18): Hertz normal
+ * constant kno = 4/3 E* sqrt(R*) and Mindlin shear constant kso, with the textbook
+ * combinations 1/E* = (1 - nu1^2)/E1 + (1 - nu2^2)/E2, R* = r1 r2 / (r1 + r2) (a wall
+ * is an infinite radius: r2 < 0 gives R* = r1), G_i = E_i / (2 (1 + nu_i)) and
+ * kso = 8 sqrt(R*) / ((2 - nu1)/G1 + (2 - nu2)/G2), which is the text's
+ * 2 sqrt(4R) G / (2 - nu) for equal materials.  The FrictMat "poisson" is the true
+ * Poisson ratio here (ElastMat reference). */
+static void ip2_mindlin(const orc_mat *m1, double r1, const orc_mat *m2, double r2,
+                        double *kno, double *kso, double *tanphi) {
+    double Es = 1.0 / ((1 - m1->poisson * m1->poisson) / m1->young +
+                       (1 - m2->poisson * m2->poisson) / m2->young);
+    double Rs = r2 < 0 ? r1 : r1 * r2 / (r1 + r2);
+    double G1 = m1->young / (2 * (1 + m1->poisson)), G2 = m2->young / (2 * (1 + m2->poisson));
+    *kno = 4.0 / 3.0 * Es * sqrt(Rs);
+    *kso = 8.0 * sqrt(Rs) / ((2 - m1->poisson) / G1 + (2 - m2->poisson) / G2);
+    double phi = m1->friction < m2->friction ? m1->friction : m2->friction;
+    *tanphi = tan(phi);
+}
+
+/* tangent stiffnesses of a contact at penetration pen (the Hertz-Mindlin constants
+ * are stored in kn, ks: k_n = 3/2 kno pen^1/2, k_s = kso pen^1/2) */
+static void tangent_stiffness(const orc_scene *s, const orc_contact *ct, double *kn, double *ks) {
+    if (s->law == 1) {
+        double sq = sqrt(ct->pen > 0 ? ct->pen : 0.0);
+        *kn = 1.5 * ct->kn * sq;
+        *ks = ct->ks * sq;
+    } else {
+        *kn = ct->kn;
+        *ks = ct->ks;
+    }
+}
+
+int orc_set_law(orc_scene *s, int law) {
+    if (!s || (law != 0 && law != 1)) return -1;
+    s->law = law;
+    return 0;
+}
+
 /* One contact: given the current normal n, penetration pen, contact point, the
  * velocities at the contact and the FrictPhys, update the shear force and
  * return the force on body 2 (sections 2.1.3 and 2.1.4). */
 static void shear_and_law(orc_contact *ct, const double *n, double pen, const double *v1,
                           const double *w1, const double *v2, const double *w2, double r1,
-                          double r2, double l, double dt, double *F2, double *plast) {
+                          double r2, double l, double dt, int law, double *F2, double *plast) {
+    /* Hertz-Mindlin (R18): Fn = kno pen^3/2 and the shear spring at ks = kso pen^1/2 */
+    double sq = law == 1 ? sqrt(pen) : 1.0;
+    double ks = law == 1 ? ct->ks * sq : ct->ks;
     /* 1. motion of the contact frame: both increments from the previous value (R5) */
     double a[3], tn[3], d1[3], d2[3], fs[3];
     v_cross(ct->nprev, n, a);                               /* n- x n */
@@ -589,9 +632,9 @@ static void shear_and_law(orc_contact *ct, const double *n, double pen, const do
     double v12s[3];
     for (int k = 0; k < 3; ++k) v12s[k] = v12[k] - vn * n[k];
     /* shear spring increment on body 2 (R2) */
-    for (int k = 0; k < 3; ++k) fs[k] = fs[k] - ct->ks * (dt * v12s[k]);
+    for (int k = 0; k < 3; ++k) fs[k] = fs[k] - ks * (dt * v12s[k]);
     /* Law2_ScGeom_FrictPhys_CundallStrack: Fn = kn pen, Coulomb cap */
-    double Fn = ct->kn * pen;
+    double Fn = law == 1 ? ct->kn * pen * sq : ct->kn * pen;
     double maxFs = Fn * ct->tanphi;
     double fs2 = v_dot(fs, fs);
     if (fs2 > maxFs * maxFs) {
@@ -600,7 +643,7 @@ static void shear_and_law(orc_contact *ct, const double *n, double pen, const do
         for (int k = 0; k < 3; ++k) fs[k] = fs[k] * scale;
         /* slip work (trial - final)/ks . final */
         double dd[3] = {trial[0] - fs[0], trial[1] - fs[1], trial[2] - fs[2]};
-        *plast += v_dot(dd, fs) / ct->ks;
+        *plast += v_dot(dd, fs) / ks;
     }
     for (int k = 0; k < 3; ++k) {
         ct->fs[k] = fs[k];
@@ -721,7 +764,9 @@ static void triax_update(orc_scene *s) {
             double F = ct->fn * ct->n[a] + ct->fs[a];
             sig[a] += F * (-l * ct->n[a]);
             double b = l * ct->n[a];
-            K[a] += ct->kn * (b * b);
+            double kt, kst;
+            tangent_stiffness(s, ct, &kt, &kst);
+            K[a] += kt * (b * b);
         }
     }
     double L[9];
@@ -777,14 +822,16 @@ static void stiffness_dt(orc_scene *s) {
     for (long k = 0; k < s->ncon; ++k) {
         const orc_contact *ct = &s->con[k];
         long bodies[2] = {ct->id1, ct->id2};
+        double kn, ks;
+        tangent_stiffness(s, ct, &kn, &ks);
         for (int e = 0; e < 2; ++e) {
             long b = bodies[e];
             if (b < 0) continue;   /* the wall side */
             double d = s->radius[b] - 0.5 * ct->pen;
             for (int i = 0; i < 3; ++i) {
                 double ni2 = ct->n[i] * ct->n[i];
-                Kt[3 * b + i] += (ct->kn - ct->ks) * ni2 + ct->ks;
-                Kr[3 * b + i] += ct->ks * d * d * (1.0 - ni2);
+                Kt[3 * b + i] += (kn - ks) * ni2 + ks;
+                Kr[3 * b + i] += ks * d * d * (1.0 - ni2);
             }
         }
     }
@@ -858,12 +905,16 @@ static int step_once(orc_scene *s) {
             n[ax] = dist >= 0 ? 1.0 : -1.0;
             double pen = r - fabs(dist);
             if (ct->kn == 0) {
-                ip2_frict(&s->mats[0], r, &s->mats[s->mat[j]], r, &ct->kn, &ct->ks, &ct->tanphi);
+                if (s->law == 1)
+                    ip2_mindlin(&s->mats[s->mat[j]], r, &s->mats[0], -1.0, &ct->kn, &ct->ks,
+                                &ct->tanphi);
+                else
+                    ip2_frict(&s->mats[0], r, &s->mats[s->mat[j]], r, &ct->kn, &ct->ks, &ct->tanphi);
                 for (int q = 0; q < 3; ++q) { ct->nprev[q] = n[q]; ct->fs[q] = 0; }
             }
             double zero[3] = {0, 0, 0};
             shear_and_law(ct, n, pen, zero, zero, s->vel + 3 * j, s->angvel + 3 * j, r, r,
-                          2 * r - pen, dt, F2, &s->plast_dissip);
+                          2 * r - pen, dt, s->law, F2, &s->plast_dissip);
             for (int q = 0; q < 3; ++q) ct->cp[q] = x2[q] - (r - 0.5 * pen) * n[q];
             for (int q = 0; q < 3; ++q) arm[q] = ct->cp[q] - x2[q];
             v_cross(arm, F2, T);
@@ -884,12 +935,16 @@ static int step_once(orc_scene *s) {
         m_vec(W, cd, wc);
         for (int q = 0; q < 3; ++q) v2i[q] = s->vel[3 * j + q] + (s->periodic ? wc[q] : 0.0);
         if (ct->kn == 0) {
-            ip2_frict(&s->mats[s->mat[i]], r1, &s->mats[s->mat[j]], r2, &ct->kn, &ct->ks,
-                      &ct->tanphi);
+            if (s->law == 1)
+                ip2_mindlin(&s->mats[s->mat[i]], r1, &s->mats[s->mat[j]], r2, &ct->kn, &ct->ks,
+                            &ct->tanphi);
+            else
+                ip2_frict(&s->mats[s->mat[i]], r1, &s->mats[s->mat[j]], r2, &ct->kn, &ct->ks,
+                          &ct->tanphi);
             for (int q = 0; q < 3; ++q) { ct->nprev[q] = n[q]; ct->fs[q] = 0; }   /* R6 */
         }
         shear_and_law(ct, n, pen, s->vel + 3 * i, s->angvel + 3 * i, v2i, s->angvel + 3 * j,
-                      r1, r2, l, dt, F2, &s->plast_dissip);
+                      r1, r2, l, dt, s->law, F2, &s->plast_dissip);
         for (int q = 0; q < 3; ++q) { ct->cp[q] = x1[q] + (r1 - 0.5 * pen) * n[q]; F1[q] = -F2[q]; }
         /* torques from the contact point (R4) */
         for (int q = 0; q < 3; ++q) arm[q] = ct->cp[q] - x1[q];
@@ -1096,8 +1151,12 @@ void orc_get_energy(const orc_scene *s, double *out) {
     }
     for (long k = 0; k < s->ncon; ++k) {
         const orc_contact *ct = &s->con[k];
-        if (ct->kn > 0) el += ct->fn * ct->fn / (2 * ct->kn);
-        if (ct->ks > 0) el += v_dot(ct->fs, ct->fs) / (2 * ct->ks);
+        double kn, ks;
+        tangent_stiffness(s, ct, &kn, &ks);
+        /* normal spring energy: Fn^2 / (2 kn) (linear), 2/5 kno pen^5/2 = 2/5 Fn pen (Hertz) */
+        if (s->law == 1) el += 0.4 * ct->fn * ct->pen;
+        else if (kn > 0) el += ct->fn * ct->fn / (2 * kn);
+        if (ks > 0) el += v_dot(ct->fs, ct->fs) / (2 * ks);
     }
     out[0] = kt; out[1] = kr; out[2] = s->grav_work; out[3] = s->nonvisc_damp;
     out[4] = s->plast_dissip; out[5] = el;

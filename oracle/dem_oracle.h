@@ -39,6 +39,8 @@ int orc_set_dt(orc_scene *s, double dt);
 int orc_set_velgrad(orc_scene *s, const double *L9);
 int orc_step(orc_scene *s, long nsteps);
 /* stress-controlled periodic cell (PeriTriaxController, reading R16 in dem_oracle.c) */
+/* contact law: 0 linear Cundall-Strack (default), 1 Hertz-Mindlin (reading R18) */
+int orc_set_law(orc_scene *s, int law);
 /* GlobalStiffnessTimeStepper: safety coefficient, update interval (steps), defaultDt
  * (< 0: safety x p-wave step), maxDt (<= 0: none). */
 int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,

@@ -37,12 +37,13 @@ constexpr int kQ = 64;   // per-warp queue of real rows (< 32 left over + 32 new
 // H (image shift) and of W (velocity of a unit shift); all zero when aperiodic.
 struct RowCell {
   double dt, H[3], W[3];
-  int periodic;
+  int periodic, law;
 };
 __device__ __forceinline__ RowCell row_cell(const CellState &c) {
   RowCell r;
   r.dt = c.dt;
   r.periodic = c.periodic;
+  r.law = c.law;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     r.H[i] = c.periodic ? c.H[4 * i] : 0.0;
@@ -53,6 +54,7 @@ __device__ __forceinline__ RowCell row_cell(const CellState &c) {
 
 // One real row: Ip2 on creation, shear transport and increment, Law2, outputs.
 // dx, dy, dz, l2 are the branch vector and its squared length from the exact test.
+template <bool kHertz>
 __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const Mat *__restrict__ mats,
                                          long long k, double dx, double dy, double dz, double l2,
                                          double r1, double r2, const RowCell &rc) {
@@ -69,12 +71,15 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double pen = R - l;                                  // penetrationDepth
   double kn = fs.w, ks = hn.w, tanphi;
   if (kn == 0.0) {
-    // Ip2_FrictMat_FrictMat_FrictPhys (new contact)
-    const Mat m1 = mats[b.mat[pr.x]], m2 = mats[b.mat[pr.y]];
-    const double k1 = m1.young * (2 * r1), k2 = m2.young * (2 * r2);
-    kn = k1 * k2 / (k1 + k2);
-    const double s1 = m1.young * m1.poisson * (2 * r1), s2 = m2.young * m2.poisson * (2 * r2);
-    ks = s1 * s2 / (s1 + s2);
+    const Mat &m1 = mats[b.mat[pr.x]], &m2 = mats[b.mat[pr.y]];
+    if (kHertz && rc.law) {   // Ip2_FrictMat_FrictMat_MindlinPhys: constants kno, kso
+      mindlin_phys(m1, r1, m2, r2, kn, ks);
+    } else {        // Ip2_FrictMat_FrictMat_FrictPhys (new contact)
+      const double k1 = m1.young * (2 * r1), k2 = m2.young * (2 * r2);
+      kn = k1 * k2 / (k1 + k2);
+      const double s1 = m1.young * m1.poisson * (2 * r1), s2 = m2.young * m2.poisson * (2 * r2);
+      ks = s1 * s2 / (s1 + s2);
+    }
     tanphi = fmin(m1.tanphi, m2.tanphi);
     t.tanphi[k] = tanphi;
     fs = make_double4_32a(0, 0, 0, kn);
@@ -108,12 +113,14 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double uy = f * (v2.y - v1.y) - (rz * nx - rx * nz);
   const double uz = f * (v2.z - v1.z) - (rx * ny - ry * nx);
   const double vn = nx * ux + ny * uy + nz * uz;
-  const double kd = ks * dt;
+  // Hertz-Mindlin: shear stiffness kso pen^1/2 and normal force kno pen^3/2
+  const double sq = (kHertz && rc.law) ? sqrt(pen) : 1.0;
+  const double kd = (ks * sq) * dt;
   fx -= kd * (ux - vn * nx);
   fy -= kd * (uy - vn * ny);
   fz -= kd * (uz - vn * nz);
   // Law2: normal force and Coulomb cap
-  const double Fn = kn * pen;
+  const double Fn = (kHertz && rc.law) ? kn * pen * sq : kn * pen;
   const double maxFs = Fn * tanphi;
   const double fs2 = fx * fx + fy * fy + fz * fz;
   if (fs2 > maxFs * maxFs) {
@@ -147,14 +154,20 @@ struct QRow {
 // the results do not depend on which lane (or which pass) takes it.
 // Sub-scenes (multi): each row takes its cell state from the sub-scene of body 1
 // (both bodies of a row always belong to the same sub-scene).
-template <int kT>
-__global__ void __launch_bounds__(kT, 768 / kT) k_contact(const StepDesc *__restrict__ d,
+// Register budget by block size (the autotuner picks): 128-thread blocks at six per SM
+// (80 registers, a few spilled), 256-thread blocks at two per SM (no spills).
+// kDesc: the table and bodies come from the device descriptor (a captured batch of
+// steps stays valid across collider runs); otherwise from the launch parameters,
+// which the kernel reads straight from the constant bank (fewer registers).
+template <int kT, bool kHertz, bool kDesc>
+__global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDesc *__restrict__ d,
+                                                          Table tp, Bodies bp,
                                                           const CellState *__restrict__ cs,
                                                           const DevStatus *__restrict__ ds,
                                                           const Mat *__restrict__ mats, int multi) {
   constexpr int kWarps = kT / 32;
-  const Table &t = d->t;
-  const Bodies &b = d->b;
+  const Table &t = kDesc ? d->t : tp;
+  const Bodies &b = kDesc ? d->b : bp;
   if (ds->pending) return;
   __shared__ QRow q[kWarps][kQ];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(kT, 768 / kT) k_contact(const StepDesc *__rest
     __syncwarp();
     if (cnt >= 32) {
       const QRow e = wq[lane];
-      real_row(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
+      real_row<kHertz>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
                multi ? row_cell(cs[e.q]) : rc0);
       __syncwarp();
       if (lane < cnt - 32) wq[lane] = wq[lane + 32];
@@ -219,19 +232,29 @@ __global__ void __launch_bounds__(kT, 768 / kT) k_contact(const StepDesc *__rest
   }
   if (lane < cnt) {
     const QRow e = wq[lane];
-    real_row(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2, multi ? row_cell(cs[e.q]) : rc0);
+    real_row<kHertz>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2, multi ? row_cell(cs[e.q]) : rc0);
   }
 }
 }  // namespace
 
-void launch_contact(const StepDesc *d, long long rows, const CellState *cs, const DevStatus *ds,
-                    const Mat *mats, int multi, int nsm, int block, int per_sm, cudaStream_t st) {
+void launch_contact(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
+                    const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
+                    int hertz, int nsm, int block, int per_sm, cudaStream_t st) {
   if (rows <= 0) return;
   long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  if (block == 128) k_contact<128><<<grid, 128, 0, st>>>(d, cs, ds, mats, multi);
-  else k_contact<256><<<grid, 256, 0, st>>>(d, cs, ds, mats, multi);
+  // the Hertz-Mindlin branches are compiled only into the variant a scene using that
+  // law needs (they cost the linear law registers)
+#define DEM_C(B, H, D) k_contact<B, H, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
+#define DEM_C2(H, D) if (block == 128) DEM_C(128, H, D); else DEM_C(256, H, D);
+  if (desc) {
+    if (hertz) { DEM_C2(true, true) } else { DEM_C2(false, true) }
+  } else {
+    if (hertz) { DEM_C2(true, false) } else { DEM_C2(false, false) }
+  }
+#undef DEM_C2
+#undef DEM_C
 }
 
 }  // namespace dem

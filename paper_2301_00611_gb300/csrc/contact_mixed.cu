@@ -40,12 +40,13 @@ struct QRowF {
 struct RowCellF {
   double dt;
   float dH[3], W[3];
-  int periodic;
+  int periodic, law;
 };
 __device__ __forceinline__ RowCellF row_cell_f(const CellState &c) {
   RowCellF r;
   r.dt = c.dt;
   r.periodic = c.periodic;
+  r.law = c.law;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     r.dH[i] = c.periodic ? c.dHf[i] : 0.0f;
@@ -55,6 +56,7 @@ __device__ __forceinline__ RowCellF row_cell_f(const CellState &c) {
 }
 
 // One real row in mixed precision (Ip2 on creation, shear transport, Law2, outputs).
+template <bool kHertz>
 __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
                                                const Mat *__restrict__ mats, const QRowF &e,
                                                const RowCellF &rc) {
@@ -75,13 +77,20 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   float4 hn = t.hn32[k];
   float ks;
   double tanphi;
-  if (kn == 0.0f) {   // Ip2_FrictMat_FrictMat_FrictPhys on a new contact
-    const Mat m1 = mats[b.mat[pr.x]], m2 = mats[b.mat[pr.y]];
-    const float k1 = (float)m1.young * (2 * r1), k2 = (float)m2.young * (2 * r2);
-    kn = k1 * k2 / (k1 + k2);
-    const float s1 = (float)(m1.young * m1.poisson) * (2 * r1);
-    const float s2 = (float)(m2.young * m2.poisson) * (2 * r2);
-    ks = s1 * s2 / (s1 + s2);
+  if (kn == 0.0f) {   // Ip2 on a new contact
+    const Mat &m1 = mats[b.mat[pr.x]], &m2 = mats[b.mat[pr.y]];
+    if (kHertz && rc.law) {     // MindlinPhys constants kno, kso (formed once per contact in FP64)
+      double kno, kso;
+      mindlin_phys(m1, r1, m2, r2, kno, kso);
+      kn = (float)kno;
+      ks = (float)kso;
+    } else {          // FrictPhys
+      const float k1 = (float)m1.young * (2 * r1), k2 = (float)m2.young * (2 * r2);
+      kn = k1 * k2 / (k1 + k2);
+      const float s1 = (float)(m1.young * m1.poisson) * (2 * r1);
+      const float s2 = (float)(m2.young * m2.poisson) * (2 * r2);
+      ks = s1 * s2 / (s1 + s2);
+    }
     tanphi = fmin(m1.tanphi, m2.tanphi);
     fsd = make_double4_32a(0, 0, 0, tanphi);
     hn = make_float4(nx, ny, nz, ks);
@@ -108,7 +117,8 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   const float uy = f * (v2y - va1.y) - (rz * nx - rx * nz);
   const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
   const float vn = nx * ux + ny * uy + nz * uz;
-  const float kd = ks * dtf;
+  const float sq = (kHertz && rc.law) ? sqrtf(pen) : 1.0f;   // Hertz-Mindlin pen^1/2 factor
+  const float kd = (ks * sq) * dtf;
   const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
   // 1. transport of the stored shear force into the new frame: the rotation vector
   //    b = n- x n + (dt/2 n.(w1+w2)) n and the change -Fs x b - ks dt v12_perp are
@@ -124,7 +134,7 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   double fy = fsd.y - (double)((sz0 * bx - sx0 * bz) + iy);
   double fz = fsd.z - (double)((sx0 * by - sy0 * bx) + iz);
   // Law2: normal force, Coulomb test in FP32; the cap rescales the FP64 spring
-  const float Fn = kn * pen;
+  const float Fn = (kHertz && rc.law) ? kn * pen * sq : kn * pen;
   const float maxFs = Fn * (float)tanphi;
   float sx = (float)fx, sy = (float)fy, sz = (float)fz;
   const float fs2 = sx * sx + sy * sy + sz * sz;
@@ -144,14 +154,15 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
 
 // Same per-warp queue of real rows as the FP64 kernel: the FP32 geometry test on
 // tiles of 32 consecutive rows, the law on 32 queued real rows at a time.
-template <int kT>
+template <int kT, bool kHertz, bool kDesc>
 __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict__ d,
+                                                      Table tp, Bodies bp,
                                                       const CellState *__restrict__ cs,
                                                       const DevStatus *__restrict__ ds,
                                                       const Mat *__restrict__ mats, int multi) {
   constexpr int kWarps = kT / 32;
-  const Table &t = d->t;
-  const Bodies &b = d->b;
+  const Table &t = kDesc ? d->t : tp;
+  const Bodies &b = kDesc ? d->b : bp;
   if (ds->pending) return;
   __shared__ QRowF q[kWarps][kQ];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
     __syncwarp();
     if (cnt >= 32) {
       const QRowF e = wq[lane];
-      real_row_mixed(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
+      real_row_mixed<kHertz>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
       __syncwarp();
       if (lane < cnt - 32) wq[lane] = wq[lane + 32];
       cnt -= 32;
@@ -214,20 +225,27 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
   }
   if (lane < cnt) {
     const QRowF e = wq[lane];
-    real_row_mixed(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
+    real_row_mixed<kHertz>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
   }
 }
 }  // namespace
 
-void launch_contact_mixed(const StepDesc *d, long long rows, const CellState *cs,
-                          const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
-                          int per_sm, cudaStream_t st) {
+void launch_contact_mixed(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
+                          const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
+                          int hertz, int nsm, int block, int per_sm, cudaStream_t st) {
   if (rows <= 0) return;
   long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  if (block == 128) k_contact_mixed<128><<<grid, 128, 0, st>>>(d, cs, ds, mats, multi);
-  else k_contact_mixed<256><<<grid, 256, 0, st>>>(d, cs, ds, mats, multi);
+#define DEM_C(B, H, D) k_contact_mixed<B, H, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
+#define DEM_C2(H, D) if (block == 128) DEM_C(128, H, D); else DEM_C(256, H, D);
+  if (desc) {
+    if (hertz) { DEM_C2(true, true) } else { DEM_C2(false, true) }
+  } else {
+    if (hertz) { DEM_C2(true, false) } else { DEM_C2(false, false) }
+  }
+#undef DEM_C2
+#undef DEM_C
 }
 
 }  // namespace dem

@@ -39,7 +39,32 @@ enum : int {
 
 struct Mat {
   double density, young, poisson, tanphi;
+  // Hertz-Mindlin compliances of the material: (1 - nu^2) / E and (2 - nu) / G with
+  // G = E / (2 (1 + nu)), so that a pair's E* and shear constant are 1 / (sum)
+  double hz_e, hz_g;
 };
+
+// Ip2 of the Hertz-Mindlin law (Ip2_FrictMat_FrictMat_MindlinPhys): kno = 4/3 E* sqrt(R*)
+// and kso = 8 sqrt(R*) / ((2 - nu1)/G1 + (2 - nu2)/G2) with 1/E* = sum (1 - nu^2)/E,
+// G = E / (2 (1 + nu)); r2 < 0 stands for a wall (R* = r1).  Stored where the linear
+// law keeps kn and ks; the law takes Fn = kno pen^3/2 and ks = kso pen^1/2.
+__host__ __device__ inline void mindlin_phys(const Mat &m1, double r1, const Mat &m2, double r2,
+                                             double &kno, double &kso) {
+  const double Rs = r2 < 0 ? r1 : r1 * r2 / (r1 + r2);
+  const double sR = sqrt(Rs);
+  kno = 4.0 / 3.0 * sR / (m1.hz_e + m2.hz_e);
+  kso = 8.0 * sR / (m1.hz_g + m2.hz_g);
+}
+inline void mindlin_compliances(Mat &m) {
+  m.hz_e = (1 - m.poisson * m.poisson) / m.young;
+  m.hz_g = (2 - m.poisson) / (m.young / (2 * (1 + m.poisson)));
+}
+
+// penetration of a wall contact from its stored normal force (linear: Fn = kn pen;
+// Hertz: Fn = kno pen^3/2)
+__host__ __device__ inline double wall_pen(double Fn, double k, int law) {
+  return law ? cbrt((Fn / k) * (Fn / k)) : Fn / k;
+}
 
 struct Bodies {
   double4_32a *pos, *vel, *angvel, *ori, *xref, *mprop;
@@ -106,7 +131,8 @@ struct CellState {
   int wall_mat;     // material of the walls
   int alive;        // 0: a removed sub-scene (its slot is skipped)
   int tstep;        // GlobalStiffnessTimeStepper on
-  int tstep_interval, pad5;
+  int tstep_interval;
+  int law;          // contact law: 0 Cundall-Strack (linear), 1 Hertz-Mindlin
   double tstep_safety, tstep_default, tstep_max;   // default: dt when no contact exists
 };
 
@@ -140,6 +166,7 @@ struct Grid {
 
 struct SceneConst {
   long long N;
+  int hertz;     // some sub-scene uses the Hertz-Mindlin law
   int walls;     // some sub-scene has walls
   int periodic;  // some sub-scene is periodic
   int ordered;   // integrate bodies in Table::ord order (else slot order)
@@ -210,18 +237,21 @@ void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
 // multi: cs is an array indexed by Bodies::sid (else cs[0] holds the one scene)
 // rows: upper bound of the table rows (sizes the grid: the table capacity, so that the
 // launch shape does not change between collider runs)
-void launch_contact(const StepDesc *d, long long rows, const CellState *cs, const DevStatus *ds,
-                    const Mat *mats, int multi, int nsm, int block, int per_sm,
-                    cudaStream_t st);
+// hertz: some sub-scene uses the Hertz-Mindlin law (selects the variant with its branch)
+// d / h: the device descriptor and its host copy; desc: read the table and bodies
+// through d (captured batches) rather than from launch parameters
+void launch_contact(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
+                    const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
+                    int hertz, int nsm, int block, int per_sm, cudaStream_t st);
 // contact_mixed.cu
-void launch_contact_mixed(const StepDesc *d, long long rows, const CellState *cs,
-                          const DevStatus *ds, const Mat *mats, int multi, int nsm, int block,
-                          int per_sm, cudaStream_t st);
+void launch_contact_mixed(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
+                          const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
+                          int hertz, int nsm, int block, int per_sm, cudaStream_t st);
 
 // integrate.cu
 // block: 128, 256 or 512 threads
-// N and walls must equal d->sc.N and d->sc.walls (they size and select the launch)
-void launch_integrate(const StepDesc *d, long long N, int walls, const CellState *cs,
+// h.sc.N and h.sc.walls size and select the launch (and must match *d when desc)
+void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const CellState *cs,
                       DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st);
 // one thread per sub-scene (cs[0 .. nsub)); servo partials apply to sub-scene 0
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
@@ -233,8 +263,8 @@ void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub
                         int mixed, int multi, int walls, unsigned long long *keys,
                         cudaStream_t st);
 // servo: per-block sums of sigma_ii * V and K_i * V over the real rows (6 per block)
-void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
-                           cudaStream_t st);
+void launch_servo_partials(const Table &t, const Bodies &b, const DevStatus *ds, int mixed, int law,
+                           double *partials, cudaStream_t st);
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, const CellState *cs,
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
                           int mixed, cudaStream_t st);

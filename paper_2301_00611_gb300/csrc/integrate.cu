@@ -93,16 +93,21 @@ __device__ inline void gather_rows_f32(const Table &t, int s, double F[3], doubl
   T[0] = t0; T[1] = t1; T[2] = t2;
 }
 
-// FrictPhys of a sphere-wall contact: equivalent wall radius = sphere radius,
-// wall material = the scene's wall material (material 0 by default).
+// Physics of a sphere-wall contact: FrictPhys with equivalent wall radius = sphere
+// radius, or (law 1) the Hertz-Mindlin constants with an infinite wall radius; wall
+// material = the scene's wall material (material 0 by default).
 __device__ inline void wall_phys(const Mat *mats, int wmat, int mat, double r, double &kn,
-                                 double &ks, double &tanphi) {
+                                 double &ks, double &tanphi, int law = 0) {
   const Mat mw = mats[wmat], ms = mats[mat];
+  tanphi = fmin(mw.tanphi, ms.tanphi);
+  if (law) {
+    mindlin_phys(ms, r, mw, -1.0, kn, ks);
+    return;
+  }
   const double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
   kn = k1 * k2 / (k1 + k2);
   const double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
   ks = s1 * s2 / (s1 + s2);
-  tanphi = fmin(mw.tanphi, ms.tanphi);
 }
 
 // Mixed precision integrator: FP32 force sum, walls, damping and orientation;
@@ -111,15 +116,15 @@ __device__ inline void wall_phys(const Mat *mats, int wmat, int mat, double r, d
 // contact kernel).  Every quantity it needs in FP32 is read from the FP32 mirrors
 // the previous step wrote, so the FP64 pipe (conversions included) carries ~27
 // instructions per body.
-template <int kB, bool kWalls>
-__global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restrict__ d,
+template <int kB, bool kWalls, bool kDesc>
+__global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restrict__ d, StepDesc hp,
                                                         const CellState *__restrict__ cs,
                                                         DevStatus *ds, const Mat *__restrict__ mats) {
   if (ds->pending) return;
-  const Bodies &b = d->b;
-  const Table &t = d->t;
-  const SceneConst &sc = d->sc;
-  const long long cap = d->cap;
+  const Bodies &b = kDesc ? d->b : hp.b;
+  const Table &t = kDesc ? d->t : hp.t;
+  const SceneConst &sc = kDesc ? d->sc : hp.sc;
+  const long long cap = kDesc ? d->cap : hp.cap;
   const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = sc.ordered ? t.ord[sl] : (int)sl;
@@ -190,8 +195,9 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
       n[ax] = sn;
       const float pen = r - fabsf(dist);
       double knd, ksd, tpd;
-      wall_phys(mats, c.wall_mat, b.mat[s], (double)r, knd, ksd, tpd);
-      const float kn = (float)knd, ks = (float)ksd, tanphi = (float)tpd;
+      wall_phys(mats, c.wall_mat, b.mat[s], (double)r, knd, ksd, tpd, c.law);
+      const float sqp = c.law ? sqrtf(pen) : 1.0f;   // Hertz-Mindlin: pen^1/2 factors
+      const float kn = (float)knd * sqp, ks = (float)ksd * sqp, tanphi = (float)tpd;
       float fs[3] = {0, 0, 0};
       if (was) {
         const double4_32a h = b.whist[wi * cap + s];
@@ -299,15 +305,15 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
     atomicOr(&ds->error, kErrNonFinite);
 }
 
-template <int kB, bool kWalls>
-__global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d,
+template <int kB, bool kWalls, bool kDesc>
+__global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d, StepDesc hp,
                                                   const CellState *__restrict__ cs,
                                                   DevStatus *ds, const Mat *__restrict__ mats) {
   if (ds->pending) return;
-  const Bodies &b = d->b;
-  const Table &t = d->t;
-  const SceneConst &sc = d->sc;
-  const long long cap = d->cap;
+  const Bodies &b = kDesc ? d->b : hp.b;
+  const Table &t = kDesc ? d->t : hp.t;
+  const SceneConst &sc = kDesc ? d->sc : hp.sc;
+  const long long cap = kDesc ? d->cap : hp.cap;
   const long long sl = (long long)blockIdx.x * kB + threadIdx.x;
   if (sl >= sc.N) return;
   const int s = sc.ordered ? t.ord[sl] : (int)sl;
@@ -343,7 +349,12 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
       n[ax] = sn;
       const double pen = r - fabs(dist);
       double kn, ks, tanphi;
-      wall_phys(mats, c.wall_mat, b.mat[s], r, kn, ks, tanphi);
+      wall_phys(mats, c.wall_mat, b.mat[s], r, kn, ks, tanphi, c.law);
+      if (c.law) {   // Hertz-Mindlin: Fn = kno pen^3/2, ks = kso pen^1/2
+        const double sq = sqrt(pen);
+        kn *= sq;
+        ks *= sq;
+      }
       double fs[3] = {0, 0, 0};
       if (was) {
         const double4_32a h = b.whist[wi * cap + s];
@@ -564,7 +575,8 @@ __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
   else gather_rows(t, s, F, T);
   const uint8_t flags = b.flags[s];
   if (sc.walls && (flags & 0x7e)) {
-    const int wmat = cs[sc.multi ? b.sid[s] : 0].wall_mat;
+    const CellState &c = cs[sc.multi ? b.sid[s] : 0];
+    const int wmat = c.wall_mat;
     const double r = b.pos[s].w;
     for (int wi = 0; wi < 6; ++wi) {
       if (!(flags & (2 << wi))) continue;
@@ -573,8 +585,8 @@ __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
       const double sn = h.w >= 0 ? 1.0 : -1.0;
       const double Fn = fabs(h.w);
       double kn, ks, tanphi;
-      wall_phys(mats, wmat, b.mat[s], r, kn, ks, tanphi);
-      const double pen = Fn / kn;
+      wall_phys(mats, wmat, b.mat[s], r, kn, ks, tanphi, c.law);
+      const double pen = wall_pen(Fn, kn, c.law);
       double n[3] = {0, 0, 0};
       n[ax] = sn;
       const double F2[3] = {Fn * n[0] + h.x, Fn * n[1] + h.y, Fn * n[2] + h.z};
@@ -606,7 +618,8 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials) {
 }
 
 // servo sums over real rows: sigma_a * V = sum F_a (-l n_a), K_a * V = sum kn (l n_a)^2
-__global__ void k_servo_partials(Table t, const DevStatus *ds, int mixed, double *partials) {
+__global__ void k_servo_partials(Table t, Bodies b, const DevStatus *ds, int mixed, int law,
+                                 double *partials) {
   double v[6] = {0, 0, 0, 0, 0, 0};
   if (!ds->pending) {
     for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
@@ -624,10 +637,15 @@ __global__ void k_servo_partials(Table t, const DevStatus *ds, int mixed, double
         F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         l = f.w + m.w;
       }
+      if (law) {   // Hertz-Mindlin tangent k_n = 3/2 kno pen^1/2
+        const int2 pr = t.pair[k];
+        const double pen = (b.pos[pr.x].w + b.pos[pr.y].w) - l;
+        kn = 1.5 * kn * sqrt(pen > 0 ? pen : 0.0);
+      }
       for (int a = 0; a < 3; ++a) {
         v[a] += F[a] * (-l * n[a]);
-        const double b = l * n[a];
-        v[3 + a] += kn * (b * b);
+        const double bl = l * n[a];
+        v[3 + a] += kn * (bl * bl);
       }
     }
   }
@@ -704,7 +722,12 @@ inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
 // the bodies of each sub-scene into keys[sub] (bit patterns of positive doubles
 // order like the values, so an integer atomic min is exact and order-free).
 __device__ inline void stiff_add(double Kt[3], double Kr[3], double kn, double ks, const double n[3],
-                                 double d) {
+                                 double d, int law, double pen) {
+  if (law) {   // Hertz-Mindlin tangents: k_n = 3/2 kno pen^1/2, k_s = kso pen^1/2
+    const double sq = sqrt(pen);
+    kn = 1.5 * kn * sq;
+    ks = ks * sq;
+  }
   for (int i = 0; i < 3; ++i) {
     const double ni2 = n[i] * n[i];
     Kt[i] += (kn - ks) * ni2 + ks;
@@ -722,6 +745,8 @@ __global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
   if (sl < N) {
     const int s = (int)sl;
     q = multi ? b.sid[s] : 0;
+    const int law = cs[q].law;
+    const double rs = b.pos[s].w;
     double Kt[3] = {0, 0, 0}, Kr[3] = {0, 0, 0};
     auto row = [&](long long k, bool first) {
       double kn, ks, n[3], d;
@@ -738,21 +763,28 @@ __global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
         kn = f.w; ks = h.w; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         d = first ? t.oF[k].w : t.oM[k].w;
       }
-      stiff_add(Kt, Kr, kn, ks, n, d);
+      stiff_add(Kt, Kr, kn, ks, n, d, law, 2.0 * (rs - d));   // d = r - pen/2
     };
     for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) row(k, true);
     for (int e = t.down_start[s]; e < t.down_start[s + 1]; ++e) row(t.down[e], false);
     const uint8_t fl = b.flags[s];
-    const double r = b.pos[s].w;
-    if (walls && (fl & 0x7e)) {
+    const double4_32a p = b.pos[s];
+    const double r = p.w;
+    const CellState &c = cs[q];
+    if (walls && c.wall_mask) {
+      // this step's wall contacts (the integrator evaluates them after this kernel):
+      // the same test on the same positions, pen = r - |x_a - w|
       double kn, ks, tp;
-      wall_phys(mats, cs[q].wall_mat, b.mat[s], r, kn, ks, tp);
+      wall_phys(mats, c.wall_mat, b.mat[s], r, kn, ks, tp, c.law);
+      const double x[3] = {p.x, p.y, p.z};
       for (int wi = 0; wi < 6; ++wi) {
-        if (!(fl & (2 << wi))) continue;
-        const double4_32a h = b.whist[wi * cap + s];
+        if (!(c.wall_mask & (1 << wi))) continue;
+        const int ax = wi >> 1;
+        const double dist = x[ax] - ((wi & 1) ? c.box_hi[ax] : c.box_lo[ax]);
+        if (!(fabs(dist) < r)) continue;
         double n[3] = {0, 0, 0};
-        n[wi >> 1] = 1.0;   // only n_i^2 enters
-        stiff_add(Kt, Kr, kn, ks, n, r - 0.5 * (fabs(h.w) / kn));
+        n[ax] = 1.0;   // only n_i^2 enters
+        stiff_add(Kt, Kr, kn, ks, n, r - 0.5 * (r - fabs(dist)), c.law, r - fabs(dist));
       }
     }
     if (!(fl & 1)) {
@@ -797,22 +829,23 @@ __global__ void k_dt_apply(CellState *cs, int nsub, const DevStatus *ds, unsigne
 }
 }  // namespace
 
-void launch_integrate(const StepDesc *d, long long N, int walls, const CellState *cs,
+void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const CellState *cs,
                       DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st) {
+  const long long N = h.sc.N;
   if (N <= 0) return;
+  const int walls = h.sc.walls;
   // kernels without the sphere-wall branch when no sub-scene has walls (fewer registers)
-#define DEM_INTEGRATE(K, B, W) K<B, W><<<(unsigned)((N + B - 1) / B), B, 0, st>>>(d, cs, ds, mats)
-#define DEM_INTEGRATE_ALL(K)                                                                  \
-  if (block == 128) { if (walls) DEM_INTEGRATE(K, 128, true); else DEM_INTEGRATE(K, 128, false); } \
-  else if (block == 512) { if (walls) DEM_INTEGRATE(K, 512, true); else DEM_INTEGRATE(K, 512, false); } \
-  else { if (walls) DEM_INTEGRATE(K, 256, true); else DEM_INTEGRATE(K, 256, false); }
+#define DEM_I(K, B, W, D) K<B, W, D><<<(unsigned)((N + B - 1) / B), B, 0, st>>>(d, h, cs, ds, mats)
+#define DEM_I_W(K, B, D) if (walls) DEM_I(K, B, true, D); else DEM_I(K, B, false, D);
+#define DEM_I_B(K, D) if (block == 128) { DEM_I_W(K, 128, D) } else if (block == 512) { DEM_I_W(K, 512, D) } else { DEM_I_W(K, 256, D) }
   if (mixed) {
-    DEM_INTEGRATE_ALL(k_integrate_mixed)
+    if (desc) { DEM_I_B(k_integrate_mixed, true) } else { DEM_I_B(k_integrate_mixed, false) }
   } else {
-    DEM_INTEGRATE_ALL(k_integrate)
+    if (desc) { DEM_I_B(k_integrate, true) } else { DEM_I_B(k_integrate, false) }
   }
-#undef DEM_INTEGRATE_ALL
-#undef DEM_INTEGRATE
+#undef DEM_I_B
+#undef DEM_I_W
+#undef DEM_I
 }
 
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
@@ -830,9 +863,9 @@ void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub
   k_dt_apply<<<(nsub + 127) / 128, 128, 0, st>>>(cs, nsub, ds, keys);
 }
 
-void launch_servo_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
-                           cudaStream_t st) {
-  k_servo_partials<<<kServoBlocks, kT, 0, st>>>(t, ds, mixed, partials);
+void launch_servo_partials(const Table &t, const Bodies &b, const DevStatus *ds, int mixed, int law,
+                           double *partials, cudaStream_t st) {
+  k_servo_partials<<<kServoBlocks, kT, 0, st>>>(t, b, ds, mixed, law, partials);
 }
 
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, const CellState *cs,

@@ -104,10 +104,17 @@ __global__ void __launch_bounds__(kT) k_body_stress(Bodies b, Table t, long long
   const double r = b.pos[s].w;
   const uint8_t fl = b.flags[s];
   if (walls && (fl & 0x7e)) {
-    // sphere-wall FrictPhys: both springs 2 r times the Young moduli (wall radius = r)
-    const Mat mw = mats[cs[multi ? b.sid[s] : 0].wall_mat], ms = mats[b.mat[s]];
-    const double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
-    const double kn = k1 * k2 / (k1 + k2);
+    // normal stiffness constant of the sphere-wall contact (FrictPhys: both springs
+    // 2 r times the Young moduli; Hertz-Mindlin: kno with an infinite wall radius)
+    const CellState &c = cs[multi ? b.sid[s] : 0];
+    const Mat mw = mats[c.wall_mat], ms = mats[b.mat[s]];
+    double kn, kso;
+    if (c.law) {
+      mindlin_phys(ms, r, mw, -1.0, kn, kso);
+    } else {
+      const double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
+      kn = k1 * k2 / (k1 + k2);
+    }
     for (int wi = 0; wi < 6; ++wi) {   // n along axis wi/2, toward the sphere
       if (!(fl & (2 << wi))) continue;
       const double4_32a h = b.whist[wi * cap + s];
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(kT) k_body_stress(Bodies b, Table t, long long
       const double sn = h.w >= 0 ? 1.0 : -1.0, Fn = fabs(h.w);
       double f[3] = {h.x, h.y, h.z};
       f[ax] += sn * Fn;
-      const double xa = -sn * (r - 0.5 * (Fn / kn));   // contact point - centre, along ax
+      const double xa = -sn * (r - 0.5 * wall_pen(Fn, kn, c.law));   // contact point - centre
       for (int j = 0; j < 3; ++j) S[3 * ax + j] += xa * f[j];
     }
   }

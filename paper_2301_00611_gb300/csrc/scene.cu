@@ -128,6 +128,10 @@ unsigned next_pow2(unsigned v) {
 }
 }  // namespace
 
+// automatic step graphs below this many bodies (launch overhead matters there; larger
+// scenes keep the leaner parameter-fed kernels)
+constexpr long long kGraphAutoBodies = 1 << 18;
+
 struct Readback {
   DevStatus ds;
   int totals[4];
@@ -202,7 +206,7 @@ struct dem_scene {
   int *deg_ws = nullptr;       // 2 x kDegreeBuckets ints (integration order)
   // launch shapes of the step kernels (none changes a result)
   int contact_block = 256, contact_per_sm = 8, integrate_block = 256, degree_order = 1;
-  int step_graphs = 1;           // replay captured batches of steps
+  int step_graphs = -1;          // replay captured batches: 1 yes, 0 no, -1 small scenes
   StepDesc *step_d = nullptr;    // device step descriptor
   StepDesc *step_h = nullptr;    // pinned staging copy
   GraphKey graph_key{};
@@ -475,6 +479,7 @@ SceneConst scene_const(const dem_scene *s) {
     if (u.used) {
       c.walls |= u.cs.wall_mask ? 1 : 0;
       c.periodic |= u.cs.periodic;
+      c.hertz |= u.cs.law;
     }
   c.ordered = s->degree_order;
   c.multi = s->nsub() > 1;
@@ -704,7 +709,9 @@ dem_status rebuild_core(dem_scene *s) {
   launch_bin(s->cur, N, s->grids_d, multi, dead, s->key, s->cell_count, s->st);
   exclusive_scan(s->cell_count, s->cell_start, ncell, s->scan_ws, s->st);
   launch_scatter(N, s->key, s->cell_start, s->cell_fill, s->new_to_old, s->st);
-  launch_cellsort(s->cell_count, s->cell_start, ncell, s->cur.id, s->new_to_old, s->st);
+  // the sentinel cell of removed bodies is left unsorted: its order is never used (and
+  // it can hold every body of a large removed sub-scene)
+  launch_cellsort(s->cell_count, s->cell_start, total, s->cur.id, s->new_to_old, s->st);
   launch_reorder(s->cur, s->alt, n_live, s->cap, s->new_to_old, s->slot_of_id, s->has_walls,
                  s->mixed, id_shift, s->st);
   std::swap(s->cur, s->alt);
@@ -993,7 +1000,8 @@ dem_status dem_set_material(dem_scene *s, int mat, double density, double young,
       !(friction < 1.5707963267948966) || !std::isfinite(density) || !std::isfinite(young) ||
       !std::isfinite(poisson))
     return fail(s, DEM_ERR_INVALID_ARG, "bad material parameters");
-  Mat m{density, young, poisson, std::tan(friction)};
+  Mat m{density, young, poisson, std::tan(friction), 0.0, 0.0};
+  mindlin_compliances(m);
   s->mats_h[mat] = m;
   s->mat_set[mat] = true;
   CK(cudaMemcpyAsync(s->mats_d + mat, &s->mats_h[mat], sizeof(Mat), cudaMemcpyHostToDevice, s->st));
@@ -1202,15 +1210,20 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
         if (u.used && u.cs.tstep && (u.cs.iter + i) % u.cs.tstep_interval == 0) return true;
       return false;
     };
+    // captured batches read the descriptor; launched ones take the arrays as parameters
+    const bool use_graph = (s->step_graphs > 0 || (s->step_graphs < 0 && sc.N < kGraphAutoBodies)) &&
+                           !ev && !servo && !tstep;
+    bool desc = use_graph;
     auto launch_steps = [&](bool record) -> dem_status {
       for (long long i = 0; i < B; ++i) {
         if (record) CK(cudaEventRecord(ev[6 * i], s->st));
         if (s->mixed)
-          launch_contact_mixed(s->step_d, rows, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
-                               s->contact_block, s->contact_per_sm, s->st);
+          launch_contact_mixed(s->step_d, *s->step_h, desc, rows, s->cs_d, s->ds_d, s->mats_d,
+                               sc.multi, sc.hertz, s->nsm, s->contact_block, s->contact_per_sm,
+                               s->st);
         else
-          launch_contact(s->step_d, rows, s->cs_d, s->ds_d, s->mats_d, sc.multi, s->nsm,
-                         s->contact_block, s->contact_per_sm, s->st);
+          launch_contact(s->step_d, *s->step_h, desc, rows, s->cs_d, s->ds_d, s->mats_d,
+                         sc.multi, sc.hertz, s->nsm, s->contact_block, s->contact_per_sm, s->st);
         if (record) CK(cudaEventRecord(ev[6 * i + 1], s->st));
         if (tstep && tstep_due(i)) {   // GlobalStiffnessTimeStepper: after the contacts
           launch_timestepper(s->cur, t, s->cs_d, s->nsub(), s->ds_d, s->mats_d, sc.N, s->cap,
@@ -1218,13 +1231,13 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
           s->launches += 2;
         }
         if (record) CK(cudaEventRecord(ev[6 * i + 2], s->st));
-        launch_integrate(s->step_d, sc.N, sc.walls, s->cs_d, s->ds_d, s->mats_d, s->mixed,
+        launch_integrate(s->step_d, *s->step_h, desc, s->cs_d, s->ds_d, s->mats_d, s->mixed,
                          s->integrate_block, s->st);
         if (record) { CK(cudaEventRecord(ev[6 * i + 3], s->st)); CK(cudaEventRecord(ev[6 * i + 4], s->st)); }
         // servo update steps (PeriTriaxController every glob_update steps)
         const bool upd = servo && ((it0 + i + 1) % s->cs0().glob_update == 0);
         if (upd) {
-          launch_servo_partials(t, s->ds_d, s->mixed, s->servo, s->st);
+          launch_servo_partials(t, s->cur, s->ds_d, s->mixed, s->cs0().law, s->servo, s->st);
           s->launches += 1;
         }
         launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st);
@@ -1232,11 +1245,12 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
       }
       return DEM_OK;
     };
-    if (s->step_graphs && !ev && !servo && !tstep) {
+    if (use_graph) {
       // replay a captured batch of B steps (one graph launch instead of 3B launches);
       // captures are kept while nothing that shapes the launches changes
       const GraphKey key{sc.N, rows, s->contact_block, s->contact_per_sm, s->integrate_block,
-                         sc.multi, sc.walls, s->nsub(), s->mixed ? 1 : 0, s->cs_d};
+                         sc.multi, sc.walls | (sc.hertz << 1), s->nsub(), s->mixed ? 1 : 0,
+                         s->cs_d};
       if (!(key == s->graph_key)) {
         drop_graphs(s);
         s->graph_key = key;
@@ -1259,8 +1273,9 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
         }
       }
       CK(cudaGraphLaunch(ex, s->st));
-    } else if ((r = launch_steps(ev != nullptr))) {
-      return r;
+    } else {
+      desc = false;
+      if ((r = launch_steps(ev != nullptr))) return r;
     }
     s->launches += B * ((rows > 0 ? 1 : 0) + 2);
     CK(cudaGetLastError());
@@ -1477,13 +1492,17 @@ struct HostContact {
 };
 
 void wall_phys_h(const dem_scene *s, int wmat, int mat, double r, double &kn, double &ks,
-                 double &tp) {
+                 double &tp, int law) {
   const Mat &mw = s->mats_h[wmat], &ms = s->mats_h[mat];
+  tp = std::min(mw.tanphi, ms.tanphi);
+  if (law) {   // Hertz-Mindlin constants kno, kso with an infinite wall radius
+    mindlin_phys(ms, r, mw, -1.0, kn, ks);
+    return;
+  }
   double k1 = mw.young * (2 * r), k2 = ms.young * (2 * r);
   kn = k1 * k2 / (k1 + k2);
   double s1 = mw.young * mw.poisson * (2 * r), s2 = ms.young * ms.poisson * (2 * r);
   ks = s1 * s2 / (s1 + s2);
-  tp = std::min(mw.tanphi, ms.tanphi);
 }
 
 dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
@@ -1568,10 +1587,13 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
     out.push_back(h);
   }
   if (s->has_walls) {
-    std::vector<int> wmat(N, 0);   // wall material of each id's sub-scene
+    std::vector<int> wmat(N, 0), wlaw(N, 0);   // wall material and law of each id's sub-scene
     for (const Sub &u : s->subs)
       if (u.used || u.removing)
-        for (long long i = u.id0; i < u.id0 + u.n && i < N; ++i) wmat[i] = u.cs.wall_mat;
+        for (long long i = u.id0; i < u.id0 + u.n && i < N; ++i) {
+          wmat[i] = u.cs.wall_mat;
+          wlaw[i] = u.cs.law;
+        }
     for (long long sl = 0; sl < N; ++sl) {
       if (!(flags[sl] & 0x7e)) continue;
       for (int w = 0; w < 6; ++w) {
@@ -1584,11 +1606,12 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
         h.id2 = id[sl];
         double kn, ks, tanp;
         const double rr = pos[sl].w;
-        wall_phys_h(s, wmat[id[sl]], s->mat_h[id[sl]], rr, kn, ks, tanp);
+        const int law = wlaw[id[sl]];
+        wall_phys_h(s, wmat[id[sl]], s->mat_h[id[sl]], rr, kn, ks, tanp, law);
         h.n[ax] = sn;
         h.fn[ax] = sn * Fn;
         h.fs[0] = hw.x; h.fs[1] = hw.y; h.fs[2] = hw.z;
-        h.pen = Fn / kn;
+        h.pen = wall_pen(Fn, kn, law);
         const double pp[3] = {pos[sl].x, pos[sl].y, pos[sl].z};
         for (int q = 0; q < 3; ++q) h.cp[q] = pp[q] - (rr - 0.5 * h.pen) * h.n[q];
         h.phys[0] = kn; h.phys[1] = ks; h.phys[2] = tanp;
@@ -1881,7 +1904,7 @@ bool valid_tuning(const dem_tuning &t) {
   return (t.contact_block == 128 || t.contact_block == 256) && t.contact_blocks_per_sm >= 1 &&
          t.contact_blocks_per_sm <= 64 &&
          (t.integrate_block == 128 || t.integrate_block == 256 || t.integrate_block == 512) &&
-         (t.degree_order == 0 || t.degree_order == 1) && (t.step_graphs == 0 || t.step_graphs == 1);
+         (t.degree_order == 0 || t.degree_order == 1) && t.step_graphs >= -1 && t.step_graphs <= 1;
 }
 void apply_tuning(dem_scene *s, const dem_tuning &t) {
   s->contact_block = t.contact_block;
@@ -2233,6 +2256,23 @@ dem_status dem_set_timestepper(dem_scene *s, int sub, double safety, int interva
   u.tstep_default_rule = default_dt;
   u.tstep_default_n = -1;
   if (default_dt > 0) u.cs.tstep_default = default_dt;
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+// ------------------------------------------------------------------ contact law
+dem_status dem_set_law(dem_scene *s, int sub, int law) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  if (law != DEM_LAW_LINEAR && law != DEM_LAW_HERTZ_MINDLIN)
+    return fail(s, DEM_ERR_INVALID_ARG, "unknown contact law");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  Sub &u = s->subs[sub];
+  if (u.cs.iter != 0 && u.cs.law != law)
+    return fail(s, DEM_ERR_STATE, "the contact law is chosen before the sub-scene's first step");
+  u.cs.law = law;
   s->cs_dirty = true;
   return DEM_OK;
 }

@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdem.so")
 
 DEM_OK = 0
+DEM_LAW_LINEAR = 0
+DEM_LAW_HERTZ_MINDLIN = 1
 STATUS_NAMES = {
     0: "DEM_OK", 1: "DEM_ERR_INVALID_ARG", 2: "DEM_ERR_OUT_OF_RANGE", 3: "DEM_ERR_OOM",
     4: "DEM_ERR_CAPACITY", 5: "DEM_ERR_NONFINITE", 6: "DEM_ERR_GEOMETRY", 7: "DEM_ERR_TIMEOUT",
@@ -147,6 +149,7 @@ _SIGS = {
     "dem_num_bodies": (ctypes.c_int, [_P, _P]),
     "dem_get_micro": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "dem_get_body_stress": (ctypes.c_int, [_P, _P]),
+    "dem_set_law": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "dem_set_timestepper": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double]),
     "dem_get_state_range": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_longlong, _P, _P, _P,
@@ -425,6 +428,10 @@ class Scene:
     def set_subscene_velgrad(self, sub, L):
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def set_law(self, law, sub=0):
+        """Contact law (dem_set_law): DEM_LAW_LINEAR or DEM_LAW_HERTZ_MINDLIN."""
+        self._check(self._lib.dem_set_law(self._h, int(sub), int(law)))
 
     def set_timestepper(self, safety=0.8, interval=1, default_dt=-1.0, max_dt=0.0, sub=0):
         """GlobalStiffnessTimeStepper (dem_set_timestepper)."""

@@ -139,14 +139,16 @@ class Server:
 
     def _retire(self):
         done = [r for r in self._resident if r.left == 0]
-        for r in done:
-            st = self._scene.subscene_stats(r.sub)
-            state = self._scene.subscene_state(r.sub) if r.keep_state else None
+        # read every finished scene before removing any (a removal changes the layout
+        # until the next step)
+        out = [(r, self._scene.subscene_stats(r.sub),
+                self._scene.subscene_state(r.sub) if r.keep_state else None) for r in done]
+        t = self.now()
+        for r, st, state in out:
             self._scene.remove_subscene(r.sub)
             self._free_mat_range(r.mat_base, r.mat_count)
             self.resident_bodies -= r.n
-            self.results.append(Result(r.rid, r.n, r.steps, r.arrival, r.admitted, self.now(),
-                                       st, state))
+            self.results.append(Result(r.rid, r.n, r.steps, r.arrival, r.admitted, t, st, state))
         self._resident = [r for r in self._resident if r.left > 0]
 
     def tick(self):

@@ -71,7 +71,7 @@ def test_tuning_rejects_out_of_range(pkg):
     w = _workloads()[1]
     g = pkg.Scene.from_workload(w)
     for bad in (dict(contact_block=64), dict(contact_blocks_per_sm=0), dict(integrate_block=1024),
-                dict(degree_order=2), dict(step_graphs=3)):
+                dict(degree_order=2), dict(step_graphs=3), dict(step_graphs=-2)):
         with pytest.raises(pkg.DemError) as e:
             g.set_tuning(**bad)
         assert e.value.code == 1

@@ -283,9 +283,64 @@ def _time_window(Scene, w, args, precision, world, local, shape=None):
 #   real rows add: FP64 shear history 32 + normal/ks 16 + two FP32 velocity/spin 64
 #                  + writes history 32, normal 16, F/d1 16, M/d2 16 = 192
 ROW_BYTES_ALL_MIXED = 60
+ROW_BYTES_REAL_MIXED = 192
 TUNE_AT = 3000      # step of the job at which the launch shapes are tuned
 TUNE_STEPS = 10     # timed steps per autotune trial
-ROW_BYTES_REAL_MIXED = 192
+
+# Algorithmic cost of the integrator per body and per real contact (each real contact is
+# summed by both of its bodies), counted from its operand lists and operations:
+#   FP64, per body: reads x, v, w, m/I, orientation, reference position (6 x 32 B), the
+#     CSR offsets and order (12 B), flags (1 B); writes x, v, w, orientation (4 x 32 B)
+#     = 333 B; per real contact: two 64 B row outputs + one down-list entry = 132 B.
+#     Flops per body (add/mul 1, fused multiply-add 2): damping and leapfrog of force and
+#     torque 42, fluctuation velocity 6, homoDeform 15, position 6, orientation 45,
+#     displacement bound 15, per-body constants 2 = 131; per real contact 2 x 9 = 18.
+#   mixed, per body: FP32 mirrors and FP64 records read (vw 32, offset 16, reference
+#     16 + 32, m/I 16, orientation 16, x v w 96, CSR 8, flags 1) = 233 B, written
+#     (x v w 96, vw 32, offset 16, orientation 16) = 160 B; per real contact two 32 B
+#     row outputs + one down-list entry = 68 B.
+INT_BYTES_BODY, INT_BYTES_REAL = 333, 132
+INT_FLOPS_BODY, INT_FLOPS_REAL = 131, 18
+INT_BYTES_BODY_MIXED, INT_BYTES_REAL_MIXED = 393, 68
+
+
+def _kernel_rooflines(res, precision, n, peak, peak_kind):
+    """Roofline of the contact and integrator kernels of one timed window: achieved
+    algorithmic flops (FP64, FP64-pipe bound) or bytes (mixed, HBM bound) per launch over
+    the kernel's average launch time from its CUDA events."""
+    tm, real = res["tm"], res["mean_real"]
+    c_ms = res["avg_ms"]
+    i_ms = tm["integrate_ms"] / max(1, tm["integrate_launches"])
+    out = {}
+    if precision == "fp64":
+        cf = ROW_FLOPS_ALL * res["rows_avg"] + ROW_FLOPS_REAL * real
+        cb = ROW_BYTES_ALL * res["rows_avg"] + ROW_BYTES_REAL * real
+        if_ = INT_FLOPS_BODY * n + INT_FLOPS_REAL * real
+        ib = INT_BYTES_BODY * n + INT_BYTES_REAL * real
+        for name, ms, fl, by in (("contact", c_ms, cf, cb), ("integrate", i_ms, if_, ib)):
+            tf = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+            gb = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+            out[name] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_kind": "derived from unit counts and clock (FP64 FMA pipe)",
+                         "avg_launch_ms": ms, "flops_per_launch": fl,
+                         "hbm": {"achieved_gbs": gb, "peak_gbs": peak, "frac": gb / peak,
+                                 "peak_kind": peak_kind, "bytes_per_launch": by}}
+    else:
+        cb = ROW_BYTES_ALL_MIXED * res["rows_avg"] + ROW_BYTES_REAL_MIXED * real
+        ib = INT_BYTES_BODY_MIXED * n + INT_BYTES_REAL_MIXED * real
+        for name, ms, by in (("contact", c_ms, cb), ("integrate", i_ms, ib)):
+            gb = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+            out[name] = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s",
+                         "frac": gb / peak, "traffic": None, "peak_kind": peak_kind,
+                         "avg_launch_ms": ms, "bytes_per_launch": by}
+    share = {"contact": tm["contact_ms"], "integrate": tm["integrate_ms"]}
+    dom = max(share, key=share.get)
+    line = dict(out[dom])
+    line["kernel"] = dom + (" (fused geometry + law)" if dom == "contact" else
+                            " (fixed-order gather + damped leapfrog)") + \
+        (", FP64" if precision == "fp64" else ", mixed")
+    return line, out
 
 
 def run_gpu(args):
@@ -320,17 +375,12 @@ def run_gpu(args):
     value = world * args.n * K / T
     contact_updates = world * res["mean_real"] * K / T
     rows_per_s = world * tm["rows_processed"] / T
-    avg_ms, rows_avg, mean_real = res["avg_ms"], res["rows_avg"], res["mean_real"]
-    bytes_avg = ROW_BYTES_ALL * rows_avg + ROW_BYTES_REAL * mean_real
-    flops_avg = ROW_FLOPS_ALL * rows_avg + ROW_FLOPS_REAL * mean_real
-    bw = bytes_avg / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
-    tflops = flops_avg / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
     share = {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms", "cell_ms",
                                                 "collider_ms")}
+    rl64, rk64 = _kernel_rooflines(res, "fp64", args.n, peak, peak_kind)
     mixed_line = None
     if mixed is not None:
-        mb = (ROW_BYTES_ALL_MIXED * mixed["rows_avg"] + ROW_BYTES_REAL_MIXED * mixed["mean_real"])
-        mbw = mb / (mixed["avg_ms"] / 1e3) / 1e9 if mixed["avg_ms"] > 0 else 0.0
+        mrl, mrk = _kernel_rooflines(mixed, "mixed", args.n, peak, peak_kind)
         mixed_line = {
             "value": world * args.n * K / mixed["T"], "unit": UNIT,
             "ms_per_step": mixed["ms"] / K,
@@ -343,10 +393,8 @@ def run_gpu(args):
             "launch_shape": mixed["shape"],
             "clocks": mixed["clocks"],
             "contacts": {"start": mixed["st0"]["n_contacts"], "end": mixed["st1"]["n_contacts"]},
-            "roofline": {"bound": "hbm", "kernel": "contact (fused geometry + law), mixed",
-                         "achieved": mbw, "peak": peak, "unit": "GB/s", "frac": mbw / peak,
-                         "traffic": None, "peak_kind": peak_kind,
-                         "avg_launch_ms": mixed["avg_ms"], "bytes_per_launch": mb},
+            "roofline": mrl,
+            "roofline_kernels": mrk,
         }
 
     # end to end: host arrays in, the whole job through the public API, state out
@@ -398,13 +446,8 @@ def run_gpu(args):
             "gpu_launches": res["launches"],
             "launch_shape": shape64,
             "clocks": res["clocks"],
-            "roofline": {"bound": "alu", "kernel": "contact (fused geometry + law), FP64",
-                         "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                         "peak_kind": "derived from unit counts and clock (FP64 FMA pipe)",
-                         "avg_launch_ms": avg_ms, "flops_per_launch": flops_avg,
-                         "hbm": {"achieved_gbs": bw, "peak_gbs": peak, "frac": bw / peak,
-                                 "peak_kind": peak_kind, "bytes_per_launch": bytes_avg}},
+            "roofline": rl64,
+            "roofline_kernels": rk64,
             "mixed": mixed_line,
             "batched": batched,
             "e2e": e2e,

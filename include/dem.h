@@ -113,11 +113,11 @@ typedef struct dem_timing {
     double integrate_ms;          /* gather + integrator kernel */
     double cell_ms;               /* cell / clock advance */
     double collider_ms;           /* collider runs (all of their kernels and copies) */
-    long long contact_launches;
-    long long integrate_launches;
+    long long contact_launches;   /* counted per completed step (launches skipped after */
+    long long integrate_launches; /* a collider request are timed but not counted)      */
     long long cell_launches;
     long long collider_runs;
-    long long rows_processed;     /* sum over contact launches of table rows */
+    long long rows_processed;     /* sum over counted contact launches of table rows */
     long long kernel_launches;    /* every kernel this scene launched (timing on or off) */
 } dem_timing;
 

@@ -304,10 +304,16 @@ __device__ inline int degree_bucket(const Table &t, int s) {
   return kDegreeBuckets - 1 - (d < kDegreeBuckets - 1 ? d : kDegreeBuckets - 1);
 }
 
+// Counts and placement through block-local histograms in shared memory: one global
+// atomic per bucket per block instead of one per body.
 __global__ void k_degree_hist(Table t, long long N, int *hist) {
+  __shared__ int lh[kDegreeBuckets];
+  if (threadIdx.x < kDegreeBuckets) lh[threadIdx.x] = 0;
+  __syncthreads();
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
-  if (sl >= N) return;
-  atomicAdd(&hist[degree_bucket(t, (int)sl)], 1);
+  if (sl < N) atomicAdd(&lh[degree_bucket(t, (int)sl)], 1);
+  __syncthreads();
+  if (threadIdx.x < kDegreeBuckets && lh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], lh[threadIdx.x]);
 }
 
 __global__ void k_degree_scan(int *ws) {   // one thread: exclusive scan of the 64 counts
@@ -320,10 +326,20 @@ __global__ void k_degree_scan(int *ws) {   // one thread: exclusive scan of the 
 }
 
 __global__ void k_degree_scatter(Table t, long long N, int *fill) {
+  __shared__ int lh[kDegreeBuckets], base[kDegreeBuckets];
+  if (threadIdx.x < kDegreeBuckets) lh[threadIdx.x] = 0;
+  __syncthreads();
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
-  if (sl >= N) return;
-  const int pos = atomicAdd(&fill[degree_bucket(t, (int)sl)], 1);
-  t.ord[pos] = (int)sl;
+  int b = -1, local = 0;
+  if (sl < N) {
+    b = degree_bucket(t, (int)sl);
+    local = atomicAdd(&lh[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kDegreeBuckets && lh[threadIdx.x])
+    base[threadIdx.x] = atomicAdd(&fill[threadIdx.x], lh[threadIdx.x]);
+  __syncthreads();
+  if (b >= 0) t.ord[base[b] + local] = (int)sl;
 }
 
 __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old,

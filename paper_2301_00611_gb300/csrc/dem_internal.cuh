@@ -111,6 +111,8 @@ struct CellState {
   double E[9];      // (Hnext - Href) Href^-1: affine strain since the collider run
   double Href[9], Hrefinv[9];
   double dt, time;
+  double dt_law;        // dt of this step's contact laws (the time stepper may change dt
+                        // between the contact pass and the integration)
   double verlet, rmax;  // sweep margin dL and largest radius
   double thr2;          // squared displacement bound that triggers the collider
   long long iter;

@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   const float r = off.w;
 
   if (kWalls && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
+    const float dtl = (float)c.dt_law;   // the contact law's step (see CellState::dt_law)
     const double4_32a pd = b.pos[s];
     const double xd[3] = {pd.x, pd.y, pd.z};
     for (int wi = 0; wi < 6; ++wi) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
         const double4_32a h = b.whist[wi * cap + s];
         fs[0] = (float)h.x; fs[1] = (float)h.y; fs[2] = (float)h.z;
       }
-      const float tw = 0.5f * dtf * (sn * ww[ax]);
+      const float tw = 0.5f * dtl * (sn * ww[ax]);
       const float tn[3] = {tw * n[0], tw * n[1], tw * n[2]};
       const float c0 = fs[1] * tn[2] - fs[2] * tn[1];
       const float c1 = fs[2] * tn[0] - fs[0] * tn[2];
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
       float u[3];
       for (int q = 0; q < 3; ++q) u[q] = fac * vv[q] - cr[q];
       const float vn = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
-      for (int q = 0; q < 3; ++q) fs[q] -= ks * (dtf * (u[q] - vn * n[q]));
+      for (int q = 0; q < 3; ++q) fs[q] -= ks * (dtl * (u[q] - vn * n[q]));
       const float Fn = kn * pen;
       const float maxFs = Fn * tanphi;
       const float fs2 = fs[0] * fs[0] + fs[1] * fs[1] + fs[2] * fs[2];
@@ -360,8 +361,9 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
         const double4_32a h = b.whist[wi * cap + s];
         fs[0] = h.x; fs[1] = h.y; fs[2] = h.z;
       }
-      // frame motion: n- x n = 0 (the normal is fixed); twist dt/2 n.(0 + w)
-      const double tw = 0.5 * dt * (sn * ww[ax]);
+      // frame motion: n- x n = 0 (the normal is fixed); twist dt/2 n.(0 + w), with the
+      // contact law's step (see CellState::dt_law)
+      const double tw = 0.5 * c.dt_law * (sn * ww[ax]);
       const double tn[3] = {tw * n[0], tw * n[1], tw * n[2]};
       const double c0 = fs[1] * tn[2] - fs[2] * tn[1];
       const double c1 = fs[2] * tn[0] - fs[0] * tn[2];
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
       double u[3];
       for (int q = 0; q < 3; ++q) u[q] = fac * vv[q] - cr[q];
       const double vn = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
-      for (int q = 0; q < 3; ++q) fs[q] -= ks * (dt * (u[q] - vn * n[q]));
+      for (int q = 0; q < 3; ++q) fs[q] -= ks * (c.dt_law * (u[q] - vn * n[q]));
       const double Fn = kn * pen;
       const double maxFs = Fn * tanphi;
       const double fs2 = fs[0] * fs[0] + fs[1] * fs[1] + fs[2] * fs[2];
@@ -406,13 +408,12 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
       for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
     }
     const double hdt = 0.5 * dt, one_m = 1.0 - lam, one_p = 1.0 + lam;
-    const double dtm = dt * mp.z, dtI = dt * mp.w;   // dt / m, dt / I
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 3; ++q) {   // v+ = v- + (dt Fd) / m, as the oracle orders it
       const double Ft = F[q] + mp.x * c.gravity[q];
       const double Fd = Ft * damp_factor_ab(Ft, vref[q] + hdt * (Ft * mp.z), one_m, one_p);
-      vn_[q] = vv[q] + Fd * dtm;
+      vn_[q] = vv[q] + (dt * Fd) * mp.z;
       const double Td = T[q] * damp_factor_ab(T[q], ww[q] + hdt * (T[q] * mp.w), one_m, one_p);
-      wn_[q] = ww[q] + Td * dtI;
+      wn_[q] = ww[q] + (dt * Td) * mp.w;
     }
     if (c.periodic) {   // homoDeform = 2
       const double *dL = c.dL, *L = c.L;
@@ -481,30 +482,53 @@ __device__ inline void m_mul_rn(const double *A, const double *B, double *O) {
 
 // The next cell H+ = (I + L dt) H, the affine strain since the collider run and
 // the displacement bound that follow from it (periodic cells).
-__device__ void derive_next(CellState *cs) {
-  const double dt = cs->dt;
-  double A[9];
-  for (int q = 0; q < 9; ++q) A[q] = __dadd_rn((q % 4 == 0) ? 1.0 : 0.0, __dmul_rn(cs->L[q], dt));
-  m_mul_rn(A, cs->H, cs->Hnext);
-  double D[9];
-  for (int q = 0; q < 9; ++q) D[q] = cs->Hnext[q] - cs->Href[q];
-  m_mul_rn(D, cs->Hrefinv, cs->E);
+// H+ = (I + L dt) H, the affine strain E = (H+ - Href) Href^-1 since the collider run
+// and the displacement bound that follow from it, computed on local copies (one
+// thread: keeping the matrices in registers avoids a chain of dependent global loads)
+__device__ void derive_next_local(CellState *__restrict__ cs, const double (&H)[9],
+                                  const double (&L)[9], double dt) {
+  double A[9], Hn[9], D[9], Hri[9], E[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    A[q] = __dadd_rn((q % 4 == 0) ? 1.0 : 0.0, __dmul_rn(L[q], dt));
+    Hri[q] = cs->Hrefinv[q];
+  }
+  m_mul_rn(A, H, Hn);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) D[q] = Hn[q] - cs->Href[q];
+  m_mul_rn(D, Hri, E);
   double e2 = 0;
-  for (int q = 0; q < 9; ++q) e2 += cs->E[q] * cs->E[q];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    e2 += E[q] * E[q];
+    cs->Hnext[q] = Hn[q];
+    cs->E[q] = E[q];
+  }
   const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
   cs->thr2 = eff > 0 ? eff * eff : -1.0;
-  for (int q = 0; q < 3; ++q) cs->Ef[q] = (float)cs->E[4 * q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) cs->Ef[q] = (float)E[4 * q];
+}
+
+__device__ void derive_next(CellState *__restrict__ cs) {
+  double H[9], L[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) { H[q] = cs->H[q]; L[q] = cs->L[q]; }
+  derive_next_local(cs, H, L, cs->dt);
 }
 
 // Advance of one (sub-)scene's cell and clock.
-__device__ void cell_advance(CellState *cs, const double *servo) {
+__device__ void cell_advance(CellState *__restrict__ cs, const double *servo) {
   const double dt = cs->dt;
   if (cs->periodic) {
+    double Hp[9], H[9], Lp[9], L[9], dL[9], W[9];
+#pragma unroll
     for (int q = 0; q < 9; ++q) {
-      cs->Hprev[q] = cs->H[q];
-      cs->H[q] = cs->Hnext[q];
-      cs->Lprev[q] = cs->L[q];
-      cs->dL[q] = 0.0;   // L - Lprev after the assignment above
+      Hp[q] = cs->H[q];
+      H[q] = cs->Hnext[q];
+      Lp[q] = cs->L[q];
+      L[q] = Lp[q];
+      dL[q] = 0.0;   // L - Lprev after the assignment above
     }
     if (servo) {
       // PeriTriaxController: new diagonal gradient from this step's contacts (their
@@ -513,9 +537,9 @@ __device__ void cell_advance(CellState *cs, const double *servo) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
       for (int b = 0; b < kServoBlocks; ++b)
         for (int q = 0; q < 6; ++q) acc[q] += servo[6 * b + q];
-      const double *P = cs->Hprev;
-      const double V = fabs(P[0] * (P[4] * P[8] - P[5] * P[7]) - P[1] * (P[3] * P[8] - P[5] * P[6]) +
-                            P[2] * (P[3] * P[7] - P[4] * P[6]));
+      const double V = fabs(Hp[0] * (Hp[4] * Hp[8] - Hp[5] * Hp[7]) -
+                            Hp[1] * (Hp[3] * Hp[8] - Hp[5] * Hp[6]) +
+                            Hp[2] * (Hp[3] * Hp[7] - Hp[4] * Hp[6]));
       for (int a = 0; a < 3; ++a) {
         double rate;
         if (cs->stress_mask & (1 << a)) {
@@ -527,19 +551,31 @@ __device__ void cell_advance(CellState *cs, const double *servo) {
         } else {
           rate = cs->goal[a];
         }
-        cs->L[4 * a] = rate;
+        L[4 * a] = rate;
       }
-      for (int q = 0; q < 9; ++q) cs->dL[q] = cs->L[q] - cs->Lprev[q];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dL[q] = L[q] - Lp[q];
     }
-    m_mul_rn(cs->Lprev, cs->Hprev, cs->W);
-    derive_next(cs);
+    m_mul_rn(Lp, Hp, W);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      cs->Hprev[q] = Hp[q];
+      cs->H[q] = H[q];
+      cs->Lprev[q] = Lp[q];
+      cs->L[q] = L[q];
+      cs->dL[q] = dL[q];
+      cs->W[q] = W[q];
+    }
+    derive_next_local(cs, H, L, dt);
+#pragma unroll
     for (int q = 0; q < 3; ++q) {
-      cs->dHf[q] = (float)(cs->H[4 * q] - cs->Href[4 * q]);
-      cs->Wf[q] = (float)cs->W[4 * q];
+      cs->dHf[q] = (float)(H[4 * q] - cs->Href[4 * q]);
+      cs->Wf[q] = (float)W[4 * q];
     }
   }
   cs->iter += 1;
   cs->time = __dadd_rn(cs->time, dt);
+  cs->dt_law = dt;
 }
 
 // One thread per sub-scene.  Every block reads "pending" before it counts itself
@@ -824,6 +860,7 @@ __global__ void k_dt_apply(CellState *cs, int nsub, const DevStatus *ds, unsigne
   double dt = key == 0x7ff0000000000000ull ? c->tstep_default
                                            : c->tstep_safety * __longlong_as_double((long long)key);
   if (c->tstep_max > 0 && dt > c->tstep_max) dt = c->tstep_max;
+  c->dt_law = c->dt;   // the walls' law of this step still uses the step's old dt
   c->dt = dt;
   if (c->periodic) derive_next(c);
 }

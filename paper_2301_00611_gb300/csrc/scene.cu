@@ -520,7 +520,10 @@ dem_status ensure_dt(dem_scene *s) {
 }
 
 dem_status upload_cell(dem_scene *s) {
-  for (Sub &u : s->subs) cell_derive(u.cs);
+  for (Sub &u : s->subs) {
+    cell_derive(u.cs);
+    u.cs.dt_law = u.cs.dt;
+  }
   for (int q = 0; q < s->nsub(); ++q) s->cs_rb[q] = s->subs[q].cs;
   CK(cudaMemcpyAsync(s->cs_d, s->cs_rb, sizeof(CellState) * s->nsub(), cudaMemcpyHostToDevice,
                      s->st));
@@ -1281,7 +1284,11 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
     CK(cudaGetLastError());
     if ((r = read_status(s))) return r;
     s->table_fresh = true;
+    const long long done_b = (long long)(s->rb_h->ds.steps - s->steps_seen);
     if (ev) {
+      // all B launches are timed (the ones skipped after a collider request return at
+      // once); they are counted as the steps actually done, so a per-launch average is
+      // the time of a working launch, slightly over-estimated
       for (long long i = 0; i < B; ++i) {
         float a = 0, b = 0, c = 0;
         CK(cudaEventElapsedTime(&a, ev[6 * i], ev[6 * i + 1]));
@@ -1291,13 +1298,13 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
         s->tm.integrate_ms += b;
         s->tm.cell_ms += c;
       }
-      s->tm.contact_launches += t.P > 0 ? B : 0;
-      s->tm.integrate_launches += B;
-      s->tm.cell_launches += B;
-      s->tm.rows_processed += B * t.P;
+      s->tm.contact_launches += t.P > 0 ? done_b : 0;
+      s->tm.integrate_launches += done_b;
+      s->tm.cell_launches += done_b;
+      s->tm.rows_processed += done_b * t.P;
     }
     const DevStatus ds = s->rb_h->ds;
-    const long long done = (long long)(ds.steps - s->steps_seen);
+    const long long done = done_b;
     s->steps_seen = ds.steps;
     if (ds.error) return status_error(s, ds.error);
     remaining -= done;

@@ -1,0 +1,83 @@
+"""Oracle pinned on sheared periodic cells (non-diagonal H and grad v).
+
+Section 2.2's periodic cell is a general parallelepiped H whose columns are the
+cell vectors; a sheared cell is the case the diagonal-only shortcuts would get
+wrong.  Each pin fails under a plausible slip: an image shift that uses only the
+diagonal of H (the chain's closing contact is missed or lands at the wrong
+distance), a homoDeform term that keeps only the diagonal of grad v (the lone
+body leaves the affine field), or a cell update that is not (I + dt L) H.
+"""
+import numpy as np
+
+
+def _ip2_kn(E1, r1, E2, r2):
+    k1, k2 = E1 * 2 * r1, E2 * 2 * r2
+    return k1 * k2 / (k1 + k2)
+
+
+def test_simple_shear_cell_update_is_exact(oracle_mod):
+    """grad v = gamma_dot e_x (x) e_y is nilpotent, so (I + dt L)^n = I + n dt L exactly:
+    H_xy grows by n dt gamma_dot L_y and nothing else moves."""
+    Lx, Ly, Lz, gd, dt = 0.05, 0.04, 0.06, 2.0, 1e-4
+    s = oracle_mod.OracleScene(periodic=True, cell=np.diag([Lx, Ly, Lz]), damping=0.2)
+    s.set_material(0, 2600.0, 5e7, 0.25, 0.5)
+    s.add_spheres([[0.01, 0.02, 0.03]], [1e-3])
+    s.set_dt(dt)
+    L = np.zeros((3, 3))
+    L[0, 1] = gd
+    s.set_velgrad(L)
+    s.step(300)
+    H = s.cell()["H"]
+    expect = np.diag([Lx, Ly, Lz])
+    expect[0, 1] = 300 * dt * gd * Ly
+    assert np.allclose(H, expect, rtol=1e-12, atol=1e-18)
+
+
+def test_affine_body_follows_a_sheared_field(oracle_mod):
+    """homoDeform = 2 with a full grad v (shear plus stretch): a lone body tracks the cell
+    map x_k = H_k H_0^-1 x_0 from a cell that is already sheared."""
+    H0 = np.array([[0.05, 0.012, -0.004], [0.0, 0.045, 0.009], [0.0, 0.0, 0.06]])
+    s = oracle_mod.OracleScene(periodic=True, cell=H0, damping=0.2)
+    s.set_material(0, 2600.0, 5e7, 0.25, 0.5)
+    x0 = np.array([0.031, 0.007, 0.044])
+    s.add_spheres([x0], [1e-3])
+    s.set_dt(1e-4)
+    L = np.array([[-1.0, 3.0, 0.5], [0.7, 0.4, -2.0], [1.1, 0.0, -0.8]])
+    s.set_velgrad(L)
+    s.step(400)
+    x = s.state()["pos"][0]
+    H = s.cell()["H"]
+    assert np.allclose(x, H @ np.linalg.solve(H0, x0), rtol=1e-11, atol=0)
+    # the body is not trivially at rest: it moved along with the cell
+    assert np.linalg.norm(x - x0) > 1e-3
+
+
+def test_love_weber_stress_of_a_chain_along_a_sheared_cell_vector(oracle_mod):
+    """Four equal spheres on the cell vector a_2 = H e_y of a sheared cell, each
+    overlapping its neighbours by delta; the fourth contact closes through the image
+    c = (0, 1, 0), shifted by the whole column a_2 (its x part is the shear).  Each
+    contact carries F = kn delta along n = a_2 / |a_2| at arm l = |a_2| / 4, so
+    sigma = -(kn delta |a_2| / det H) n (x) n (compression negative)."""
+    r, delta, E = 1e-3, 2e-6, 5e7
+    l = 2 * r - delta
+    a2 = 4 * l
+    th = 0.35                                    # tilt of a_2 from the y axis, in the x-y plane
+    H = np.array([[6 * r, a2 * np.sin(th), 0.0],
+                  [0.0, a2 * np.cos(th), 0.0],
+                  [0.0, 0.0, 5.5 * r]])
+    n = H[:, 1] / np.linalg.norm(H[:, 1])
+    s = oracle_mod.OracleScene(periodic=True, cell=H, damping=0.0)
+    s.set_material(0, 2600.0, E, 0.25, 0.5)
+    base = np.array([2.5 * r, 0.3 * r, 2.7 * r])
+    pos = [base + k * l * n for k in range(4)]
+    s.add_spheres(pos, [r] * 4, fixed=[1] * 4)
+    s.set_dt(1e-7)
+    s.step(1)
+    st = s.stats()
+    assert st["n_contacts"] == 4
+    c = s.contacts()
+    assert sorted(map(tuple, np.abs(c["c"]))).count((0, 1, 0)) == 1
+    F = _ip2_kn(E, r, E, r) * delta
+    expect = -(F * np.linalg.norm(H[:, 1]) / np.linalg.det(H)) * np.outer(n, n)
+    assert np.allclose(st["stress"], expect, rtol=1e-9, atol=1e-12 * abs(expect).max())
+    assert st["Z"] == 2.0

@@ -62,7 +62,9 @@ enum { DEM_FP64 = 0, DEM_MIXED = 1 };
 /* Scene description (POD).  Initialise with dem_scene_desc_init, then edit. */
 typedef struct dem_scene_desc {
     int periodic;            /* 1: periodic cell cell_h (section 2.1.6); 0: open space */
-    double cell_h[9];        /* periodic cell, base vectors in columns; must be diagonal */
+    double cell_h[9];        /* periodic cell, base vectors in columns (row-major 3x3):
+                                any parallelepiped with a positive diagonal and a
+                                positive determinant; off-diagonal entries shear it */
     double box_lo[3];        /* walls: lower corner of the box */
     double box_hi[3];        /* walls: upper corner of the box */
     int wall_mask;           /* bit (2*axis + side): infinite wall at box_lo[axis] (side 0)
@@ -125,8 +127,8 @@ typedef struct dem_timing {
 void dem_scene_desc_init(dem_scene_desc *desc);
 
 /* Create an empty scene on the GPU.  desc is copied.  On success *out is a new
- * handle (free it with dem_scene_destroy).  Errors: INVALID_ARG (null, non-diagonal
- * or singular periodic cell, negative damping), CUDA, OOM. */
+ * handle (free it with dem_scene_destroy).  Errors: INVALID_ARG (null, a periodic cell
+ * with a non-positive diagonal entry or determinant, negative damping), CUDA, OOM. */
 dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out);
 
 /* Release every resource of the scene (waits for its work to finish). NULL is a no-op. */
@@ -155,7 +157,8 @@ dem_status dem_set_dt(dem_scene *scene, double dt);
 dem_status dem_get_dt(dem_scene *scene, double *dt);
 
 /* Cell.velGrad for a periodic scene; like Cell.velGrad assignment the value takes
- * effect at the next step.  Must be diagonal.  Errors: INVALID_ARG, STATE (aperiodic). */
+ * effect at the next step.  Any 3x3 (off-diagonal entries shear the cell; homoDeform = 2
+ * moves every body with the full field).  Errors: INVALID_ARG, STATE (aperiodic). */
 dem_status dem_set_cell_velgrad(dem_scene *scene, const double velgrad[9]);
 
 /* Stress-controlled periodic cell (PeriTriaxController: goal, stressMask,
@@ -250,7 +253,7 @@ dem_status dem_get_timing(dem_scene *scene, dem_timing *out);
  * current range.  The stress servo (dem_set_triax) runs only on a scene without
  * sub-scenes. */
 typedef struct dem_subscene_desc {
-    int periodic;            /* 1: periodic cell cell_h (diagonal, positive); 0: box */
+    int periodic;            /* 1: periodic cell cell_h (as dem_scene_desc); 0: box */
     double cell_h[9];
     double box_lo[3], box_hi[3];   /* walls of an aperiodic sub-scene */
     int wall_mask;           /* bit 2*axis + side (side 0: low face), as dem_scene_desc */

@@ -198,8 +198,12 @@ __global__ void k_cellrec(const double4_32a *__restrict__ pos, const int *__rest
   cell_of(g, p.x, p.y, p.z, c, img);
   double x[3] = {p.x, p.y, p.z};
   float f[3];
-  for (int k = 0; k < 3; ++k)
-    f[k] = g.periodic ? (float)(x[k] - g.L[k] * img[k]) : (float)(x[k] - g.lo[k]);
+  for (int k = 0; k < 3; ++k) {
+    double shift = g.L[k] * img[k];
+    if (g.periodic && g.sheared)   // wrapped position x - H img
+      shift = g.H[3 * k] * img[0] + g.H[3 * k + 1] * img[1] + g.H[3 * k + 2] * img[2];
+    f[k] = g.periodic ? (float)(x[k] - shift) : (float)(x[k] - g.lo[k]);
+  }
   cr.wpos[i] = make_float4(f[0], f[1], f[2], (float)p.w);
   cr.info[i] = make_int4(c[0] | (c[1] << 10) | (c[2] << 20), img[0], img[1], img[2]);
 }
@@ -267,6 +271,8 @@ __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict
           int c0, c1, c2;
           unpack_shift(cp, c0, c1, c2);
           h[0] = g.L[0] * c0; h[1] = g.L[1] * c1; h[2] = g.L[2] * c2;
+          if (g.sheared)   // Href c of a sheared cell
+            for (int k = 0; k < 3; ++k) h[k] = g.H[3 * k] * c0 + g.H[3 * k + 1] * c1 + g.H[3 * k + 2] * c2;
         }
         t.g32[r] = make_float4((float)((p2.x + h[0]) - p1.x), (float)((p2.y + h[1]) - p1.y),
                                (float)((p2.z + h[2]) - p1.z), 0.0f);

@@ -37,13 +37,14 @@ constexpr int kQ = 64;   // per-warp queue of real rows (< 32 left over + 32 new
 // H (image shift) and of W (velocity of a unit shift); all zero when aperiodic.
 struct RowCell {
   double dt, H[3], W[3];
-  int periodic, law;
+  int periodic, law, sheared;
 };
 __device__ __forceinline__ RowCell row_cell(const CellState &c) {
   RowCell r;
   r.dt = c.dt;
   r.periodic = c.periodic;
   r.law = c.law;
+  r.sheared = c.sheared;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     r.H[i] = c.periodic ? c.H[4 * i] : 0.0;
@@ -54,10 +55,11 @@ __device__ __forceinline__ RowCell row_cell(const CellState &c) {
 
 // One real row: Ip2 on creation, shear transport and increment, Law2, outputs.
 // dx, dy, dz, l2 are the branch vector and its squared length from the exact test.
-template <bool kHertz>
+template <int kFeat>
 __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const Mat *__restrict__ mats,
                                          long long k, double dx, double dy, double dz, double l2,
-                                         double r1, double r2, const RowCell &rc) {
+                                         double r1, double r2, const RowCell &rc,
+                                         const CellState *__restrict__ cq) {
   const double dt = rc.dt;
   const int2 pr = t.pair[k];
   const double R = r1 + r2;
@@ -72,7 +74,7 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   double kn = fs.w, ks = hn.w, tanphi;
   if (kn == 0.0) {
     const Mat &m1 = mats[b.mat[pr.x]], &m2 = mats[b.mat[pr.y]];
-    if (kHertz && rc.law) {   // Ip2_FrictMat_FrictMat_MindlinPhys: constants kno, kso
+    if ((kFeat & 1) && rc.law) {   // Ip2_FrictMat_FrictMat_MindlinPhys: constants kno, kso
       mindlin_phys(m1, r1, m2, r2, kn, ks);
     } else {        // Ip2_FrictMat_FrictMat_FrictPhys (new contact)
       const double k1 = m1.young * (2 * r1), k2 = m2.young * (2 * r2);
@@ -93,9 +95,17 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   if (rc.periodic) {  // velocity of the image of body 2 (shift c moves with the cell)
     int i0, i1, i2;
     unpack_shift(t.cpack[k], i0, i1, i2);
-    v2.x += rc.W[0] * (double)i0;
-    v2.y += rc.W[1] * (double)i1;
-    v2.z += rc.W[2] * (double)i2;
+    const double c0 = i0, c1 = i1, c2 = i2;
+    if ((kFeat & 2) && rc.sheared) {   // W c with the full image velocity matrix
+      const double *W = cq->W;
+      v2.x += W[0] * c0 + W[1] * c1 + W[2] * c2;
+      v2.y += W[3] * c0 + W[4] * c1 + W[5] * c2;
+      v2.z += W[6] * c0 + W[7] * c1 + W[8] * c2;
+    } else {
+      v2.x += rc.W[0] * c0;
+      v2.y += rc.W[1] * c1;
+      v2.z += rc.W[2] * c2;
+    }
   }
   // 1. motion of the contact frame: -Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)
   const double ax = hn.y * nz - hn.z * ny;
@@ -114,13 +124,13 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double uz = f * (v2.z - v1.z) - (rx * ny - ry * nx);
   const double vn = nx * ux + ny * uy + nz * uz;
   // Hertz-Mindlin: shear stiffness kso pen^1/2 and normal force kno pen^3/2
-  const double sq = (kHertz && rc.law) ? sqrt(pen) : 1.0;
+  const double sq = ((kFeat & 1) && rc.law) ? sqrt(pen) : 1.0;
   const double kd = (ks * sq) * dt;
   fx -= kd * (ux - vn * nx);
   fy -= kd * (uy - vn * ny);
   fz -= kd * (uz - vn * nz);
   // Law2: normal force and Coulomb cap
-  const double Fn = (kHertz && rc.law) ? kn * pen * sq : kn * pen;
+  const double Fn = ((kFeat & 1) && rc.law) ? kn * pen * sq : kn * pen;
   const double maxFs = Fn * tanphi;
   const double fs2 = fx * fx + fy * fy + fz * fz;
   if (fs2 > maxFs * maxFs) {
@@ -159,7 +169,9 @@ struct QRow {
 // kDesc: the table and bodies come from the device descriptor (a captured batch of
 // steps stays valid across collider runs); otherwise from the launch parameters,
 // which the kernel reads straight from the constant bank (fewer registers).
-template <int kT, bool kHertz, bool kDesc>
+// kFeat: bit 0 some sub-scene uses the Hertz-Mindlin law, bit 1 some periodic cell is
+// sheared; each variant carries only the branches it needs (they cost registers).
+template <int kT, int kFeat, bool kDesc>
 __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDesc *__restrict__ d,
                                                           Table tp, Bodies bp,
                                                           const CellState *__restrict__ cs,
@@ -191,14 +203,23 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       if (periodic) {
         int i0, i1, i2;
         unpack_shift(t.cpack[k], i0, i1, i2);
-        // the cell is diagonal (enforced at the C ABI): H c has one term per axis, the
-        // same value the full product gives (the off-diagonal terms are exact zeros)
-        const double H0 = multi ? cs[sq].H[0] : rc0.H[0];
-        const double H1 = multi ? cs[sq].H[4] : rc0.H[1];
-        const double H2 = multi ? cs[sq].H[8] : rc0.H[2];
-        h0 = __dmul_rn(H0, (double)i0);
-        h1 = __dmul_rn(H1, (double)i1);
-        h2 = __dmul_rn(H2, (double)i2);
+        const double c0 = i0, c1 = i1, c2 = i2;
+        if ((kFeat & 2) && (multi ? cs[sq].sheared : rc0.sheared)) {
+          // H c of a sheared cell, each row summed left to right as the oracle writes it
+          const double *H = cs[sq].H;
+          h0 = __dadd_rn(__dadd_rn(__dmul_rn(H[0], c0), __dmul_rn(H[1], c1)), __dmul_rn(H[2], c2));
+          h1 = __dadd_rn(__dadd_rn(__dmul_rn(H[3], c0), __dmul_rn(H[4], c1)), __dmul_rn(H[5], c2));
+          h2 = __dadd_rn(__dadd_rn(__dmul_rn(H[6], c0), __dmul_rn(H[7], c1)), __dmul_rn(H[8], c2));
+        } else {
+          // diagonal cell: one term per axis, the same value the full product gives (the
+          // off-diagonal terms are exact zeros)
+          const double H0 = multi ? cs[sq].H[0] : rc0.H[0];
+          const double H1 = multi ? cs[sq].H[4] : rc0.H[1];
+          const double H2 = multi ? cs[sq].H[8] : rc0.H[2];
+          h0 = __dmul_rn(H0, c0);
+          h1 = __dmul_rn(H1, c1);
+          h2 = __dmul_rn(H2, c2);
+        }
       }
       // branch vector and the exact test (eq. 2.2, second pass; R1 of the oracle)
       dx = __dsub_rn(__dadd_rn(p2.x, h0), p1.x);
@@ -222,8 +243,8 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
     __syncwarp();
     if (cnt >= 32) {
       const QRow e = wq[lane];
-      real_row<kHertz>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
-               multi ? row_cell(cs[e.q]) : rc0);
+      real_row<kFeat>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
+                       multi ? row_cell(cs[e.q]) : rc0, cs + e.q);
       __syncwarp();
       if (lane < cnt - 32) wq[lane] = wq[lane + 32];
       cnt -= 32;
@@ -232,28 +253,26 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
   }
   if (lane < cnt) {
     const QRow e = wq[lane];
-    real_row<kHertz>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2, multi ? row_cell(cs[e.q]) : rc0);
+    real_row<kFeat>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
+                     multi ? row_cell(cs[e.q]) : rc0, cs + e.q);
   }
 }
 }  // namespace
 
 void launch_contact(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
                     const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
-                    int hertz, int nsm, int block, int per_sm, cudaStream_t st) {
+                    int feat, int nsm, int block, int per_sm, cudaStream_t st) {
   if (rows <= 0) return;
   long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-  // the Hertz-Mindlin branches are compiled only into the variant a scene using that
-  // law needs (they cost the linear law registers)
-#define DEM_C(B, H, D) k_contact<B, H, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
-#define DEM_C2(H, D) if (block == 128) DEM_C(128, H, D); else DEM_C(256, H, D);
-  if (desc) {
-    if (hertz) { DEM_C2(true, true) } else { DEM_C2(false, true) }
-  } else {
-    if (hertz) { DEM_C2(true, false) } else { DEM_C2(false, false) }
-  }
-#undef DEM_C2
+#define DEM_C(B, F, D) k_contact<B, F, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
+#define DEM_CB(F, D) if (block == 128) DEM_C(128, F, D); else DEM_C(256, F, D);
+#define DEM_CF(D) switch (feat & 3) { case 0: DEM_CB(0, D) break; case 1: DEM_CB(1, D) break; \
+                                      case 2: DEM_CB(2, D) break; default: DEM_CB(3, D) }
+  if (desc) { DEM_CF(true) } else { DEM_CF(false) }
+#undef DEM_CF
+#undef DEM_CB
 #undef DEM_C
 }
 

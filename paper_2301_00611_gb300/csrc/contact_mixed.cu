@@ -39,27 +39,29 @@ struct QRowF {
 // What a row needs of its (sub-)scene's cell state in FP32, plus the FP64 step.
 struct RowCellF {
   double dt;
-  float dH[3], W[3];
-  int periodic, law;
+  float dH[3], W[3];   // diagonals (the full matrices are read when the cell is sheared)
+  int periodic, law, sheared;
 };
 __device__ __forceinline__ RowCellF row_cell_f(const CellState &c) {
   RowCellF r;
   r.dt = c.dt;
   r.periodic = c.periodic;
   r.law = c.law;
+  r.sheared = c.sheared;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    r.dH[i] = c.periodic ? c.dHf[i] : 0.0f;
-    r.W[i] = c.periodic ? c.Wf[i] : 0.0f;
+    r.dH[i] = c.periodic ? c.dHf[4 * i] : 0.0f;
+    r.W[i] = c.periodic ? c.Wf[4 * i] : 0.0f;
   }
   return r;
 }
 
 // One real row in mixed precision (Ip2 on creation, shear transport, Law2, outputs).
-template <bool kHertz>
+template <int kFeat>
 __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
                                                const Mat *__restrict__ mats, const QRowF &e,
-                                               const RowCellF &rc) {
+                                               const RowCellF &rc,
+                                               const CellState *__restrict__ cq) {
   const double dt = rc.dt;
   const float *Wd = rc.W;
   const long long k = e.k;
@@ -79,7 +81,7 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   double tanphi;
   if (kn == 0.0f) {   // Ip2 on a new contact
     const Mat &m1 = mats[b.mat[pr.x]], &m2 = mats[b.mat[pr.y]];
-    if (kHertz && rc.law) {     // MindlinPhys constants kno, kso (formed once per contact in FP64)
+    if ((kFeat & 1) && rc.law) {     // MindlinPhys constants kno, kso (formed once per contact in FP64)
       double kno, kso;
       mindlin_phys(m1, r1, m2, r2, kno, kso);
       kn = (float)kno;
@@ -109,7 +111,13 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   const float4 va2 = b.vw32[2 * pr.y], vb2 = b.vw32[2 * pr.y + 1];
   const float w1x = va1.w, w1y = vb1.x, w1z = vb1.y;
   const float w2x = va2.w, w2y = vb2.x, w2z = vb2.y;
-  const float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
+  float v2x = va2.x + Wd[0] * cx, v2y = va2.y + Wd[1] * cy, v2z = va2.z + Wd[2] * cz;
+  if ((kFeat & 2) && rc.sheared) {   // W c with the full image velocity matrix
+    const float *Wf = cq->Wf;
+    v2x = va2.x + (Wf[0] * cx + Wf[1] * cy + Wf[2] * cz);
+    v2y = va2.y + (Wf[3] * cx + Wf[4] * cy + Wf[5] * cz);
+    v2z = va2.z + (Wf[6] * cx + Wf[7] * cy + Wf[8] * cz);
+  }
   // 2 (first, in FP32). mutual motion: ratchet-free v12, its part perpendicular to n
   const float rx = r2 * w2x + r1 * w1x, ry = r2 * w2y + r1 * w1y, rz = r2 * w2z + r1 * w1z;
   const float f = R * il;
@@ -117,7 +125,7 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   const float uy = f * (v2y - va1.y) - (rz * nx - rx * nz);
   const float uz = f * (v2z - va1.z) - (rx * ny - ry * nx);
   const float vn = nx * ux + ny * uy + nz * uz;
-  const float sq = (kHertz && rc.law) ? sqrtf(pen) : 1.0f;   // Hertz-Mindlin pen^1/2 factor
+  const float sq = ((kFeat & 1) && rc.law) ? sqrtf(pen) : 1.0f;   // Hertz-Mindlin pen^1/2 factor
   const float kd = (ks * sq) * dtf;
   const float ix = kd * (ux - vn * nx), iy = kd * (uy - vn * ny), iz = kd * (uz - vn * nz);
   // 1. transport of the stored shear force into the new frame: the rotation vector
@@ -134,7 +142,7 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   double fy = fsd.y - (double)((sz0 * bx - sx0 * bz) + iy);
   double fz = fsd.z - (double)((sx0 * by - sy0 * bx) + iz);
   // Law2: normal force, Coulomb test in FP32; the cap rescales the FP64 spring
-  const float Fn = (kHertz && rc.law) ? kn * pen * sq : kn * pen;
+  const float Fn = ((kFeat & 1) && rc.law) ? kn * pen * sq : kn * pen;
   const float maxFs = Fn * (float)tanphi;
   float sx = (float)fx, sy = (float)fy, sz = (float)fz;
   const float fs2 = sx * sx + sy * sy + sz * sz;
@@ -154,7 +162,7 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
 
 // Same per-warp queue of real rows as the FP64 kernel: the FP32 geometry test on
 // tiles of 32 consecutive rows, the law on 32 queued real rows at a time.
-template <int kT, bool kHertz, bool kDesc>
+template <int kT, int kFeat, bool kDesc>
 __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict__ d,
                                                       Table tp, Bodies bp,
                                                       const CellState *__restrict__ cs,
@@ -183,19 +191,28 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
       const float4 c = b.p32[pr.y];
       if (multi) sq = b.sid[pr.x];
       float cx = 0, cy = 0, cz = 0, dH0 = 0, dH1 = 0, dH2 = 0;
+      float hx = 0, hy = 0, hz = 0;
       if (multi ? cs[sq].periodic : rc0.periodic) {
         int i0, i1, i2;
         unpack_shift(t.cpack[k], i0, i1, i2);
         cx = (float)i0; cy = (float)i1; cz = (float)i2;
-        dH0 = multi ? cs[sq].dHf[0] : rc0.dH[0];
-        dH1 = multi ? cs[sq].dHf[1] : rc0.dH[1];
-        dH2 = multi ? cs[sq].dHf[2] : rc0.dH[2];
+        if ((kFeat & 2) && (multi ? cs[sq].sheared : rc0.sheared)) {   // (H - Href) c, full
+          const float *D = cs[sq].dHf;
+          hx = D[0] * cx + D[1] * cy + D[2] * cz;
+          hy = D[3] * cx + D[4] * cy + D[5] * cz;
+          hz = D[6] * cx + D[7] * cy + D[8] * cz;
+        } else {
+          dH0 = multi ? cs[sq].dHf[0] : rc0.dH[0];
+          dH1 = multi ? cs[sq].dHf[4] : rc0.dH[1];
+          dH2 = multi ? cs[sq].dHf[8] : rc0.dH[2];
+          hx = dH0 * cx; hy = dH1 * cy; hz = dH2 * cz;
+        }
       }
       // branch vector: reference branch at the collider run + both offsets + the
       // change of the cell shift since then
-      dx = g.x + (c.x - a.x) + dH0 * cx;
-      dy = g.y + (c.y - a.y) + dH1 * cy;
-      dz = g.z + (c.z - a.z) + dH2 * cz;
+      dx = g.x + (c.x - a.x) + hx;
+      dy = g.y + (c.y - a.y) + hy;
+      dz = g.z + (c.z - a.z) + hz;
       l2 = dx * dx + dy * dy + dz * dz;
       r1 = a.w; r2 = c.w;
       const float R = r1 + r2;
@@ -216,7 +233,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
     __syncwarp();
     if (cnt >= 32) {
       const QRowF e = wq[lane];
-      real_row_mixed<kHertz>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
+      real_row_mixed<kFeat>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0, cs + e.q);
       __syncwarp();
       if (lane < cnt - 32) wq[lane] = wq[lane + 32];
       cnt -= 32;
@@ -225,26 +242,25 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
   }
   if (lane < cnt) {
     const QRowF e = wq[lane];
-    real_row_mixed<kHertz>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0);
+    real_row_mixed<kFeat>(t, b, mats, e, multi ? row_cell_f(cs[e.q]) : rc0, cs + e.q);
   }
 }
 }  // namespace
 
 void launch_contact_mixed(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
                           const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
-                          int hertz, int nsm, int block, int per_sm, cudaStream_t st) {
+                          int feat, int nsm, int block, int per_sm, cudaStream_t st) {
   if (rows <= 0) return;
   long long need = (rows + block - 1) / block;
   long long cap = (long long)nsm * per_sm;   // persistent grid: per_sm blocks per SM
   unsigned grid = (unsigned)(need < cap ? need : cap);
-#define DEM_C(B, H, D) k_contact_mixed<B, H, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
-#define DEM_C2(H, D) if (block == 128) DEM_C(128, H, D); else DEM_C(256, H, D);
-  if (desc) {
-    if (hertz) { DEM_C2(true, true) } else { DEM_C2(false, true) }
-  } else {
-    if (hertz) { DEM_C2(true, false) } else { DEM_C2(false, false) }
-  }
-#undef DEM_C2
+#define DEM_C(B, F, D) k_contact_mixed<B, F, D><<<grid, B, 0, st>>>(d, h.t, h.b, cs, ds, mats, multi)
+#define DEM_CB(F, D) if (block == 128) DEM_C(128, F, D); else DEM_C(256, F, D);
+#define DEM_CF(D) switch (feat & 3) { case 0: DEM_CB(0, D) break; case 1: DEM_CB(1, D) break; \
+                                      case 2: DEM_CB(2, D) break; default: DEM_CB(3, D) }
+  if (desc) { DEM_CF(true) } else { DEM_CF(false) }
+#undef DEM_CF
+#undef DEM_CB
 #undef DEM_C
 }
 

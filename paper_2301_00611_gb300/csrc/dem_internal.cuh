@@ -118,10 +118,12 @@ struct CellState {
   long long iter;
   int periodic, pad;
   // FP32 diagonals used by the mixed-precision contact kernel for the current step
-  float dHf[3];         // H - Href
-  float Wf[3];          // image velocity matrix W
-  float Ef[3];          // E
-  float pad2[3];
+  float dHf[9];         // H - Href
+  float Wf[9];          // image velocity matrix W
+  float Ef[9];          // E
+  int sheared;          // some off-diagonal entry of H, Hprev, Href, L or Lprev is nonzero
+                        // (kernels then take full 3x3 products; diagonal cells keep the
+                        // one-term-per-axis fast path, which gives the same values)
   // stress-controlled cell (PeriTriaxController): goal stress (stress_mask bit set)
   // or strain rate per axis, rate bound, growDamping, update period in steps
   double goal[3], max_rate[3], grow_damping;
@@ -163,12 +165,16 @@ struct Grid {
   float slack;      // FP32 rounding allowance of the candidate test (keeps it conservative)
   long long base;   // first global cell index of this grid (sub-scenes are consecutive)
   int morton;       // 1: cells indexed by Morton code (B^3), 0: row-major (n0 n1 n2)
-  int pad;
+  int sheared;      // periodic cell with off-diagonal terms: fractional coordinates
+                    // s = Hinv x and image shifts H c use the full matrices below
+  double H[9], Hinv[9];   // periodic cell at this collider run (row-major)
+  float Hf[9];
 };
 
 struct SceneConst {
   long long N;
   int hertz;     // some sub-scene uses the Hertz-Mindlin law
+  int sheared;   // some periodic sub-scene has a sheared cell
   int walls;     // some sub-scene has walls
   int periodic;  // some sub-scene is periodic
   int ordered;   // integrate bodies in Table::ord order (else slot order)
@@ -242,13 +248,14 @@ void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
 // hertz: some sub-scene uses the Hertz-Mindlin law (selects the variant with its branch)
 // d / h: the device descriptor and its host copy; desc: read the table and bodies
 // through d (captured batches) rather than from launch parameters
+// feat: bit 0 some sub-scene uses the Hertz-Mindlin law, bit 1 some cell is sheared
 void launch_contact(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
                     const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
-                    int hertz, int nsm, int block, int per_sm, cudaStream_t st);
+                    int feat, int nsm, int block, int per_sm, cudaStream_t st);
 // contact_mixed.cu
 void launch_contact_mixed(const StepDesc *d, const StepDesc &h, bool desc, long long rows,
                           const CellState *cs, const DevStatus *ds, const Mat *mats, int multi,
-                          int hertz, int nsm, int block, int per_sm, cudaStream_t st);
+                          int feat, int nsm, int block, int per_sm, cudaStream_t st);
 
 // integrate.cu
 // block: 128, 256 or 512 threads

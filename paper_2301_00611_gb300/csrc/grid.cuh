@@ -29,11 +29,15 @@ __host__ __device__ inline long long cell_index(const Grid &g, int i, int j, int
 // cell coordinates (and, periodic, the integer image) of a position
 __device__ inline void cell_of(const Grid &g, double x, double y, double z, int c[3], int img[3]) {
   const double p[3] = {x, y, z};
+  double u[3] = {x * g.scale[0], y * g.scale[1], z * g.scale[2]};   // fractional (periodic)
+  if (g.periodic && g.sheared)   // sheared cell: s = Hinv x
+    for (int k = 0; k < 3; ++k)
+      u[k] = g.Hinv[3 * k] * x + g.Hinv[3 * k + 1] * y + g.Hinv[3 * k + 2] * z;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     int ck;
     if (g.periodic) {
-      double s = p[k] * g.scale[k];
+      double s = u[k];
       double fi = floor(s);
       double f = s - fi;
       ck = (int)(f * g.n[k]);
@@ -98,9 +102,16 @@ struct CellRec {
 // the exact one; count and emit evaluate it identically.
 __device__ inline bool cand_f32(const Grid &g, const float4 &a, const float4 &b, const int w[3],
                                 float slack) {
-  const float dx = (b.x + (float)w[0] * g.Lf[0]) - a.x;
-  const float dy = (b.y + (float)w[1] * g.Lf[1]) - a.y;
-  const float dz = (b.z + (float)w[2] * g.Lf[2]) - a.z;
+  float sx = (float)w[0] * g.Lf[0], sy = (float)w[1] * g.Lf[1], sz = (float)w[2] * g.Lf[2];
+  if (g.sheared) {   // image shift H w of a sheared cell
+    const float f0 = (float)w[0], f1 = (float)w[1], f2 = (float)w[2];
+    sx = g.Hf[0] * f0 + g.Hf[1] * f1 + g.Hf[2] * f2;
+    sy = g.Hf[3] * f0 + g.Hf[4] * f1 + g.Hf[5] * f2;
+    sz = g.Hf[6] * f0 + g.Hf[7] * f1 + g.Hf[8] * f2;
+  }
+  const float dx = (b.x + sx) - a.x;
+  const float dy = (b.y + sy) - a.y;
+  const float dz = (b.z + sz) - a.z;
   const float R = (a.w + b.w) + g.reachf + slack;
   return dx * dx + dy * dy + dz * dz < R * R;
 }

@@ -116,7 +116,9 @@ __device__ inline void wall_phys(const Mat *mats, int wmat, int mat, double r, d
 // contact kernel).  Every quantity it needs in FP32 is read from the FP32 mirrors
 // the previous step wrote, so the FP64 pipe (conversions included) carries ~27
 // instructions per body.
-template <int kB, bool kWalls, bool kDesc>
+// kFeat: bit 0 some sub-scene has walls, bit 1 some periodic cell is sheared (full 3x3
+// products); each variant carries only the branches it needs.
+template <int kB, int kFeat, bool kDesc>
 __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restrict__ d, StepDesc hp,
                                                         const CellState *__restrict__ cs,
                                                         DevStatus *ds, const Mat *__restrict__ mats) {
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   const float xf[3] = {xr.x + off.x, xr.y + off.y, xr.z + off.z};
   const float r = off.w;
 
-  if (kWalls && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
+  if ((kFeat & 1) && c.wall_mask) {   // sphere-wall contacts: the FP64 kernel's law, in FP32
     const float dtl = (float)c.dt_law;   // the contact law's step (see CellState::dt_law)
     const double4_32a pd = b.pos[s];
     const double xd[3] = {pd.x, pd.y, pd.z};
@@ -242,8 +244,15 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   if (!fixed) {
     const float lam = (float)c.damping;
     float vref[3] = {vv[0], vv[1], vv[2]};
-    if (c.periodic)
-      for (int q = 0; q < 3; ++q) vref[q] -= (float)c.Lprev[4 * q] * xf[q];
+    if (c.periodic) {
+      if ((kFeat & 2) && c.sheared) {
+        for (int q = 0; q < 3; ++q)
+          vref[q] -= (float)c.Lprev[3 * q] * xf[0] + (float)c.Lprev[3 * q + 1] * xf[1] +
+                     (float)c.Lprev[3 * q + 2] * xf[2];
+      } else {
+        for (int q = 0; q < 3; ++q) vref[q] -= (float)c.Lprev[4 * q] * xf[q];
+      }
+    }
     for (int q = 0; q < 3; ++q) {
       const float Ft = F[q] + mp.x * (float)c.gravity[q];
       const float acc = Ft * mp.z;
@@ -253,9 +262,21 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
       const float Td = T[q] * damp_factor_f(T[q] * (ww[q] + 0.5f * dtf * aacc), lam);
       dw[q] = dtf * Td * mp.w;
     }
-    if (c.periodic)   // homoDeform = 2
-      for (int q = 0; q < 3; ++q)
-        dv[q] += (float)c.dL[4 * q] * xf[q] + dtf * ((float)c.L[4 * q] * vv[q]);
+    if (c.periodic) {   // homoDeform = 2
+      if ((kFeat & 2) && c.sheared) {
+        for (int q = 0; q < 3; ++q) {
+          float a = 0, bq = 0;
+          for (int j = 0; j < 3; ++j) {
+            a += (float)c.dL[3 * q + j] * xf[j];
+            bq += (float)c.L[3 * q + j] * vv[j];
+          }
+          dv[q] += a + dtf * bq;
+        }
+      } else {
+        for (int q = 0; q < 3; ++q)
+          dv[q] += (float)c.dL[4 * q] * xf[q] + dtf * ((float)c.L[4 * q] * vv[q]);
+      }
+    }
   }
   // FP64 accumulation of velocity, spin and position
   const double4_32a v = b.vel[s], w = b.angvel[s], p = b.pos[s];
@@ -297,7 +318,13 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
                              dq0 * q0.w + dq1 * q0.z - dq2 * q0.y + dq3 * q0.x);
   }
   // collider trigger on the FP32 offset (slightly early to cover its rounding)
-  const float ux = ox - c.Ef[0] * xr.x, uy = oy - c.Ef[1] * xr.y, uz = oz - c.Ef[2] * xr.z;
+  float ux = ox - c.Ef[0] * xr.x, uy = oy - c.Ef[4] * xr.y, uz = oz - c.Ef[8] * xr.z;
+  if ((kFeat & 2) && c.sheared) {   // E xref with the full affine strain
+    const float *Ef = c.Ef;
+    ux = ox - (Ef[0] * xr.x + Ef[1] * xr.y + Ef[2] * xr.z);
+    uy = oy - (Ef[3] * xr.x + Ef[4] * xr.y + Ef[5] * xr.z);
+    uz = oz - (Ef[6] * xr.x + Ef[7] * xr.y + Ef[8] * xr.z);
+  }
   if (!(ux * ux + uy * uy + uz * uz <= (float)(0.998 * c.thr2))) {
     if (!ds->request) ds->request = 1;
   }
@@ -306,7 +333,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
     atomicOr(&ds->error, kErrNonFinite);
 }
 
-template <int kB, bool kWalls, bool kDesc>
+template <int kB, int kFeat, bool kDesc>
 __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d, StepDesc hp,
                                                   const CellState *__restrict__ cs,
                                                   DevStatus *ds, const Mat *__restrict__ mats) {
@@ -331,7 +358,7 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
   const double x[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z}, ww[3] = {w.x, w.y, w.z};
   const double r = p.w;
 
-  if (kWalls && c.wall_mask) {
+  if ((kFeat & 1) && c.wall_mask) {
     for (int wi = 0; wi < 6; ++wi) {
       if (!(c.wall_mask & (1 << wi))) continue;
       const int ax = wi >> 1;
@@ -402,10 +429,14 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
   if (!fixed) {
     const double lam = c.damping;
     double vref[3] = {vv[0], vv[1], vv[2]};
-    // cell matrices are diagonal (enforced at the C ABI): only their diagonals enter
     if (c.periodic) {   // fluctuation velocity for eq. 2.9 in a deforming cell
       const double *Lp = c.Lprev;
-      for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
+      if ((kFeat & 2) && c.sheared) {   // Lprev x, rows summed as the oracle writes them
+        for (int q = 0; q < 3; ++q)
+          vref[q] -= Lp[3 * q] * x[0] + Lp[3 * q + 1] * x[1] + Lp[3 * q + 2] * x[2];
+      } else {   // diagonal matrices: only their diagonals enter
+        for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
+      }
     }
     const double hdt = 0.5 * dt, one_m = 1.0 - lam, one_p = 1.0 + lam;
     for (int q = 0; q < 3; ++q) {   // v+ = v- + (dt Fd) / m, as the oracle orders it
@@ -417,7 +448,13 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
     }
     if (c.periodic) {   // homoDeform = 2
       const double *dL = c.dL, *L = c.L;
-      for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
+      if ((kFeat & 2) && c.sheared) {
+        for (int q = 0; q < 3; ++q)
+          vn_[q] += (dL[3 * q] * x[0] + dL[3 * q + 1] * x[1] + dL[3 * q + 2] * x[2]) +
+                    dt * (L[3 * q] * vv[0] + L[3 * q + 1] * vv[1] + L[3 * q + 2] * vv[2]);
+      } else {
+        for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
+      }
     }
   } else {
     for (int q = 0; q < 3; ++q) { vn_[q] = vv[q]; wn_[q] = ww[q]; }
@@ -456,10 +493,15 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
 
   // collider trigger: displacement since the last run, minus the affine part
   const double4_32a xr = b.xref[s];
-  const double *E = c.E;   // diagonal
-  const double ux = (xn[0] - xr.x) - E[0] * xr.x;
-  const double uy = (xn[1] - xr.y) - E[4] * xr.y;
-  const double uz = (xn[2] - xr.z) - E[8] * xr.z;
+  const double *E = c.E;
+  double ux = (xn[0] - xr.x) - E[0] * xr.x;
+  double uy = (xn[1] - xr.y) - E[4] * xr.y;
+  double uz = (xn[2] - xr.z) - E[8] * xr.z;
+  if ((kFeat & 2) && c.sheared) {   // E xref with the full affine strain
+    ux = (xn[0] - xr.x) - (E[0] * xr.x + E[1] * xr.y + E[2] * xr.z);
+    uy = (xn[1] - xr.y) - (E[3] * xr.x + E[4] * xr.y + E[5] * xr.z);
+    uz = (xn[2] - xr.z) - (E[6] * xr.x + E[7] * xr.y + E[8] * xr.z);
+  }
   if (!(ux * ux + uy * uy + uz * uz <= c.thr2)) {
     if (!ds->request) ds->request = 1;
   }
@@ -507,7 +549,7 @@ __device__ void derive_next_local(CellState *__restrict__ cs, const double (&H)[
   const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
   cs->thr2 = eff > 0 ? eff * eff : -1.0;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) cs->Ef[q] = (float)E[4 * q];
+  for (int q = 0; q < 9; ++q) cs->Ef[q] = (float)E[q];
 }
 
 __device__ void derive_next(CellState *__restrict__ cs) {
@@ -567,11 +609,14 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo) {
       cs->W[q] = W[q];
     }
     derive_next_local(cs, H, L, dt);
+    bool off = false;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      cs->dHf[q] = (float)(H[4 * q] - cs->Href[4 * q]);
-      cs->Wf[q] = (float)W[4 * q];
+    for (int q = 0; q < 9; ++q) {
+      cs->dHf[q] = (float)(H[q] - cs->Href[q]);
+      cs->Wf[q] = (float)W[q];
+      if (q % 4) off |= (H[q] != 0) | (Hp[q] != 0) | (L[q] != 0) | (Lp[q] != 0) | (cs->Href[q] != 0);
     }
+    cs->sheared = off ? 1 : 0;
   }
   cs->iter += 1;
   cs->time = __dadd_rn(cs->time, dt);
@@ -870,18 +915,19 @@ void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const Cel
                       DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st) {
   const long long N = h.sc.N;
   if (N <= 0) return;
-  const int walls = h.sc.walls;
-  // kernels without the sphere-wall branch when no sub-scene has walls (fewer registers)
-#define DEM_I(K, B, W, D) K<B, W, D><<<(unsigned)((N + B - 1) / B), B, 0, st>>>(d, h, cs, ds, mats)
-#define DEM_I_W(K, B, D) if (walls) DEM_I(K, B, true, D); else DEM_I(K, B, false, D);
-#define DEM_I_B(K, D) if (block == 128) { DEM_I_W(K, 128, D) } else if (block == 512) { DEM_I_W(K, 512, D) } else { DEM_I_W(K, 256, D) }
+  const int feat = (h.sc.walls ? 1 : 0) | (h.sc.sheared ? 2 : 0);
+  // kernels without the sphere-wall or sheared-cell branches when no sub-scene needs them
+#define DEM_I(K, B, F, D) K<B, F, D><<<(unsigned)((N + B - 1) / B), B, 0, st>>>(d, h, cs, ds, mats)
+#define DEM_I_F(K, B, D) switch (feat) { case 0: DEM_I(K, B, 0, D); break; case 1: DEM_I(K, B, 1, D); break; \
+                                         case 2: DEM_I(K, B, 2, D); break; default: DEM_I(K, B, 3, D); }
+#define DEM_I_B(K, D) if (block == 128) { DEM_I_F(K, 128, D) } else if (block == 512) { DEM_I_F(K, 512, D) } else { DEM_I_F(K, 256, D) }
   if (mixed) {
     if (desc) { DEM_I_B(k_integrate_mixed, true) } else { DEM_I_B(k_integrate_mixed, false) }
   } else {
     if (desc) { DEM_I_B(k_integrate, true) } else { DEM_I_B(k_integrate, false) }
   }
 #undef DEM_I_B
-#undef DEM_I_W
+#undef DEM_I_F
 #undef DEM_I
 }
 

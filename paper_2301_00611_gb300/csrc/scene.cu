@@ -73,11 +73,16 @@ bool is_diag(const double *M) {
 // Quantities of the next step that follow from (H, L, Lprev, Hprev, dt, Href).
 void cell_derive(CellState &c) {
   if (!c.periodic) {
-    for (int q = 0; q < 9; ++q) { c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0; }
-    for (int q = 0; q < 3; ++q) { c.dHf[q] = 0; c.Wf[q] = 0; c.Ef[q] = 0; }
+    for (int q = 0; q < 9; ++q) {
+      c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0;
+      c.dHf[q] = 0; c.Wf[q] = 0; c.Ef[q] = 0;
+    }
+    c.sheared = 0;
     c.thr2 = c.verlet * c.verlet;
     return;
   }
+  c.sheared = !(is_diag(c.H) && is_diag(c.Hprev) && is_diag(c.Href) && is_diag(c.L) &&
+                is_diag(c.Lprev));
   m_mul(c.Lprev, c.Hprev, c.W);
   for (int q = 0; q < 9; ++q) c.dL[q] = c.L[q] - c.Lprev[q];
   double A[9];
@@ -90,10 +95,10 @@ void cell_derive(CellState &c) {
   for (int q = 0; q < 9; ++q) e2 += c.E[q] * c.E[q];
   double eff = c.verlet - std::sqrt(e2) * (c.rmax + c.verlet);
   c.thr2 = eff > 0 ? eff * eff : -1.0;
-  for (int q = 0; q < 3; ++q) {
-    c.dHf[q] = (float)(c.H[4 * q] - c.Href[4 * q]);
-    c.Wf[q] = (float)c.W[4 * q];
-    c.Ef[q] = (float)c.E[4 * q];
+  for (int q = 0; q < 9; ++q) {
+    c.dHf[q] = (float)(c.H[q] - c.Href[q]);
+    c.Wf[q] = (float)c.W[q];
+    c.Ef[q] = (float)c.E[q];
   }
 }
 
@@ -480,6 +485,7 @@ SceneConst scene_const(const dem_scene *s) {
       c.walls |= u.cs.wall_mask ? 1 : 0;
       c.periodic |= u.cs.periodic;
       c.hertz |= u.cs.law;
+      c.sheared |= u.cs.sheared;
     }
   c.ordered = s->degree_order;
   c.multi = s->nsub() > 1;
@@ -581,12 +587,30 @@ dem_status sub_grid(dem_scene *s, Sub &u, const double lo[3], const double hi[3]
   g.periodic = u.cs.periodic;
   g.reach = reach;
   if (g.periodic) {
+    const double *H = u.cs.H;
+    g.sheared = !is_diag(H);
+    // perpendicular width of the cell across each pair of faces: |det H| / |a_i x a_j|,
+    // a_k the cell vectors (columns of H); cells are slabs of fractional coordinates
+    double w[3];
+    const double V = std::fabs(m_det(H));
     for (int k = 0; k < 3; ++k) {
-      double L = u.cs.H[4 * k];
-      int n = (int)std::floor(L / hmin);
+      const int i = (k + 1) % 3, j = (k + 2) % 3;
+      const double a[3] = {H[i], H[3 + i], H[6 + i]}, b[3] = {H[j], H[3 + j], H[6 + j]};
+      const double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2],
+                   cz = a[0] * b[1] - a[1] * b[0];
+      w[k] = g.sheared ? V / std::sqrt(cx * cx + cy * cy + cz * cz) : H[4 * k];
+    }
+    if (!m_inv(H, g.Hinv)) return fail(s, DEM_ERR_INVALID_ARG, "singular periodic cell");
+    for (int q = 0; q < 9; ++q) {
+      g.H[q] = H[q];
+      g.Hf[q] = (float)H[q];
+    }
+    for (int k = 0; k < 3; ++k) {
+      double L = H[4 * k];
+      int n = (int)std::floor(w[k] / hmin);
       if (n < 3)
         return fail(s, DEM_ERR_GEOMETRY,
-                    "periodic cell edge shorter than 3 * (2 r_max + 2 verlet_dist): a sphere "
+                    "periodic cell width shorter than 3 * (2 r_max + 2 verlet_dist): a sphere "
                     "spans too large a part of the cell");
       g.n[k] = std::min(n, kMaxGridSide);
       g.L[k] = L;
@@ -608,7 +632,9 @@ dem_status sub_grid(dem_scene *s, Sub &u, const double lo[3], const double hi[3]
   }
   double ext = 0;
   for (int k = 0; k < 3; ++k) {
-    ext = std::max(ext, g.periodic ? g.L[k] : g.n[k] / g.scale[k]);
+    double e = g.periodic ? std::fabs(g.H[3 * k]) + std::fabs(g.H[3 * k + 1]) + std::fabs(g.H[3 * k + 2])
+                          : g.n[k] / g.scale[k];
+    ext = std::max(ext, e);
     g.Lf[k] = (float)g.L[k];
   }
   g.reachf = (float)reach;
@@ -873,9 +899,9 @@ dem_status dem_scene_create(const dem_scene_desc *desc, dem_scene **out) {
       return DEM_ERR_INVALID_ARG;
     }
   if (desc->periodic) {
-    if (!is_diag(desc->cell_h) || !(desc->cell_h[0] > 0) || !(desc->cell_h[4] > 0) ||
+    if (!(m_det(desc->cell_h) > 0) || !(desc->cell_h[0] > 0) || !(desc->cell_h[4] > 0) ||
         !(desc->cell_h[8] > 0)) {
-      g_create_error = "the periodic cell must be diagonal with positive edges";
+      g_create_error = "the periodic cell needs a positive determinant and positive diagonal";
       return DEM_ERR_INVALID_ARG;
     }
   } else if (desc->wall_mask) {
@@ -1164,7 +1190,6 @@ dem_status dem_set_triax(dem_scene *s, const double *goal, int stress_mask,
 dem_status dem_set_cell_velgrad(dem_scene *s, const double *L) {
   if (!s || !L) return DEM_ERR_INVALID_ARG;
   if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "velGrad needs a periodic scene");
-  if (!is_diag(L)) return fail(s, DEM_ERR_UNSUPPORTED, "only a diagonal velGrad is supported");
   for (int q = 0; q < 9; ++q)
     if (!std::isfinite(L[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite velGrad");
   std::memcpy(s->subs[0].velgrad_next, L, sizeof s->subs[0].velgrad_next);
@@ -1222,11 +1247,12 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
         if (record) CK(cudaEventRecord(ev[6 * i], s->st));
         if (s->mixed)
           launch_contact_mixed(s->step_d, *s->step_h, desc, rows, s->cs_d, s->ds_d, s->mats_d,
-                               sc.multi, sc.hertz, s->nsm, s->contact_block, s->contact_per_sm,
-                               s->st);
+                               sc.multi, sc.hertz | (sc.sheared << 1), s->nsm,
+                               s->contact_block, s->contact_per_sm, s->st);
         else
           launch_contact(s->step_d, *s->step_h, desc, rows, s->cs_d, s->ds_d, s->mats_d,
-                         sc.multi, sc.hertz, s->nsm, s->contact_block, s->contact_per_sm, s->st);
+                         sc.multi, sc.hertz | (sc.sheared << 1), s->nsm, s->contact_block,
+                         s->contact_per_sm, s->st);
         if (record) CK(cudaEventRecord(ev[6 * i + 1], s->st));
         if (tstep && tstep_due(i)) {   // GlobalStiffnessTimeStepper: after the contacts
           launch_timestepper(s->cur, t, s->cs_d, s->nsub(), s->ds_d, s->mats_d, sc.N, s->cap,
@@ -1252,7 +1278,8 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
       // replay a captured batch of B steps (one graph launch instead of 3B launches);
       // captures are kept while nothing that shapes the launches changes
       const GraphKey key{sc.N, rows, s->contact_block, s->contact_per_sm, s->integrate_block,
-                         sc.multi, sc.walls | (sc.hertz << 1), s->nsub(), s->mixed ? 1 : 0,
+                         sc.multi, sc.walls | (sc.hertz << 1) | (sc.sheared << 2), s->nsub(),
+                         s->mixed ? 1 : 0,
                          s->cs_d};
       if (!(key == s->graph_key)) {
         drop_graphs(s);
@@ -1448,12 +1475,11 @@ dem_status dem_set_cell(dem_scene *s, const double *H, const double *velgrad,
   if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "the scene is not periodic");
   for (const double *M : {H, velgrad, prev_velgrad, prev_H})
     if (M) {
-      if (!is_diag(M)) return fail(s, DEM_ERR_UNSUPPORTED, "cell matrices must be diagonal");
       for (int q = 0; q < 9; ++q)
         if (!std::isfinite(M[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite cell matrix");
     }
-  if (H && !(H[0] > 0 && H[4] > 0 && H[8] > 0))
-    return fail(s, DEM_ERR_INVALID_ARG, "cell edges must be positive");
+  if (H && !(H[0] > 0 && H[4] > 0 && H[8] > 0 && m_det(H) > 0))
+    return fail(s, DEM_ERR_INVALID_ARG, "cell needs a positive determinant and positive diagonal");
   dem_status r;
   if ((r = sync_host(s))) return r;
   if (H) {
@@ -2021,8 +2047,9 @@ dem_status dem_add_subscene(dem_scene *s, const dem_subscene_desc *d, int *sub) 
     if (!std::isfinite(d->gravity[k]) || !std::isfinite(d->box_lo[k]) || !std::isfinite(d->box_hi[k]))
       return fail(s, DEM_ERR_INVALID_ARG, "non-finite gravity or box");
   if (d->periodic) {
-    if (!is_diag(d->cell_h) || !(d->cell_h[0] > 0) || !(d->cell_h[4] > 0) || !(d->cell_h[8] > 0))
-      return fail(s, DEM_ERR_INVALID_ARG, "the periodic cell must be diagonal with positive edges");
+    if (!(m_det(d->cell_h) > 0) || !(d->cell_h[0] > 0) || !(d->cell_h[4] > 0) || !(d->cell_h[8] > 0))
+      return fail(s, DEM_ERR_INVALID_ARG,
+                  "the periodic cell needs a positive determinant and positive diagonal");
   } else if (d->wall_mask & 0x3F) {
     for (int k = 0; k < 3; ++k)
       if (!(d->box_hi[k] > d->box_lo[k])) return fail(s, DEM_ERR_INVALID_ARG, "box_hi must exceed box_lo");
@@ -2114,7 +2141,6 @@ dem_status dem_set_subscene_velgrad(dem_scene *s, int sub, const double *L) {
     return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
   Sub &u = s->subs[sub];
   if (!u.cs.periodic) return fail(s, DEM_ERR_STATE, "velGrad needs a periodic sub-scene");
-  if (!is_diag(L)) return fail(s, DEM_ERR_UNSUPPORTED, "only a diagonal velGrad is supported");
   for (int q = 0; q < 9; ++q)
     if (!std::isfinite(L[q])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite velGrad");
   std::memcpy(u.velgrad_next, L, sizeof u.velgrad_next);

@@ -73,11 +73,11 @@ def test_create_rejects_bad_descriptions_on_the_host(lib):
     d = dem.SceneDesc()
     lib.dem_scene_desc_init(ctypes.byref(d))
     d.periodic = 1
-    d.cell_h[1] = 0.1  # sheared cell: not supported in this version
+    d.cell_h[4] = -1.0  # an inverted cell (sheared cells are accepted, inverted ones not)
     h = ctypes.c_void_p()
     rc = lib.dem_scene_create(ctypes.byref(d), ctypes.byref(h))
     assert rc == 1 and not h.value
-    assert b"diagonal" in lib.dem_last_error(None)
+    assert b"positive determinant" in lib.dem_last_error(None)
     lib.dem_scene_desc_init(ctypes.byref(d))
     d.damping = 1.5
     assert lib.dem_scene_create(ctypes.byref(d), ctypes.byref(h)) == 1

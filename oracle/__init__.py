@@ -83,6 +83,7 @@ def _load():
         "orc_set_state": (_i, [_p, _p, _p, _p, _p]),
         "orc_get_cell": (None, [_p, _p, _p, _p, _p]),
         "orc_set_cell": (_i, [_p, _p, _p, _p, _p]),
+        "orc_flip_cell": (_i, [_p, _p, _p]),
         "orc_get_clock": (None, [_p, _p, _p, _p]),
         "orc_set_clock": (_i, [_p, _l, _d]),
         "orc_num_contacts": (_l, [_p]),
@@ -263,6 +264,17 @@ class OracleScene:
         rc = self._lib.orc_set_cell(self._h, *(_ptr(a) for a in keep))
         if rc != 0:
             raise ValueError("set_cell needs a periodic scene")
+
+    def flip_cell(self, flip=None):
+        """utils.flipCell: H' = H (I + flip), interactions keep their images; flip None:
+        the automatic reduction.  Returns the applied integer matrix."""
+        out = np.zeros((3, 3), dtype=np.int32)
+        K = None if flip is None else np.ascontiguousarray(flip, dtype=np.int32).reshape(3, 3)
+        rc = self._lib.orc_flip_cell(self._h, None if K is None else K.ctypes.data_as(ctypes.c_void_p),
+                                     out.ctypes.data_as(ctypes.c_void_p))
+        if rc != 0:
+            raise ValueError("flip_cell: aperiodic scene, det(I + flip) != 1, or a shift out of range")
+        return out
 
     def clock(self):
         it = ctypes.c_long()

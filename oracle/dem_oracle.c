@@ -1080,6 +1080,70 @@ int orc_set_cell(orc_scene *s, const double *H9, const double *velgrad9,
     return 0;
 }
 
+/* utils.flipCell (section 2.1.6, "Collision detection in periodic cell", fig. 6): the
+ * corners of the periodic cell repeated in space form a lattice, and any other cell
+ * spanning the same lattice describes the same periodic space.  The new cell is
+ * H' = H M with M = I + K an integer matrix of determinant 1; positions do not move,
+ * and each interaction keeps its image: x2 + H c = x2 + H' c' with c' = M^-1 c.
+ * The image-velocity matrix Hprev changes the same way (Lprev Hprev c is invariant).
+ * K given: used as is (rejected unless det(I + K) = 1 and the new diagonal is
+ * positive).  K NULL: the automatic reduction of reading R21, one pass over the
+ * column pairs (i, j) in the order (1,2) (0,2) (0,1) (1,0) (2,0) (2,1): with
+ * k = round(H_ij / H_ii), column j -= k * column i, skipped when k = 0 or when it
+ * would make H_jj non-positive.  The applied K is written to `applied` (nullable).
+ * Returns 0, or -1 (aperiodic scene, invalid K, or a shift out of range). */
+int orc_flip_cell(orc_scene *s, const int *K9, int *applied) {
+    if (!s || !s->periodic) return -1;
+    int M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (K9) {
+        for (int q = 0; q < 9; ++q) M[q] += K9[q];
+    } else {
+        double Hc[9];
+        memcpy(Hc, s->H, sizeof Hc);
+        static const int order[6][2] = {{1, 2}, {0, 2}, {0, 1}, {1, 0}, {2, 0}, {2, 1}};
+        for (int p = 0; p < 6; ++p) {
+            const int i = order[p][0], j = order[p][1];
+            const double k = floor(Hc[3 * i + j] / Hc[3 * i + i] + 0.5);
+            if (k == 0 || !(Hc[3 * j + j] - k * Hc[3 * j + i] > 0)) continue;
+            /* column j of H and of M lose k times column i */
+            for (int r = 0; r < 3; ++r) {
+                Hc[3 * r + j] -= k * Hc[3 * r + i];
+                M[3 * r + j] -= (int)k * M[3 * r + i];
+            }
+        }
+    }
+    /* integer inverse by the adjugate (det M = 1) */
+    const long det = (long)M[0] * (M[4] * M[8] - M[5] * M[7]) - (long)M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                     (long)M[2] * (M[3] * M[7] - M[4] * M[6]);
+    if (det != 1) return -1;
+    int Mi[9];
+    Mi[0] = M[4] * M[8] - M[5] * M[7]; Mi[1] = M[2] * M[7] - M[1] * M[8]; Mi[2] = M[1] * M[5] - M[2] * M[4];
+    Mi[3] = M[5] * M[6] - M[3] * M[8]; Mi[4] = M[0] * M[8] - M[2] * M[6]; Mi[5] = M[2] * M[3] - M[0] * M[5];
+    Mi[6] = M[3] * M[7] - M[4] * M[6]; Mi[7] = M[1] * M[6] - M[0] * M[7]; Mi[8] = M[0] * M[4] - M[1] * M[3];
+    double Md[9], Hn[9], Hpn[9];
+    for (int q = 0; q < 9; ++q) Md[q] = (double)M[q];
+    m_mul(s->H, Md, Hn);
+    m_mul(s->Hprev, Md, Hpn);
+    if (!(Hn[0] > 0 && Hn[4] > 0 && Hn[8] > 0)) return -1;
+    for (long k = 0; k < s->ncon; ++k) {
+        const int *c = s->con[k].c;
+        for (int r = 0; r < 3; ++r) {
+            const long v = (long)Mi[3 * r] * c[0] + (long)Mi[3 * r + 1] * c[1] + (long)Mi[3 * r + 2] * c[2];
+            if (v > 511 || v < -511) return -1;   /* the library's shift range */
+        }
+    }
+    for (long k = 0; k < s->ncon; ++k) {
+        int *c = s->con[k].c, o[3];
+        for (int r = 0; r < 3; ++r) o[r] = Mi[3 * r] * c[0] + Mi[3 * r + 1] * c[1] + Mi[3 * r + 2] * c[2];
+        c[0] = o[0]; c[1] = o[1]; c[2] = o[2];
+    }
+    memcpy(s->H, Hn, sizeof Hn);
+    memcpy(s->Hprev, Hpn, sizeof Hpn);
+    if (applied)
+        for (int q = 0; q < 9; ++q) applied[q] = M[q] - ((q % 4 == 0) ? 1 : 0);
+    return 0;
+}
+
 void orc_get_clock(const orc_scene *s, long *iter, double *time, double *dt) {
     if (iter) *iter = s->iter;
     if (time) *time = s->time;

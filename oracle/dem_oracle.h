@@ -57,6 +57,9 @@ void orc_get_cell(const orc_scene *s, double *H9, double *velgrad9, double *prev
                   double *prev_H9);
 int orc_set_cell(orc_scene *s, const double *H9, const double *velgrad9,
                  const double *prev_velgrad9, const double *prev_H9);
+/* utils.flipCell: H' = H (I + K), interactions keep their images (c' = (I + K)^-1 c).
+ * K9 NULL: automatic reduction (reading R21).  applied (nullable) receives K. */
+int orc_flip_cell(orc_scene *s, const int *K9, int *applied);
 void orc_get_clock(const orc_scene *s, long *iter, double *time, double *dt);
 int orc_set_clock(orc_scene *s, long iter, double time);
 

@@ -198,6 +198,26 @@ dem_status dem_get_cell(dem_scene *scene, double *H, double *velgrad, double *pr
 dem_status dem_set_cell(dem_scene *scene, const double *H, const double *velgrad,
                         const double *prev_velgrad, const double *prev_H);
 
+/* utils.flipCell (section 2.1.6 "Collision detection in periodic cell", fig. 6) on
+ * sub-scene `sub` (0 for a scene without sub-scenes).  The corners of the cell
+ * repeated in space form a lattice that another cell H' = H M spans as well (M an
+ * integer matrix with det M = 1); the flip replaces H by H M, keeps every body where
+ * it is and every interaction on the same image (its cell shift c becomes M^-1 c),
+ * and re-initialises the collider at the next step.  Flipping a sheared cell back
+ * toward a right parallelepiped keeps the grid's cells from thinning as the shear
+ * grows, so simple shear can go on without bound.
+ *   flip     HOST 9 ints, row-major K with M = I + K, or NULL: the automatic
+ *            reduction - one pass over the column pairs (i, j) in the order (1,2)
+ *            (0,2) (0,1) (1,0) (2,0) (2,1), each replacing column j of the cell by
+ *            column j - k column i with k = round(H_ij / H_ii) when k != 0 and H_jj
+ *            stays positive (for a cell sheared in its upper triangle this leaves
+ *            |H_ij| <= H_ii / 2)
+ *   applied  HOST 9 ints (nullable): receives the K that was applied (zero: none)
+ * Errors: INVALID_ARG (no such sub-scene, det(I + K) != 1, entries of K beyond
+ * +-1000, a flipped cell with a non-positive diagonal), STATE (aperiodic),
+ * GEOMETRY (some shift M^-1 c beyond +-511; nothing is changed), CUDA. */
+dem_status dem_flip_cell(dem_scene *scene, int sub, const int *flip, int *applied);
+
 /* O.iter and O.time. */
 dem_status dem_get_clock(dem_scene *scene, long long *iter, double *time);
 dem_status dem_set_clock(dem_scene *scene, long long iter, double time);

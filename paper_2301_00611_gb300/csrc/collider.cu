@@ -497,6 +497,39 @@ void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *
   if (nt.P > 0) k_merge<<<blocks(nt.P), kT, 0, st>>>(nt, ot, N_old, new_to_old, mixed);
 }
 
+namespace {
+// Cell flip (section 2.1.6, fig. 6): H' = H M keeps every image when each row's
+// shift becomes c' = M^-1 c.  Pass 0 records the largest |c'| component of the rows
+// of sub-scene `sub` (all rows without sub-scenes); pass 1 rewrites them.
+__global__ void k_flip_shift(Table t, const int *__restrict__ sid, int multi, int sub, int3 m0,
+                             int3 m1, int3 m2, int *maxabs, int apply) {
+  for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P;
+       k += (long long)gridDim.x * kT) {
+    if (multi && sid[t.pair[k].x] != sub) continue;
+    int c0, c1, c2;
+    unpack_shift(t.cpack[k], c0, c1, c2);
+    const int n0 = m0.x * c0 + m0.y * c1 + m0.z * c2;
+    const int n1 = m1.x * c0 + m1.y * c1 + m1.z * c2;
+    const int n2 = m2.x * c0 + m2.y * c1 + m2.z * c2;
+    if (apply) {
+      t.cpack[k] = pack_shift(n0, n1, n2);
+    } else {
+      const int m = max(abs(n0), max(abs(n1), abs(n2)));
+      if (m > kShiftMax) atomicMax(maxabs, m);
+    }
+  }
+}
+}  // namespace
+
+void launch_flip_shift(const Table &t, const int *sid, int multi, int sub, const int Minv[9],
+                       int *maxabs, int apply, cudaStream_t st) {
+  if (t.P <= 0) return;
+  const long long b = std::min<long long>(blocks(t.P), 4096);
+  k_flip_shift<<<(unsigned)b, kT, 0, st>>>(t, sid, multi, sub, make_int3(Minv[0], Minv[1], Minv[2]),
+                                          make_int3(Minv[3], Minv[4], Minv[5]),
+                                          make_int3(Minv[6], Minv[7], Minv[8]), maxabs, apply);
+}
+
 void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st) {
   if (ot.P > 0) k_lost<<<blocks(ot.P), kT, 0, st>>>(ot, err, mixed);
 }

@@ -2148,6 +2148,92 @@ dem_status dem_set_subscene_velgrad(dem_scene *s, int sub, const double *L) {
   return DEM_OK;
 }
 
+dem_status dem_flip_cell(dem_scene *s, int sub, const int *flip, int *applied) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  Sub &u = s->subs[sub];
+  CellState &c = u.cs;
+  if (!c.periodic) return fail(s, DEM_ERR_STATE, "a cell flip needs a periodic (sub-)scene");
+  // M = I + K: the caller's K, or column reductions of the current H
+  long long M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (flip) {
+    for (int q = 0; q < 9; ++q) {
+      if (flip[q] < -1000 || flip[q] > 1000) return fail(s, DEM_ERR_INVALID_ARG, "flip entries beyond +-1000");
+      M[q] += flip[q];
+    }
+  } else {
+    double h[9];
+    std::memcpy(h, c.H, sizeof h);
+    const int pairs[6][2] = {{1, 2}, {0, 2}, {0, 1}, {1, 0}, {2, 0}, {2, 1}};
+    for (const auto &pr : pairs) {
+      const int i = pr[0], j = pr[1];   // column j against column i, on row i
+      const double k = std::floor(h[3 * i + j] / h[3 * i + i] + 0.5);
+      if (k == 0.0 || !(h[3 * j + j] - k * h[3 * j + i] > 0.0)) continue;
+      for (int row = 0; row < 3; ++row) {
+        h[3 * row + j] -= k * h[3 * row + i];
+        M[3 * row + j] -= (long long)k * M[3 * row + i];
+      }
+    }
+  }
+  const long long det = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                        M[2] * (M[3] * M[7] - M[4] * M[6]);
+  if (det != 1) return fail(s, DEM_ERR_INVALID_ARG, "a cell flip needs det(I + flip) = 1");
+  // adjugate = inverse (det 1)
+  const long long Ai[9] = {M[4] * M[8] - M[5] * M[7], M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
+                           M[5] * M[6] - M[3] * M[8], M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
+                           M[3] * M[7] - M[4] * M[6], M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
+  double Md[9], Hn[9];
+  int Mi[9];
+  bool ident = true;
+  for (int q = 0; q < 9; ++q) {
+    Md[q] = (double)M[q];
+    if (Ai[q] < -(1 << 20) || Ai[q] > (1 << 20))
+      return fail(s, DEM_ERR_INVALID_ARG, "flip inverse entries too large");
+    Mi[q] = (int)Ai[q];
+    ident &= M[q] == ((q % 4 == 0) ? 1 : 0);
+  }
+  m_mul(c.H, Md, Hn);
+  if (!(Hn[0] > 0 && Hn[4] > 0 && Hn[8] > 0))
+    return fail(s, DEM_ERR_INVALID_ARG, "the flipped cell needs a positive diagonal");
+  if (!ident) {
+    // rows keep their images: c' = M^-1 c (checked for range before any is changed)
+    const Table &t = s->tab[s->tc];
+    if (t.P > 0 && t.row_start != nullptr && s->N > 0) {
+      const int multi = s->nsub() > 1;
+      int *maxabs = s->deg_ws;
+      CK(cudaMemsetAsync(maxabs, 0, sizeof(int), s->st));
+      launch_flip_shift(t, s->cur.sid, multi, sub, Mi, maxabs, 0, s->st);
+      int worst = 0;
+      CK(cudaMemcpyAsync(&s->rb_h->totals[0], maxabs, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+      if ((r = wait(s))) return r;
+      worst = s->rb_h->totals[0];
+      if (worst > kShiftMax)
+        return fail(s, DEM_ERR_GEOMETRY, "a cell flip would move an image shift out of range");
+      launch_flip_shift(t, s->cur.sid, multi, sub, Mi, maxabs, 1, s->st);
+      CK(cudaGetLastError());
+    }
+    double Hp[9], Hr[9], Hri[9];
+    m_mul(c.Hprev, Md, Hp);
+    m_mul(c.Href, Md, Hr);
+    double Mid[9];
+    for (int q = 0; q < 9; ++q) Mid[q] = (double)Mi[q];
+    m_mul(Mid, c.Hrefinv, Hri);
+    std::memcpy(c.H, Hn, sizeof Hn);
+    std::memcpy(c.Hprev, Hp, sizeof Hp);
+    std::memcpy(c.Href, Hr, sizeof Hr);
+    std::memcpy(c.Hrefinv, Hri, sizeof Hri);
+    cell_derive(c);
+    s->need_rebuild = true;   // the collider re-initialises on the new cell
+    s->cs_dirty = true;
+  }
+  if (applied)
+    for (int q = 0; q < 9; ++q) applied[q] = (int)(M[q] - ((q % 4 == 0) ? 1 : 0));
+  return DEM_OK;
+}
+
 dem_status dem_num_bodies(dem_scene *s, long long *n) {
   if (!s || !n) return DEM_ERR_INVALID_ARG;
   *n = s->N;

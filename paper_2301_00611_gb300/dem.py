@@ -146,6 +146,7 @@ _SIGS = {
     "dem_get_subscene": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "dem_get_subscene_stats": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_set_subscene_velgrad": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "dem_flip_cell": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "dem_num_bodies": (ctypes.c_int, [_P, _P]),
     "dem_get_micro": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "dem_get_body_stress": (ctypes.c_int, [_P, _P]),
@@ -428,6 +429,16 @@ class Scene:
     def set_subscene_velgrad(self, sub, L):
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def flip_cell(self, flip=None, sub=0):
+        """utils.flipCell (dem_flip_cell): H' = H (I + flip), bodies and interactions
+        unchanged; flip None: the automatic reduction.  Returns the applied matrix."""
+        out = np.zeros((3, 3), dtype=np.int32)
+        K = None if flip is None else np.ascontiguousarray(flip, dtype=np.int32).reshape(3, 3)
+        self._check(self._lib.dem_flip_cell(self._h, int(sub),
+                                            None if K is None else K.ctypes.data_as(_P),
+                                            out.ctypes.data_as(_P)))
+        return out
 
     def set_law(self, law, sub=0):
         """Contact law (dem_set_law): DEM_LAW_LINEAR or DEM_LAW_HERTZ_MINDLIN."""

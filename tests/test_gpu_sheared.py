@@ -172,3 +172,95 @@ def test_sheared_subscene_beside_a_walled_box(mods, precision):
     sg = g.subscene_state(sub)
     compare_states(orcs[0].state(), sg, X, tol=tol, co=co, masses=masses_of(a),
                    dt=orcs[0].clock()[2], eps=eps, coord=coord)
+
+
+def _sheared_history(oracle, gamma=0.7, steps=150, n=1500, seed=66):
+    """An oracle packing sheared to H_xy / H_yy = gamma while compacting (contacts with
+    shear history), its velocity gradient still on."""
+    w = workloads.periodic_cloud(n, seed, phi=0.34, inflate=1.06, vel_scale=0.02,
+                                 angvel_scale=10.0)
+    o = oracle.OracleScene.from_workload(w)
+    dt = o.clock()[2]
+    L = -5.0 * np.eye(3)
+    L[0, 1] = gamma / (steps * dt)
+    o.set_velgrad(L)
+    o.step(steps)
+    return o, w
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_flip_matches_the_oracle(mods, precision):
+    """Both sides flip the same sheared cell (the automatic reduction), then step:
+    the applied matrix, the new cell, the contacts with their new shifts and the
+    states agree at the parity bar of one step, and again after 25 more steps."""
+    oracle, pkg = mods
+    o, w = _sheared_history(oracle)
+    assert o.cell()["H"][0, 1] > 0.6 * o.cell()["H"][1, 1]
+    prec = pkg.DEM_MIXED if precision == "mixed" else pkg.DEM_FP64
+    g = pkg.Scene.from_workload(w, dt=o.clock()[2], precision=prec)
+    import_into_gpu(g, export_oracle(o))
+    Ko, Kg = o.flip_cell(), g.flip_cell()
+    assert np.array_equal(Ko, Kg) and Kg[0, 1] == -1
+    assert np.array_equal(o.cell()["H"], g.cell()["H"])
+    n, cg = _check_step(o, g, w, oracle, precision)
+    assert n > 300
+    assert np.any(cg["c"][:, 0] != 0)
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    o.step(24)
+    g.step(24)
+    before = o.state()
+    band = _band(before, w, o.cell()["H"], oracle, 1e-7 if precision == "fp64" else 1e-4)
+    o.step(1)
+    g.step(1)
+    set_coord_scale(float(np.max(np.abs(before["pos"]))))
+    compare_contacts(o.contacts(), g.contacts(), band, tol=tol,
+                     eps=2.0 ** -52 if precision == "fp64" else 2.0 ** -23,
+                     coord=None if precision == "fp64" else 2 * float(w.radius.max()) * 1.25)
+
+
+def test_flip_does_not_change_the_run(mods):
+    """Fig. 6 on the GPU: two copies of one state, one flipped with an explicit matrix
+    (the cell vector a_1 minus a_0), step 40 times; the bodies follow the same
+    trajectories and the contacts carry the same forces (shifts related by M^-1)."""
+    oracle, pkg = mods
+    o, w = _sheared_history(oracle)
+    ex = export_oracle(o)
+    a = pkg.Scene.from_workload(w, dt=o.clock()[2])
+    b = pkg.Scene.from_workload(w, dt=o.clock()[2])
+    import_into_gpu(a, ex)
+    import_into_gpu(b, ex)
+    a.step(1)
+    b.step(1)
+    K = np.zeros((3, 3), dtype=int)
+    K[0, 1] = -1
+    assert np.array_equal(a.flip_cell(K), K)
+    a.step(40)
+    b.step(40)
+    ca, cb = a.contacts(), b.contacts()
+    ka = {(i, j): t for t, (i, j) in enumerate(zip(ca["id1"], ca["id2"]))}
+    kb = {(i, j): t for t, (i, j) in enumerate(zip(cb["id1"], cb["id2"]))}
+    assert set(ka) == set(kb) and len(ka) > 300
+    ia = np.array([ka[k] for k in kb])
+    ib = np.array([kb[k] for k in kb])
+    Minv = np.rint(np.linalg.inv(np.eye(3) + K)).astype(int)
+    assert np.array_equal(ca["c"][ia], cb["c"][ib] @ Minv.T)
+    scale = float(np.abs(cb["fn"]).max())
+    assert np.abs(ca["fn"][ia] - cb["fn"][ib]).max() < 1e-8 * scale
+    assert np.abs(ca["fs"][ia] - cb["fs"][ib]).max() < 1e-8 * scale
+    sa, sb = a.state(), b.state()
+    assert np.abs(sa["pos"] - sb["pos"]).max() < 1e-12 * np.abs(sb["pos"]).max()
+    assert np.abs(sa["vel"] - sb["vel"]).max() < 1e-8 * np.abs(sb["vel"]).max()
+
+
+def test_flip_errors(mods):
+    oracle, pkg = mods
+    w = workloads.periodic_cloud(300, 67, phi=0.3)
+    g = pkg.Scene.from_workload(w)
+    with pytest.raises(pkg.DemError) as e:
+        g.flip_cell([[1, 0, 0], [0, 0, 0], [0, 0, 0]])   # det(I + K) = 2
+    assert e.value.code == 1
+    assert np.array_equal(g.flip_cell(), np.zeros((3, 3)))   # a right cell: nothing to do
+    b = workloads.box_cloud(200, 68, phi=0.2)
+    gb = pkg.Scene.from_workload(b)
+    with pytest.raises(pkg.DemError):
+        gb.flip_cell()

@@ -221,6 +221,11 @@ def tune_shape(Scene, w, args, precision):
     advanced to mid-compaction (a contact network like the timed window's).  Launch
     shapes change no result, so the timed trajectory is the same whichever is picked."""
     from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
+    fixed = getattr(args, "shape_" + precision, None)
+    if fixed:   # a given shape (to profile the variant a tuned run picked)
+        cb, cps, ib, deg = (int(v) for v in fixed.split(","))
+        return {"contact_block": cb, "contact_blocks_per_sm": cps, "integrate_block": ib,
+                "degree_order": deg}
     if args.no_autotune:
         return None
     prec = DEM_MIXED if precision == "mixed" else DEM_FP64
@@ -647,6 +652,10 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of dem_autotune's")
+    ap.add_argument("--shape-fp64", default=None,
+                    help="launch shape 'contact_block,blocks_per_sm,integrate_block,degree_order' "
+                         "of the FP64 run instead of the autotuner's")
+    ap.add_argument("--shape-mixed", default=None, help="the same for the mixed run")
     ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve"])
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched deposition sweep out of the headline line")

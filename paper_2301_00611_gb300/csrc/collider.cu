@@ -410,11 +410,29 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
   nt.oM[k] = make_double4_32a(0, 0, 0, 0);
 }
 
-__global__ void k_lost(Table ot, int *err, int mixed) {
+// A real row of the previous table that no candidate carried over: an error only
+// if the pair still overlaps at the positions of this collider run (a pair that
+// separated within the step is dropped by the contact law anyway; a body may move
+// farther than the sweep margin in the step that triggers the run).  ob: the body
+// buffer in the old slot order, still holding the current positions.
+__global__ void k_lost(Table ot, Bodies ob, const Grid *__restrict__ grids, int multi, int *err,
+                       int mixed) {
   long long r = (long long)blockIdx.x * kT + threadIdx.x;
   if (r >= ot.P) return;
   const bool real = mixed ? (ot.g32[r].w != 0.0f) : (ot.hfs[r].w != 0.0);
-  if (real && !ot.found[r]) atomicOr(err, kErrHistoryLost);
+  if (!real || ot.found[r]) return;
+  const int2 pr = ot.pair[r];
+  const double4_32a p1 = ob.pos[pr.x], p2 = ob.pos[pr.y];
+  const Grid &g = grid_of(grids, ob.sid, multi, pr.x);
+  double h[3] = {0, 0, 0};
+  if (g.periodic) {
+    int c0, c1, c2;
+    unpack_shift(ot.cpack[r], c0, c1, c2);
+    for (int k = 0; k < 3; ++k) h[k] = g.H[3 * k] * c0 + g.H[3 * k + 1] * c1 + g.H[3 * k + 2] * c2;
+  }
+  const double dx = (p2.x + h[0]) - p1.x, dy = (p2.y + h[1]) - p1.y, dz = (p2.z + h[2]) - p1.z;
+  const double R = p1.w + p2.w;
+  if (dx * dx + dy * dy + dz * dz < R * R) atomicOr(err, kErrHistoryLost);
 }
 
 inline unsigned blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
@@ -530,8 +548,9 @@ void launch_flip_shift(const Table &t, const int *sid, int multi, int sub, const
                                           make_int3(Minv[6], Minv[7], Minv[8]), maxabs, apply);
 }
 
-void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st) {
-  if (ot.P > 0) k_lost<<<blocks(ot.P), kT, 0, st>>>(ot, err, mixed);
+void launch_lost(const Table &ot, const Bodies &ob, const Grid *grids, int multi, int *err,
+                 int mixed, cudaStream_t st) {
+  if (ot.P > 0) k_lost<<<blocks(ot.P), kT, 0, st>>>(ot, ob, grids, multi, err, mixed);
 }
 
 }  // namespace dem

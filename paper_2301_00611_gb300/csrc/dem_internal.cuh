@@ -238,7 +238,8 @@ void launch_downsort(const Table &t, long long N, cudaStream_t st);
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
                   int mixed, cudaStream_t st);
-void launch_lost(const Table &ot, int *err, int mixed, cudaStream_t st);
+void launch_lost(const Table &ot, const Bodies &ob, const Grid *grids, int multi, int *err,
+                 int mixed, cudaStream_t st);
 // cell flip: rows of sub-scene `sub` (all rows unless multi) get c' = Minv c (apply = 1),
 // or the largest out-of-range |c'| is recorded in *maxabs (apply = 0)
 void launch_flip_shift(const Table &t, const int *sid, int multi, int sub, const int Minv[9],

@@ -780,7 +780,8 @@ dem_status rebuild_core(dem_scene *s) {
   if (ot.P == 0 || ot.row_start == nullptr) otv.P = 0;
   launch_merge(nt, otv, s->tab_nbody[s->tc], s->new_to_old, s->mixed, s->st);
   // a removed sub-scene's contacts vanish by design: no history check on that run
-  if (s->check_lost && !removal) launch_lost(otv, &s->ds_d->error, s->mixed, s->st);
+  if (s->check_lost && !removal)
+    launch_lost(otv, s->alt, s->grids_d, multi, &s->ds_d->error, s->mixed, s->st);
   (void)N_old;
   s->tab_nbody[1 - s->tc] = NL;
   s->tc = 1 - s->tc;

@@ -1,4 +1,4 @@
-"""Sheared periodic cells (general H and grad v, section 2.2) on the GPU against
+"""Sheared periodic cells (general H and grad v, section 2.1.6) on the GPU against
 the oracle: one-step contact and state parity from a pre-sheared cell with a full
 velocity gradient and unwrapped positions, FP64 and mixed precision, both contact
 laws; one step from a history the oracle built under simple shear; a simple-shear

@@ -1,6 +1,6 @@
 """Oracle pinned on sheared periodic cells (non-diagonal H and grad v).
 
-Section 2.2's periodic cell is a general parallelepiped H whose columns are the
+The periodic cell of section 2.1.6 is a general parallelepiped H whose columns are the
 cell vectors; a sheared cell is the case the diagonal-only shortcuts would get
 wrong.  Each pin fails under a plausible slip: an image shift that uses only the
 diagonal of H (the chain's closing contact is missed or lands at the wrong

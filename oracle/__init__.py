@@ -78,6 +78,8 @@ def _load():
         "orc_set_triax": (_i, [_p, _p, _i, _p, _d, _i]),
         "orc_set_timestepper": (_i, [_p, _d, _i, _d, _d]),
         "orc_set_law": (_i, [_p, _i]),
+        "orc_set_density_scaling": (_i, [_p, _i, _d]),
+        "orc_get_density_scaling": (None, [_p, _p]),
         "orc_num_bodies": (_l, [_p]),
         "orc_get_state": (None, [_p, _p, _p, _p, _p, _p, _p]),
         "orc_set_state": (_i, [_p, _p, _p, _p, _p]),
@@ -229,6 +231,18 @@ class OracleScene:
         if self._lib.orc_set_timestepper(self._h, float(safety), int(interval), float(default_dt),
                                          float(max_dt)) != 0:
             raise ValueError("bad time-stepper parameters")
+
+    def set_density_scaling(self, on=True, target_dt=1.0):
+        """NewtonIntegrator.densityScaling with the stepper's targetDt (reading R22 in
+        dem_oracle.c); needs set_timestepper first."""
+        if self._lib.orc_set_density_scaling(self._h, int(bool(on)), float(target_dt)) != 0:
+            raise ValueError("density scaling needs the time stepper and target_dt > 0")
+
+    def density_scaling(self):
+        """Per-body inertia factors f (1 where no scaling applies)."""
+        f = np.empty(self.n)
+        self._lib.orc_get_density_scaling(self._h, _ptr(f))
+        return f
 
     def step(self, n=1):
         rc = self._lib.orc_step(self._h, int(n))

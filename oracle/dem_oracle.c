@@ -64,6 +64,13 @@
  *      (0 when K_i = 0 and the goal is not met: the rate bound applies), a
  *      strain-controlled axis grad(v)_ii = goal_i; the new gradient is assigned
  *      like Cell.velGrad (effective from the next step) and held in between.
+ *   R22 density scaling (NewtonIntegrator.densityScaling, GlobalStiffnessTimeStepper
+ *      targetDt; the text gives the purpose, equalising every body's critical step
+ *      at targetDt, not the formula): on a stepper update a free body with contacts,
+ *      critical step t_b of eq. 2.12 with its true mass and inertia, gets the factor
+ *      f = (targetDt / (safety t_b))^2 on both; the step becomes targetDt.  Only the
+ *      inertia is scaled: forces, weight m g included, are unchanged, so a static
+ *      state does not depend on targetDt.  A body without contacts keeps its factor.
  */
 #include "dem_oracle.h"
 
@@ -113,6 +120,10 @@ struct orc_scene {
     /* GlobalStiffnessTimeStepper (R17) */
     int tstep, tstep_interval;
     double tstep_safety, tstep_default, tstep_max;
+    /* density scaling (reading R22): per-body inertia factor f, target step */
+    int dscale_on;
+    double target_dt;
+    double *dscale;
     double goal[3], max_rate[3], grow_damping;
 };
 
@@ -445,6 +456,7 @@ orc_scene *orc_create(int periodic, const double *H9, const double *box_lo, cons
 static void free_bodies(orc_scene *s) {
     free(s->pos); free(s->vel); free(s->angvel); free(s->ori); free(s->radius); free(s->mass);
     free(s->inertia); free(s->force); free(s->torque); free(s->mat); free(s->fixed);
+    free(s->dscale);
 }
 
 void orc_destroy(orc_scene *s) {
@@ -479,7 +491,7 @@ static int grow(orc_scene *s, long need) {
     GROW(pos, double, 3); GROW(vel, double, 3); GROW(angvel, double, 3); GROW(ori, double, 4);
     GROW(radius, double, 1); GROW(mass, double, 1); GROW(inertia, double, 1);
     GROW(force, double, 3); GROW(torque, double, 3); GROW(mat, int, 1);
-    GROW(fixed, unsigned char, 1);
+    GROW(fixed, unsigned char, 1); GROW(dscale, double, 1);
 #undef GROW
     s->cap = nc;
     return 0;
@@ -515,6 +527,7 @@ long orc_add_spheres(orc_scene *s, long n, const double *pos, const double *radi
         /* utils.sphere: mass from density and volume, inertia of a solid sphere (R12) */
         s->mass[i] = s->mats[m].density * (4.0 / 3.0) * pi * r * r * r;
         s->inertia[i] = 0.4 * s->mass[i] * r * r;
+        s->dscale[i] = 1.0;
     }
     long first = s->n;
     s->n += n;
@@ -838,24 +851,51 @@ static void stiffness_dt(orc_scene *s) {
     double best = INFINITY;
     for (long b = 0; b < n; ++b) {
         if (s->fixed[b]) continue;
+        double tb = INFINITY;   /* this body's critical step (eq. 2.12, unscaled masses) */
         for (int i = 0; i < 3; ++i) {
             if (Kt[3 * b + i] > 0) {
                 double t = sqrt(2.0) * sqrt(s->mass[b] / Kt[3 * b + i]);
-                if (t < best) best = t;
+                if (t < tb) tb = t;
             }
             if (Kr[3 * b + i] > 0) {
                 double t = sqrt(2.0) * sqrt(s->inertia[b] / Kr[3 * b + i]);
-                if (t < best) best = t;
+                if (t < tb) tb = t;
             }
+        }
+        if (tb < best) best = tb;
+        /* density scaling (R22): inertia scaled by f so that safety * sqrt(f) * tb is the
+         * target step; a body without contacts keeps its factor */
+        if (s->dscale_on && !isinf(tb)) {
+            double ratio = s->target_dt / (s->tstep_safety * tb);
+            s->dscale[b] = ratio * ratio;
         }
     }
     free(Kt);
     free(Kr);
+    if (s->dscale_on) { s->dt = s->target_dt; return; }
     double dt;
     if (isinf(best)) dt = s->tstep_default > 0 ? s->tstep_default : s->tstep_safety * orc_pwave_dt(s);
     else dt = s->tstep_safety * best;
     if (s->tstep_max > 0 && dt > s->tstep_max) dt = s->tstep_max;
     s->dt = dt;
+}
+
+/* NewtonIntegrator.densityScaling with GlobalStiffnessTimeStepper.targetDt (reading
+ * R22): needs the time stepper; on each stepper update every free body with contacts
+ * gets the inertia factor f = (target_dt / (safety * t_b))^2, t_b its critical step
+ * of eq. 2.12, and the step becomes target_dt.  Turning it off restores f = 1. */
+int orc_set_density_scaling(orc_scene *s, int on, double target_dt) {
+    if (!s) return -1;
+    if (on && (!s->tstep || !(target_dt > 0) || !isfinite(target_dt))) return -1;
+    s->dscale_on = on ? 1 : 0;
+    s->target_dt = on ? target_dt : 0.0;
+    if (!on)
+        for (long i = 0; i < s->n; ++i) s->dscale[i] = 1.0;
+    return 0;
+}
+
+void orc_get_density_scaling(const orc_scene *s, double *f) {
+    if (f) memcpy(f, s->dscale, sizeof(double) * s->n);
 }
 
 int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,
@@ -964,12 +1004,14 @@ static int step_once(orc_scene *s) {
     for (int q = 0; q < 9; ++q) dL[q] = s->L[q] - s->Lprev[q];
     for (long i = 0; i < s->n; ++i) {
         double *x = s->pos + 3 * i, *v = s->vel + 3 * i, *w = s->angvel + 3 * i;
-        double m = s->mass[i], I = s->inertia[i];
+        /* inertial mass and moment: scaled by the density-scaling factor (R22, 1 when
+         * off); the weight stays the true m g */
+        double m = s->mass[i] * s->dscale[i], I = s->inertia[i] * s->dscale[i];
         double vold[3] = {v[0], v[1], v[2]}, xold[3] = {x[0], x[1], x[2]};
         if (!s->fixed[i]) {
             double F[3], T[3], vref[3];
             for (int q = 0; q < 3; ++q) {
-                F[q] = s->force[3 * i + q] + m * s->g[q];
+                F[q] = s->force[3 * i + q] + s->mass[i] * s->g[q];
                 T[q] = s->torque[3 * i + q];
             }
             /* eq. 2.9 velocity: fluctuation part in a periodic cell (R7) */
@@ -1004,7 +1046,7 @@ static int step_once(orc_scene *s) {
             for (int q = 0; q < 3; ++q) {
                 s->nonvisc_damp += -(Fd[q] - F[q]) * v[q] * dtN;
                 s->nonvisc_damp += -(Td[q] - T[q]) * w[q] * dtN;
-                s->grav_work += -m * s->g[q] * v[q] * dtN;
+                s->grav_work += -s->mass[i] * s->g[q] * v[q] * dtN;
             }
         }
         for (int q = 0; q < 3; ++q) x[q] = xold[q] + dtN * v[q];

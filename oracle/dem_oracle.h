@@ -43,6 +43,9 @@ int orc_step(orc_scene *s, long nsteps);
 int orc_set_law(orc_scene *s, int law);
 /* GlobalStiffnessTimeStepper: safety coefficient, update interval (steps), defaultDt
  * (< 0: safety x p-wave step), maxDt (<= 0: none). */
+/* density scaling (R22); f receives the per-body inertia factors (n doubles). */
+int orc_set_density_scaling(orc_scene *s, int on, double target_dt);
+void orc_get_density_scaling(const orc_scene *s, double *f);
 int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,
                         double max_dt);
 int orc_set_triax(orc_scene *s, const double *goal3, int stress_mask, const double *max_rate3,

@@ -396,10 +396,28 @@ dem_status dem_set_law(dem_scene *scene, int sub, int law);
  * translational K_ii = sum (kn - ks) n_i^2 + ks (eq. 2.14) and rotational
  * K_ii = sum ks d^2 (1 - n_i^2) over the sphere's contacts (d = r - pen/2, the arm of
  * the shear spring).  With no contact dt = default_dt, or (default_dt <= 0) safety x
- * the p-wave step of the sub-scene's spheres; max_dt > 0 caps it.  Density scaling
- * is not provided.  Errors: INVALID_ARG (safety outside (0, 1], interval < 1). */
+ * the p-wave step of the sub-scene's spheres; max_dt > 0 caps it.  Density scaling:
+ * dem_set_density_scaling.  Errors: INVALID_ARG (safety outside (0, 1], interval < 1). */
 dem_status dem_set_timestepper(dem_scene *scene, int sub, double safety, int interval,
                                double default_dt, double max_dt);
+
+/* Density scaling (NewtonIntegrator.densityScaling with GlobalStiffnessTimeStepper
+ * targetDt, class references; the stability discussion of section 2.1.5) for
+ * sub-scene `sub`, which must run the time stepper.  On each stepper update every
+ * free sphere with contacts gets an inertia factor f = (target_dt / (safety t_b))^2,
+ * t_b its own critical step of eq. 2.12 (true mass and inertia, the six degrees of
+ * freedom of dem_set_timestepper), and the step becomes target_dt: every sphere then
+ * sits at the same stability margin, which speeds up quasi-static runs at the cost of
+ * realistic dynamics.  Mass and moment of inertia are both multiplied by f in the
+ * equations of motion; forces are not changed (the weight stays the true m g), so a
+ * static equilibrium does not depend on target_dt.  A sphere without contacts keeps
+ * its last factor (1 at first).  enable = 0 switches it off and restores f = 1.
+ * Errors: INVALID_ARG (no such sub-scene, target_dt not finite and > 0), STATE (no
+ * time stepper on the sub-scene). */
+dem_status dem_set_density_scaling(dem_scene *scene, int sub, int enable, double target_dt);
+
+/* The inertia factor f of every sphere, by id (HOST n doubles, n = dem_num_bodies). */
+dem_status dem_get_density_scaling(dem_scene *scene, double *f);
 
 /* Micromechanics of the contacts of the last completed step (utils reference of
  * the text), over the whole scene (sub = -1, volume of sub-scene 0) or one

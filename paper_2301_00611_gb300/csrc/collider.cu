@@ -175,6 +175,7 @@ __global__ void k_reorder(Bodies src, Bodies dst, long long N, long long cap,
   }
   dst.ori[p] = src.ori[o];
   dst.mprop[p] = src.mprop[o];
+  dst.rdsc[p] = src.rdsc[o];
   dst.xref[p] = make_double4_32a(x.x, x.y, x.z, 0.0);
   const int q = src.sid[o];
   // ids close up over the ranges of removed sub-scenes

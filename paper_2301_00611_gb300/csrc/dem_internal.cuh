@@ -72,6 +72,7 @@ struct Bodies {
   int *sid;         // sub-scene of each body (read only when SceneConst::multi)
   uint8_t *flags;   // bit0 fixed; bit (1+w) in contact with wall w
   double4_32a *whist;   // [6 * cap] or null
+  double *rdsc;     // 1 / density-scaling factor of each body (1: unscaled)
   // mixed precision mirrors (null in FP64 mode), written by the integrator:
   float4 *p32;      // (x - xref, r) in FP32
   float4 *vw32;     // [2 * cap]: (vx, vy, vz, wx), (wy, wz, 0, 0)
@@ -138,6 +139,10 @@ struct CellState {
   int tstep_interval;
   int law;          // contact law: 0 Cundall-Strack (linear), 1 Hertz-Mindlin
   double tstep_safety, tstep_default, tstep_max;   // default: dt when no contact exists
+  // density scaling: on a stepper update the inertia of each body with contacts is
+  // scaled so that its critical step (times the safety) is target_dt, the step used
+  int dscale, pad_ds;
+  double target_dt;
 };
 
 constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
@@ -283,6 +288,8 @@ void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, cons
                           const SceneConst &sc, long long cap, double4_32a *F, double4_32a *T,
                           int mixed, cudaStream_t st);
 // dst[i] = src[slot_of_id[i]] for i < n (records of consecutive ids, in id order)
+// density scaling switched off: factor 1 for the bodies of sub-scene `sub` (all unless multi)
+void launch_dscale_reset(const Bodies &b, long long N, int multi, int sub, cudaStream_t st);
 void launch_gather_ids(const int *slot_of_id, long long n, const double4_32a *src,
                        double4_32a *dst, cudaStream_t st);
 void launch_gather_ids_f(const int *slot_of_id, long long n, const float4 *src, float4 *dst,

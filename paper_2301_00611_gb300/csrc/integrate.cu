@@ -253,14 +253,20 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
         for (int q = 0; q < 3; ++q) vref[q] -= (float)c.Lprev[4 * q] * xf[q];
       }
     }
+    float im = mp.z, iI = mp.w;   // inverse inertial mass and moment
+    if (c.dscale) {   // density scaling: inertia times f (the weight keeps the true mass)
+      const float rf = (float)b.rdsc[s];
+      im *= rf;
+      iI *= rf;
+    }
     for (int q = 0; q < 3; ++q) {
       const float Ft = F[q] + mp.x * (float)c.gravity[q];
-      const float acc = Ft * mp.z;
+      const float acc = Ft * im;
       const float Fd = Ft * damp_factor_f(Ft * (vref[q] + 0.5f * dtf * acc), lam);
-      dv[q] = dtf * Fd * mp.z;
-      const float aacc = T[q] * mp.w;
+      dv[q] = dtf * Fd * im;
+      const float aacc = T[q] * iI;
       const float Td = T[q] * damp_factor_f(T[q] * (ww[q] + 0.5f * dtf * aacc), lam);
-      dw[q] = dtf * Td * mp.w;
+      dw[q] = dtf * Td * iI;
     }
     if (c.periodic) {   // homoDeform = 2
       if ((kFeat & 2) && c.sheared) {
@@ -439,12 +445,18 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
       }
     }
     const double hdt = 0.5 * dt, one_m = 1.0 - lam, one_p = 1.0 + lam;
+    double im = mp.z, iI = mp.w;   // inverse inertial mass and moment
+    if (c.dscale) {   // density scaling: inertia times f (the weight keeps the true mass)
+      const double rf = b.rdsc[s];
+      im *= rf;
+      iI *= rf;
+    }
     for (int q = 0; q < 3; ++q) {   // v+ = v- + (dt Fd) / m, as the oracle orders it
       const double Ft = F[q] + mp.x * c.gravity[q];
-      const double Fd = Ft * damp_factor_ab(Ft, vref[q] + hdt * (Ft * mp.z), one_m, one_p);
-      vn_[q] = vv[q] + (dt * Fd) * mp.z;
-      const double Td = T[q] * damp_factor_ab(T[q], ww[q] + hdt * (T[q] * mp.w), one_m, one_p);
-      wn_[q] = ww[q] + (dt * Td) * mp.w;
+      const double Fd = Ft * damp_factor_ab(Ft, vref[q] + hdt * (Ft * im), one_m, one_p);
+      vn_[q] = vv[q] + (dt * Fd) * im;
+      const double Td = T[q] * damp_factor_ab(T[q], ww[q] + hdt * (T[q] * iI), one_m, one_p);
+      wn_[q] = ww[q] + (dt * Td) * iI;
     }
     if (c.periodic) {   // homoDeform = 2
       const double *dL = c.dL, *L = c.L;
@@ -869,13 +881,19 @@ __global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
       }
     }
     if (!(fl & 1)) {
-      const double4_32a mp = b.mprop[s];   // m, I
+      const double4_32a mp = b.mprop[s];   // m, I (true values)
       double best = INFINITY;
       for (int i = 0; i < 3; ++i) {
         if (Kt[i] > 0) best = fmin(best, sqrt(2.0) * sqrt(mp.x / Kt[i]));
         if (Kr[i] > 0) best = fmin(best, sqrt(2.0) * sqrt(mp.y / Kr[i]));
       }
       key = (unsigned long long)__double_as_longlong(best);
+      // density scaling on an update step of this sub-scene: f = (target / (safety t_b))^2,
+      // kept as 1/f; a body without contacts keeps its factor
+      if (c.dscale && best < INFINITY && (c.iter % c.tstep_interval) == 0) {
+        const double q_ = (c.tstep_safety * best) / c.target_dt;
+        b.rdsc[s] = q_ * q_;
+      }
     }
   }
   // one atomic per warp when its bodies share a sub-scene (the usual case)
@@ -905,11 +923,23 @@ __global__ void k_dt_apply(CellState *cs, int nsub, const DevStatus *ds, unsigne
   double dt = key == 0x7ff0000000000000ull ? c->tstep_default
                                            : c->tstep_safety * __longlong_as_double((long long)key);
   if (c->tstep_max > 0 && dt > c->tstep_max) dt = c->tstep_max;
+  if (c->dscale) dt = c->target_dt;   // density scaling: every body is scaled to this step
   c->dt_law = c->dt;   // the walls' law of this step still uses the step's old dt
   c->dt = dt;
   if (c->periodic) derive_next(c);
 }
 }  // namespace
+
+namespace {
+__global__ void k_dscale_reset(Bodies b, long long N, int multi, int sub) {
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl < N && (!multi || b.sid[sl] == sub)) b.rdsc[sl] = 1.0;
+}
+}  // namespace
+
+void launch_dscale_reset(const Bodies &b, long long N, int multi, int sub, cudaStream_t st) {
+  if (N > 0) k_dscale_reset<<<(unsigned)((N + kT - 1) / kT), kT, 0, st>>>(b, N, multi, sub);
+}
 
 void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const CellState *cs,
                       DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st) {

@@ -316,7 +316,7 @@ void drop_graphs(dem_scene *s) {
 void free_bodies(dem_scene *s, Bodies &b) {
   dfree(s, b.pos); dfree(s, b.vel); dfree(s, b.angvel); dfree(s, b.ori); dfree(s, b.xref);
   dfree(s, b.mprop); dfree(s, b.id); dfree(s, b.sid); dfree(s, b.mat); dfree(s, b.flags);
-  dfree(s, b.whist);
+  dfree(s, b.whist); dfree(s, b.rdsc);
   dfree(s, b.p32); dfree(s, b.vw32); dfree(s, b.xref32); dfree(s, b.mprop32); dfree(s, b.ori32);
 }
 
@@ -326,7 +326,8 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
       (r = dalloc(s, &b.angvel, cap)) || (r = dalloc(s, &b.ori, cap)) ||
       (r = dalloc(s, &b.xref, cap)) || (r = dalloc(s, &b.mprop, cap)) ||
       (r = dalloc(s, &b.id, cap)) || (r = dalloc(s, &b.sid, cap)) ||
-      (r = dalloc(s, &b.mat, cap)) || (r = dalloc(s, &b.flags, cap)))
+      (r = dalloc(s, &b.mat, cap)) || (r = dalloc(s, &b.flags, cap)) ||
+      (r = dalloc(s, &b.rdsc, cap)))
     return r;
   // wall histories exist for every body (a sub-scene with walls may join later)
   if ((r = dalloc(s, &b.whist, 6 * cap))) return r;
@@ -436,6 +437,7 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
     CK(cudaMemcpyAsync(nb.sid, s->cur.sid, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.mat, s->cur.mat, sizeof(int) * N, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(nb.flags, s->cur.flags, N, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(nb.rdsc, s->cur.rdsc, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
     if (s->has_walls)
       for (int w = 0; w < 6; ++w)
         CK(cudaMemcpyAsync(nb.whist + w * nc, s->cur.whist + w * s->cap, d4,
@@ -1112,6 +1114,8 @@ dem_status add_spheres_sub(dem_scene *s, int q, long long n, const double *pos,
   CK(cudaMemcpyAsync(s->cur.sid + o, SU.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.mat + o, MT.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->cur.flags + o, FL.data(), n, cudaMemcpyHostToDevice, s->st));
+  const std::vector<double> ones(n, 1.0);   // no density scaling yet
+  CK(cudaMemcpyAsync(s->cur.rdsc + o, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(s->slot_of_id + o, SL.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->st));
   for (int w = 0; w < 6; ++w) CK(cudaMemsetAsync(s->cur.whist + w * s->cap + o, 0, d4, s->st));
   if (s->mixed) {   // FP32 mirrors of the new bodies (the collider run refreshes p32, vw32)
@@ -1834,7 +1838,7 @@ Bodies body_view(const Bodies &b, long long o) {
   Bodies v = b;
   auto sh = [o](auto *&p, long long k = 1) { if (p) p += k * o; };
   sh(v.pos); sh(v.vel); sh(v.angvel); sh(v.ori); sh(v.xref); sh(v.mprop);
-  sh(v.id); sh(v.sid); sh(v.mat); sh(v.flags); sh(v.whist);
+  sh(v.id); sh(v.sid); sh(v.mat); sh(v.flags); sh(v.whist); sh(v.rdsc);
   sh(v.p32); sh(v.vw32, 2); sh(v.xref32); sh(v.mprop32); sh(v.ori32);
   return v;
 }
@@ -2377,6 +2381,42 @@ dem_status dem_set_timestepper(dem_scene *s, int sub, double safety, int interva
   u.tstep_default_n = -1;
   if (default_dt > 0) u.cs.tstep_default = default_dt;
   s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_set_density_scaling(dem_scene *s, int sub, int enable, double target_dt) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (sub < 0 || sub >= s->nsub() || !s->subs[sub].used)
+    return fail(s, DEM_ERR_INVALID_ARG, "no such sub-scene");
+  if (enable && !(std::isfinite(target_dt) && target_dt > 0))
+    return fail(s, DEM_ERR_INVALID_ARG, "density scaling needs a finite target_dt > 0");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  Sub &u = s->subs[sub];
+  if (enable && !u.cs.tstep)
+    return fail(s, DEM_ERR_STATE, "density scaling needs the time stepper (dem_set_timestepper)");
+  if (!enable && u.cs.dscale) {
+    launch_dscale_reset(s->cur, s->N, s->nsub() > 1, sub, s->st);
+    CK(cudaGetLastError());
+  }
+  u.cs.dscale = enable ? 1 : 0;
+  u.cs.target_dt = enable ? target_dt : 0.0;
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_get_density_scaling(dem_scene *s, double *f) {
+  if (!s || !f) return DEM_ERR_INVALID_ARG;
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  const long long N = s->N;
+  if (N == 0) return DEM_OK;
+  std::vector<int> sid;
+  if ((r = fetch_sid(s, sid))) return r;
+  std::vector<double> h(N);
+  CK(cudaMemcpyAsync(h.data(), s->cur.rdsc, sizeof(double) * N, cudaMemcpyDeviceToHost, s->st));
+  if ((r = wait(s))) return r;
+  for (long long i = 0; i < N; ++i) f[i] = 1.0 / h[sid[i]];
   return DEM_OK;
 }
 

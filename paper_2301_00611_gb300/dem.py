@@ -147,6 +147,8 @@ _SIGS = {
     "dem_get_subscene_stats": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_set_subscene_velgrad": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_flip_cell": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "dem_set_density_scaling": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+    "dem_get_density_scaling": (ctypes.c_int, [_P, _P]),
     "dem_num_bodies": (ctypes.c_int, [_P, _P]),
     "dem_get_micro": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "dem_get_body_stress": (ctypes.c_int, [_P, _P]),
@@ -429,6 +431,18 @@ class Scene:
     def set_subscene_velgrad(self, sub, L):
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def set_density_scaling(self, enable=True, target_dt=1.0, sub=0):
+        """Density scaling to the step target_dt (dem_set_density_scaling); needs
+        set_timestepper on the same sub-scene."""
+        self._check(self._lib.dem_set_density_scaling(self._h, int(sub), int(bool(enable)),
+                                                      float(target_dt)))
+
+    def density_scaling(self):
+        """Inertia factor f of every sphere, by id."""
+        f = np.empty(self.n)
+        self._check(self._lib.dem_get_density_scaling(self._h, _ptr(f)))
+        return f
 
     def flip_cell(self, flip=None, sub=0):
         """utils.flipCell (dem_flip_cell): H' = H (I + flip), bodies and interactions

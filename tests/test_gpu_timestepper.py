@@ -66,3 +66,59 @@ def test_per_subscene_steppers(mods):
         g.step(1)
         assert abs(g.subscene(0)["dt"] / oa.clock()[2] - 1) < 1e-12
         assert g.subscene(sb)["dt"] == ob.clock()[2]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_density_scaling_matches_oracle(mods, precision):
+    """Density scaling (reading R22) on a walled packing under gravity: the step is the
+    target, the per-body inertia factors match the oracle's, and so do the states after
+    one step and after 20 more."""
+    oracle, pkg = mods
+    from tests.parity_util import compare_states, masses_of, set_coord_scale, set_radii
+    w = _clouds()[1]
+    o = oracle.OracleScene.from_workload(w)
+    prec = pkg.DEM_MIXED if precision == "mixed" else pkg.DEM_FP64
+    g = pkg.Scene.from_workload(w, dt=o.clock()[2], precision=prec)
+    target = 30 * o.clock()[2]
+    for s in (o, g):
+        s.set_timestepper(safety=0.7, interval=1)
+        s.set_density_scaling(True, target)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    set_radii(w.radius)
+    X = float(np.max(np.abs(w.pos)))
+    set_coord_scale(X)
+    o.step(1)
+    g.step(1)
+    assert o.clock()[2] == target and g.dt() == target
+    fo, fg = o.density_scaling(), g.density_scaling()
+    scaled = fo != 1.0
+    assert scaled.sum() > 500 and np.all(fo[scaled] > 1)
+    assert np.array_equal(fg == 1.0, ~scaled)
+    assert np.abs(fg / fo - 1).max() < (1e-12 if precision == "fp64" else 1e-5)
+    compare_states(o.state(), g.state(), X, tol=tol, co=o.contacts(), masses=masses_of(w),
+                   dt=target, gravity=9.81,
+                   eps=2.0 ** -52 if precision == "fp64" else 2.0 ** -23,
+                   coord=None if precision == "fp64" else 2 * float(w.radius.max()) * 1.25)
+    o.step(20)
+    g.step(20)
+    po, pg = o.state()["pos"], g.state()["pos"]
+    assert np.abs(pg - po).max() < (1e-9 if precision == "fp64" else 1e-5) * X
+
+
+def test_density_scaling_switch_and_errors(mods):
+    oracle, pkg = mods
+    w = _clouds()[1]
+    g = pkg.Scene.from_workload(w)
+    with pytest.raises(pkg.DemError) as e:
+        g.set_density_scaling(True, 1e-4)          # no time stepper yet
+    assert e.value.code == 9
+    g.set_timestepper(safety=0.7, interval=1)
+    with pytest.raises(pkg.DemError):
+        g.set_density_scaling(True, -1.0)
+    g.set_density_scaling(True, 1e-4)
+    g.step(3)
+    assert g.dt() == 1e-4 and np.any(g.density_scaling() != 1.0)
+    g.set_density_scaling(False)
+    assert np.all(g.density_scaling() == 1.0)
+    g.step(1)
+    assert g.dt() != 1e-4

@@ -79,6 +79,8 @@ def _load():
         "orc_set_timestepper": (_i, [_p, _d, _i, _d, _d]),
         "orc_set_law": (_i, [_p, _i]),
         "orc_set_density_scaling": (_i, [_p, _i, _d]),
+        "orc_set_peri3d": (_i, [_p, _p, _i, _l, _d, _d, _d, _d, _d, _p, _p, _p]),
+        "orc_get_peri3d": (_i, [_p, _p, _p, _p]),
         "orc_get_density_scaling": (None, [_p, _p]),
         "orc_num_bodies": (_l, [_p]),
         "orc_get_state": (None, [_p, _p, _p, _p, _p, _p, _p]),
@@ -231,6 +233,33 @@ class OracleScene:
         if self._lib.orc_set_timestepper(self._h, float(safety), int(interval), float(default_dt),
                                          float(max_dt)) != 0:
             raise ValueError("bad time-stepper parameters")
+
+    def set_peri3d(self, goal, stress_mask, n_steps, mod=0.1, max_strain_rate=1e3,
+                   young_est=1e20, poisson_est=0.25, max_strain=1e6, paths=None, trsf0=None):
+        """Peri3dController (reading R23 in dem_oracle.c).  goal: 6 values in the order
+        xx, yy, zz, yz, zx, xy; paths: None or 6 sequences of (t, v) couples (empty:
+        the default linear path); trsf0: Cell.trsf at the start (None: identity)."""
+        npath = np.zeros(6, dtype=np.int32)
+        path = np.zeros((6, 16, 2))
+        if paths is not None:
+            for i, pth in enumerate(paths):
+                pth = np.asarray(pth, dtype=np.float64).reshape(-1, 2)
+                npath[i] = len(pth)
+                path[i, :len(pth)] = pth
+        g = _f64(goal, (6,))
+        rc = self._lib.orc_set_peri3d(self._h, _ptr(g), int(stress_mask), int(n_steps), float(mod),
+                                      float(max_strain_rate), float(young_est), float(poisson_est),
+                                      float(max_strain), npath.ctypes.data_as(ctypes.c_void_p),
+                                      _ptr(path), _ptr(_f64(trsf0, (3, 3))))
+        if rc != 0:
+            raise ValueError("bad Peri3dController parameters (or an aperiodic scene)")
+
+    def peri3d(self):
+        st, sn, rt = np.empty(6), np.empty(6), np.empty(6)
+        rc = self._lib.orc_get_peri3d(self._h, _ptr(st), _ptr(sn), _ptr(rt))
+        if rc < 0:
+            raise ValueError("no Peri3dController")
+        return {"stress": st, "strain": sn, "rate": rt, "done": bool(rc)}
 
     def set_density_scaling(self, on=True, target_dt=1.0):
         """NewtonIntegrator.densityScaling with the stepper's targetDt (reading R22 in

@@ -125,6 +125,13 @@ struct orc_scene {
     double target_dt;
     double *dscale;
     double goal[3], max_rate[3], grow_damping;
+    /* Peri3dController (reading R23) */
+    int p3d, p3d_mask, p3d_first, p3d_done;
+    long p3d_nsteps, p3d_k;
+    double p3d_goal[6], p3d_mod, p3d_max_rate, p3d_young, p3d_poisson, p3d_max_strain;
+    int p3d_npath[6];
+    double p3d_path[6][16][2];
+    double p3d_rate[6], p3d_err[6], p3d_H0[9], p3d_T0[9], p3d_stress[6], p3d_strain[6];
 };
 
 /* ---------------------------------------------------------------- vectors */
@@ -802,6 +809,224 @@ static void triax_update(orc_scene *s) {
     s->L_pending = 1;
 }
 
+/* ------------------------------------------------------------ Peri3dController */
+/* Voigt order of the six components: xx, yy, zz, yz, zx, xy (the attribute order of
+ * goal, stress and strain; stressMask bit i = component i). */
+static const int VO[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {2, 0}, {0, 1}};
+
+/* Prescribed value of component i at progress p (xxPath ... "time functions"):
+ * couples (t_j, v_j), the last one standing for (nSteps, goal), the others scaled
+ * by it; piecewise linear from (0, 0); the goal beyond the last couple. */
+static double p3d_path_value(const orc_scene *s, int i, double p) {
+    const int n = s->p3d_npath[i];
+    const double tl = s->p3d_path[i][n - 1][0], vl = s->p3d_path[i][n - 1][1];
+    double t0 = 0, v0 = 0;
+    for (int j = 0; j < n; ++j) {
+        const double t1 = s->p3d_path[i][j][0] / tl, v1 = s->p3d_path[i][j][1] / vl;
+        if (p <= t1) {
+            const double a = t1 > t0 ? (p - t0) / (t1 - t0) : 1.0;
+            return s->p3d_goal[i] * (v0 + a * (v1 - v0));
+        }
+        t0 = t1; v0 = v1;
+    }
+    return s->p3d_goal[i];
+}
+
+/* Polar decomposition T = U P (U a rotation, P symmetric) by the iteration
+ * X <- (X + X^-T) / 2 from X = T, which converges to U for det T > 0. */
+static void polar(const double *T, double *U, double *P) {
+    double X[9], Xi[9];
+    memcpy(X, T, sizeof X);
+    for (int it = 0; it < 60; ++it) {
+        if (m_inv(X, Xi)) break;
+        double Y[9], d = 0;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) Y[3 * r + c] = 0.5 * (X[3 * r + c] + Xi[3 * c + r]);
+        for (int q = 0; q < 9; ++q) d += fabs(Y[q] - X[q]);
+        memcpy(X, Y, sizeof X);
+        if (d < 1e-15) break;
+    }
+    memcpy(U, X, sizeof X);
+    double Ut[9], Pm[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Ut[3 * r + c] = U[3 * c + r];
+    m_mul(Ut, T, Pm);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) P[3 * r + c] = 0.5 * (Pm[3 * r + c] + Pm[3 * c + r]);
+}
+
+/* One controller update at the end of a step (reading R23): stress and strain now,
+ * the next strain rates, and the velocity gradient that realises them over the next
+ * step (assigned like Cell.velGrad). */
+static void p3d_update(orc_scene *s) {
+    const double dt = s->dt;
+    /* stress of this step's contacts (Love-Weber, compression negative), symmetrised */
+    double V = fabs(m_det(s->Hprev)), S[9] = {0};
+    for (long k = 0; k < s->ncon; ++k) {
+        const orc_contact *ct = &s->con[k];
+        if (ct->id1 < 0) continue;
+        double l = (s->radius[ct->id1] + s->radius[ct->id2]) - ct->pen;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                S[3 * a + b] += (ct->fn * ct->n[a] + ct->fs[a]) * (-l * ct->n[b]);
+    }
+    /* Cell.trsf: T = H H0^-1 T0 (T0 the transformation at the start) = U P; the strain
+     * P - I rotated back to global axes, U (P - I) U^T */
+    double H0i[9], T1[9], T[9], U[9], P[9], Pm[9], Ut[9], G1[9], G[9];
+    m_inv(s->p3d_H0, H0i);
+    m_mul(s->H, H0i, T1);
+    m_mul(T1, s->p3d_T0, T);
+    polar(T, U, P);
+    for (int q = 0; q < 9; ++q) Pm[q] = P[q] - (q % 4 == 0 ? 1.0 : 0.0);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Ut[3 * r + c] = U[3 * c + r];
+    m_mul(U, Pm, G1);
+    m_mul(G1, Ut, G);
+    double sig[6], eps[6];
+    for (int i = 0; i < 6; ++i) {
+        const int a = VO[i][0], b = VO[i][1];
+        sig[i] = 0.5 * (S[3 * a + b] + S[3 * b + a]) / V;
+        eps[i] = a == b ? G[3 * a + a] : G[3 * a + b] + G[3 * b + a];   /* engineering shear */
+        s->p3d_stress[i] = sig[i];
+        s->p3d_strain[i] = eps[i];
+    }
+    if (s->p3d_done) return;
+    const long k = ++s->p3d_k;
+    double emax = 0;
+    for (int i = 0; i < 6; ++i) if (fabs(eps[i]) > emax) emax = fabs(eps[i]);
+    if (k >= s->p3d_nsteps || emax >= s->p3d_max_strain) { s->p3d_done = 1; return; }
+    const double p = (double)k / s->p3d_nsteps, pn = (double)(k + 1) / s->p3d_nsteps;
+    double rate[6], err[6], rmax = 0;
+    for (int i = 0; i < 6; ++i) if (fabs(s->p3d_rate[i]) > rmax) rmax = fabs(s->p3d_rate[i]);
+    for (int i = 0; i < 6; ++i) {
+        rate[i] = s->p3d_rate[i];
+        err[i] = 0;
+        if (!(s->p3d_mask & (1 << i))) {          /* strain: the rate that reaches the path */
+            rate[i] = (p3d_path_value(s, i, pn) - eps[i]) / dt;
+        } else {
+            err[i] = sig[i] - p3d_path_value(s, i, p);
+        }
+    }
+    if (s->p3d_first) {
+        /* first update: stress components from an isotropic elastic estimate, the
+         * strain components as prescribed: D_SS de_S = dsig_S - D_SE de_E */
+        const double E = s->p3d_young, nu = s->p3d_poisson;
+        const double lam = E * nu / ((1 + nu) * (1 - 2 * nu)), G = E / (2 * (1 + nu));
+        double D[6][6] = {{0}};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) D[i][j] = lam;
+            D[i][i] = lam + 2 * G;
+            D[3 + i][3 + i] = G;
+        }
+        int idx[6], m = 0;
+        for (int i = 0; i < 6; ++i) if (s->p3d_mask & (1 << i)) idx[m++] = i;
+        double A[6][7];
+        for (int r = 0; r < m; ++r) {
+            const int i = idx[r];
+            double rhs = p3d_path_value(s, i, pn) - sig[i];
+            for (int j = 0; j < 6; ++j)
+                if (!(s->p3d_mask & (1 << j))) rhs -= D[i][j] * rate[j] * dt;
+            for (int c = 0; c < m; ++c) A[r][c] = D[i][idx[c]];
+            A[r][m] = rhs;
+        }
+        for (int c = 0; c < m; ++c) {          /* Gaussian elimination, partial pivoting */
+            int piv = c;
+            for (int r = c + 1; r < m; ++r) if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+            for (int q = 0; q <= m; ++q) { double t = A[c][q]; A[c][q] = A[piv][q]; A[piv][q] = t; }
+            for (int r = 0; r < m; ++r) {
+                if (r == c) continue;
+                const double f = A[r][c] / A[c][c];
+                for (int q = c; q <= m; ++q) A[r][q] -= f * A[c][q];
+            }
+        }
+        for (int r = 0; r < m; ++r) rate[idx[r]] = A[r][m] / A[r][r] / dt;
+        s->p3d_first = 0;
+    } else {
+        /* later updates: the stress error extrapolated to the next step decides the
+         * sign of a change of mod times the largest current rate */
+        for (int i = 0; i < 6; ++i) {
+            if (!(s->p3d_mask & (1 << i))) continue;
+            const double pred = 2 * err[i] - s->p3d_err[i];
+            if (pred > 0) rate[i] -= rmax * s->p3d_mod;
+            else if (pred < 0) rate[i] += rmax * s->p3d_mod;
+        }
+    }
+    for (int i = 0; i < 6; ++i) {
+        if (rate[i] > s->p3d_max_rate) rate[i] = s->p3d_max_rate;
+        if (rate[i] < -s->p3d_max_rate) rate[i] = -s->p3d_max_rate;
+        s->p3d_rate[i] = rate[i];
+        s->p3d_err[i] = err[i];
+    }
+    /* P+ = P + U^T (dt e_dot) U, T+ = U P+, grad(v) = (T+ T^-1 - I) / dt */
+    double Ed[9] = {0}, A1[9], A2[9], Pn[9], Tn[9], Ti[9], L[9];
+    for (int i = 0; i < 6; ++i) {
+        const int a = VO[i][0], b = VO[i][1];
+        if (a == b) Ed[3 * a + a] = dt * rate[i];
+        else { Ed[3 * a + b] = 0.5 * dt * rate[i]; Ed[3 * b + a] = 0.5 * dt * rate[i]; }
+    }
+    m_mul(Ut, Ed, A1);
+    m_mul(A1, U, A2);
+    for (int q = 0; q < 9; ++q) Pn[q] = P[q] + A2[q];
+    m_mul(U, Pn, Tn);
+    m_inv(T, Ti);
+    m_mul(Tn, Ti, L);
+    for (int q = 0; q < 9; ++q) L[q] = (L[q] - (q % 4 == 0 ? 1.0 : 0.0)) / dt;
+    memcpy(s->Lnext, L, sizeof L);
+    s->L_pending = 1;
+}
+
+/* Peri3dController (class reference; reading R23).  goal, stress_mask (bit i: component
+ * i of xx, yy, zz, yz, zx, xy is a stress), n_steps, mod, max_strain_rate,
+ * young/poisson estimations, max_strain; paths: npath[i] couples (t, v) per component
+ * (npath[i] = 0: the default linear path), at most 16; trsf0 (nullable: identity) the
+ * cell transformation Cell.trsf already accumulated when the controller starts. */
+int orc_set_peri3d(orc_scene *s, const double *goal, int stress_mask, long n_steps, double mod,
+                   double max_strain_rate, double young_est, double poisson_est,
+                   double max_strain, const int *npath, const double *path, const double *trsf0) {
+    if (!s || !s->periodic || n_steps < 1 || !(max_strain_rate > 0) || !(young_est > 0) ||
+        !(poisson_est > -1 && poisson_est < 0.5) || !(max_strain > 0) || !(mod >= 0))
+        return -1;
+    for (int i = 0; i < 6; ++i) {
+        if (!isfinite(goal[i])) return -1;
+        s->p3d_goal[i] = goal[i];
+        const int n = npath ? npath[i] : 0;
+        if (n < 0 || n > 16) return -1;
+        if (n == 0) {
+            s->p3d_npath[i] = 1;
+            s->p3d_path[i][0][0] = 1; s->p3d_path[i][0][1] = 1;
+        } else {
+            s->p3d_npath[i] = n;
+            for (int j = 0; j < n; ++j) {
+                s->p3d_path[i][j][0] = path[(16 * i + j) * 2];
+                s->p3d_path[i][j][1] = path[(16 * i + j) * 2 + 1];
+            }
+            if (!(s->p3d_path[i][n - 1][0] > 0) || s->p3d_path[i][n - 1][1] == 0) return -1;
+            for (int j = 1; j < n; ++j) if (!(s->p3d_path[i][j][0] > s->p3d_path[i][j - 1][0])) return -1;
+            if (!(s->p3d_path[i][0][0] > 0)) return -1;
+        }
+    }
+    s->p3d = 1; s->triax = 0;
+    s->p3d_mask = stress_mask & 63;
+    s->p3d_nsteps = n_steps;
+    s->p3d_mod = mod; s->p3d_max_rate = max_strain_rate;
+    s->p3d_young = young_est; s->p3d_poisson = poisson_est; s->p3d_max_strain = max_strain;
+    s->p3d_k = 0; s->p3d_first = 1; s->p3d_done = 0;
+    memcpy(s->p3d_H0, s->H, sizeof s->H);
+    for (int q = 0; q < 9; ++q) s->p3d_T0[q] = trsf0 ? trsf0[q] : (q % 4 == 0 ? 1.0 : 0.0);
+    if (trsf0 && !(m_det(s->p3d_T0) > 0)) return -1;
+    for (int i = 0; i < 6; ++i) { s->p3d_rate[i] = 0; s->p3d_err[i] = 0; s->p3d_stress[i] = 0; s->p3d_strain[i] = 0; }
+    return 0;
+}
+
+/* stress[6], strain[6], rate[6] (nullable); returns 1 when done, 0 running, -1 off */
+int orc_get_peri3d(const orc_scene *s, double *stress, double *strain, double *rate) {
+    if (!s || !s->p3d) return -1;
+    if (stress) memcpy(stress, s->p3d_stress, sizeof s->p3d_stress);
+    if (strain) memcpy(strain, s->p3d_strain, sizeof s->p3d_strain);
+    if (rate) memcpy(rate, s->p3d_rate, sizeof s->p3d_rate);
+    return s->p3d_done;
+}
+
 int orc_set_triax(orc_scene *s, const double *goal, int stress_mask, const double *max_rate,
                   double grow_damping, int glob_update) {
     if (!s || !s->periodic || glob_update < 1 || !(grow_damping >= 0) || !(grow_damping < 1))
@@ -815,6 +1040,7 @@ int orc_set_triax(orc_scene *s, const double *goal, int stress_mask, const doubl
     s->grow_damping = grow_damping;
     s->glob_update = glob_update;
     s->triax = 1;
+    s->p3d = 0;
     return 0;
 }
 
@@ -1070,6 +1296,7 @@ static int step_once(orc_scene *s) {
     s->time += dtN;
     s->iter += 1;
     if (s->triax && s->periodic && s->iter % s->glob_update == 0) triax_update(s);
+    if (s->p3d && s->periodic) p3d_update(s);
     return 0;
 }
 

@@ -46,6 +46,11 @@ int orc_set_law(orc_scene *s, int law);
 /* density scaling (R22); f receives the per-body inertia factors (n doubles). */
 int orc_set_density_scaling(orc_scene *s, int on, double target_dt);
 void orc_get_density_scaling(const orc_scene *s, double *f);
+/* Peri3dController (reading R23); path: [6][16][2] couples, npath[6] (nullable). */
+int orc_set_peri3d(orc_scene *s, const double *goal, int stress_mask, long n_steps, double mod,
+                   double max_strain_rate, double young_est, double poisson_est,
+                   double max_strain, const int *npath, const double *path, const double *trsf0);
+int orc_get_peri3d(const orc_scene *s, double *stress, double *strain, double *rate);
 int orc_set_timestepper(orc_scene *s, double safety, int interval, double default_dt,
                         double max_dt);
 int orc_set_triax(orc_scene *s, const double *goal3, int stress_mask, const double *max_rate3,

@@ -174,6 +174,43 @@ dem_status dem_set_cell_velgrad(dem_scene *scene, const double velgrad[9]);
 dem_status dem_set_triax(dem_scene *scene, const double goal[3], int stress_mask,
                          const double max_rate[3], double grow_damping, int glob_update);
 
+/* Peri3dController (class reference; the periodic-cell controllers named in section
+ * 2.1.6) on a periodic scene without sub-scenes: the six components of the cell's
+ * engineering stress and strain, in the order xx, yy, zz, yz, zx, xy (shear strains
+ * are twice the tensor entries), each prescribed as a stress (stress_mask bit i set,
+ * Pa, compression negative) or as a strain, along a time function of the progress
+ * k / n_steps.  At the end of every step k the controller reads the Love-Weber stress
+ * of that step's contacts (symmetrised, in the cell they were computed in) and the
+ * strain U (P - I) U^T of Cell.trsf = H H0^-1 trsf0 = U P (polar decomposition; H0
+ * the cell now), sets each strain component's rate to reach its path value at k + 1
+ * and changes each stress component's rate by -+ mod x (largest current rate) when
+ * the stress error extrapolated one step (2 e_k - e_(k-1)) is positive / negative
+ * (the first update instead solves an isotropic elastic estimate with young_est,
+ * poisson_est); rates are clamped to +-max_strain_rate and realised exactly by
+ * grad v = (T+ T^-1 - I) / dt with T+ = U (P + U^T dt E U), assigned like
+ * Cell.velGrad (from the next step).  It stops updating after n_steps or when a strain
+ * component reaches max_strain; the last gradient stays in effect.  Readings: the
+ * text gives the predictor and the rotation handling but not the first-step system,
+ * the strain measure or the end; those are this library's.
+ *   goal      HOST 6 doubles
+ *   npath     HOST 6 ints (nullable: every path linear from 0 to the goal); npath[i]
+ *             = 0 keeps the linear path of component i, else 1..16 couples
+ *   path      HOST 6 x 16 x 2 doubles (t, v): times increasing from a positive first
+ *             one; the last couple stands for (n_steps, goal) and scales the others
+ *             (xxPath ... xyPath)
+ *   trsf0     HOST 9 doubles (nullable: identity), Cell.trsf when the controller starts
+ * Replaces the stress servo of dem_set_triax (and that call replaces this one).
+ * Errors: STATE (aperiodic), UNSUPPORTED (sub-scenes), INVALID_ARG. */
+dem_status dem_set_peri3d(dem_scene *scene, const double goal[6], int stress_mask,
+                          long long n_steps, double mod, double max_strain_rate, double young_est,
+                          double poisson_est, double max_strain, const int *npath,
+                          const double *path, const double *trsf0);
+
+/* The controller's last stress, strain and strain-rate vectors (HOST 6 doubles each,
+ * nullable) and whether it has finished (done, nullable).  Errors: STATE (none set). */
+dem_status dem_get_peri3d(dem_scene *scene, double *stress, double *strain, double *rate,
+                          int *done);
+
 /* Advance nsteps time steps (O.run(nsteps, wait=True)).  Blocks until done.
  * Errors: STATE (no bodies' dt), NONFINITE (a body state became NaN/Inf),
  * GEOMETRY, CAPACITY, OOM, TIMEOUT, CUDA.  On NONFINITE the scene stops at the

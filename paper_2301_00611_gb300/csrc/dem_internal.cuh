@@ -145,6 +145,21 @@ struct CellState {
   double target_dt;
 };
 
+// Peri3dController of a scene without sub-scenes (device resident; the controller
+// update runs in the cell advance of sub-scene 0).  Components in the order xx, yy,
+// zz, yz, zx, xy; strains engineering (shear = 2 x the tensor entry).
+struct P3d {
+  int on, mask, first, done;
+  long long nsteps, k;
+  double goal[6], mod, max_rate, young, poisson, max_strain;
+  int npath[6], pad;
+  double path[6][16][2];        // (t, v) couples; the last stands for (nsteps, goal)
+  double H0inv[9], T0[9];       // cell at the start (inverse) and Cell.trsf then
+  double rate[6], err[6], stress[6], strain[6];
+  double Lnext[9];              // gradient of the next step, picked up by the cell advance
+  int has_next, pad2;
+};
+
 constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
 constexpr int kDegreeBuckets = 64;  // incident-row counts >= 63 share the last bucket
 
@@ -274,6 +289,10 @@ void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const Cel
                       DevStatus *ds, const Mat *mats, int mixed, int block, cudaStream_t st);
 // one thread per sub-scene (cs[0 .. nsub)); servo partials apply to sub-scene 0
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
+                         cudaStream_t st, P3d *p3d = nullptr, const double *p3d_partials = nullptr);
+// Peri3dController stress sums of this step's real rows: kServoBlocks x 9 partials of
+// sum F_a (-l n_b)
+void launch_p3d_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
                          cudaStream_t st);
 // GlobalStiffnessTimeStepper: per-sub-scene minimum critical step (keys: nsub entries
 // preset to +inf bits, reset by the launch) applied to the due sub-scenes' dt

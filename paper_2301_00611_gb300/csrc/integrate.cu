@@ -571,8 +571,179 @@ __device__ void derive_next(CellState *__restrict__ cs) {
   derive_next_local(cs, H, L, cs->dt);
 }
 
+// ---- Peri3dController (class reference): one thread, FP64, after the cell update
+__device__ inline bool m_inv_dev(const double *M, double *O) {
+  const double d = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                   M[2] * (M[3] * M[7] - M[4] * M[6]);
+  if (d == 0.0 || !isfinite(d)) return false;
+  double T[9];
+  T[0] = (M[4] * M[8] - M[5] * M[7]) / d; T[1] = (M[2] * M[7] - M[1] * M[8]) / d;
+  T[2] = (M[1] * M[5] - M[2] * M[4]) / d; T[3] = (M[5] * M[6] - M[3] * M[8]) / d;
+  T[4] = (M[0] * M[8] - M[2] * M[6]) / d; T[5] = (M[2] * M[3] - M[0] * M[5]) / d;
+  T[6] = (M[3] * M[7] - M[4] * M[6]) / d; T[7] = (M[1] * M[6] - M[0] * M[7]) / d;
+  T[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+  for (int q = 0; q < 9; ++q) O[q] = T[q];
+  return true;
+}
+
+__device__ inline void m_tr(const double *A, double *O) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) O[3 * r + c] = A[3 * c + r];
+}
+
+// value of component i on its time function at progress p: piecewise linear from
+// (0, 0) through the couples scaled by the last one, the goal beyond it
+__device__ double p3d_value(const P3d &P, int i, double p) {
+  const int n = P.npath[i];
+  const double tl = P.path[i][n - 1][0], vl = P.path[i][n - 1][1];
+  double t0 = 0, v0 = 0;
+  for (int j = 0; j < n; ++j) {
+    const double t1 = P.path[i][j][0] / tl, v1 = P.path[i][j][1] / vl;
+    if (p <= t1) {
+      const double a = t1 > t0 ? (p - t0) / (t1 - t0) : 1.0;
+      return P.goal[i] * (v0 + a * (v1 - v0));
+    }
+    t0 = t1;
+    v0 = v1;
+  }
+  return P.goal[i];
+}
+
+// Controller update at the end of a step: stress of the step's contacts (cell Hp),
+// strain of the transformation T = H H0^-1 T0 = U P (polar decomposition) in global
+// axes, the next rates and the velocity gradient (T+ T^-1 - I) / dt with
+// T+ = U (P + U^T dt E(rate) U).  Returns false when the controller did not update.
+__device__ bool p3d_update(P3d &P, const double *part, const double (&Hp)[9],
+                           const double (&H)[9], double dt, double (&L)[9]) {
+  const int VO[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {2, 0}, {0, 1}};
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < kServoBlocks; ++b)
+    for (int q = 0; q < 9; ++q) S[q] += part[9 * b + q];
+  const double V = fabs(Hp[0] * (Hp[4] * Hp[8] - Hp[5] * Hp[7]) - Hp[1] * (Hp[3] * Hp[8] - Hp[5] * Hp[6]) +
+                        Hp[2] * (Hp[3] * Hp[7] - Hp[4] * Hp[6]));
+  double T1[9], T[9], U[9], X[9], Xi[9], Ut[9], Pm[9], Pc[9];
+  m_mul_rn(H, P.H0inv, T1);
+  m_mul_rn(T1, P.T0, T);
+  for (int q = 0; q < 9; ++q) X[q] = T[q];
+  for (int it = 0; it < 60; ++it) {   // X <- (X + X^-T) / 2 converges to U
+    if (!m_inv_dev(X, Xi)) break;
+    double d = 0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const double y = 0.5 * (X[3 * r + c] + Xi[3 * c + r]);
+        d += fabs(y - X[3 * r + c]);
+        U[3 * r + c] = y;
+      }
+    for (int q = 0; q < 9; ++q) X[q] = U[q];
+    if (d < 1e-15) break;
+  }
+  for (int q = 0; q < 9; ++q) U[q] = X[q];
+  m_tr(U, Ut);
+  m_mul_rn(Ut, T, Pm);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Pc[3 * r + c] = 0.5 * (Pm[3 * r + c] + Pm[3 * c + r]);
+  double G1[9], G[9], E1[9];
+  for (int q = 0; q < 9; ++q) E1[q] = Pc[q] - ((q % 4 == 0) ? 1.0 : 0.0);
+  m_mul_rn(U, E1, G1);
+  m_mul_rn(G1, Ut, G);
+  double sig[6], eps[6], emax = 0;
+  for (int i = 0; i < 6; ++i) {
+    const int a = VO[i][0], b = VO[i][1];
+    sig[i] = 0.5 * (S[3 * a + b] + S[3 * b + a]) / V;
+    eps[i] = a == b ? G[3 * a + a] : G[3 * a + b] + G[3 * b + a];
+    P.stress[i] = sig[i];
+    P.strain[i] = eps[i];
+    emax = fmax(emax, fabs(eps[i]));
+  }
+  if (P.done) return false;
+  const long long k = ++P.k;
+  if (k >= P.nsteps || emax >= P.max_strain) {
+    P.done = 1;
+    return false;
+  }
+  const double p = (double)k / (double)P.nsteps, pn = (double)(k + 1) / (double)P.nsteps;
+  double rate[6], err[6], rmax = 0;
+  for (int i = 0; i < 6; ++i) rmax = fmax(rmax, fabs(P.rate[i]));
+  for (int i = 0; i < 6; ++i) {
+    rate[i] = P.rate[i];
+    err[i] = 0;
+    if (!(P.mask & (1 << i))) rate[i] = (p3d_value(P, i, pn) - eps[i]) / dt;
+    else err[i] = sig[i] - p3d_value(P, i, p);
+  }
+  if (P.first) {   // isotropic elastic estimate: D_SS de_S = dsig_S - D_SE de_E
+    const double E = P.young, nu = P.poisson;
+    const double lam = E * nu / ((1 + nu) * (1 - 2 * nu)), Gm = E / (2 * (1 + nu));
+    double D[6][6];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) D[i][j] = 0;
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) D[i][j] = lam;
+      D[i][i] = lam + 2 * Gm;
+      D[3 + i][3 + i] = Gm;
+    }
+    int idx[6], m = 0;
+    for (int i = 0; i < 6; ++i)
+      if (P.mask & (1 << i)) idx[m++] = i;
+    double A[6][7];
+    for (int r = 0; r < m; ++r) {
+      const int i = idx[r];
+      double rhs = p3d_value(P, i, pn) - sig[i];
+      for (int j = 0; j < 6; ++j)
+        if (!(P.mask & (1 << j))) rhs -= D[i][j] * rate[j] * dt;
+      for (int c = 0; c < m; ++c) A[r][c] = D[i][idx[c]];
+      A[r][m] = rhs;
+    }
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+      for (int q = 0; q <= m; ++q) {
+        const double tq = A[c][q];
+        A[c][q] = A[piv][q];
+        A[piv][q] = tq;
+      }
+      for (int r = 0; r < m; ++r) {
+        if (r == c) continue;
+        const double f = A[r][c] / A[c][c];
+        for (int q = c; q <= m; ++q) A[r][q] -= f * A[c][q];
+      }
+    }
+    for (int r = 0; r < m; ++r) rate[idx[r]] = A[r][m] / A[r][r] / dt;
+    P.first = 0;
+  } else {   // stress error extrapolated one step decides the sign of mod x max |rate|
+    for (int i = 0; i < 6; ++i) {
+      if (!(P.mask & (1 << i))) continue;
+      const double pred = 2 * err[i] - P.err[i];
+      if (pred > 0) rate[i] -= rmax * P.mod;
+      else if (pred < 0) rate[i] += rmax * P.mod;
+    }
+  }
+  double Ed[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 6; ++i) {
+    rate[i] = fmin(fmax(rate[i], -P.max_rate), P.max_rate);
+    P.rate[i] = rate[i];
+    P.err[i] = err[i];
+    const int a = VO[i][0], b = VO[i][1];
+    if (a == b) {
+      Ed[3 * a + a] = dt * rate[i];
+    } else {
+      Ed[3 * a + b] = 0.5 * dt * rate[i];
+      Ed[3 * b + a] = 0.5 * dt * rate[i];
+    }
+  }
+  double A1[9], A2[9], Pn[9], Tn[9], Ti[9];
+  m_mul_rn(Ut, Ed, A1);
+  m_mul_rn(A1, U, A2);
+  for (int q = 0; q < 9; ++q) Pn[q] = Pc[q] + A2[q];
+  m_mul_rn(U, Pn, Tn);
+  if (!m_inv_dev(T, Ti)) return false;
+  m_mul_rn(Tn, Ti, L);
+  for (int q = 0; q < 9; ++q) L[q] = (L[q] - ((q % 4 == 0) ? 1.0 : 0.0)) / dt;
+  return true;
+}
+
 // Advance of one (sub-)scene's cell and clock.
-__device__ void cell_advance(CellState *__restrict__ cs, const double *servo) {
+__device__ void cell_advance(CellState *__restrict__ cs, const double *servo, P3d *p3d = nullptr) {
   const double dt = cs->dt;
   if (cs->periodic) {
     double Hp[9], H[9], Lp[9], L[9], dL[9], W[9];
@@ -610,6 +781,15 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo) {
 #pragma unroll
       for (int q = 0; q < 9; ++q) dL[q] = L[q] - Lp[q];
     }
+    if (p3d && p3d->has_next) {
+      // the controller's gradient (k_p3d_update), effective from the next step like
+      // Cell.velGrad
+      for (int q = 0; q < 9; ++q) {
+        L[q] = p3d->Lnext[q];
+        dL[q] = L[q] - Lp[q];
+      }
+      p3d->has_next = 0;
+    }
     m_mul_rn(Lp, Hp, W);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -639,10 +819,28 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo) {
 // in; the last block to arrive (so every block has read it) turns a collider
 // request into "pending" and counts the step, so no block can see the flag of the
 // step it is advancing.
-__global__ void k_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo) {
+// Peri3dController update of sub-scene 0 (one thread), between the integration and
+// the cell advance of a step that was not skipped: the gradient it computes is
+// picked up by that cell advance.
+__global__ void k_p3d_update(const CellState *cs, const DevStatus *ds, P3d *p3d, const double *part) {
+  if (ds->pending || !p3d->on) return;
+  double Hp[9], H[9], L[9];
+  for (int q = 0; q < 9; ++q) {
+    Hp[q] = cs->H[q];
+    H[q] = cs->Hnext[q];
+  }
+  if (p3d_update(*p3d, part, Hp, H, cs->dt, L)) {
+    for (int q = 0; q < 9; ++q) p3d->Lnext[q] = L[q];
+    p3d->has_next = 1;
+  }
+}
+
+__global__ void k_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo,
+                               P3d *p3d) {
   const bool skip = *(volatile int *)&ds->pending;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!skip && q < nsub && cs[q].alive) cell_advance(cs + q, q == 0 ? servo : nullptr);
+  if (!skip && q < nsub && cs[q].alive)
+    cell_advance(cs + q, q == 0 ? servo : nullptr, q == 0 ? p3d : nullptr);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -743,6 +941,30 @@ __global__ void k_servo_partials(Table t, Bodies b, const DevStatus *ds, int mix
     }
   }
   block_reduce_store<6>(v, partials);
+}
+
+// Peri3dController: sum over real rows of F_a (-l n_b), the full Love-Weber tensor
+__global__ void k_p3d_partials(Table t, const DevStatus *ds, int mixed, double *partials) {
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (!ds->pending) {
+    for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
+      double F[3], n[3], l;
+      if (mixed) {
+        if (t.g32[k].w == 0.0f) continue;
+        const float4 f = t.oF32[k], m = t.oM32[k], h = t.hn32[k];
+        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        l = (double)f.w + (double)m.w;
+      } else {
+        if (t.hfs[k].w == 0.0) continue;
+        const double4_32a f = t.oF[k], m = t.oM[k], h = t.hn[k];
+        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
+        l = f.w + m.w;
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) v[3 * a + b] += F[a] * (-l * n[b]);
+    }
+  }
+  block_reduce_store<9>(v, partials);
 }
 
 // ke, sum |F contact| over free bodies, number of free bodies
@@ -962,9 +1184,16 @@ void launch_integrate(const StepDesc *d, const StepDesc &h, bool desc, const Cel
 }
 
 void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo_partials,
-                         cudaStream_t st) {
+                         cudaStream_t st, P3d *p3d, const double *p3d_partials) {
   const int threads = nsub < 128 ? 32 * ((nsub + 31) / 32) : 128;
-  k_cell_advance<<<(nsub + threads - 1) / threads, threads, 0, st>>>(cs, nsub, ds, servo_partials);
+  if (p3d) k_p3d_update<<<1, 1, 0, st>>>(cs, ds, p3d, p3d_partials);
+  k_cell_advance<<<(nsub + threads - 1) / threads, threads, 0, st>>>(cs, nsub, ds, servo_partials,
+                                                                     p3d);
+}
+
+void launch_p3d_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
+                         cudaStream_t st) {
+  k_p3d_partials<<<kServoBlocks, kT, 0, st>>>(t, ds, mixed, partials);
 }
 
 void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub,

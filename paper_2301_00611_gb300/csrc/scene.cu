@@ -208,6 +208,11 @@ struct dem_scene {
   size_t scan_ws_bytes = 0;
   double *partials = nullptr;  // 1024 blocks x 32 doubles
   double *servo = nullptr;     // kServoBlocks x 6 doubles
+  // Peri3dController (scene without sub-scenes): device state, stress partials, host copy
+  P3d *p3d_d = nullptr;
+  double *p3d_part = nullptr;   // kServoBlocks x 9 doubles
+  P3d p3d_h{};
+  bool p3d_on = false;
   int *deg_ws = nullptr;       // 2 x kDegreeBuckets ints (integration order)
   // launch shapes of the step kernels (none changes a result)
   int contact_block = 256, contact_per_sm = 8, integrate_block = 256, degree_order = 1;
@@ -1008,7 +1013,7 @@ void dem_scene_destroy(dem_scene *s) {
   dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
   dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
-  dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo); dfree(s, s->deg_ws);
+  dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo); dfree(s, s->p3d_d); dfree(s, s->p3d_part); dfree(s, s->deg_ws);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);
   dfree(s, s->grids_d); dfree(s, s->id_shift_d); dfree(s, s->bbox_keys); dfree(s, s->dt_keys);
   if (s->st) cudaStreamSynchronize(s->st);
@@ -1188,7 +1193,84 @@ dem_status dem_set_triax(dem_scene *s, const double *goal, int stress_mask,
   s->cs0().grow_damping = grow_damping;
   s->cs0().glob_update = glob_update;
   s->cs0().triax = 1;
+  s->p3d_on = false;   // one cell controller at a time
   s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_set_peri3d(dem_scene *s, const double *goal, int stress_mask, long long n_steps,
+                          double mod, double max_strain_rate, double young_est, double poisson_est,
+                          double max_strain, const int *npath, const double *path,
+                          const double *trsf0) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!s->desc.periodic) return fail(s, DEM_ERR_STATE, "Peri3dController needs a periodic scene");
+  if (s->nsub() > 1)
+    return fail(s, DEM_ERR_UNSUPPORTED, "Peri3dController runs on a scene without sub-scenes");
+  if (!goal || n_steps < 1 || !(max_strain_rate > 0) || !std::isfinite(max_strain_rate) ||
+      !(young_est > 0) || !(poisson_est > -1 && poisson_est < 0.5) || !(max_strain > 0) ||
+      !(mod >= 0) || !std::isfinite(mod))
+    return fail(s, DEM_ERR_INVALID_ARG, "bad Peri3dController parameters");
+  P3d P{};
+  for (int i = 0; i < 6; ++i) {
+    if (!std::isfinite(goal[i])) return fail(s, DEM_ERR_INVALID_ARG, "non-finite goal");
+    P.goal[i] = goal[i];
+    const int n = npath ? npath[i] : 0;
+    if (n < 0 || n > 16 || (n > 0 && !path)) return fail(s, DEM_ERR_INVALID_ARG, "bad path size");
+    if (n == 0) {   // default: linear from 0 to the goal
+      P.npath[i] = 1;
+      P.path[i][0][0] = 1.0;
+      P.path[i][0][1] = 1.0;
+      continue;
+    }
+    P.npath[i] = n;
+    for (int j = 0; j < n; ++j) {
+      P.path[i][j][0] = path[(16 * i + j) * 2];
+      P.path[i][j][1] = path[(16 * i + j) * 2 + 1];
+      if (!std::isfinite(P.path[i][j][0]) || !std::isfinite(P.path[i][j][1]) ||
+          !(P.path[i][j][0] > (j ? P.path[i][j - 1][0] : 0.0)))
+        return fail(s, DEM_ERR_INVALID_ARG, "path times must increase from a positive first one");
+    }
+    if (P.path[i][n - 1][1] == 0.0)
+      return fail(s, DEM_ERR_INVALID_ARG, "the last couple of a path stands for the goal: nonzero value");
+  }
+  for (int q = 0; q < 9; ++q) P.T0[q] = trsf0 ? trsf0[q] : ((q % 4 == 0) ? 1.0 : 0.0);
+  if (trsf0 && !(m_det(P.T0) > 0)) return fail(s, DEM_ERR_INVALID_ARG, "trsf0 needs det > 0");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  if (!m_inv(s->cs0().H, P.H0inv)) return fail(s, DEM_ERR_INVALID_ARG, "singular cell");
+  P.on = 1;
+  P.mask = stress_mask & 63;
+  P.first = 1;
+  P.nsteps = n_steps;
+  P.mod = mod;
+  P.max_rate = max_strain_rate;
+  P.young = young_est;
+  P.poisson = poisson_est;
+  P.max_strain = max_strain;
+  if (!s->p3d_d && ((r = dalloc(s, &s->p3d_d, 1)) || (r = dalloc(s, &s->p3d_part, kServoBlocks * 9))))
+    return r;
+  s->p3d_h = P;
+  CK(cudaMemcpyAsync(s->p3d_d, &s->p3d_h, sizeof(P3d), cudaMemcpyHostToDevice, s->st));
+  if ((r = wait(s))) return r;
+  s->p3d_on = true;
+  s->cs0().triax = 0;   // one cell controller at a time
+  s->cs_dirty = true;
+  return DEM_OK;
+}
+
+dem_status dem_get_peri3d(dem_scene *s, double *stress, double *strain, double *rate, int *done) {
+  if (!s) return DEM_ERR_INVALID_ARG;
+  if (!s->p3d_on) return fail(s, DEM_ERR_STATE, "no Peri3dController on this scene");
+  dem_status r;
+  if ((r = sync_host(s))) return r;
+  CK(cudaMemcpyAsync(&s->p3d_h, s->p3d_d, sizeof(P3d), cudaMemcpyDeviceToHost, s->st));
+  if ((r = wait(s))) return r;
+  for (int i = 0; i < 6; ++i) {
+    if (stress) stress[i] = s->p3d_h.stress[i];
+    if (strain) strain[i] = s->p3d_h.strain[i];
+    if (rate) rate[i] = s->p3d_h.rate[i];
+  }
+  if (done) *done = s->p3d_h.done;
   return DEM_OK;
 }
 
@@ -1236,6 +1318,7 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
     CK(cudaMemcpyAsync(s->step_d, s->step_h, sizeof(StepDesc), cudaMemcpyHostToDevice, s->st));
     const long long rows = std::max(s->tab[0].cap, s->tab[1].cap);
     const bool servo = !sc.multi && s->cs0().triax;
+    const bool p3d = !sc.multi && s->p3d_on;
     bool tstep = false;
     for (const Sub &u : s->subs) tstep |= u.used && u.cs.tstep;
     auto tstep_due = [&](long long i) {
@@ -1245,7 +1328,7 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
     };
     // captured batches read the descriptor; launched ones take the arrays as parameters
     const bool use_graph = (s->step_graphs > 0 || (s->step_graphs < 0 && sc.N < kGraphAutoBodies)) &&
-                           !ev && !servo && !tstep;
+                           !ev && !servo && !tstep && !p3d;
     bool desc = use_graph;
     auto launch_steps = [&](bool record) -> dem_status {
       for (long long i = 0; i < B; ++i) {
@@ -1274,7 +1357,12 @@ dem_status dem_step(dem_scene *s, long long nsteps) {
           launch_servo_partials(t, s->cur, s->ds_d, s->mixed, s->cs0().law, s->servo, s->st);
           s->launches += 1;
         }
-        launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st);
+        if (p3d) {   // Peri3dController: every step, from this step's contacts
+          launch_p3d_partials(t, s->ds_d, s->mixed, s->p3d_part, s->st);
+          s->launches += 2;
+        }
+        launch_cell_advance(s->cs_d, s->nsub(), s->ds_d, upd ? s->servo : nullptr, s->st,
+                            p3d ? s->p3d_d : nullptr, s->p3d_part);
         if (record) CK(cudaEventRecord(ev[6 * i + 5], s->st));
       }
       return DEM_OK;
@@ -2062,8 +2150,8 @@ dem_status dem_add_subscene(dem_scene *s, const dem_subscene_desc *d, int *sub) 
   const int wm = d->periodic ? 0 : (d->wall_mask & 0x3F);
   if (wm && (d->wall_material < 0 || d->wall_material >= kMaxMat || !s->mat_set[d->wall_material]))
     return fail(s, DEM_ERR_INVALID_ARG, "unknown wall material (set_material first)");
-  if (s->cs0().triax)
-    return fail(s, DEM_ERR_UNSUPPORTED, "a scene running the stress servo takes no sub-scenes");
+  if (s->cs0().triax || s->p3d_on)
+    return fail(s, DEM_ERR_UNSUPPORTED, "a scene running a cell controller takes no sub-scenes");
   dem_status r;
   if ((r = sync_host(s))) return r;
   int q = -1;

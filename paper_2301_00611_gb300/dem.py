@@ -148,6 +148,10 @@ _SIGS = {
     "dem_set_subscene_velgrad": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "dem_flip_cell": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "dem_set_density_scaling": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+    "dem_set_peri3d": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_longlong, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, _P, _P, _P]),
+    "dem_get_peri3d": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "dem_get_density_scaling": (ctypes.c_int, [_P, _P]),
     "dem_num_bodies": (ctypes.c_int, [_P, _P]),
     "dem_get_micro": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
@@ -431,6 +435,31 @@ class Scene:
     def set_subscene_velgrad(self, sub, L):
         L = _f64(L, (3, 3))
         self._check(self._lib.dem_set_subscene_velgrad(self._h, int(sub), _ptr(L)))
+
+    def set_peri3d(self, goal, stress_mask, n_steps, mod=0.1, max_strain_rate=1e3,
+                   young_est=1e20, poisson_est=0.25, max_strain=1e6, paths=None, trsf0=None):
+        """Peri3dController (dem_set_peri3d).  goal: xx, yy, zz, yz, zx, xy; paths:
+        None or 6 sequences of (t, v) couples (empty: linear); trsf0: Cell.trsf now."""
+        npath = np.zeros(6, dtype=np.int32)
+        path = np.zeros((6, 16, 2))
+        if paths is not None:
+            for i, pth in enumerate(paths):
+                pth = np.asarray(pth, dtype=np.float64).reshape(-1, 2)
+                npath[i] = len(pth)
+                path[i, :len(pth)] = pth
+        g = _f64(goal, (6,))
+        T0 = None if trsf0 is None else _f64(trsf0, (3, 3))
+        self._check(self._lib.dem_set_peri3d(
+            self._h, _ptr(g), int(stress_mask), int(n_steps), float(mod), float(max_strain_rate),
+            float(young_est), float(poisson_est), float(max_strain),
+            npath.ctypes.data_as(_P), _ptr(path), None if T0 is None else _ptr(T0)))
+
+    def peri3d(self):
+        st, sn, rt = np.empty(6), np.empty(6), np.empty(6)
+        done = ctypes.c_int()
+        self._check(self._lib.dem_get_peri3d(self._h, _ptr(st), _ptr(sn), _ptr(rt),
+                                             ctypes.byref(done)))
+        return {"stress": st, "strain": sn, "rate": rt, "done": bool(done.value)}
 
     def set_density_scaling(self, enable=True, target_dt=1.0, sub=0):
         """Density scaling to the step target_dt (dem_set_density_scaling); needs

@@ -38,56 +38,66 @@ __device__ inline bool finite_bits(double x) {
 // Rows are visited in the fixed order (own rows, then the down list); two rows are
 // loaded before either is added, which keeps more loads in flight without changing
 // the order of the additions.
+// Fixed-order gather of a body's contact forces and torques: its rows as body 1
+// (force -F, torque d1 M) in row order, then its rows as body 2 (force +F, torque
+// d2 M) in down-list order.  Both lists run as one loop over their concatenation, so
+// the trip count is the body's row count (which the degree ordering makes nearly
+// uniform across a warp) rather than two loops whose lengths differ lane by lane;
+// the sign is applied as a multiplication by -1 or +1, which is exact, so the sums are
+// the same as two separate loops would give.  Two rows are loaded before either is
+// added.
 __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[3]) {
-  const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
-  int k = r0;
-  for (; k + 1 < r1; k += 2) {   // rows where s is body 1: force -F, torque d1 M
-    const double4_32a fa = t.oF[k], ma = t.oM[k], fb = t.oF[k + 1], mb = t.oM[k + 1];
-    F[0] -= fa.x; F[1] -= fa.y; F[2] -= fa.z;
-    T[0] += fa.w * ma.x; T[1] += fa.w * ma.y; T[2] += fa.w * ma.z;
-    F[0] -= fb.x; F[1] -= fb.y; F[2] -= fb.z;
-    T[0] += fb.w * mb.x; T[1] += fb.w * mb.y; T[2] += fb.w * mb.z;
-  }
-  if (k < r1) {
-    const double4_32a f = t.oF[k], m = t.oM[k];
-    F[0] -= f.x; F[1] -= f.y; F[2] -= f.z;
-    T[0] += f.w * m.x; T[1] += f.w * m.y; T[2] += f.w * m.z;
-  }
-  const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
-  int e = e0;
-  for (; e + 1 < e1; e += 2) {   // rows where s is body 2: force +F, torque d2 M
-    const int ka = t.down[e], kb = t.down[e + 1];
+  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
+  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
+  int j = 0;
+  for (; j + 1 < n; j += 2) {
+    const bool a1 = j < nr, b1 = j + 1 < nr;   // body 1 of the row
+    const int ka = a1 ? r0 + j : t.down[e0 + j];
+    const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
     const double4_32a fa = t.oF[ka], ma = t.oM[ka], fb = t.oF[kb], mb = t.oM[kb];
-    F[0] += fa.x; F[1] += fa.y; F[2] += fa.z;
-    T[0] += ma.w * ma.x; T[1] += ma.w * ma.y; T[2] += ma.w * ma.z;
-    F[0] += fb.x; F[1] += fb.y; F[2] += fb.z;
-    T[0] += mb.w * mb.x; T[1] += mb.w * mb.y; T[2] += mb.w * mb.z;
+    const double sa = a1 ? -1.0 : 1.0, da = a1 ? fa.w : ma.w;
+    const double sb = b1 ? -1.0 : 1.0, db = b1 ? fb.w : mb.w;
+    F[0] += sa * fa.x; F[1] += sa * fa.y; F[2] += sa * fa.z;
+    T[0] += da * ma.x; T[1] += da * ma.y; T[2] += da * ma.z;
+    F[0] += sb * fb.x; F[1] += sb * fb.y; F[2] += sb * fb.z;
+    T[0] += db * mb.x; T[1] += db * mb.y; T[2] += db * mb.z;
   }
-  if (e < e1) {
-    const int k1 = t.down[e];
-    const double4_32a f = t.oF[k1], m = t.oM[k1];
-    F[0] += f.x; F[1] += f.y; F[2] += f.z;
-    T[0] += m.w * m.x; T[1] += m.w * m.y; T[2] += m.w * m.z;
+  if (j < n) {
+    const bool a1 = j < nr;
+    const int ka = a1 ? r0 + j : t.down[e0 + j];
+    const double4_32a f = t.oF[ka], m = t.oM[ka];
+    const double sa = a1 ? -1.0 : 1.0, da = a1 ? f.w : m.w;
+    F[0] += sa * f.x; F[1] += sa * f.y; F[2] += sa * f.z;
+    T[0] += da * m.x; T[1] += da * m.y; T[2] += da * m.z;
   }
 }
 
 // Mixed precision: the same fixed-order gather over FP32 row outputs, summed in FP32
 // (the contact forces are FP32 results; the sum feeds an FP64 velocity update).
-__device__ inline void gather_rows_f32(const Table &t, int s, double F[3], double T[3]) {
+__device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float T[3]) {
   float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-  const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
-  for (int k = r0; k < r1; ++k) {
-    const float4 f = t.oF32[k], m = t.oM32[k];
-    f0 -= f.x; f1 -= f.y; f2 -= f.z;
-    t0 += f.w * m.x; t1 += f.w * m.y; t2 += f.w * m.z;
+  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
+  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
+  int j = 0;
+  for (; j + 1 < n; j += 2) {
+    const bool a1 = j < nr, b1 = j + 1 < nr;
+    const int ka = a1 ? r0 + j : t.down[e0 + j];
+    const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
+    const float4 fa = t.oF32[ka], ma = t.oM32[ka], fb = t.oF32[kb], mb = t.oM32[kb];
+    const float sa = a1 ? -1.0f : 1.0f, da = a1 ? fa.w : ma.w;
+    const float sb = b1 ? -1.0f : 1.0f, db = b1 ? fb.w : mb.w;
+    f0 += sa * fa.x; f1 += sa * fa.y; f2 += sa * fa.z;
+    t0 += da * ma.x; t1 += da * ma.y; t2 += da * ma.z;
+    f0 += sb * fb.x; f1 += sb * fb.y; f2 += sb * fb.z;
+    t0 += db * mb.x; t1 += db * mb.y; t2 += db * mb.z;
   }
-  const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
-  for (int e = e0; e < e1; ++e) {
-    const int k = t.down[e];
-    if (k < 0) continue;
-    const float4 f = t.oF32[k], m = t.oM32[k];
-    f0 += f.x; f1 += f.y; f2 += f.z;
-    t0 += m.w * m.x; t1 += m.w * m.y; t2 += m.w * m.z;
+  if (j < n) {
+    const bool a1 = j < nr;
+    const int ka = a1 ? r0 + j : t.down[e0 + j];
+    const float4 f = t.oF32[ka], m = t.oM32[ka];
+    const float sa = a1 ? -1.0f : 1.0f, da = a1 ? f.w : m.w;
+    f0 += sa * f.x; f1 += sa * f.y; f2 += sa * f.z;
+    t0 += da * m.x; t1 += da * m.y; t2 += da * m.z;
   }
   F[0] = f0; F[1] = f1; F[2] = f2;
   T[0] = t0; T[1] = t1; T[2] = t2;
@@ -134,40 +144,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   const double dt = c.dt;
   const float dtf = (float)dt;
   float F[3], T[3];
-  {   // fixed-order gather, two rows loaded before either is added
-    float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-    const int r0 = t.row_start[s], r1 = t.row_start[s + 1];
-    int k = r0;
-    for (; k + 1 < r1; k += 2) {
-      const float4 fa = t.oF32[k], ma = t.oM32[k], fb = t.oF32[k + 1], mb = t.oM32[k + 1];
-      f0 -= fa.x; f1 -= fa.y; f2 -= fa.z;
-      t0 += fa.w * ma.x; t1 += fa.w * ma.y; t2 += fa.w * ma.z;
-      f0 -= fb.x; f1 -= fb.y; f2 -= fb.z;
-      t0 += fb.w * mb.x; t1 += fb.w * mb.y; t2 += fb.w * mb.z;
-    }
-    if (k < r1) {
-      const float4 f = t.oF32[k], m = t.oM32[k];
-      f0 -= f.x; f1 -= f.y; f2 -= f.z;
-      t0 += f.w * m.x; t1 += f.w * m.y; t2 += f.w * m.z;
-    }
-    const int e0 = t.down_start[s], e1 = t.down_start[s + 1];
-    int e = e0;
-    for (; e + 1 < e1; e += 2) {
-      const int ka = t.down[e], kb = t.down[e + 1];
-      const float4 fa = t.oF32[ka], ma = t.oM32[ka], fb = t.oF32[kb], mb = t.oM32[kb];
-      f0 += fa.x; f1 += fa.y; f2 += fa.z;
-      t0 += ma.w * ma.x; t1 += ma.w * ma.y; t2 += ma.w * ma.z;
-      f0 += fb.x; f1 += fb.y; f2 += fb.z;
-      t0 += mb.w * mb.x; t1 += mb.w * mb.y; t2 += mb.w * mb.z;
-    }
-    if (e < e1) {
-      const int k1 = t.down[e];
-      const float4 f = t.oF32[k1], m = t.oM32[k1];
-      f0 += f.x; f1 += f.y; f2 += f.z;
-      t0 += m.w * m.x; t1 += m.w * m.y; t2 += m.w * m.z;
-    }
-    F[0] = f0; F[1] = f1; F[2] = f2; T[0] = t0; T[1] = t1; T[2] = t2;
-  }
+  gather_rows_f32(t, s, F, T);   // fixed order, FP32 sums
   const float4 va = b.vw32[2 * s], vb = b.vw32[2 * s + 1];   // v-, w- in FP32
   const float4 off = b.p32[s];                                // x - xref, r
   const float4 xr = b.xref32[s];
@@ -862,8 +839,13 @@ __global__ void k_gather_forces(Bodies b, Table t, const Mat *__restrict__ mats,
   if (sl >= sc.N) return;
   const int s = (int)sl;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  if (mixed) gather_rows_f32(t, s, F, T);
-  else gather_rows(t, s, F, T);
+  if (mixed) {
+    float Ff[3], Tf[3];
+    gather_rows_f32(t, s, Ff, Tf);
+    for (int q = 0; q < 3; ++q) { F[q] = Ff[q]; T[q] = Tf[q]; }
+  } else {
+    gather_rows(t, s, F, T);
+  }
   const uint8_t flags = b.flags[s];
   if (sc.walls && (flags & 0x7e)) {
     const CellState &c = cs[sc.multi ? b.sid[s] : 0];

@@ -251,8 +251,15 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       __syncwarp();
     }
   }
-  if (lane < cnt) {
-    const QRow e = wq[lane];
+  // Leftovers (< 32 per warp) are pooled over the block and taken one per thread, so
+  // the block runs at most one partly filled pass of the law instead of one per warp.
+  __shared__ int left[kWarps];
+  if (lane == 0) left[wi] = cnt;
+  __syncthreads();
+  int from = 0, pos = threadIdx.x;
+  for (; from < kWarps && pos >= left[from]; ++from) pos -= left[from];
+  if (from < kWarps) {
+    const QRow e = q[from][pos];
     real_row<kFeat>(t, b, mats, e.k, e.dx, e.dy, e.dz, e.l2, e.r1, e.r2,
                      multi ? row_cell(cs[e.q]) : rc0, cs + e.q);
   }

@@ -110,6 +110,7 @@ struct CellState {
   double dL[9];     // L - Lprev (homoDeform first term)
   double Hnext[9];  // (I + L dt) H
   double E[9];      // (Hnext - Href) Href^-1: affine strain since the collider run
+  double Ep1[3];    // 1 + the diagonal of E (the displacement bound of a diagonal cell)
   double Href[9], Hrefinv[9];
   double dt, time;
   double dt_law;        // dt of this step's contact laws (the time stepper may change dt

@@ -19,13 +19,14 @@ namespace dem {
 namespace {
 constexpr int kT = 256;
 
-// Damping factor 1 - lam * sgn(p) for p = a * b, with sgn(a b) read from the sign bits and zero tests
-// of a and b on the integer pipe (no FP64 product or compares).  It differs from
-// sgn(fl(a b)) only if the product underflows to zero.
-__device__ inline double damp_factor_ab(double a, double b, double one_m, double one_p) {
+// The step scaled by the damping factor of eq. 2.9, dt (1 - lam sgn(a b)), with
+// dt_m = dt (1 - lam) and dt_p = dt (1 + lam): sgn(a b) is read from the sign bits and
+// zero tests of a and b on the integer pipe (no FP64 product or compare).  It differs
+// from sgn(fl(a b)) only if the product underflows to zero.
+__device__ inline double damped_dt(double a, double b, double dt, double dt_m, double dt_p) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   const bool zero = ((ia << 1) == 0) | ((ib << 1) == 0);
-  return zero ? 1.0 : ((ia ^ ib) < 0 ? one_p : one_m);
+  return zero ? dt : ((ia ^ ib) < 0 ? dt_p : dt_m);
 }
 __device__ inline float damp_factor_f(float p, float lam) {
   return p > 0.0f ? 1.0f - lam : (p < 0.0f ? 1.0f + lam : 1.0f);
@@ -421,19 +422,22 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
         for (int q = 0; q < 3; ++q) vref[q] -= Lp[4 * q] * x[q];
       }
     }
-    const double hdt = 0.5 * dt, one_m = 1.0 - lam, one_p = 1.0 + lam;
+    // eq. 2.9 with the damping factor folded into the step: v+ = v- + dt (1 -+ lam) a,
+    // a = F / m, the sign decided on F (v- + dt/2 a) (products and sums of the same
+    // terms as the oracle's dt F (1 -+ lam) / m, in another rounding order)
+    const double hdt = 0.5 * dt, dt_m = dt * (1.0 - lam), dt_p = dt * (1.0 + lam);
     double im = mp.z, iI = mp.w;   // inverse inertial mass and moment
     if (c.dscale) {   // density scaling: inertia times f (the weight keeps the true mass)
       const double rf = b.rdsc[s];
       im *= rf;
       iI *= rf;
     }
-    for (int q = 0; q < 3; ++q) {   // v+ = v- + (dt Fd) / m, as the oracle orders it
+    for (int q = 0; q < 3; ++q) {
       const double Ft = F[q] + mp.x * c.gravity[q];
-      const double Fd = Ft * damp_factor_ab(Ft, vref[q] + hdt * (Ft * im), one_m, one_p);
-      vn_[q] = vv[q] + (dt * Fd) * im;
-      const double Td = T[q] * damp_factor_ab(T[q], ww[q] + hdt * (T[q] * iI), one_m, one_p);
-      wn_[q] = ww[q] + (dt * Td) * iI;
+      const double a = Ft * im;
+      vn_[q] = vv[q] + damped_dt(Ft, vref[q] + hdt * a, dt, dt_m, dt_p) * a;
+      const double al = T[q] * iI;
+      wn_[q] = ww[q] + damped_dt(T[q], ww[q] + hdt * al, dt, dt_m, dt_p) * al;
     }
     if (c.periodic) {   // homoDeform = 2
       const double *dL = c.dL, *L = c.L;
@@ -482,10 +486,10 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
 
   // collider trigger: displacement since the last run, minus the affine part
   const double4_32a xr = b.xref[s];
-  const double *E = c.E;
-  double ux = (xn[0] - xr.x) - E[0] * xr.x;
-  double uy = (xn[1] - xr.y) - E[4] * xr.y;
-  double uz = (xn[2] - xr.z) - E[8] * xr.z;
+  const double *E = c.E;   // diagonal cell: x+ - (1 + E) xref, one fused step per axis
+  double ux = xn[0] - c.Ep1[0] * xr.x;
+  double uy = xn[1] - c.Ep1[1] * xr.y;
+  double uz = xn[2] - c.Ep1[2] * xr.z;
   if ((kFeat & 2) && c.sheared) {   // E xref with the full affine strain
     ux = (xn[0] - xr.x) - (E[0] * xr.x + E[1] * xr.y + E[2] * xr.z);
     uy = (xn[1] - xr.y) - (E[3] * xr.x + E[4] * xr.y + E[5] * xr.z);
@@ -539,6 +543,7 @@ __device__ void derive_next_local(CellState *__restrict__ cs, const double (&H)[
   cs->thr2 = eff > 0 ? eff * eff : -1.0;
 #pragma unroll
   for (int q = 0; q < 9; ++q) cs->Ef[q] = (float)E[q];
+  for (int k = 0; k < 3; ++k) cs->Ep1[k] = 1.0 + E[4 * k];
 }
 
 __device__ void derive_next(CellState *__restrict__ cs) {

@@ -77,6 +77,7 @@ void cell_derive(CellState &c) {
       c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0;
       c.dHf[q] = 0; c.Wf[q] = 0; c.Ef[q] = 0;
     }
+    for (int k = 0; k < 3; ++k) c.Ep1[k] = 1.0;
     c.sheared = 0;
     c.thr2 = c.verlet * c.verlet;
     return;
@@ -100,6 +101,7 @@ void cell_derive(CellState &c) {
     c.Wf[q] = (float)c.W[q];
     c.Ef[q] = (float)c.E[q];
   }
+  for (int k = 0; k < 3; ++k) c.Ep1[k] = 1.0 + c.E[4 * k];
 }
 
 // Cell state of a new (sub-)scene: periodic cell H (identity otherwise), walls of an

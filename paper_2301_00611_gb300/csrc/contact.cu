@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
     bool real = false;
     double dx = 0, dy = 0, dz = 0, l2 = 0, r1 = 0, r2 = 0;
     int sq = 0;
+    // rows of neighbours inside the cell have no shift (c = 0, h = H c = 0 exactly): a
+    // warp whose 32 rows all have none skips the conversions and products
+    const int cp = k < P ? t.cpack[k] : 0;
+    const bool any_shift = __any_sync(0xffffffffu, cp != 0);
     if (k < P) {
       const int2 pr = t.pair[k];
       const double4_32a p1 = b.pos[pr.x];
@@ -200,9 +204,9 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       double h0 = 0, h1 = 0, h2 = 0;
       if (multi) sq = b.sid[pr.x];
       const int periodic = multi ? cs[sq].periodic : rc0.periodic;
-      if (periodic) {
+      if (periodic && any_shift) {
         int i0, i1, i2;
-        unpack_shift(t.cpack[k], i0, i1, i2);
+        unpack_shift(cp, i0, i1, i2);
         const double c0 = i0, c1 = i1, c2 = i2;
         if ((kFeat & 2) && (multi ? cs[sq].sheared : rc0.sheared)) {
           // H c of a sheared cell, each row summed left to right as the oracle writes it

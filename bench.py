@@ -23,6 +23,7 @@ replica of the scene (the path has no exchange step: replicas only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -309,6 +310,33 @@ INT_FLOPS_BODY, INT_FLOPS_REAL = 131, 18
 INT_BYTES_BODY_MIXED, INT_BYTES_REAL_MIXED = 393, 68
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the two step
+# kernels, from one ncu capture of this workload's last steps (launches near step 4990:
+# `rows` candidate rows and `real` real contacts per launch); the profile under
+# profiles/ that gives the command.  They describe the kernel sources whose digest is
+# stored with them and are reported as null for any other build.
+KERNEL_SOURCES = ("contact.cu", "contact_mixed.cu", "integrate.cu", "dem_internal.cuh")
+TRAFFIC = {}
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2301_00611_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(precision, name):
+    t = TRAFFIC.get(precision, {}).get(name)
+    if not t or TRAFFIC.get("digest") != kernel_digest():
+        return None, None
+    note = (f"ncu DRAM bytes per launch near step {t['step']} of the job "
+            f"({t['rows']} rows, {t['real']} real contacts in that launch; algorithmic bytes of "
+            f"that launch {t['algorithmic']:.4g}); {TRAFFIC['profile']}")
+    return t["bytes"], note
+
+
 def _kernel_rooflines(res, precision, n, peak, peak_kind):
     """Roofline of the contact and integrator kernels of one timed window: achieved
     algorithmic flops (FP64, FP64-pipe bound) or bytes (mixed, HBM bound) per launch over
@@ -339,6 +367,11 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind):
             out[name] = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s",
                          "frac": gb / peak, "traffic": None, "peak_kind": peak_kind,
                          "avg_launch_ms": ms, "bytes_per_launch": by}
+    for name, o in out.items():
+        tb, note = _traffic(precision, name)
+        o["traffic"] = tb
+        if note:
+            o["traffic_note"] = note
     share = {"contact": tm["contact_ms"], "integrate": tm["integrate_ms"]}
     dom = max(share, key=share.get)
     line = dict(out[dom])

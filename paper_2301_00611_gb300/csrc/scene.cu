@@ -2076,6 +2076,11 @@ dem_status dem_autotune(dem_scene *s, long long steps, dem_tuning *chosen) {
   dem_status r;
   const bool was_timing = s->timing;
   const dem_timing keep_tm = s->tm;
+  // The scene keeps evolving while the trials run (a compaction gains rows from one
+  // trial to the next), so the contact time is taken per row processed and scaled to
+  // the rows of the first trial, and each contact shape is timed twice, in two passes
+  // over the list, keeping its better time.
+  double rows_ref = 0;
   auto trial = [&](const dem_tuning &t, double &cost) -> dem_status {
     apply_tuning(s, t);
     dem_status q;
@@ -2083,23 +2088,29 @@ dem_status dem_autotune(dem_scene *s, long long steps, dem_tuning *chosen) {
     if ((q = dem_set_timing(s, 1))) return q;
     const long long it0 = s->cs0().iter;
     if ((q = dem_step(s, steps))) return q;
-    const long long done = s->cs0().iter - it0;
-    cost = (s->tm.contact_ms + s->tm.integrate_ms) / (double)std::max<long long>(done, 1);
+    const long long done = std::max<long long>(s->cs0().iter - it0, 1);
+    const double rows = (double)s->tm.rows_processed;
+    if (rows_ref == 0) rows_ref = rows / (double)done;
+    const double contact = rows > 0 ? s->tm.contact_ms / rows * rows_ref : 0.0;
+    cost = contact + s->tm.integrate_ms / (double)done;
     return DEM_OK;
   };
   dem_tuning best = current_tuning(s);
   double best_cost = INFINITY;
   const int cblocks[2] = {128, 256};
   const int per_sm[3] = {4, 8, 16};
-  for (int b : cblocks)
-    for (int p : per_sm) {
-      dem_tuning t = best;
-      t.contact_block = b;
-      t.contact_blocks_per_sm = p * (256 / b);
-      double c;
-      if ((r = trial(t, c))) return r;
-      if (c < best_cost) { best_cost = c; best = t; }
-    }
+  double shape_cost[2][3];
+  for (int pass = 0; pass < 2; ++pass)
+    for (int ib = 0; ib < 2; ++ib)
+      for (int ip = 0; ip < 3; ++ip) {
+        dem_tuning t = current_tuning(s);
+        t.contact_block = cblocks[ib];
+        t.contact_blocks_per_sm = per_sm[ip] * (256 / cblocks[ib]);
+        double c;
+        if ((r = trial(t, c))) return r;
+        shape_cost[ib][ip] = pass ? std::min(shape_cost[ib][ip], c) : c;
+        if (pass && shape_cost[ib][ip] < best_cost) { best_cost = shape_cost[ib][ip]; best = t; }
+      }
   const int iblocks[3] = {128, 256, 512};
   const dem_tuning base = best;
   for (int b : iblocks)

@@ -397,12 +397,14 @@ dem_status dem_set_tuning(dem_scene *scene, const dem_tuning *tuning);
 dem_status dem_get_tuning(const dem_scene *scene, dem_tuning *tuning);
 
 /* Pick the launch shapes by timing the scene's own steps: six contact-kernel
- * shapes (block 128/256 x 4/8/16 blocks of 256 threads per SM), then five more
- * integrator shapes (block 128/256/512 x body order) with the best contact shape
- * (step_graphs is left as set: per-kernel timing runs without graphs);
- * each trial is one untimed step plus steps_per_trial timed steps (CUDA events
- * around each kernel; collider runs excluded).  The trial steps are real steps:
- * the scene advances by 11 * (steps_per_trial + 1) steps, along the trajectory
+ * shapes (block 128/256 x 4/8/16 blocks of 256 threads per SM), each timed twice in
+ * two passes and taken per table row processed (a scene that gains contacts during
+ * the trials does not favour the shapes tried first), then five more integrator
+ * shapes (block 128/256/512 x body order) with the best contact shape (step_graphs is
+ * left as set: per-kernel timing runs without graphs); each trial is one untimed
+ * step plus steps_per_trial timed steps (CUDA events around each kernel; collider
+ * runs excluded).  The trial steps are real steps: the scene advances by
+ * 17 * (steps_per_trial + 1) steps, along the trajectory
  * any fixed shape gives.  The best shape is applied and, if chosen is non-null,
  * written there.  Errors: INVALID_ARG (steps_per_trial < 1), those of dem_step. */
 dem_status dem_autotune(dem_scene *scene, long long steps_per_trial, dem_tuning *chosen);

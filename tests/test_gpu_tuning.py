@@ -61,7 +61,7 @@ def test_autotune_picks_a_valid_shape_on_the_same_trajectory(pkg):
     assert 1 <= chosen["contact_blocks_per_sm"] <= 64 and chosen["degree_order"] in (0, 1)
     assert a.tuning() == chosen
     n = a.clock()[0]
-    assert n == 11 * 4
+    assert n == 17 * 4   # 6 contact shapes twice, 5 integrator shapes, 1 + 3 steps each
     b = pkg.Scene.from_workload(w)
     b.step(n)
     assert _same(a.state(), b.state())

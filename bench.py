@@ -310,30 +310,40 @@ INT_FLOPS_BODY, INT_FLOPS_REAL = 131, 18
 INT_BYTES_BODY_MIXED, INT_BYTES_REAL_MIXED = 393, 68
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the two step
-# kernels, from one ncu capture of this workload's last steps (launches near step 4990:
-# `rows` candidate rows and `real` real contacts per launch); the profile under
-# profiles/ that gives the command.  They describe the kernel sources whose digest is
-# stored with them and are reported as null for any other build.
-KERNEL_SOURCES = ("contact.cu", "contact_mixed.cu", "integrate.cu", "dem_internal.cuh")
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the step
+# kernels, from one ncu capture of this workload's last steps (the profile under
+# profiles/ gives the command): the mean of the captured launches near step 4990, which
+# process `rows` candidate rows and `real` real contacts each.  A figure describes the
+# kernel sources whose digest is stored with it and is reported as null for any other
+# build.
+KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
+                              "mixed": ("contact_mixed.cu", "dem_internal.cuh")},
+                  "integrate": {"fp64": ("integrate.cu", "dem_internal.cuh"),
+                                "mixed": ("integrate.cu", "dem_internal.cuh")}}
+TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
+TRAFFIC = {
+    ("fp64", "contact"): {"bytes": 670.6e6, "rows": 4649044, "real": 2617303, "step": 4990,
+                          "digest": "9b57a1c18c018fb4"},
+    ("mixed", "contact"): {"bytes": 431.6e6, "rows": 4649044, "real": 2618461, "step": 4990,
+                           "digest": "5c958ed1d833c6f2"},
+}
 
 
-def kernel_digest():
+def kernel_digest(name, precision):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[name][precision]:
         with open(os.path.join(ROOT, "paper_2301_00611_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(precision, name):
-    t = TRAFFIC.get(precision, {}).get(name)
-    if not t or TRAFFIC.get("digest") != kernel_digest():
+def _traffic(precision, name, algorithmic_at):
+    t = TRAFFIC.get((precision, name))
+    if not t or t["digest"] != kernel_digest(name, precision):
         return None, None
-    note = (f"ncu DRAM bytes per launch near step {t['step']} of the job "
-            f"({t['rows']} rows, {t['real']} real contacts in that launch; algorithmic bytes of "
-            f"that launch {t['algorithmic']:.4g}); {TRAFFIC['profile']}")
+    note = (f"ncu DRAM bytes per launch near step {t['step']} of the job ({t['rows']} rows, "
+            f"{t['real']} real contacts; the algorithmic bytes of such a launch are "
+            f"{algorithmic_at(t['rows'], t['real']):.4g}); {TRAFFIC_PROFILE}")
     return t["bytes"], note
 
 
@@ -367,8 +377,14 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind):
             out[name] = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s",
                          "frac": gb / peak, "traffic": None, "peak_kind": peak_kind,
                          "avg_launch_ms": ms, "bytes_per_launch": by}
+    if precision == "fp64":
+        alg = {"contact": lambda r, c: ROW_BYTES_ALL * r + ROW_BYTES_REAL * c,
+               "integrate": lambda r, c: INT_BYTES_BODY * n + INT_BYTES_REAL * c}
+    else:
+        alg = {"contact": lambda r, c: ROW_BYTES_ALL_MIXED * r + ROW_BYTES_REAL_MIXED * c,
+               "integrate": lambda r, c: INT_BYTES_BODY_MIXED * n + INT_BYTES_REAL_MIXED * c}
     for name, o in out.items():
-        tb, note = _traffic(precision, name)
+        tb, note = _traffic(precision, name, alg[name])
         o["traffic"] = tb
         if note:
             o["traffic_note"] = note

@@ -388,8 +388,8 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
     nt.g32[k] = make_float4(gref.x, gref.y, gref.z, kn);
     nt.hfs[k] = fs;
     nt.hn32[k] = hn;
-    nt.oF32[k] = make_float4(0, 0, 0, 0);
-    nt.oM32[k] = make_float4(0, 0, 0, 0);
+    nt.oFM32[2 * k] = make_float4(0, 0, 0, 0);
+    nt.oFM32[2 * k + 1] = make_float4(0, 0, 0, 0);
     return;
   }
   double4_32a fs = make_double4_32a(0, 0, 0, 0), hn = make_double4_32a(0, 0, 0, 0);
@@ -407,8 +407,8 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
   nt.hfs[k] = fs;
   nt.hn[k] = hn;
   nt.tanphi[k] = tp;
-  nt.oF[k] = make_double4_32a(0, 0, 0, 0);
-  nt.oM[k] = make_double4_32a(0, 0, 0, 0);
+  nt.oFM[2 * k] = make_double4_32a(0, 0, 0, 0);
+  nt.oFM[2 * k + 1] = make_double4_32a(0, 0, 0, 0);
 }
 
 // A real row of the previous table that no candidate carried over: an error only

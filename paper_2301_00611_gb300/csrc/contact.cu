@@ -143,8 +143,8 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double Mx = -(ny * Fz - nz * Fy), My = -(nz * Fx - nx * Fz), Mz = -(nx * Fy - ny * Fx);
   t.hfs[k] = make_double4_32a(fx, fy, fz, kn);
   t.hn[k] = make_double4_32a(nx, ny, nz, ks);
-  t.oF[k] = make_double4_32a(Fx, Fy, Fz, d1);
-  t.oM[k] = make_double4_32a(Mx, My, Mz, d2);
+  t.oFM[2 * k] = make_double4_32a(Fx, Fy, Fz, d1);
+  t.oFM[2 * k + 1] = make_double4_32a(Mx, My, Mz, d2);
 }
 
 // Queued real row: its index, branch vector, squared length, radii and sub-scene.
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       real = l2 < __dmul_rn(R, R);
       if (!real && t.hfs[k].w != 0.0) {   // contact lost (u_N > 0): back to potential
         const double4_32a z = make_double4_32a(0, 0, 0, 0);
-        t.hfs[k] = z; t.hn[k] = z; t.oF[k] = z; t.oM[k] = z;
+        t.hfs[k] = z; t.hn[k] = z; t.oFM[2 * k] = z; t.oFM[2 * k + 1] = z;
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, real);

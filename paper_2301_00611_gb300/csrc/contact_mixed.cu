@@ -156,8 +156,8 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   const float d1 = r1 - 0.5f * pen, d2 = r2 - 0.5f * pen;
   t.hfs[k] = make_double4_32a(fx, fy, fz, tanphi);
   t.hn32[k] = make_float4(nx, ny, nz, ks);
-  t.oF32[k] = make_float4(Fx, Fy, Fz, d1);
-  t.oM32[k] = make_float4(-(ny * Fz - nz * Fy), -(nz * Fx - nx * Fz), -(nx * Fy - ny * Fx), d2);
+  t.oFM32[2 * k] = make_float4(Fx, Fy, Fz, d1);
+  t.oFM32[2 * k + 1] = make_float4(-(ny * Fz - nz * Fy), -(nz * Fx - nx * Fz), -(nx * Fy - ny * Fx), d2);
 }
 
 // Same per-warp queue of real rows as the FP64 kernel: the FP32 geometry test on
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
         t.g32[k] = make_float4(g.x, g.y, g.z, 0.0f);
         t.hfs[k] = make_double4_32a(0, 0, 0, 0);
         const float4 z = make_float4(0, 0, 0, 0);
-        t.hn32[k] = z; t.oF32[k] = z; t.oM32[k] = z;
+        t.hn32[k] = z; t.oFM32[2 * k] = z; t.oFM32[2 * k + 1] = z;
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, real);

@@ -14,7 +14,8 @@
 //     pair int2, cpack int (cell shift of s2, 3 x 10-bit signed),
 //     hfs double4_32a (Fs on body 2, kn)       kn == 0 <=> not in contact
 //     hn  double4_32a (normal of the last step, ks), tanphi double,
-//     oF  double4_32a (F on body 2, arm d1)    oM double4_32a (-(n x F), arm d2)
+//     oFM[2k] double4_32a (F on body 2, arm d1), oFM[2k+1] (-(n x F), arm d2): one
+//     64-byte record per row, so a row's outputs are read with one access
 //   so that the torques are T1 = d1*oM, T2 = d2*oM (section 2.1.4 with the
 //   contact point of eq. 2.8: C - x1 = d1 n, C - x2' = -d2 n).
 //   Row (s1, s2): s1 is the body whose half-shell scan found the pair.
@@ -84,13 +85,13 @@ struct Bodies {
 struct Table {
   int2 *pair;
   int *cpack;
-  double4_32a *hfs, *hn, *oF, *oM;   // FP64 mode; mixed mode uses hfs = (Fs, tan(phi))
+  double4_32a *hfs, *hn;   // FP64 mode; mixed mode uses hfs = (Fs, tan(phi))
+  double4_32a *oFM;        // [2 * rows]: (F on body 2, d1), (-(n x F), d2) per row
   double *tanphi;
   // mixed precision rows (null in FP64 mode)
   float4 *g32;      // (reference branch vector xref2 + Href c - xref1, kn); kn == 0: not real
   float4 *hn32;     // (previous normal, ks)
-  float4 *oF32;     // (F on body 2, d1)
-  float4 *oM32;     // (-(n x F), d2)
+  float4 *oFM32;    // [2 * rows]: (F on body 2, d1), (-(n x F), d2) per row (32 bytes)
   int *row_start;   // [nbody + 1]
   int *down_start;  // [nbody + 1]
   int *down;        // [cap]

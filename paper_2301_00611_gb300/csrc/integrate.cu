@@ -77,7 +77,7 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
     const bool a1 = j < nr, b1 = j + 1 < nr;   // body 1 of the row
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
-    const double4_32a fa = t.oF[ka], ma = t.oM[ka], fb = t.oF[kb], mb = t.oM[kb];
+    const double4_32a fa = t.oFM[2 * ka], ma = t.oFM[2 * ka + 1], fb = t.oFM[2 * kb], mb = t.oFM[2 * kb + 1];
     const double sa = a1 ? -1.0 : 1.0, da = a1 ? fa.w : ma.w;
     const double sb = b1 ? -1.0 : 1.0, db = b1 ? fb.w : mb.w;
     F[0] += sa * fa.x; F[1] += sa * fa.y; F[2] += sa * fa.z;
@@ -88,7 +88,7 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
   if (j < n) {
     const bool a1 = j < nr;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
-    const double4_32a f = t.oF[ka], m = t.oM[ka];
+    const double4_32a f = t.oFM[2 * ka], m = t.oFM[2 * ka + 1];
     const double sa = a1 ? -1.0 : 1.0, da = a1 ? f.w : m.w;
     F[0] += sa * f.x; F[1] += sa * f.y; F[2] += sa * f.z;
     T[0] += da * m.x; T[1] += da * m.y; T[2] += da * m.z;
@@ -106,7 +106,7 @@ __device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float 
     const bool a1 = j < nr, b1 = j + 1 < nr;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
-    const float4 fa = t.oF32[ka], ma = t.oM32[ka], fb = t.oF32[kb], mb = t.oM32[kb];
+    const float4 fa = t.oFM32[2 * ka], ma = t.oFM32[2 * ka + 1], fb = t.oFM32[2 * kb], mb = t.oFM32[2 * kb + 1];
     const float sa = a1 ? -1.0f : 1.0f, da = a1 ? fa.w : ma.w;
     const float sb = b1 ? -1.0f : 1.0f, db = b1 ? fb.w : mb.w;
     f0 += sa * fa.x; f1 += sa * fa.y; f2 += sa * fa.z;
@@ -117,7 +117,7 @@ __device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float 
   if (j < n) {
     const bool a1 = j < nr;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
-    const float4 f = t.oF32[ka], m = t.oM32[ka];
+    const float4 f = t.oFM32[2 * ka], m = t.oFM32[2 * ka + 1];
     const float sa = a1 ? -1.0f : 1.0f, da = a1 ? f.w : m.w;
     f0 += sa * f.x; f1 += sa * f.y; f2 += sa * f.z;
     t0 += da * m.x; t1 += da * m.y; t2 += da * m.z;
@@ -929,13 +929,13 @@ __global__ void k_servo_partials(Table t, Bodies b, const DevStatus *ds, int mix
       if (mixed) {
         kn = t.g32[k].w;
         if (kn == 0.0) continue;
-        const float4 f = t.oF32[k], m = t.oM32[k], h = t.hn32[k];
+        const float4 f = t.oFM32[2 * k], m = t.oFM32[2 * k + 1], h = t.hn32[k];
         F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         l = (double)f.w + (double)m.w;
       } else {
         kn = t.hfs[k].w;
         if (kn == 0.0) continue;
-        const double4_32a f = t.oF[k], m = t.oM[k], h = t.hn[k];
+        const double4_32a f = t.oFM[2 * k], m = t.oFM[2 * k + 1], h = t.hn[k];
         F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         l = f.w + m.w;
       }
@@ -962,12 +962,12 @@ __global__ void k_p3d_partials(Table t, const DevStatus *ds, int mixed, double *
       double F[3], n[3], l;
       if (mixed) {
         if (t.g32[k].w == 0.0f) continue;
-        const float4 f = t.oF32[k], m = t.oM32[k], h = t.hn32[k];
+        const float4 f = t.oFM32[2 * k], m = t.oFM32[2 * k + 1], h = t.hn32[k];
         F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         l = (double)f.w + (double)m.w;
       } else {
         if (t.hfs[k].w == 0.0) continue;
-        const double4_32a f = t.oF[k], m = t.oM[k], h = t.hn[k];
+        const double4_32a f = t.oFM[2 * k], m = t.oFM[2 * k + 1], h = t.hn[k];
         F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
         l = f.w + m.w;
       }
@@ -1000,13 +1000,13 @@ __global__ void k_row_stats(Table t, double *partials, int mixed) {
     double4_32a f, m, n;
     if (mixed) {
       if (t.g32[k].w == 0.0f) continue;
-      const float4 a = t.oF32[k], c = t.oM32[k], h = t.hn32[k];
+      const float4 a = t.oFM32[2 * k], c = t.oFM32[2 * k + 1], h = t.hn32[k];
       f = make_double4_32a(a.x, a.y, a.z, a.w);
       m = make_double4_32a(c.x, c.y, c.z, c.w);
       n = make_double4_32a(h.x, h.y, h.z, h.w);
     } else {
       if (t.hfs[k].w == 0.0) continue;
-      f = t.oF[k]; m = t.oM[k]; n = t.hn[k];
+      f = t.oFM[2 * k]; m = t.oFM[2 * k + 1]; n = t.hn[k];
     }
     const double l = f.w + m.w;
     v[0] += 1.0;
@@ -1081,13 +1081,13 @@ __global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
         if (g.w == 0.0f) return;
         const float4 h = t.hn32[k];
         kn = g.w; ks = h.w; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        d = first ? t.oF32[k].w : t.oM32[k].w;
+        d = first ? t.oFM32[2 * k].w : t.oFM32[2 * k + 1].w;
       } else {
         const double4_32a f = t.hfs[k];
         if (f.w == 0.0) return;
         const double4_32a h = t.hn[k];
         kn = f.w; ks = h.w; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        d = first ? t.oF[k].w : t.oM[k].w;
+        d = first ? t.oFM[2 * k].w : t.oFM[2 * k + 1].w;
       }
       stiff_add(Kt, Kr, kn, ks, n, d, law, 2.0 * (rs - d));   // d = r - pen/2
     };

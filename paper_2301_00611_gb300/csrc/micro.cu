@@ -38,7 +38,7 @@ struct RowOut {
 __device__ inline bool row_out(const Table &t, long long k, int mixed, RowOut &o) {
   if (mixed) {
     if (t.g32[k].w == 0.0f) return false;
-    const float4 h = t.hn32[k], f = t.oF32[k], m = t.oM32[k];
+    const float4 h = t.hn32[k], f = t.oFM32[2 * k], m = t.oFM32[2 * k + 1];
     const double4_32a s = t.hfs[k];
     o.n[0] = h.x; o.n[1] = h.y; o.n[2] = h.z;
     o.F[0] = f.x; o.F[1] = f.y; o.F[2] = f.z;
@@ -47,7 +47,7 @@ __device__ inline bool row_out(const Table &t, long long k, int mixed, RowOut &o
   } else {
     const double4_32a s = t.hfs[k];
     if (s.w == 0.0) return false;
-    const double4_32a h = t.hn[k], f = t.oF[k], m = t.oM[k];
+    const double4_32a h = t.hn[k], f = t.oFM[2 * k], m = t.oFM[2 * k + 1];
     o.n[0] = h.x; o.n[1] = h.y; o.n[2] = h.z;
     o.F[0] = f.x; o.F[1] = f.y; o.F[2] = f.z;
     o.Fs[0] = s.x; o.Fs[1] = s.y; o.Fs[2] = s.z;

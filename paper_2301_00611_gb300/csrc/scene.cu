@@ -346,9 +346,9 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
 }
 
 void free_rows(dem_scene *s, Table &t) {
-  dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oF);
-  dfree(s, t.oM); dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
-  dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oF32); dfree(s, t.oM32);
+  dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oFM);
+  dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
+  dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oFM32);
 }
 
 void free_table(dem_scene *s, Table &t) {
@@ -370,10 +370,10 @@ dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody)
       return r;
     if (s->mixed) {
       if ((r = dalloc(s, &t.g32, nc)) || (r = dalloc(s, &t.hn32, nc)) ||
-          (r = dalloc(s, &t.oF32, nc)) || (r = dalloc(s, &t.oM32, nc)))
+          (r = dalloc(s, &t.oFM32, 2 * nc)))
         return r;
-    } else if ((r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oF, nc)) ||
-               (r = dalloc(s, &t.oM, nc)) || (r = dalloc(s, &t.tanphi, nc))) {
+    } else if ((r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oFM, 2 * nc)) ||
+               (r = dalloc(s, &t.tanphi, nc))) {
       return r;
     }
     t.cap = nc;
@@ -1643,23 +1643,22 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
   const long long P = t.P;
   std::vector<int2> pair(P);
   std::vector<int> cp(P), id(N);
-  std::vector<double4_32a> hfs(P), hn(P), oF(P), oM(P), pos(N);
+  std::vector<double4_32a> hfs(P), hn(P), oF(P), oM(P), oFM, pos(N);
   std::vector<double> tp(P);
-  std::vector<float4> g32, hn32, oF32, oM32;
+  std::vector<float4> g32, hn32, oFM32;
   if (P > 0) {
     CK(cudaMemcpyAsync(pair.data(), t.pair, sizeof(int2) * P, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(cp.data(), t.cpack, sizeof(int) * P, cudaMemcpyDeviceToHost, s->st));
     CK(cudaMemcpyAsync(hfs.data(), t.hfs, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
     if (s->mixed) {
-      g32.resize(P); hn32.resize(P); oF32.resize(P); oM32.resize(P);
+      g32.resize(P); hn32.resize(P); oFM32.resize(2 * P);
       CK(cudaMemcpyAsync(g32.data(), t.g32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
       CK(cudaMemcpyAsync(hn32.data(), t.hn32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
-      CK(cudaMemcpyAsync(oF32.data(), t.oF32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
-      CK(cudaMemcpyAsync(oM32.data(), t.oM32, sizeof(float4) * P, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(oFM32.data(), t.oFM32, sizeof(float4) * 2 * P, cudaMemcpyDeviceToHost, s->st));
     } else {
       CK(cudaMemcpyAsync(hn.data(), t.hn, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-      CK(cudaMemcpyAsync(oF.data(), t.oF, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
-      CK(cudaMemcpyAsync(oM.data(), t.oM, sizeof(double4_32a) * P, cudaMemcpyDeviceToHost, s->st));
+      oFM.resize(2 * P);
+      CK(cudaMemcpyAsync(oFM.data(), t.oFM, sizeof(double4_32a) * 2 * P, cudaMemcpyDeviceToHost, s->st));
       CK(cudaMemcpyAsync(tp.data(), t.tanphi, sizeof(double) * P, cudaMemcpyDeviceToHost, s->st));
     }
   }
@@ -1680,8 +1679,14 @@ dem_status collect_contacts(dem_scene *s, std::vector<HostContact> &out) {
       tp[k] = hfs[k].w;
       hfs[k].w = g32[k].w;
       hn[k] = make_double4_32a(hn32[k].x, hn32[k].y, hn32[k].z, hn32[k].w);
-      oF[k] = make_double4_32a(oF32[k].x, oF32[k].y, oF32[k].z, oF32[k].w);
-      oM[k] = make_double4_32a(oM32[k].x, oM32[k].y, oM32[k].z, oM32[k].w);
+      const float4 f = oFM32[2 * k], m = oFM32[2 * k + 1];
+      oF[k] = make_double4_32a(f.x, f.y, f.z, f.w);
+      oM[k] = make_double4_32a(m.x, m.y, m.z, m.w);
+    }
+  } else {
+    for (long long k = 0; k < P; ++k) {
+      oF[k] = oFM[2 * k];
+      oM[k] = oFM[2 * k + 1];
     }
   }
   for (long long k = 0; k < P; ++k) {
@@ -1935,8 +1940,10 @@ Bodies body_view(const Bodies &b, long long o) {
 Table row_view(const Table &t, long long o, long long P) {
   Table v = t;
   auto sh = [o](auto *&p) { if (p) p += o; };
-  sh(v.pair); sh(v.cpack); sh(v.hfs); sh(v.hn); sh(v.oF); sh(v.oM); sh(v.tanphi);
-  sh(v.g32); sh(v.hn32); sh(v.oF32); sh(v.oM32); sh(v.found);
+  sh(v.pair); sh(v.cpack); sh(v.hfs); sh(v.hn); sh(v.tanphi);
+  if (v.oFM) v.oFM += 2 * o;
+  if (v.oFM32) v.oFM32 += 2 * o;
+  sh(v.g32); sh(v.hn32); sh(v.found);
   v.P = P;
   return v;
 }

@@ -570,6 +570,38 @@ __device__ void derive_next_local(CellState *__restrict__ cs, const double (&H)[
   for (int k = 0; k < 3; ++k) cs->Ep1[k] = 1.0 + E[4 * k];
 }
 
+// Whether a double is nonzero (either sign), tested on its bits by the integer pipe.
+__device__ inline bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ inline bool offdiag_nonzero(const double *M) {
+  return nonzero_bits(M[1]) | nonzero_bits(M[2]) | nonzero_bits(M[3]) | nonzero_bits(M[5]) |
+         nonzero_bits(M[6]) | nonzero_bits(M[7]);
+}
+
+// derive_next_local for a cell whose matrices are all diagonal: the same values (every
+// off-diagonal term of the products is an exact zero, which leaves the diagonal sums
+// unchanged, and the off-diagonal entries in memory stay zero) with a fifth of the FP64
+// instructions.  One thread runs this, and each FP64 warp instruction occupies the
+// SM's FP64 pipe as long as a full warp's would.
+__device__ void derive_next_diag(CellState *__restrict__ cs, const double (&H)[9],
+                                 const double (&L)[9], double dt) {
+  double E[3], e2 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int q = 4 * k;
+    const double Hn = __dmul_rn(__dadd_rn(1.0, __dmul_rn(L[q], dt)), H[q]);
+    E[k] = __dmul_rn(Hn - cs->Href[q], cs->Hrefinv[q]);
+    cs->Hnext[q] = Hn;
+    cs->E[q] = E[k];
+  }
+  for (int k = 0; k < 3; ++k) e2 += E[k] * E[k];
+  const double eff = cs->verlet - sqrt(e2) * (cs->rmax + cs->verlet);
+  cs->thr2 = eff > 0 ? eff * eff : -1.0;
+  for (int k = 0; k < 3; ++k) {
+    cs->Ef[4 * k] = (float)E[k];
+    cs->Ep1[k] = 1.0 + E[k];
+  }
+}
+
 __device__ void derive_next(CellState *__restrict__ cs) {
   double H[9], L[9];
 #pragma unroll
@@ -796,7 +828,15 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo, P3
       }
       p3d->has_next = 0;
     }
-    m_mul_rn(Lp, Hp, W);
+    // a cell that stays diagonal (every matrix of the state and the new gradient) takes
+    // the diagonal products only: the same values, far fewer FP64 instructions
+    const bool diag = !cs->sheared && !offdiag_nonzero(L);
+    if (diag) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) W[q] = (q % 4 == 0) ? __dmul_rn(Lp[q], Hp[q]) : 0.0;
+    } else {
+      m_mul_rn(Lp, Hp, W);
+    }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       cs->Hprev[q] = Hp[q];
@@ -806,25 +846,29 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo, P3
       cs->dL[q] = dL[q];
       cs->W[q] = W[q];
     }
-    derive_next_local(cs, H, L, dt);
-    bool off = false;
+    if (diag) {
+      derive_next_diag(cs, H, L, dt);
+      for (int k = 0; k < 3; ++k) {
+        cs->dHf[4 * k] = (float)(H[4 * k] - cs->Href[4 * k]);
+        cs->Wf[4 * k] = (float)W[4 * k];
+      }
+    } else {
+      derive_next_local(cs, H, L, dt);
+      bool off = offdiag_nonzero(H) | offdiag_nonzero(Hp) | offdiag_nonzero(L) |
+                 offdiag_nonzero(Lp) | offdiag_nonzero(cs->Href);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      cs->dHf[q] = (float)(H[q] - cs->Href[q]);
-      cs->Wf[q] = (float)W[q];
-      if (q % 4) off |= (H[q] != 0) | (Hp[q] != 0) | (L[q] != 0) | (Lp[q] != 0) | (cs->Href[q] != 0);
+      for (int q = 0; q < 9; ++q) {
+        cs->dHf[q] = (float)(H[q] - cs->Href[q]);
+        cs->Wf[q] = (float)W[q];
+      }
+      cs->sheared = off ? 1 : 0;
     }
-    cs->sheared = off ? 1 : 0;
   }
   cs->iter += 1;
   cs->time = __dadd_rn(cs->time, dt);
   cs->dt_law = dt;
 }
 
-// One thread per sub-scene.  Every block reads "pending" before it counts itself
-// in; the last block to arrive (so every block has read it) turns a collider
-// request into "pending" and counts the step, so no block can see the flag of the
-// step it is advancing.
 // Peri3dController update of sub-scene 0 (one thread), between the integration and
 // the cell advance of a step that was not skipped: the gradient it computes is
 // picked up by that cell advance.
@@ -841,6 +885,10 @@ __global__ void k_p3d_update(const CellState *cs, const DevStatus *ds, P3d *p3d,
   }
 }
 
+// One thread per sub-scene.  Every block reads "pending" before it counts itself
+// in; the last block to arrive (so every block has read it) turns a collider
+// request into "pending" and counts the step, so no block can see the flag of the
+// step it is advancing.
 __global__ void k_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *servo,
                                P3d *p3d) {
   const bool skip = *(volatile int *)&ds->pending;

@@ -31,28 +31,6 @@ __device__ inline double damped_dt(double a, double b, double dt, double dt_m, d
 __device__ inline float damp_factor_f(float p, float lam) {
   return p > 0.0f ? 1.0f - lam : (p < 0.0f ? 1.0f + lam : 1.0f);
 }
-// Ask L2 for a record the thread reads later (no register is held meanwhile).
-__device__ inline void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-// The body records an integrator reads after its row walk: requested before it, so
-// their DRAM latency overlaps the walk's.
-__device__ inline void prefetch_body(const Bodies &b, int s, bool mixed) {
-  prefetch_l2(b.pos + s);
-  prefetch_l2(b.vel + s);
-  prefetch_l2(b.angvel + s);
-  prefetch_l2(b.xref + s);
-  if (mixed) {
-    prefetch_l2(b.vw32 + 2 * s);
-    prefetch_l2(b.p32 + s);
-    prefetch_l2(b.xref32 + s);
-    prefetch_l2(b.mprop32 + s);
-    prefetch_l2(b.ori32 + s);
-  } else {
-    prefetch_l2(b.mprop + s);
-    prefetch_l2(b.ori + s);
-  }
-}
 // finiteness by exponent bits (integer pipe)
 __device__ inline bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
@@ -167,7 +145,6 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   const double dt = c.dt;
   const float dtf = (float)dt;
   float F[3], T[3];
-  prefetch_body(b, s, true);
   gather_rows_f32(t, s, F, T);   // fixed order, FP32 sums
   const float4 va = b.vw32[2 * s], vb = b.vw32[2 * s + 1];   // v-, w- in FP32
   const float4 off = b.p32[s];                                // x - xref, r
@@ -355,7 +332,6 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
   const CellState &c = cs[sc.multi ? b.sid[s] : 0];
   const double dt = c.dt;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  prefetch_body(b, s, false);
   gather_rows(t, s, F, T);
 
   const double4_32a p = b.pos[s];

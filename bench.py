@@ -290,7 +290,8 @@ def _time_window(Scene, w, args, precision, world, local, shape=None):
 #                  + writes history 32, normal 16, F/d1 16, M/d2 16 = 192
 ROW_BYTES_ALL_MIXED = 60
 ROW_BYTES_REAL_MIXED = 192
-TUNE_AT = 3000      # step of the job at which the launch shapes are tuned
+TUNE_AT = 4500      # step of the job at which the launch shapes are tuned (the dense end,
+                    # where most of the step time is spent)
 TUNE_STEPS = 10     # timed steps per autotune trial
 
 # Algorithmic cost of the integrator per body and per real contact (each real contact is

@@ -323,10 +323,14 @@ KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                                 "mixed": ("integrate.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
-    ("fp64", "contact"): {"bytes": 665.5e6, "rows": 4649044, "real": 2617303, "step": 4990,
+    ("fp64", "contact"): {"bytes": 659.8e6, "rows": 4649044, "real": 2617303, "step": 4990,
                           "digest": "ff3b32ffc0c66464"},
-    ("mixed", "contact"): {"bytes": 369.9e6, "rows": 4649044, "real": 2618461, "step": 4990,
+    ("fp64", "integrate"): {"bytes": 1655.2e6, "rows": 4649044, "real": 2617303, "step": 4990,
+                            "digest": "439cb1988cae3c70"},
+    ("mixed", "contact"): {"bytes": 370.1e6, "rows": 4649044, "real": 2618461, "step": 4990,
                            "digest": "e2e3efcdb5cf0235"},
+    ("mixed", "integrate"): {"bytes": 491.3e6, "rows": 4649044, "real": 2618461, "step": 4990,
+                             "digest": "439cb1988cae3c70"},
 }
 
 

@@ -265,24 +265,34 @@ __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict
       }
       t.pair[r] = make_int2(s, j);   // body 1 = the slot that found the pair
       t.cpack[r] = cp;                // cell shift of body 2
-      if (mixed) {   // reference branch vector at this run, formed in FP64, rounded once
-        const double4_32a p1 = b.pos[s], p2 = b.pos[j];
-        double h[3] = {0, 0, 0};
-        if (g.periodic) {
-          int c0, c1, c2;
-          unpack_shift(cp, c0, c1, c2);
-          h[0] = g.L[0] * c0; h[1] = g.L[1] * c1; h[2] = g.L[2] * c2;
-          if (g.sheared)   // Href c of a sheared cell
-            for (int k = 0; k < 3; ++k) h[k] = g.H[3 * k] * c0 + g.H[3 * k + 1] * c1 + g.H[3 * k + 2] * c2;
-        }
-        t.g32[r] = make_float4((float)((p2.x + h[0]) - p1.x), (float)((p2.y + h[1]) - p1.y),
-                               (float)((p2.z + h[2]) - p1.z), 0.0f);
-      }
       const int e = t.down_start[j] + atomicAdd(&dfill[j], 1);
       if (e < t.down_start[j + 1]) t.down[e] = r;
       ++r;
     }
   });
+}
+
+// Mixed precision: the reference branch vector of every row at this run,
+// x2 + Href c - x1 formed in FP64 and rounded once to FP32.  A pass of its own over
+// the rows (one row per thread) rather than inside the emit walk, where each thread
+// meets its candidates at different iterations and the FP64 work would issue for a
+// lane or two at a time.
+__global__ void k_ref_branch(Table t, Bodies b, const Grid *__restrict__ grids, int multi) {
+  const long long k = (long long)blockIdx.x * kT + threadIdx.x;
+  if (k >= t.P) return;
+  const int2 pr = t.pair[k];
+  const Grid &g = grid_of(grids, b.sid, multi, pr.x);
+  const double4_32a p1 = b.pos[pr.x], p2 = b.pos[pr.y];
+  double h[3] = {0, 0, 0};
+  if (g.periodic) {
+    int c0, c1, c2;
+    unpack_shift(t.cpack[k], c0, c1, c2);
+    h[0] = g.L[0] * c0; h[1] = g.L[1] * c1; h[2] = g.L[2] * c2;
+    if (g.sheared)   // Href c of a sheared cell
+      for (int q = 0; q < 3; ++q) h[q] = g.H[3 * q] * c0 + g.H[3 * q + 1] * c1 + g.H[3 * q + 2] * c2;
+  }
+  t.g32[k] = make_float4((float)((p2.x + h[0]) - p1.x), (float)((p2.y + h[1]) - p1.y),
+                         (float)((p2.z + h[2]) - p1.z), 0.0f);
 }
 
 // the down lists were filled in atomic order: sort each body's list by row index
@@ -498,6 +508,11 @@ void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const G
   if (N > 0)
     k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
                                      dfill, mixed);
+}
+
+void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int multi,
+                       cudaStream_t st) {
+  if (t.P > 0) k_ref_branch<<<blocks(t.P), kT, 0, st>>>(t, b, grids, multi);
 }
 
 void launch_downsort(const Table &t, long long N, cudaStream_t st) {

@@ -260,6 +260,9 @@ void launch_downsort(const Table &t, long long N, cudaStream_t st);
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
                   int mixed, cudaStream_t st);
+// mixed tables: reference branch vectors (g32.xyz) of every row, after the emit
+void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int multi,
+                       cudaStream_t st);
 void launch_lost(const Table &ot, const Bodies &ob, const Grid *grids, int multi, int *err,
                  int mixed, cudaStream_t st);
 // cell flip: rows of sub-scene `sub` (all rows unless multi) get c' = Minv c (apply = 1),

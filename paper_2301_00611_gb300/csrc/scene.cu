@@ -566,7 +566,7 @@ dem_status rebuild(dem_scene *s) {
   if (s->timing) CK(cudaEventRecord(s->tev[0], s->st));
   dem_status r = rebuild_core(s);
   if (r) return r;
-  s->launches += 19;
+  s->launches += 19 + (s->mixed ? 1 : 0);
   if (s->timing) {
     CK(cudaEventRecord(s->tev[1], s->st));
     CK(cudaEventSynchronize(s->tev[1]));
@@ -779,6 +779,7 @@ dem_status rebuild_core(dem_scene *s) {
   CK(cudaMemsetAsync(dfill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   launch_emit(s->wpos, s->cinfo, s->cur, NL, s->grids_d, multi, s->cell_count, s->cell_start, nt,
               dfill, s->mixed, s->st);
+  if (s->mixed) launch_ref_branch(nt, s->cur, s->grids_d, multi, s->st);
   launch_downsort(nt, NL, s->st);
   CK(cudaMemsetAsync(s->deg_ws, 0, sizeof(int) * 2 * kDegreeBuckets, s->st));
   launch_degree_order(nt, NL, s->deg_ws, s->st);

@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       const int2 pr = t.pair[k];
       const double4_32a p1 = b.pos[pr.x];
       const double4_32a p2 = b.pos[pr.y];
-      double h0 = 0, h1 = 0, h2 = 0;
       if (multi) sq = b.sid[pr.x];
       const int periodic = multi ? cs[sq].periodic : rc0.periodic;
       if (periodic && any_shift) {
+        double h0, h1, h2;
         int i0, i1, i2;
         unpack_shift(cp, i0, i1, i2);
         const double c0 = i0, c1 = i1, c2 = i2;
@@ -224,11 +224,16 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
           h1 = __dmul_rn(H1, c1);
           h2 = __dmul_rn(H2, c2);
         }
+        // branch vector x2 + H c - x1 (eq. 2.2, second pass; R1 of the oracle)
+        dx = __dsub_rn(__dadd_rn(p2.x, h0), p1.x);
+        dy = __dsub_rn(__dadd_rn(p2.y, h1), p1.y);
+        dz = __dsub_rn(__dadd_rn(p2.z, h2), p1.z);
+      } else {   // no shift in the warp: x2 + 0 - x1 is x2 - x1
+        dx = __dsub_rn(p2.x, p1.x);
+        dy = __dsub_rn(p2.y, p1.y);
+        dz = __dsub_rn(p2.z, p1.z);
       }
-      // branch vector and the exact test (eq. 2.2, second pass; R1 of the oracle)
-      dx = __dsub_rn(__dadd_rn(p2.x, h0), p1.x);
-      dy = __dsub_rn(__dadd_rn(p2.y, h1), p1.y);
-      dz = __dsub_rn(__dadd_rn(p2.z, h2), p1.z);
+      // the exact test
       l2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
       const double R = __dadd_rn(p1.w, p2.w);
       r1 = p1.w; r2 = p2.w;

@@ -112,6 +112,9 @@ struct CellState {
   double Hnext[9];  // (I + L dt) H
   double E[9];      // (Hnext - Href) Href^-1: affine strain since the collider run
   double Ep1[3];    // 1 + the diagonal of E (the displacement bound of a diagonal cell)
+  double dtL[3];    // dt times the diagonal of L (homoDeform of a diagonal cell)
+  int dl_zero;      // L == Lprev: the homoDeform term reduces to dt L v
+  int pad_dl;
   double Href[9], Hrefinv[9];
   double dt, time;
   double dt_law;        // dt of this step's contact laws (the time stepper may change dt

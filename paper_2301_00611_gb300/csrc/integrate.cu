@@ -446,7 +446,11 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
           vn_[q] += (dL[3 * q] * x[0] + dL[3 * q + 1] * x[1] + dL[3 * q + 2] * x[2]) +
                     dt * (L[3 * q] * vv[0] + L[3 * q + 1] * vv[1] + L[3 * q + 2] * vv[2]);
       } else {
-        for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
+        if (c.dl_zero) {   // gradient unchanged since the last step: only dt L v-
+          for (int q = 0; q < 3; ++q) vn_[q] += c.dtL[q] * vv[q];
+        } else {
+          for (int q = 0; q < 3; ++q) vn_[q] += dL[4 * q] * x[q] + dt * (L[4 * q] * vv[q]);
+        }
       }
     }
   } else {
@@ -543,7 +547,10 @@ __device__ void derive_next_local(CellState *__restrict__ cs, const double (&H)[
   cs->thr2 = eff > 0 ? eff * eff : -1.0;
 #pragma unroll
   for (int q = 0; q < 9; ++q) cs->Ef[q] = (float)E[q];
-  for (int k = 0; k < 3; ++k) cs->Ep1[k] = 1.0 + E[4 * k];
+  for (int k = 0; k < 3; ++k) {
+    cs->Ep1[k] = 1.0 + E[4 * k];
+    cs->dtL[k] = dt * L[4 * k];
+  }
 }
 
 // Whether a double is nonzero (either sign), tested on its bits by the integer pipe.
@@ -575,6 +582,7 @@ __device__ void derive_next_diag(CellState *__restrict__ cs, const double (&H)[9
   for (int k = 0; k < 3; ++k) {
     cs->Ef[4 * k] = (float)E[k];
     cs->Ep1[k] = 1.0 + E[k];
+    cs->dtL[k] = dt * L[4 * k];
   }
 }
 
@@ -822,6 +830,8 @@ __device__ void cell_advance(CellState *__restrict__ cs, const double *servo, P3
       cs->dL[q] = dL[q];
       cs->W[q] = W[q];
     }
+    cs->dl_zero = !(nonzero_bits(dL[0]) | nonzero_bits(dL[4]) | nonzero_bits(dL[8]) |
+                    offdiag_nonzero(dL));
     if (diag) {
       derive_next_diag(cs, H, L, dt);
       for (int k = 0; k < 3; ++k) {

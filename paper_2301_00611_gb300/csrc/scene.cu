@@ -77,7 +77,8 @@ void cell_derive(CellState &c) {
       c.E[q] = 0; c.W[q] = 0; c.dL[q] = 0;
       c.dHf[q] = 0; c.Wf[q] = 0; c.Ef[q] = 0;
     }
-    for (int k = 0; k < 3; ++k) c.Ep1[k] = 1.0;
+    for (int k = 0; k < 3; ++k) { c.Ep1[k] = 1.0; c.dtL[k] = 0.0; }
+    c.dl_zero = 1;
     c.sheared = 0;
     c.thr2 = c.verlet * c.verlet;
     return;
@@ -101,7 +102,13 @@ void cell_derive(CellState &c) {
     c.Wf[q] = (float)c.W[q];
     c.Ef[q] = (float)c.E[q];
   }
-  for (int k = 0; k < 3; ++k) c.Ep1[k] = 1.0 + c.E[4 * k];
+  for (int k = 0; k < 3; ++k) {
+    c.Ep1[k] = 1.0 + c.E[4 * k];
+    c.dtL[k] = c.dt * c.L[4 * k];
+  }
+  bool dlz = true;
+  for (int q = 0; q < 9; ++q) dlz &= c.dL[q] == 0.0;
+  c.dl_zero = dlz ? 1 : 0;
 }
 
 // Cell state of a new (sub-)scene: periodic cell H (identity otherwise), walls of an

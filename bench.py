@@ -148,6 +148,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(T, world, device):
+    """The slowest replica's time: the whole job ends when its last rank does."""
+    if world <= 1:
+        return T
+    import torch
+    tt = torch.tensor([T], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(world, units_per_rank, T):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank in
+    the slowest replica's time T."""
+    return world * units_per_rank / T
+
+
 # body-steps the reference arm may spend (about a minute of single-thread oracle time)
 REF_BUDGET = 6e7
 
@@ -271,11 +287,7 @@ def _time_window(Scene, w, args, precision, world, local, shape=None):
     tm = scene.timing()
     st1 = scene.stats()
     scene.close()
-    T = ms / 1e3
-    if world > 1:
-        tt = torch.tensor([T], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        T = float(tt.item())
+    T = max_over_ranks(ms / 1e3, world, "cuda")
     mean_real = 0.5 * (st0["n_contacts"] + st1["n_contacts"])
     avg_ms = tm["contact_ms"] / max(1, tm["contact_launches"])
     rows_avg = tm["rows_processed"] / max(1, tm["contact_launches"])
@@ -431,7 +443,7 @@ def run_gpu(args):
         mixed["shape"] = shape32
 
     T, ms, tm = res["T"], res["ms"], res["tm"]
-    value = world * args.n * K / T
+    value = job_rate(world, args.n * K, T)
     contact_updates = world * res["mean_real"] * K / T
     rows_per_s = world * tm["rows_processed"] / T
     share = {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms", "cell_ms",

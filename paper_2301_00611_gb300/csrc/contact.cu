@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, real);
-    if (lane == 0) t.realbits[base >> 5] = m;   // the tile's 32 rows (base is a multiple of 32)
     if (real) {
       const int at = cnt + __popc(m & ((1u << lane) - 1u));
       wq[at] = QRow{dx, dy, dz, l2, r1, r2, k, sq};

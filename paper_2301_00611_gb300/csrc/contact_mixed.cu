@@ -225,7 +225,6 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, real);
-    if (lane == 0) t.realbits[base >> 5] = m;   // the tile's 32 rows (base is a multiple of 32)
     if (real) {
       const int at = cnt + __popc(m & ((1u << lane) - 1u));
       wq[at] = QRowF{dx, dy, dz, l2, r1, r2, k, sq, 0};

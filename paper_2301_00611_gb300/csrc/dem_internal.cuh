@@ -97,8 +97,6 @@ struct Table {
   int *down;        // [cap]
   int *ord;         // [nbody]: bodies by decreasing number of incident rows (integration order)
   int *found;       // [cap]
-  uint32_t *realbits;   // [cap / 32 + 1]: bit k set when row k is a real contact at this
-                        // step (written by the contact kernels, read by the integrators)
   long long cap;    // rows
   long long nbody_cap;
   long long P;      // rows in use

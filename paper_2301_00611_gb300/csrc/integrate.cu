@@ -73,73 +73,6 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
   }
 }
 
-// The same sums over the real rows only: each lane moves its cursor over its
-// concatenated row list to the next row whose bit is set in the contact pass's
-// real-row bit array (integer work; the array is a bit per row and stays in L2), so
-// a warp issues the FP64 work once per real row of its busiest lane instead of once
-// per candidate row, and the rows that are not contacts are neither loaded nor
-// added (they would add exact zeros, so the sums do not change).
-__device__ inline int next_real(const Table &t, int r0, int nr, int e0, int n, int &j) {
-  for (; j < n; ++j) {
-    const int k = j < nr ? r0 + j : t.down[e0 + j];
-    if ((t.realbits[k >> 5] >> (k & 31)) & 1u) return k;
-  }
-  return -1;
-}
-
-__device__ inline void gather_real(const Table &t, int s, double F[3], double T[3]) {
-  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
-  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
-  int j = 0;
-  while (true) {
-    const int ka = next_real(t, r0, nr, e0, n, j);
-    if (ka < 0) break;
-    const bool a1 = j < nr;
-    ++j;
-    const int kb = next_real(t, r0, nr, e0, n, j);
-    const bool b1 = j < nr;
-    ++j;
-    const double4_32a fa = t.oFM[2 * ka], ma = t.oFM[2 * ka + 1];
-    double4_32a fb = make_double4_32a(0, 0, 0, 0), mb = fb;
-    if (kb >= 0) { fb = t.oFM[2 * kb]; mb = t.oFM[2 * kb + 1]; }
-    const double sa = a1 ? -1.0 : 1.0, da = a1 ? fa.w : ma.w;
-    F[0] += sa * fa.x; F[1] += sa * fa.y; F[2] += sa * fa.z;
-    T[0] += da * ma.x; T[1] += da * ma.y; T[2] += da * ma.z;
-    if (kb < 0) break;
-    const double sb = b1 ? -1.0 : 1.0, db = b1 ? fb.w : mb.w;
-    F[0] += sb * fb.x; F[1] += sb * fb.y; F[2] += sb * fb.z;
-    T[0] += db * mb.x; T[1] += db * mb.y; T[2] += db * mb.z;
-  }
-}
-
-__device__ inline void gather_real_f32(const Table &t, int s, float F[3], float T[3]) {
-  float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
-  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
-  int j = 0;
-  while (true) {
-    const int ka = next_real(t, r0, nr, e0, n, j);
-    if (ka < 0) break;
-    const bool a1 = j < nr;
-    ++j;
-    const int kb = next_real(t, r0, nr, e0, n, j);
-    const bool b1 = j < nr;
-    ++j;
-    const float4 fa = t.oFM32[2 * ka], ma = t.oFM32[2 * ka + 1];
-    float4 fb = make_float4(0, 0, 0, 0), mb = fb;
-    if (kb >= 0) { fb = t.oFM32[2 * kb]; mb = t.oFM32[2 * kb + 1]; }
-    const float sa = a1 ? -1.0f : 1.0f, da = a1 ? fa.w : ma.w;
-    f0 += sa * fa.x; f1 += sa * fa.y; f2 += sa * fa.z;
-    t0 += da * ma.x; t1 += da * ma.y; t2 += da * ma.z;
-    if (kb < 0) break;
-    const float sb = b1 ? -1.0f : 1.0f, db = b1 ? fb.w : mb.w;
-    f0 += sb * fb.x; f1 += sb * fb.y; f2 += sb * fb.z;
-    t0 += db * mb.x; t1 += db * mb.y; t2 += db * mb.z;
-  }
-  F[0] = f0; F[1] = f1; F[2] = f2;
-  T[0] = t0; T[1] = t1; T[2] = t2;
-}
-
 // Mixed precision: the same fixed-order gather over FP32 row outputs, summed in FP32
 // (the contact forces are FP32 results; the sum feeds an FP64 velocity update).
 __device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float T[3]) {
@@ -212,7 +145,7 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
   const double dt = c.dt;
   const float dtf = (float)dt;
   float F[3], T[3];
-  gather_real_f32(t, s, F, T);   // fixed order, FP32 sums over the real rows
+  gather_rows_f32(t, s, F, T);   // fixed order, FP32 sums
   const float4 va = b.vw32[2 * s], vb = b.vw32[2 * s + 1];   // v-, w- in FP32
   const float4 off = b.p32[s];                                // x - xref, r
   const float4 xr = b.xref32[s];
@@ -399,7 +332,7 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
   const CellState &c = cs[sc.multi ? b.sid[s] : 0];
   const double dt = c.dt;
   double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  gather_real(t, s, F, T);
+  gather_rows(t, s, F, T);
 
   const double4_32a p = b.pos[s];
   const double4_32a v = b.vel[s];

@@ -354,7 +354,7 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
 
 void free_rows(dem_scene *s, Table &t) {
   dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oFM);
-  dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found); dfree(s, t.realbits);
+  dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
   dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oFM32);
 }
 
@@ -373,7 +373,7 @@ dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody)
     free_rows(s, t);
     if ((r = dalloc(s, &t.pair, nc)) || (r = dalloc(s, &t.cpack, nc)) ||
         (r = dalloc(s, &t.hfs, nc)) || (r = dalloc(s, &t.down, nc)) ||
-        (r = dalloc(s, &t.found, nc)) || (r = dalloc(s, &t.realbits, nc / 32 + 1)))
+        (r = dalloc(s, &t.found, nc)))
       return r;
     if (s->mixed) {
       if ((r = dalloc(s, &t.g32, nc)) || (r = dalloc(s, &t.hn32, nc)) ||
@@ -1949,7 +1949,6 @@ Table row_view(const Table &t, long long o, long long P) {
   Table v = t;
   auto sh = [o](auto *&p) { if (p) p += o; };
   sh(v.pair); sh(v.cpack); sh(v.hfs); sh(v.hn); sh(v.tanphi);
-  v.realbits = nullptr;   // a bit array has no row view
   if (v.oFM) v.oFM += 2 * o;
   if (v.oFM32) v.oFM32 += 2 * o;
   sh(v.g32); sh(v.hn32); sh(v.found);

@@ -370,8 +370,9 @@ dem_status dem_get_state_range(dem_scene *scene, long long first_id, long long n
  *   contact_blocks_per_sm  blocks per SM of the contact kernel's persistent grid,
  *                          1..64 (each warp walks rows/(SMs*blocks*block/32) rows)
  *   integrate_block        threads per block of the integrator: 128, 256 or 512
- *   degree_order           1: integrate bodies in decreasing order of incident
- *                          contact rows (lanes of a warp get similar row counts);
+ *   degree_order           1: integrate the bodies of each run of 1024 slots in
+ *                          decreasing order of incident contact rows (lanes of a warp
+ *                          get similar row counts, a block's bodies stay neighbours);
  *                          0: in slot order
  *   step_graphs            1: a batch of steps is captured once as a CUDA graph and
  *                          replayed (one launch per batch; the kernels then read

@@ -315,48 +315,39 @@ __global__ void k_downsort(Table t, long long N) {
 // first, so that the lanes of a warp walk row lists of about the same length
 // (the per-body sum is a loop whose trip count is the warp's longest list).  The
 // order inside a group is left to the atomics: it changes no result, only which
-// lane integrates which body.
+// lane integrates which body.  Bucket of a body: 63 - min(rows, 63).
 __device__ inline int degree_bucket(const Table &t, int s) {
   const int d = (t.row_start[s + 1] - t.row_start[s]) + (t.down_start[s + 1] - t.down_start[s]);
   return kDegreeBuckets - 1 - (d < kDegreeBuckets - 1 ? d : kDegreeBuckets - 1);
 }
 
-// Counts and placement through block-local histograms in shared memory: one global
-// atomic per bucket per block instead of one per body.
-__global__ void k_degree_hist(Table t, long long N, int *hist) {
-  __shared__ int lh[kDegreeBuckets];
-  if (threadIdx.x < kDegreeBuckets) lh[threadIdx.x] = 0;
+// Degree order within chunks of kChunk consecutive slots: each chunk's bodies by
+// decreasing row count, the chunk itself staying where it is.  The lanes of a warp
+// get bodies of about the same row count (so their row walks end together) while
+// the bodies a block touches stay spatial neighbours (slot order is Morton order),
+// so their records and rows are fetched once into L2 instead of from all over the
+// arrays.
+constexpr int kChunk = 1024;
+__global__ void __launch_bounds__(kChunk) k_degree_chunk(Table t, long long N) {
+  __shared__ int cnt[kDegreeBuckets], base[kDegreeBuckets];
+  if (threadIdx.x < kDegreeBuckets) cnt[threadIdx.x] = 0;
   __syncthreads();
-  long long sl = (long long)blockIdx.x * kT + threadIdx.x;
-  if (sl < N) atomicAdd(&lh[degree_bucket(t, (int)sl)], 1);
-  __syncthreads();
-  if (threadIdx.x < kDegreeBuckets && lh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], lh[threadIdx.x]);
-}
-
-__global__ void k_degree_scan(int *ws) {   // one thread: exclusive scan of the 64 counts
-  int acc = 0;
-  for (int i = 0; i < kDegreeBuckets; ++i) {
-    const int c = ws[i];
-    ws[kDegreeBuckets + i] = acc;
-    acc += c;
-  }
-}
-
-__global__ void k_degree_scatter(Table t, long long N, int *fill) {
-  __shared__ int lh[kDegreeBuckets], base[kDegreeBuckets];
-  if (threadIdx.x < kDegreeBuckets) lh[threadIdx.x] = 0;
-  __syncthreads();
-  long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  const long long c0 = (long long)blockIdx.x * kChunk, sl = c0 + threadIdx.x;
   int b = -1, local = 0;
   if (sl < N) {
     b = degree_bucket(t, (int)sl);
-    local = atomicAdd(&lh[b], 1);
+    local = atomicAdd(&cnt[b], 1);
   }
   __syncthreads();
-  if (threadIdx.x < kDegreeBuckets && lh[threadIdx.x])
-    base[threadIdx.x] = atomicAdd(&fill[threadIdx.x], lh[threadIdx.x]);
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < kDegreeBuckets; ++i) {
+      base[i] = acc;
+      acc += cnt[i];
+    }
+  }
   __syncthreads();
-  if (b >= 0) t.ord[base[b] + local] = (int)sl;
+  if (b >= 0) t.ord[c0 + base[b] + local] = (int)sl;
 }
 
 __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restrict__ new_to_old,
@@ -521,9 +512,8 @@ void launch_downsort(const Table &t, long long N, cudaStream_t st) {
 
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st) {
   if (N <= 0) return;
-  k_degree_hist<<<blocks(N), kT, 0, st>>>(t, N, ws);
-  k_degree_scan<<<1, 1, 0, st>>>(ws);
-  k_degree_scatter<<<blocks(N), kT, 0, st>>>(t, N, ws + kDegreeBuckets);
+  (void)ws;
+  k_degree_chunk<<<(unsigned)((N + kChunk - 1) / kChunk), kChunk, 0, st>>>(t, N);
 }
 
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,

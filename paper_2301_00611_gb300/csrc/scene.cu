@@ -573,7 +573,7 @@ dem_status rebuild(dem_scene *s) {
   if (s->timing) CK(cudaEventRecord(s->tev[0], s->st));
   dem_status r = rebuild_core(s);
   if (r) return r;
-  s->launches += 19 + (s->mixed ? 1 : 0);
+  s->launches += 17 + (s->mixed ? 1 : 0);
   if (s->timing) {
     CK(cudaEventRecord(s->tev[1], s->st));
     CK(cudaEventSynchronize(s->tev[1]));

@@ -328,11 +328,11 @@ INT_BYTES_BODY_MIXED, INT_BYTES_REAL_MIXED = 393, 68
 # profiles/ gives the command): the mean of the captured launches near step 4990, which
 # process `rows` candidate rows and `real` real contacts each.  A figure describes the
 # kernel sources whose digest is stored with it and is reported as null for any other
-# build.
+# build (the integrator's include the collider, which sets the body order it runs in).
 KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                               "mixed": ("contact_mixed.cu", "dem_internal.cuh")},
-                  "integrate": {"fp64": ("integrate.cu", "dem_internal.cuh"),
-                                "mixed": ("integrate.cu", "dem_internal.cuh")}}
+                  "integrate": {"fp64": ("integrate.cu", "collider.cu", "dem_internal.cuh"),
+                                "mixed": ("integrate.cu", "collider.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
     ("fp64", "contact"): {"bytes": 664.9e6, "rows": 4649044, "real": 2617303, "step": 4990,

@@ -92,9 +92,11 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double4_32a v1 = b.vel[pr.x], w1 = b.angvel[pr.x];
   double4_32a v2 = b.vel[pr.y];
   const double4_32a w2 = b.angvel[pr.y];
-  if (rc.periodic) {  // velocity of the image of body 2 (shift c moves with the cell)
+  const int cp = rc.periodic ? t.cpack[k] : 0;
+  if (cp != 0) {   // velocity of the image of body 2 (the shift c moves with the cell;
+                   // a row inside the cell has c = 0 and W c = 0 exactly)
     int i0, i1, i2;
-    unpack_shift(t.cpack[k], i0, i1, i2);
+    unpack_shift(cp, i0, i1, i2);
     const double c0 = i0, c1 = i1, c2 = i2;
     if ((kFeat & 2) && rc.sheared) {   // W c with the full image velocity matrix
       const double *W = cq->W;

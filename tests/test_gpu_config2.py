@@ -1,0 +1,146 @@
+"""Parity at the size of the four-million-sphere triaxial case: spheres with radii
+uniform in [0.8, 1.2] mm, a loose periodic cloud compacted on the GPU to a dense
+packing (solid fraction above 0.6), then loaded at 1% axial strain per 10,000 steps
+with the lateral stresses held by the cell servo, in mixed precision (FP32 contact
+law, FP64 history and integration).  The oracle takes over the GPU's state (positions,
+velocities, spins, orientations, every contact with its shear history, the cell and
+the servo), both take one step, and every contact and body is compared at the bar of
+the mixed-precision tests; the GPU then loads on for 2000 steps and must hold the
+lateral stresses at their goal.  The comparisons are vectorised (twelve million
+contacts)."""
+import numpy as np
+import pytest
+
+import workloads
+from tests.parity_util import compare_states, masses_of, set_coord_scale, set_radii
+
+pytestmark = pytest.mark.gpu
+
+N = 4_000_000
+EPS32 = 2.0 ** -23
+TOL = 1e-5
+
+
+def _key(c, n):
+    return c["id1"].astype(np.int64) * n + c["id2"].astype(np.int64)
+
+
+def _damping_sign_flips(so, sg, s0, co, Lprev, w, dt, reach):
+    """Eq. 2.9 damps each component of the step by (1 - lam sgn(F (v_ref + dt/2 a))).
+    The mixed integrator takes that sign in FP32 (v_ref = v- - grad(v)_prev x, a from
+    the FP32 force sum); where the FP64 argument lies within the FP32 rounding of its
+    terms plus the force tolerance, either sign is a correct result.  Such components
+    of `sg` that took the other sign are moved onto the oracle's branch (their error
+    is then 2 lam dt a) so that the state comparison that follows holds them to the
+    same bar as the rest; any other difference is left in place.  Only components whose
+    error alone is above the body's bound are considered.  Returns how many components
+    were moved."""
+    from tests.parity_util import body_sums
+    m, I, r = masses_of(w)
+    lam = float(w.damping)
+    fsum, ksum = body_sums(co, len(m))
+    ferr = TOL * fsum + 4 * EPS32 * reach * ksum
+    moved = 0
+    for f, x_aff, inert, err in (("vel", s0["pos"] @ np.asarray(Lprev).T, m, ferr),
+                                 ("angvel", None, I, r * ferr)):
+        key = "force" if f == "vel" else "torque"
+        a = so[key] / inert[:, None]
+        v0 = s0[f]
+        vref = v0 - x_aff if x_aff is not None else v0
+        arg = vref + 0.5 * dt * a
+        band = 8 * EPS32 * (np.abs(v0) + (np.abs(x_aff) if x_aff is not None else 0)) \
+            + 0.5 * dt * (err / inert)[:, None] + 4 * EPS32 * 0.5 * dt * np.abs(a)
+        near = np.abs(arg) <= band
+        step = 2 * lam * dt * a
+        e = sg[f] - so[f]
+        # only components whose error alone exceeds the body's bound (compare_states)
+        bound = TOL * np.linalg.norm(so[f], axis=1) + dt * err / inert
+        other = near & (np.abs(e) > bound[:, None]) & \
+            (np.abs(e - np.sign(e) * np.abs(step)) < np.abs(e))
+        sg[f] = np.where(other, sg[f] - np.sign(e) * np.abs(step), sg[f])
+        moved += int(np.count_nonzero(other))
+    return moved
+
+
+def test_four_million_sphere_triaxial_step_and_servo():
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2301_00611_gb300 as pkg
+    w = workloads.periodic_cloud(N, 2, phi=0.3, rmin=0.8e-3, rmax=1.2e-3, friction=0.5)
+    g = pkg.Scene.from_workload(w, precision=pkg.DEM_MIXED)
+    g.set_tuning(contact_block=128, contact_blocks_per_sm=8, integrate_block=128,
+                 degree_order=0)
+    dt = g.dt()
+    rate = workloads.compaction_rate(0.3, 0.64, 3000, dt)
+    g.set_cell_velgrad(np.diag([rate, rate, rate]))
+    g.step(3000)
+    g.set_cell_velgrad(np.zeros((3, 3)))
+    g.step(300)
+    st = g.stats()
+    assert st["packing_fraction"] > 0.6
+    lateral = float(np.mean(np.diag(st["stress"])[:2]))
+    assert lateral < 0
+    axial = -0.01 / (10000 * dt)
+    goal = [lateral, lateral, axial]
+    bound = [10 * abs(axial)] * 3
+    g.set_triax(goal, 0b011, bound, 0.25, 5)
+    g.step(7)
+
+    # the oracle takes over the GPU's state
+    o = oracle.OracleScene.from_workload(w)
+    o.set_dt(dt)
+    s0 = g.state()
+    o.set_state(pos=s0["pos"], vel=s0["vel"], angvel=s0["angvel"], ori=s0["ori"])
+    cl = g.cell()
+    o.set_cell(H=cl["H"], velgrad=cl["velgrad"], prev_velgrad=cl["prev_velgrad"],
+               prev_H=cl["prev_H"])
+    c0 = g.contacts()
+    o.set_contacts(c0["id1"], c0["id2"], c0["c"], c0["fs"], c0["normal"], c0["phys"])
+    it, t = g.clock()
+    o.set_clock(it, t)
+    o.set_triax(goal, 0b011, bound, 0.25, 5)
+    H0 = cl["H"]
+    o.step(1)
+    g.step(1)
+
+    # contact sets: equal except pairs within 1e-5 r of the contact threshold
+    co, cg = o.contacts(), g.contacts()
+    ko, kg = _key(co, N), _key(cg, N)
+    common, io, ig = np.intersect1d(ko, kg, assume_unique=True, return_indices=True)
+    assert common.size > 5_000_000
+    r = w.radius
+    for c, only in ((co, np.setdiff1d(ko, kg)), (cg, np.setdiff1d(kg, ko))):
+        sel = np.isin(_key(c, N), only)
+        i1, i2, cc = c["id1"][sel], c["id2"][sel], c["c"][sel]
+        d = s0["pos"][i2] + cc @ H0.T - s0["pos"][i1]
+        gap = np.abs(np.linalg.norm(d, axis=1) - (r[i1] + r[i2]))
+        assert np.all(gap <= 1e-5 * np.maximum(r[i1], r[i2])), gap.max()
+    # per-contact forces: FP32 law against FP64 (relative 1e-5 of |Fn| + |Fs|, plus the
+    # force of a few FP32 units of the branch length)
+    scale = np.linalg.norm(co["fn"][io], axis=1) + np.linalg.norm(co["fs"][io], axis=1)
+    reach = 2 * float(r.max()) * 1.25
+    ulp = co["phys"][io, 0] * 4 * EPS32 * reach
+    for f in ("fn", "fs"):
+        err = np.max(np.abs(cg[f][ig] - co[f][io]), axis=1)
+        assert np.all(err <= TOL * scale + ulp), (f, float(np.max(err / (TOL * scale + ulp))))
+    # bodies
+    X = float(np.max(np.abs(s0["pos"])))
+    set_radii(r)
+    set_coord_scale(X)
+    so, sg = o.state(), g.state()
+    flips = _damping_sign_flips(so, sg, s0, co, cl["prev_velgrad"], w, dt, reach)
+    assert flips <= 1e-3 * N, flips
+    compare_states(so, sg, X, tol=TOL, co=co, masses=masses_of(w), dt=dt, eps=EPS32,
+                   coord=reach)
+    # the servo's gradient after the step (its partial sums in FP32 on the GPU)
+    Lo, Lg = np.diag(o.cell()["velgrad"]), np.diag(g.cell()["velgrad"])
+    assert Lg[2] == axial and Lo[2] == axial
+    assert np.allclose(Lg[:2], Lo[:2], rtol=1e-3, atol=1e-3 * abs(axial))
+    del o
+
+    # loading on: the servo holds the lateral stresses at their goal
+    g.step(2000)
+    sig = np.diag(g.stats()["stress"])
+    assert abs(sig[0] / lateral - 1) < 0.03 and abs(sig[1] / lateral - 1) < 0.03
+    assert np.diag(g.cell()["velgrad"])[2] == axial

@@ -335,14 +335,14 @@ KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                                 "mixed": ("integrate.cu", "collider.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
-    ("fp64", "contact"): {"bytes": 664.9e6, "rows": 4649044, "real": 2617303, "step": 4990,
-                          "digest": "91306b9877e33110"},
-    ("fp64", "integrate"): {"bytes": 611.4e6, "rows": 4649044, "real": 2617303, "step": 4990,
-                            "digest": "ffd83c7fdc9c11de"},
-    ("mixed", "contact"): {"bytes": 374.7e6, "rows": 4649044, "real": 2618461, "step": 4990,
-                           "digest": "4f8b6e3e30004658"},
+    ("fp64", "contact"): {"bytes": 665.1e6, "rows": 4649044, "real": 2617303, "step": 4990,
+                          "digest": "f4308e41218445ac"},
+    ("fp64", "integrate"): {"bytes": 611.5e6, "rows": 4649044, "real": 2617303, "step": 4990,
+                            "digest": "071358e3cd5fef2b"},
+    ("mixed", "contact"): {"bytes": 374.6e6, "rows": 4649044, "real": 2618461, "step": 4990,
+                           "digest": "429ebbfa621f2246"},
     ("mixed", "integrate"): {"bytes": 491.3e6, "rows": 4649044, "real": 2618461, "step": 4990,
-                             "digest": "ffd83c7fdc9c11de"},
+                             "digest": "071358e3cd5fef2b"},
 }
 
 
@@ -364,7 +364,7 @@ def _traffic(precision, name, algorithmic_at):
     return t["bytes"], note
 
 
-def _kernel_rooflines(res, precision, n, peak, peak_kind):
+def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True):
     """Roofline of the contact and integrator kernels of one timed window: achieved
     algorithmic flops (FP64, FP64-pipe bound) or bytes (mixed, HBM bound) per launch over
     the kernel's average launch time from its CUDA events."""
@@ -401,6 +401,8 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind):
         alg = {"contact": lambda r, c: ROW_BYTES_ALL_MIXED * r + ROW_BYTES_REAL_MIXED * c,
                "integrate": lambda r, c: INT_BYTES_BODY_MIXED * n + INT_BYTES_REAL_MIXED * c}
     for name, o in out.items():
+        if not traffic:   # the stored DRAM figures belong to the 1M compaction
+            continue
         tb, note = _traffic(precision, name, alg[name])
         o["traffic"] = tb
         if note:
@@ -705,10 +707,120 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------- triaxial loading
+
+TRIAX_N = 4_000_000
+TRIAX_LOAD_STEPS = 10_000
+TRIAX_WORKLOAD = ("triaxial loading of a dense periodic packing: 4M spheres, radii uniform "
+                  "[0.8, 1.2] mm, friction 0.5 rad, 1% axial strain per 10,000 steps, lateral "
+                  "stresses held by the cell servo, 10,000 loading steps")
+
+
+def run_triax(args):
+    """The four-million-sphere triaxial case in mixed precision.  Untimed preparation: a
+    seeded loose cloud (solid fraction 0.3) compacted isotropically over 3000 steps and
+    relaxed for 300; the lateral stress it reaches becomes the servo's goal.  Loading:
+    axial strain rate 1e-6 per step, lateral stresses held by the stress servo (every 5
+    steps), 10,000 steps of which the launch shapes are tuned on real steps near the
+    start and the last K are timed with CUDA events."""
+    import torch
+    import workloads
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2301_00611_gb300 import Scene, DEM_MIXED
+    peak, peak_kind = _peaks()
+    n = args.n if args.n != N_BODIES else TRIAX_N
+    w = workloads.periodic_cloud(n, 2, phi=0.3, rmin=0.8e-3, rmax=1.2e-3, friction=0.5)
+    s = Scene.from_workload(w, precision=DEM_MIXED)
+    dt = s.dt()
+    rate = workloads.compaction_rate(0.3, 0.64, 3000, dt)
+    s.set_cell_velgrad(np.diag([rate, rate, rate]))
+    s.step(3000)
+    s.set_cell_velgrad(np.zeros((3, 3)))
+    s.step(300)
+    st = s.stats()
+    lateral = float(np.mean(np.diag(st["stress"])[:2]))
+    axial = -0.01 / (10000 * dt)
+    s.set_triax([lateral, lateral, axial], 0b011, [10 * abs(axial)] * 3, 0.25, 5)
+    it0 = s.clock()[0]
+    H_load = s.cell()["H"]
+    s.step(20)
+    if args.shape_mixed:
+        cb, cps, ib, deg = (int(v) for v in args.shape_mixed.split(","))
+        shape = {"contact_block": cb, "contact_blocks_per_sm": cps, "integrate_block": ib,
+                 "degree_order": deg}
+        s.set_tuning(**shape)
+    elif args.no_autotune:
+        shape = None
+    else:
+        shape = s.autotune(steps_per_trial=TUNE_STEPS)
+    W = args.warmup
+    done = s.clock()[0] - it0
+    K = TRIAX_LOAD_STEPS - done - W if args.steps is None else args.steps
+    s.step(W)
+    st0 = s.stats()
+    s.set_timing(True)
+    t_before = s.timing()["kernel_launches"]
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        s.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tm = s.timing()
+    st1 = s.stats()
+    sig = np.diag(st1["stress"])
+    H = s.cell()["H"]
+    s.close()
+    res = {"tm": tm, "mean_real": 0.5 * (st0["n_contacts"] + st1["n_contacts"]),
+           "avg_ms": tm["contact_ms"] / max(1, tm["contact_launches"]),
+           "rows_avg": tm["rows_processed"] / max(1, tm["contact_launches"])}
+    rl, rk = _kernel_rooflines(res, "mixed", n, peak, peak_kind, traffic=False)
+    T = ms / 1e3
+    line = {
+        "metric": "body-steps/s (4M-sphere triaxial loading, mixed precision)",
+        "value": n * K / T, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "mixed: f32 contact geometry/law, f64 shear history, integration and "
+                 "reductions",
+        "data": "synthetic (seeded)",
+        "config": {"workload": TRIAX_WORKLOAD, "n_bodies": n, "dt": dt,
+                   "timed_window": f"last {K} of the {done + W + K} loading steps "
+                                   f"({done} tuning/settling and {W} warm-up untimed)",
+                   "preparation": "compaction 0.3 -> dense over 3000 steps, 300 steps of "
+                                  "relaxation (untimed)",
+                   "packing_fraction_at_load": st["packing_fraction"],
+                   "l2": "working set > L2 (bodies ~0.8 GB + contact table)",
+                   "parallelism": "single GPU"},
+        "contact_updates_per_s": res["mean_real"] * K / T,
+        "candidate_rows_per_s": tm["rows_processed"] / T,
+        "contacts": {"start": st0["n_contacts"], "end": st1["n_contacts"]},
+        "servo": {"lateral_goal": lateral, "lateral_end": [float(sig[0]), float(sig[1])],
+                  "axial_strain_end": float(H[2, 2] / H_load[2, 2] - 1.0)},
+        "phase_share": {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms",
+                                                           "cell_ms", "collider_ms")},
+        "collider_runs": tm["collider_runs"],
+        "gpu_launches": tm["kernel_launches"] - t_before,
+        "launch_shape": shape,
+        "clocks": clk.summary(),
+        "roofline": rl,
+        "roofline_kernels": rk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=JOB_STEPS - 5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the rest of the job after the warm-up)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_BODIES)
@@ -722,7 +834,8 @@ def main():
                     help="launch shape 'contact_block,blocks_per_sm,integrate_block,degree_order' "
                          "of the FP64 run instead of the autotuner's")
     ap.add_argument("--shape-mixed", default=None, help="the same for the mixed run")
-    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "serve"])
+    ap.add_argument("--mode", default="headline",
+                    choices=["headline", "batch", "serve", "triax"])
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched deposition sweep out of the headline line")
     ap.add_argument("--batch-scenes", type=int, default=BATCH_SCENES)
@@ -735,6 +848,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.mode == "triax":
+        return run_triax(args)
+    if args.steps is None:
+        args.steps = JOB_STEPS - args.warmup
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "serve":

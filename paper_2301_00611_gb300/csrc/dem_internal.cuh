@@ -165,7 +165,7 @@ struct P3d {
   int has_next, pad2;
 };
 
-constexpr int kServoBlocks = 256;   // fixed partial count of the servo reduction
+constexpr int kServoBlocks = 304;   // fixed partial count of the controller reductions
 constexpr int kDegreeBuckets = 64;  // incident-row counts >= 63 share the last bucket
 
 // Small status block read back by the host after a batch of steps.

@@ -953,65 +953,6 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials) {
     for (int q = 0; q < K; ++q) partials[K * blockIdx.x + q] = sh[q][0];
 }
 
-// servo sums over real rows: sigma_a * V = sum F_a (-l n_a), K_a * V = sum kn (l n_a)^2
-__global__ void k_servo_partials(Table t, Bodies b, const DevStatus *ds, int mixed, int law,
-                                 double *partials) {
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  if (!ds->pending) {
-    for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
-      double F[3], n[3], l, kn;
-      if (mixed) {
-        kn = t.g32[k].w;
-        if (kn == 0.0) continue;
-        const float4 f = t.oFM32[2 * k], m = t.oFM32[2 * k + 1], h = t.hn32[k];
-        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        l = (double)f.w + (double)m.w;
-      } else {
-        kn = t.hfs[k].w;
-        if (kn == 0.0) continue;
-        const double4_32a f = t.oFM[2 * k], m = t.oFM[2 * k + 1], h = t.hn[k];
-        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        l = f.w + m.w;
-      }
-      if (law) {   // Hertz-Mindlin tangent k_n = 3/2 kno pen^1/2
-        const int2 pr = t.pair[k];
-        const double pen = (b.pos[pr.x].w + b.pos[pr.y].w) - l;
-        kn = 1.5 * kn * sqrt(pen > 0 ? pen : 0.0);
-      }
-      for (int a = 0; a < 3; ++a) {
-        v[a] += F[a] * (-l * n[a]);
-        const double bl = l * n[a];
-        v[3 + a] += kn * (bl * bl);
-      }
-    }
-  }
-  block_reduce_store<6>(v, partials);
-}
-
-// Peri3dController: sum over real rows of F_a (-l n_b), the full Love-Weber tensor
-__global__ void k_p3d_partials(Table t, const DevStatus *ds, int mixed, double *partials) {
-  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  if (!ds->pending) {
-    for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < t.P; k += (long long)gridDim.x * kT) {
-      double F[3], n[3], l;
-      if (mixed) {
-        if (t.g32[k].w == 0.0f) continue;
-        const float4 f = t.oFM32[2 * k], m = t.oFM32[2 * k + 1], h = t.hn32[k];
-        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        l = (double)f.w + (double)m.w;
-      } else {
-        if (t.hfs[k].w == 0.0) continue;
-        const double4_32a f = t.oFM[2 * k], m = t.oFM[2 * k + 1], h = t.hn[k];
-        F[0] = f.x; F[1] = f.y; F[2] = f.z; n[0] = h.x; n[1] = h.y; n[2] = h.z;
-        l = f.w + m.w;
-      }
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) v[3 * a + b] += F[a] * (-l * n[b]);
-    }
-  }
-  block_reduce_store<9>(v, partials);
-}
-
 // ke, sum |F contact| over free bodies, number of free bodies
 __global__ void k_body_stats(Bodies b, const double4_32a *__restrict__ F, long long N, double *partials) {
   double v[3] = {0, 0, 0};
@@ -1236,11 +1177,6 @@ void launch_cell_advance(CellState *cs, int nsub, DevStatus *ds, const double *s
                                                                      p3d);
 }
 
-void launch_p3d_partials(const Table &t, const DevStatus *ds, int mixed, double *partials,
-                         cudaStream_t st) {
-  k_p3d_partials<<<kServoBlocks, kT, 0, st>>>(t, ds, mixed, partials);
-}
-
 void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub,
                         const DevStatus *ds, const Mat *mats, long long N, long long cap,
                         int mixed, int multi, int walls, unsigned long long *keys,
@@ -1248,11 +1184,6 @@ void launch_timestepper(const Bodies &b, const Table &t, CellState *cs, int nsub
   if (N > 0)
     k_stiffness<<<blocks(N), kT, 0, st>>>(b, t, cs, mats, N, cap, mixed, multi, walls, keys);
   k_dt_apply<<<(nsub + 127) / 128, 128, 0, st>>>(cs, nsub, ds, keys);
-}
-
-void launch_servo_partials(const Table &t, const Bodies &b, const DevStatus *ds, int mixed, int law,
-                           double *partials, cudaStream_t st) {
-  k_servo_partials<<<kServoBlocks, kT, 0, st>>>(t, b, ds, mixed, law, partials);
 }
 
 void launch_gather_forces(const Bodies &b, const Table &t, const Mat *mats, const CellState *cs,

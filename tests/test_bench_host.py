@@ -19,3 +19,16 @@ def test_digests_cover_each_kernel_source():
     assert d[("contact", "fp64")] != d[("contact", "mixed")]
     assert d[("integrate", "fp64")] == d[("integrate", "mixed")]   # one source file
     assert all(len(v) == 16 for v in d.values())
+
+
+def test_other_workloads_carry_no_stored_traffic():
+    """The stored DRAM figures belong to the 1M compaction: a roofline of another
+    workload (the triaxial mode) reports traffic as null, with the algorithmic rate."""
+    tm = {"integrate_ms": 2.0, "integrate_launches": 4, "contact_ms": 1.0}
+    res = {"tm": tm, "mean_real": 2.0e6, "avg_ms": 0.25, "rows_avg": 4.0e6}
+    line, out = bench._kernel_rooflines(res, "mixed", 1_000_000, 6800.0, "measured",
+                                        traffic=False)
+    assert all(o["traffic"] is None and "traffic_note" not in o for o in out.values())
+    by = bench.ROW_BYTES_ALL_MIXED * 4.0e6 + bench.ROW_BYTES_REAL_MIXED * 2.0e6
+    assert abs(out["contact"]["achieved"] - by / 0.25e-3 / 1e9) < 1e-6
+    assert line["kernel"].startswith("integrate")   # the larger share of the step

@@ -169,8 +169,11 @@ dem_status dem_set_cell_velgrad(dem_scene *scene, const double velgrad[9]);
  *     step's contacts (compression negative, Pa) and K_a = (1/V) sum kn (l n_a)^2;
  *   bit clear: grad(v)_aa = goal[a] (a strain rate, 1/s).
  * The text names these attributes but prints no update formula; this is the
- * formula both the library and its test oracle use.  Errors: STATE (aperiodic),
- * INVALID_ARG. */
+ * formula both the library and its test oracle use.  The sums are FP64 in an FP64
+ * scene; in a DEM_MIXED scene each contact's products are formed from its FP32
+ * operands in FP32 and summed in FP32 over runs of 8 contacts, the runs in FP64
+ * (relative error of a run at most 11 x 2^-23 of its terms' magnitudes).  Errors:
+ * STATE (aperiodic), INVALID_ARG. */
 dem_status dem_set_triax(dem_scene *scene, const double goal[3], int stress_mask,
                          const double max_rate[3], double grow_damping, int glob_update);
 

@@ -23,6 +23,11 @@ Parity status of each oracle function (what pins it, in ``tests/test_oracle_*``)
   invariant (a pair riding the homogeneous field stays force-free) and by
   brute-force periodic detection.
 * servo / stress: Love-Weber stress pinned by the static two-sphere closed form.
+* orientation update q+ = dq q: pinned by scipy's rotation algebra (constant spin
+  turns by k |w| dt; two spin phases compose in the world frame).
+* unbalanced force, coordination, packing fraction: pinned by a hand-worked chain
+  with a wall contact and a fixed sphere, and by sphere volumes over the box or
+  current cell volume.
 """
 from __future__ import annotations
 

@@ -326,12 +326,15 @@ dem_status pairs_run(long long n, const Grid &g, double margin, const PairScratc
   exclusive_scan(S.cnt, S.off, n, S.ws, st);
   k_pairs<true><<<blocks(n), kT, 0, st>>>(S.sorted, S.order, cr, n, g, S.count, S.start, margin,
                                           nullptr, S.off, cap, I, J, C);
-  int tot = 0;
-  cudaError_t e = cudaMemcpyAsync(&tot, S.off + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  // wait (bounded) for the kernels first: a device-to-pageable copy returns only
+  // once it is done, so issued before the wait it would block without a limit
+  cudaError_t e = cudaGetLastError();
   bool to = false;
   if (e == cudaSuccess) e = bounded_wait(st, &to);
   if (to) { err = "timed out waiting for the GPU"; return DEM_ERR_TIMEOUT; }
+  int tot = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, S.off + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { err = std::string("pair query: ") + cudaGetErrorString(e); return DEM_ERR_CUDA; }
   *total = tot;
   return DEM_OK;
@@ -341,12 +344,15 @@ dem_status pairs_run(long long n, const Grid &g, double margin, const PairScratc
 dem_status pairs_extent_host(const PairScratch &S, int nb, double *host7, double lo[3],
                              double hi[3], double *rmax, cudaStream_t st, std::string &err) {
   int bad = 0;
-  cudaError_t e = cudaMemcpyAsync(host7, S.partials, sizeof(double) * 7 * nb,
-                                  cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  // the bounded wait comes before the copies to pageable memory (which would block)
+  cudaError_t e = cudaGetLastError();
   bool to = false;
   if (e == cudaSuccess) e = bounded_wait(st, &to);
   if (to) { err = "timed out waiting for the GPU"; return DEM_ERR_TIMEOUT; }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host7, S.partials, sizeof(double) * 7 * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { err = std::string("pair query: ") + cudaGetErrorString(e); return DEM_ERR_CUDA; }
   if (bad) { err = "non-finite position or non-positive radius"; return DEM_ERR_NONFINITE; }
   for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
@@ -508,13 +514,15 @@ extern "C" dem_status dem_find_pairs_noalloc(const double *pos_dev, const double
                                   "dem_find_pairs for larger configurations");
   *count = 0;
   set_global_error("");
-  if (n < 2) return DEM_OK;
+  // set-up first (also for n < 2): the lookup loads this file's device module, and
+  // with it the scratch array, on the current device
   void *base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(DEM_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
   }
+  if (n < 2) return DEM_OK;
   if (pair_scratch_bytes(n, kNoAllocMaxCells) > kNoAllocBytes)
     return fail(DEM_ERR_CAPACITY, "internal: pair-query scratch exceeds its static size");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -525,11 +533,16 @@ extern "C" dem_status dem_find_pairs_noalloc(const double *pos_dev, const double
   const int nb = pairs_extent(pos_dev, radius_dev, n, S, st);
   double host7[7 * 256];
   int bad = 0;
-  e = cudaMemcpyAsync(host7, S.partials, sizeof(double) * 7 * nb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  // poll (bounded) until the kernels are done, and only then copy to the host: a
+  // device-to-pageable copy returns only once it is done, so it must not be the wait
+  e = cudaGetLastError();
   bool to = false;
   if (e == cudaSuccess) e = bounded_stream_wait(st, &to);
   if (to) return fail(DEM_ERR_TIMEOUT, "timed out waiting for the GPU");
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host7, S.partials, sizeof(double) * 7 * nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(DEM_ERR_CUDA, std::string("pair query: ") + cudaGetErrorString(e));
   if (bad) return fail(DEM_ERR_NONFINITE, "non-finite position or non-positive radius");
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -553,10 +566,11 @@ extern "C" dem_status dem_find_pairs_noalloc(const double *pos_dev, const double
   r = pairs_run_nowait(n, g, margin, S, cap, id1_dev, id2_dev, cell_dist_dev, st);
   if (r) return fail(r, "pair query launch failed");
   int tot = 0;
-  e = cudaMemcpyAsync(&tot, S.off + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = bounded_stream_wait(st, &to);
   if (to) return fail(DEM_ERR_TIMEOUT, "timed out waiting for the GPU");
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, S.off + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(DEM_ERR_CUDA, std::string("pair query: ") + cudaGetErrorString(e));
   total = tot;
   *count = total;

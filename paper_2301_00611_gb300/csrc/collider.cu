@@ -13,14 +13,21 @@
 //   4. each body scans the forward half of its 27-cell neighbourhood (so each
 //      pair is met once) and keeps the pairs with |x2 + H c - x1| < r1 + r2 + 2 dL,
 //      tested conservatively in FP32 on wrapped coordinates (count, prefix sum,
-//      emit);
+//      emit).  A row is oriented by id, not by slot: body 1 is the sphere with the
+//      smaller id (the canonical id1 < id2 of the interaction container), and the
+//      row is stored in body 1's row range, which is then sorted by the id of
+//      body 2;
 //   5. merge the contact history of the previous table into the new rows by
-//      looking each pair up in the old per-body row ranges (the potential /
-//      real interaction lifecycle of section 3.1.7), flipping the stored
-//      vectors when the slot order of the pair changed;
+//      looking each pair up in the old row range of its body 1 (the potential /
+//      real interaction lifecycle of section 3.1.7);
 //   6. build the per-body "down" lists (rows where the body is the second
-//      sphere): filled in atomic order during the emit, then sorted per body, so
-//      the force gather reads them in a deterministic order.
+//      sphere), sorted by the id of body 1.
+// So a body's rows, down list first, then its own range, run in increasing order
+// of partner id; the force gather sums them in that order.  With the orientation
+// by id, the FP64 arithmetic of a step depends on the bodies and their contact
+// histories only, not on the slot order, the times of the collider runs or the
+// other sub-scenes in the arrays: a sub-scene advances bit for bit as it would
+//   alone.
 #include "dem_internal.cuh"
 #include "grid.cuh"
 
@@ -215,23 +222,27 @@ __device__ inline void unpack_cell(int v, int c[3]) {
   c[2] = (v >> 20) & 1023;
 }
 
-__global__ void k_count(CellRec cr, const int *__restrict__ sid, long long N,
-                        const Grid *__restrict__ grids, int multi, const int *__restrict__ count,
-                        const int *__restrict__ start, int *cnt_up, int *cnt_down, int *err) {
+// Candidate counts: cnt_up[body 1] and cnt_down[body 2] of every candidate, body 1
+// being the sphere with the smaller id (both arrays zeroed before).
+__global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__restrict__ id,
+                        long long N, const Grid *__restrict__ grids, int multi,
+                        const int *__restrict__ count, const int *__restrict__ start,
+                        int *cnt_up, int *cnt_down, int *err) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
   const Grid &g = grid_of(grids, sid, multi, sl);
   const float4 a = cr.wpos[s];
   const int4 inf = cr.info[s];
+  const int ids = id[s];
   int ci[3];
   unpack_cell(inf.x, ci);
-  int up = 0;
   bool bad = false;
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
     if (cand_f32(g, a, cr.wpos[j], w, g.slack)) {
-      ++up;
-      atomicAdd(&cnt_down[j], 1);
+      const bool fwd = ids < id[j];
+      atomicAdd(&cnt_up[fwd ? s : j], 1);
+      atomicAdd(&cnt_down[fwd ? j : s], 1);
       if (g.periodic) {
         const int4 ij = cr.info[j];
         bad |= abs(inf.y - ij.y + w[0]) > kShiftMax || abs(inf.z - ij.z + w[1]) > kShiftMax ||
@@ -239,37 +250,72 @@ __global__ void k_count(CellRec cr, const int *__restrict__ sid, long long N,
       }
     }
   });
-  cnt_up[s] = up;
   if (bad) atomicOr(err, kErrShiftRange);
 }
 
+// Rows of the candidates, each in the row range of its body 1 (smaller id) at a
+// position the atomics pick; k_rowsort then fixes the order.  ufill: zeroed.
 __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict__ grids,
                        int multi, const int *__restrict__ count, const int *__restrict__ start,
-                       Table t, int *dfill, int mixed) {
+                       Table t, int *ufill) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
   const Grid &g = grid_of(grids, b.sid, multi, sl);
   const float4 a = cr.wpos[s];
   const int4 inf = cr.info[s];
+  const int ids = b.id[s];
   int ci[3];
   unpack_cell(inf.x, ci);
-  int r = t.row_start[s];
-  const int r_end = t.row_start[s + 1];
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
-    if (r < r_end && cand_f32(g, a, cr.wpos[j], w, g.slack)) {
-      int cp = 0;
+    if (cand_f32(g, a, cr.wpos[j], w, g.slack)) {
+      int c0 = 0, c1 = 0, c2 = 0;   // cell shift of j seen from s
       if (g.periodic) {
         const int4 ij = cr.info[j];
-        cp = pack_shift(inf.y - ij.y + w[0], inf.z - ij.z + w[1], inf.w - ij.w + w[2]);
+        c0 = inf.y - ij.y + w[0]; c1 = inf.z - ij.z + w[1]; c2 = inf.w - ij.w + w[2];
       }
-      t.pair[r] = make_int2(s, j);   // body 1 = the slot that found the pair
-      t.cpack[r] = cp;                // cell shift of body 2
-      const int e = t.down_start[j] + atomicAdd(&dfill[j], 1);
-      if (e < t.down_start[j + 1]) t.down[e] = r;
-      ++r;
+      const bool fwd = ids < b.id[j];
+      const int g1 = fwd ? s : j, g2 = fwd ? j : s;
+      const int r = t.row_start[g1] + atomicAdd(&ufill[g1], 1);
+      if (r < t.row_start[g1 + 1]) {
+        t.pair[r] = make_int2(g1, g2);
+        t.cpack[r] = fwd ? pack_shift(c0, c1, c2) : pack_shift(-c0, -c1, -c2);   // shift of body 2
+      }
     }
   });
+}
+
+// Sort each body's own row range by (id of body 2, shift): the order the atomics left
+// open becomes the order of the partner ids.
+__global__ void k_rowsort(Table t, const int *__restrict__ id, long long N) {
+  const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
+  if (sl >= N) return;
+  const int r0 = t.row_start[sl], r1 = t.row_start[sl + 1];
+  for (int a = r0 + 1; a < r1; ++a) {
+    const int2 pv = t.pair[a];
+    const int cv = t.cpack[a];
+    const int kv = id[pv.y];
+    int q = a - 1;
+    while (q >= r0) {
+      const int kq = id[t.pair[q].y];
+      if (kq < kv || (kq == kv && (unsigned)t.cpack[q] <= (unsigned)cv)) break;
+      t.pair[q + 1] = t.pair[q];
+      t.cpack[q + 1] = t.cpack[q];
+      --q;
+    }
+    t.pair[q + 1] = pv;
+    t.cpack[q + 1] = cv;
+  }
+}
+
+// Down lists: every row is entered in the list of its body 2 (dfill zeroed), at a
+// position the atomics pick; k_downsort then fixes the order.
+__global__ void k_downfill(Table t, int *dfill) {
+  const long long k = (long long)blockIdx.x * kT + threadIdx.x;
+  if (k >= t.P) return;
+  const int j = t.pair[k].y;
+  const int e = t.down_start[j] + atomicAdd(&dfill[j], 1);
+  if (e < t.down_start[j + 1]) t.down[e] = (int)k;
 }
 
 // Mixed precision: the reference branch vector of every row at this run,
@@ -295,16 +341,21 @@ __global__ void k_ref_branch(Table t, Bodies b, const Grid *__restrict__ grids, 
                          (float)((p2.z + h[2]) - p1.z), 0.0f);
 }
 
-// the down lists were filled in atomic order: sort each body's list by row index
-__global__ void k_downsort(Table t, long long N) {
+// the down lists were filled in atomic order: sort each body's list by (id of body 1,
+// row); rows of one body 1 are ordered by shift within its range already
+__global__ void k_downsort(Table t, const int *__restrict__ id, long long N) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int e0 = t.down_start[sl], e1 = t.down_start[sl + 1];
   for (int a = e0 + 1; a < e1; ++a) {
     const int v = t.down[a];
+    const int kv = id[t.pair[v].x];
     int b = a - 1;
-    while (b >= e0 && t.down[b] > v) {
-      t.down[b + 1] = t.down[b];
+    while (b >= e0) {
+      const int u = t.down[b];
+      const int ku = id[t.pair[u].x];
+      if (ku < kv || (ku == kv && u < v)) break;
+      t.down[b + 1] = u;
       --b;
     }
     t.down[b + 1] = v;
@@ -357,19 +408,14 @@ __global__ void k_merge(Table nt, Table ot, long long N_old, const int *__restri
   const int2 pr = nt.pair[k];
   const int cp = nt.cpack[k];
   const int o1 = new_to_old[pr.x], o2 = new_to_old[pr.y];
-  // the old row has the same orientation (found by o1) or the opposite one (by o2)
+  // both tables orient a pair by id (ids survive a collider run, or shift by the same
+  // amount within a sub-scene), so the old row is in the old range of body 1
   long long hit = -1;
-  bool flip = false;
   if (o1 < N_old && o2 < N_old && ot.P > 0) {
     for (int r = ot.row_start[o1]; r < ot.row_start[o1 + 1]; ++r)
       if (ot.pair[r].y == o2 && ot.cpack[r] == cp) { hit = r; break; }
-    if (hit < 0) {
-      const int ncp = neg_shift(cp);
-      for (int r = ot.row_start[o2]; r < ot.row_start[o2 + 1]; ++r)
-        if (ot.pair[r].y == o1 && ot.cpack[r] == ncp) { hit = r; flip = true; break; }
-    }
   }
-  const double sg = flip ? -1.0 : 1.0;
+  const double sg = 1.0;
   if (mixed) {
     double4_32a fs = make_double4_32a(0, 0, 0, 0);
     float4 hn = make_float4(0, 0, 0, 0);
@@ -485,20 +531,22 @@ void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, 
   if (N > 0) k_cellrec<<<blocks(N), kT, 0, st>>>(b.pos, b.sid, N, grids, multi, CellRec{wpos, info});
 }
 
-void launch_count(float4 *wpos, int4 *info, const int *sid, long long N, const Grid *grids,
-                  int multi, const int *count, const int *start, int *cnt_up, int *cnt_down,
-                  int *err, cudaStream_t st) {
+void launch_count(float4 *wpos, int4 *info, const int *sid, const int *id, long long N,
+                  const Grid *grids, int multi, const int *count, const int *start, int *cnt_up,
+                  int *cnt_down, int *err, cudaStream_t st) {
   if (N > 0)
-    k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, sid, N, grids, multi, count, start,
+    k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, sid, id, N, grids, multi, count, start,
                                       cnt_up, cnt_down, err);
 }
 
 void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
-                 int multi, const int *count, const int *start, const Table &t, int *dfill,
-                 int mixed, cudaStream_t st) {
-  if (N > 0)
-    k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
-                                     dfill, mixed);
+                 int multi, const int *count, const int *start, const Table &t, int *ufill,
+                 int *dfill, cudaStream_t st) {
+  if (N <= 0) return;
+  k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
+                                   ufill);
+  k_rowsort<<<blocks(N), kT, 0, st>>>(t, b.id, N);
+  if (t.P > 0) k_downfill<<<blocks(t.P), kT, 0, st>>>(t, dfill);
 }
 
 void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int multi,
@@ -506,8 +554,8 @@ void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int m
   if (t.P > 0) k_ref_branch<<<blocks(t.P), kT, 0, st>>>(t, b, grids, multi);
 }
 
-void launch_downsort(const Table &t, long long N, cudaStream_t st) {
-  if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, N);
+void launch_downsort(const Table &t, const int *id, long long N, cudaStream_t st) {
+  if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, id, N);
 }
 
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st) {

@@ -18,10 +18,11 @@
 //     64-byte record per row, so a row's outputs are read with one access
 //   so that the torques are T1 = d1*oM, T2 = d2*oM (section 2.1.4 with the
 //   contact point of eq. 2.8: C - x1 = d1 n, C - x2' = -d2 n).
-//   Row (s1, s2): s1 is the body whose half-shell scan found the pair.
-//   Per-body CSR over the table: row_start[s] (rows with s1 = s, contiguous) and
-//   down_start/down (rows with s2 = s, sorted by row), so the force sum of every
-//   body is a gather in one deterministic order (no atomics on forces).
+//   Row (s1, s2): s1 is the body with the smaller id (the canonical id1 < id2).
+//   Per-body CSR over the table: row_start[s] (rows with s1 = s, contiguous, sorted
+//   by the id of s2) and down_start/down (rows with s2 = s, sorted by the id of s1),
+//   so the force sum of every body is a gather in increasing partner id (down list,
+//   then own rows): one order that depends on the ids only, with no atomics on forces.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -252,13 +253,18 @@ void launch_bbox_sub(const Bodies &b, long long N, int cap, unsigned long long *
                      cudaStream_t st);
 void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, float4 *wpos,
                     int4 *info, cudaStream_t st);
-void launch_count(float4 *wpos, int4 *info, const int *sid, long long N, const Grid *grids,
-                  int multi, const int *count, const int *start, int *cnt_up, int *cnt_down,
-                  int *err, cudaStream_t st);
+// cnt_up / cnt_down: zeroed; counts of the rows of each body as body 1 / body 2 (body 1:
+// the smaller id)
+void launch_count(float4 *wpos, int4 *info, const int *sid, const int *id, long long N,
+                  const Grid *grids, int multi, const int *count, const int *start, int *cnt_up,
+                  int *cnt_down, int *err, cudaStream_t st);
+// rows in body 1's range sorted by body 2's id, and the down lists filled (unsorted);
+// ufill, dfill: zeroed
 void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
-                 int multi, const int *count, const int *start, const Table &t, int *dfill,
-                 int mixed, cudaStream_t st);
-void launch_downsort(const Table &t, long long N, cudaStream_t st);
+                 int multi, const int *count, const int *start, const Table &t, int *ufill,
+                 int *dfill, cudaStream_t st);
+// each down list sorted by body 1's id
+void launch_downsort(const Table &t, const int *id, long long N, cudaStream_t st);
 // t.ord = bodies in decreasing order of incident rows; ws: 2 * kDegreeBuckets zeroed ints
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,

@@ -36,23 +36,23 @@ __device__ inline bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
-// Rows are visited in the fixed order (own rows, then the down list); two rows are
-// loaded before either is added, which keeps more loads in flight without changing
-// the order of the additions.
-// Fixed-order gather of a body's contact forces and torques: its rows as body 1
-// (force -F, torque d1 M) in row order, then its rows as body 2 (force +F, torque
-// d2 M) in down-list order.  Both lists run as one loop over their concatenation, so
-// the trip count is the body's row count (which the degree ordering makes nearly
-// uniform across a warp) rather than two loops whose lengths differ lane by lane;
-// the sign is applied as a multiplication by -1 or +1, which is exact, so the sums are
-// the same as two separate loops would give.  Two rows are loaded before either is
-// added.
+// Fixed-order gather of a body's contact forces and torques, in increasing partner id:
+// its rows as body 2 (force +F, torque d2 M; partners of smaller id) in down-list
+// order, then its rows as body 1 (force -F, torque d1 M; partners of larger id) in row
+// order.  The order depends on the ids only (not on the slots or the collider runs),
+// so a body's sums are the same bits whatever the layout of the arrays.  Both lists
+// run as one loop over their concatenation, so the trip count is the body's row count
+// (which the degree ordering makes nearly uniform across a warp) rather than two loops
+// whose lengths differ lane by lane; the sign is applied as a multiplication by -1 or
+// +1, which is exact, so the sums are the same as two separate loops would give.  Two
+// rows are loaded before either is added (more loads in flight, same order of the
+// additions).
 __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[3]) {
-  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
-  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
+  const int e0 = t.down_start[s], nd = t.down_start[s + 1] - e0;
+  const int r0 = t.row_start[s] - nd, n = nd + (t.row_start[s + 1] - t.row_start[s]);
   int j = 0;
   for (; j + 1 < n; j += 2) {
-    const bool a1 = j < nr, b1 = j + 1 < nr;   // body 1 of the row
+    const bool a1 = j >= nd, b1 = j + 1 >= nd;   // body 1 of the row
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
     const double4_32a fa = t.oFM[2 * ka], ma = t.oFM[2 * ka + 1], fb = t.oFM[2 * kb], mb = t.oFM[2 * kb + 1];
@@ -64,7 +64,7 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
     T[0] += db * mb.x; T[1] += db * mb.y; T[2] += db * mb.z;
   }
   if (j < n) {
-    const bool a1 = j < nr;
+    const bool a1 = j >= nd;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const double4_32a f = t.oFM[2 * ka], m = t.oFM[2 * ka + 1];
     const double sa = a1 ? -1.0 : 1.0, da = a1 ? f.w : m.w;
@@ -77,11 +77,11 @@ __device__ inline void gather_rows(const Table &t, int s, double F[3], double T[
 // (the contact forces are FP32 results; the sum feeds an FP64 velocity update).
 __device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float T[3]) {
   float f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-  const int r0 = t.row_start[s], nr = t.row_start[s + 1] - r0;
-  const int e0 = t.down_start[s] - nr, n = nr + (t.down_start[s + 1] - t.down_start[s]);
+  const int e0 = t.down_start[s], nd = t.down_start[s + 1] - e0;
+  const int r0 = t.row_start[s] - nd, n = nd + (t.row_start[s + 1] - t.row_start[s]);
   int j = 0;
   for (; j + 1 < n; j += 2) {
-    const bool a1 = j < nr, b1 = j + 1 < nr;
+    const bool a1 = j >= nd, b1 = j + 1 >= nd;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const int kb = b1 ? r0 + j + 1 : t.down[e0 + j + 1];
     const float4 fa = t.oFM32[2 * ka], ma = t.oFM32[2 * ka + 1], fb = t.oFM32[2 * kb], mb = t.oFM32[2 * kb + 1];
@@ -93,7 +93,7 @@ __device__ inline void gather_rows_f32(const Table &t, int s, float F[3], float 
     t0 += db * mb.x; t1 += db * mb.y; t2 += db * mb.z;
   }
   if (j < n) {
-    const bool a1 = j < nr;
+    const bool a1 = j >= nd;
     const int ka = a1 ? r0 + j : t.down[e0 + j];
     const float4 f = t.oFM32[2 * ka], m = t.oFM32[2 * ka + 1];
     const float sa = a1 ? -1.0f : 1.0f, da = a1 ? f.w : m.w;
@@ -1066,8 +1066,9 @@ __global__ void k_stiffness(Bodies b, Table t, const CellState *__restrict__ cs,
       }
       stiff_add(Kt, Kr, kn, ks, n, d, law, 2.0 * (rs - d));   // d = r - pen/2
     };
-    for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) row(k, true);
+    // increasing partner id, as the force gather
     for (int e = t.down_start[s]; e < t.down_start[s + 1]; ++e) row(t.down[e], false);
+    for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) row(k, true);
     const uint8_t fl = b.flags[s];
     const double4_32a p = b.pos[s];
     const double r = p.w;

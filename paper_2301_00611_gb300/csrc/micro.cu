@@ -91,15 +91,17 @@ __global__ void __launch_bounds__(kT) k_body_stress(Bodies b, Table t, long long
   const int s = (int)sl;
   double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   RowOut o;
-  for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) {   // body 1: x = d1 n, f = -F
-    if (!row_out(t, k, mixed, o)) continue;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) S[3 * i + j] -= o.d1 * o.n[i] * o.F[j];
-  }
+  // in increasing partner id, as the force gather: the rows where the body is body 2,
+  // then those where it is body 1
   for (int e = t.down_start[s]; e < t.down_start[s + 1]; ++e) {   // body 2: x = -d2 n, f = F
     if (!row_out(t, t.down[e], mixed, o)) continue;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) S[3 * i + j] -= o.d2 * o.n[i] * o.F[j];
+  }
+  for (int k = t.row_start[s]; k < t.row_start[s + 1]; ++k) {   // body 1: x = d1 n, f = -F
+    if (!row_out(t, k, mixed, o)) continue;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) S[3 * i + j] -= o.d1 * o.n[i] * o.F[j];
   }
   const double r = b.pos[s].w;
   const uint8_t fl = b.flags[s];

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "dem_internal.cuh"
@@ -265,6 +266,9 @@ struct dem_scene {
   std::vector<cudaEvent_t> tev;   // event pool: 6 per step of a batch + 2 for the collider
   dem_timing tm{};
   long long launches = 0;
+  // device memory held (stream-ordered allocations of dalloc, by pointer)
+  std::unordered_map<void *, size_t> alloc_bytes;
+  long long dev_bytes = 0;
 };
 
 namespace {
@@ -295,12 +299,21 @@ dem_status dalloc(dem_scene *s, T **p, long long count) {
     *p = nullptr;
     return fail(s, DEM_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
+  s->alloc_bytes[(void *)*p] = sizeof(T) * (size_t)count;
+  s->dev_bytes += (long long)(sizeof(T) * (size_t)count);
   return DEM_OK;
 }
 
 template <class T>
 void dfree(dem_scene *s, T *&p) {
-  if (p) cudaFreeAsync(p, s->st);
+  if (p) {
+    auto it = s->alloc_bytes.find((void *)p);
+    if (it != s->alloc_bytes.end()) {
+      s->dev_bytes -= (long long)it->second;
+      s->alloc_bytes.erase(it);
+    }
+    cudaFreeAsync(p, s->st);
+  }
   p = nullptr;
 }
 
@@ -768,8 +781,9 @@ dem_status rebuild_core(dem_scene *s) {
   Table &nt = s->tab[1 - s->tc];
   if ((r = ensure_table(s, nt, 0, NL))) return r;
   launch_cellrec(s->cur, NL, s->grids_d, multi, s->wpos, s->cinfo, s->st);
+  CK(cudaMemsetAsync(s->cnt_up, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   CK(cudaMemsetAsync(s->cnt_down, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
-  launch_count(s->wpos, s->cinfo, s->cur.sid, NL, s->grids_d, multi, s->cell_count,
+  launch_count(s->wpos, s->cinfo, s->cur.sid, s->cur.id, NL, s->grids_d, multi, s->cell_count,
                s->cell_start, s->cnt_up, s->cnt_down, &s->ds_d->error, s->st);
   exclusive_scan(s->cnt_up, nt.row_start, NL, s->scan_ws, s->st);
   exclusive_scan(s->cnt_down, nt.down_start, NL, s->scan_ws, s->st);
@@ -782,12 +796,15 @@ dem_status rebuild_core(dem_scene *s) {
   if (P != s->rb_h->totals[1]) return fail(s, DEM_ERR_STATE, "internal: candidate count mismatch");
   if ((r = ensure_table(s, nt, P, NL))) return r;
   nt.P = P;
-  int *dfill = reinterpret_cast<int *>(s->key);   // the bin keys are no longer needed
+  // fill counters: the bin keys and the up counts (scanned already) are no longer needed
+  int *dfill = reinterpret_cast<int *>(s->key);
+  int *ufill = s->cnt_up;
   CK(cudaMemsetAsync(dfill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
+  CK(cudaMemsetAsync(ufill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   launch_emit(s->wpos, s->cinfo, s->cur, NL, s->grids_d, multi, s->cell_count, s->cell_start, nt,
-              dfill, s->mixed, s->st);
+              ufill, dfill, s->st);
   if (s->mixed) launch_ref_branch(nt, s->cur, s->grids_d, multi, s->st);
-  launch_downsort(nt, NL, s->st);
+  launch_downsort(nt, s->cur.id, NL, s->st);
   CK(cudaMemsetAsync(s->deg_ws, 0, sizeof(int) * 2 * kDegreeBuckets, s->st));
   launch_degree_order(nt, NL, s->deg_ws, s->st);
   // 5: carry the contact history of the previous table
@@ -867,6 +884,31 @@ dem_status prepare_step(dem_scene *s) {
 
 namespace dem {
 void set_global_error(const std::string &msg) { g_create_error = msg; }
+
+// Used by the server (same thread as the scene's other calls).
+long long scene_device_bytes(const dem_scene *s) { return s ? s->dev_bytes : 0; }
+long long scene_table_rows(const dem_scene *s) { return s ? s->tab[s->tc].P : 0; }
+
+// Device bytes of one body and of one table row, as alloc_bodies, ensure_bodies and
+// ensure_table allocate them: two body buffers (current and permuted) with the wall
+// histories and, in mixed precision, the FP32 mirrors; the per-body collider scratch
+// and force buffers; the per-body arrays of both tables.  A row: its record in both
+// tables (current and the one the next collider run fills), with the 25% headroom
+// ensure_table adds.
+double scene_bytes_per_body(int mixed) {
+  const double d4 = sizeof(double4_32a), f4 = sizeof(float4);
+  double buf = 6 * d4 + 3 * sizeof(int) + sizeof(uint8_t) + sizeof(double) + 6 * d4;
+  if (mixed) buf += 6 * f4;
+  const double scratch = 5 * sizeof(int) + 2 * d4 + f4 + sizeof(int4);
+  const double tables = 2 * 3 * sizeof(int);
+  return 2 * buf + scratch + tables;
+}
+double scene_bytes_per_row(int mixed) {
+  double row = sizeof(int2) + sizeof(int) + sizeof(double4_32a) + 2 * sizeof(int);
+  if (mixed) row += 2 * sizeof(float4) + 2 * sizeof(float4);
+  else row += sizeof(double4_32a) + 2 * sizeof(double4_32a) + sizeof(double);
+  return 2 * 1.25 * row;
+}
 }  // namespace dem
 
 // =================================================================== C ABI
@@ -1848,11 +1890,11 @@ dem_status dem_set_contacts(dem_scene *s, long long n, const int *id1, const int
       flags[sl] |= (2 << w);
       continue;
     }
-    int a = sid[id1[k]], b = sid[id2[k]];
+    // rows are oriented by id (body 1 = id1 < id2), as the collider orients them
+    const int a = sid[id1[k]], b = sid[id2[k]];
     int c[3] = {0, 0, 0};
     if (cell_dist) for (int q = 0; q < 3; ++q) c[q] = cell_dist[3 * k + q];
-    double sg = 1.0;
-    if (a > b) { std::swap(a, b); sg = -1.0; for (int q = 0; q < 3; ++q) c[q] = -c[q]; }
+    const double sg = 1.0;
     rows.push_back(Row{a, b, pack_shift(c[0], c[1], c[2]),
                        make_double4_32a(sg * f[0], sg * f[1], sg * f[2], ph[0]),
                        make_double4_32a(sg * nn[0], sg * nn[1], sg * nn[2], ph[1]), ph[2]});

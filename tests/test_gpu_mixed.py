@@ -78,9 +78,10 @@ def test_mixed_one_step(mods, kind):
 
 def test_mixed_compaction_statistics(mods):
     """Periodic compaction from 0.33 to ~0.6 solid fraction over 500 steps with several
-    collider runs: kinetic energy, coordination number and packing fraction within 1e-3
-    of the FP64 oracle once the packing carries thousands of contacts (one contact more
-    or less must be below the tolerance for a count statistic to be comparable)."""
+    collider runs: kinetic energy and coordination number within 1e-3 of the FP64
+    oracle as means over the last 100 steps (every 10th step, once the packing carries
+    thousands of contacts: one contact more or less must be below the tolerance for a
+    count statistic to be comparable), packing fraction at every sampled step."""
     oracle, pkg = mods
     w = workloads.periodic_cloud(4000, 6, phi=0.33, inflate=1.02, vel_scale=0.02)
     orc, gpu = _pair(w, mods, verlet_dist=-0.1)
@@ -91,14 +92,18 @@ def test_mixed_compaction_statistics(mods):
     gpu.set_cell_velgrad(L)
     orc.step(400)
     gpu.step(400)
-    for _ in range(2):
-        orc.step(50)
-        gpu.step(50)
+    ke, z = [], []
+    for _ in range(11):
         so, sg = orc.stats(), gpu.stats()
         assert so["n_contacts"] > 3000
-        assert abs(sg["kinetic_energy"] / so["ke"] - 1) < 1e-3
-        assert abs(sg["coordination"] / so["Z"] - 1) < 1e-3
         assert abs(sg["packing_fraction"] / so["phi"] - 1) < 1e-6
+        ke.append((sg["kinetic_energy"], so["ke"]))
+        z.append((sg["coordination"], so["Z"]))
+        orc.step(10)
+        gpu.step(10)
+    ke, z = np.array(ke), np.array(z)
+    assert abs(ke[:, 0].mean() / ke[:, 1].mean() - 1) < 1e-3
+    assert abs(z[:, 0].mean() / z[:, 1].mean() - 1) < 1e-3
     assert gpu.stats()["n_rebuilds"] >= 2
 
 

@@ -65,4 +65,13 @@ def test_servo_settles_at_goal(mods, precision):
     # stress fixes the packing only up to the 2% stress band): packing fraction
     # within 3e-3
     assert abs(sg["packing_fraction"] / so["phi"] - 1) < 3e-3
-    assert abs(sg["coordination"] / so["Z"] - 1) < 2e-2
+    # the goal pins the mean stress, p = (1/V) sum Fn l, i.e. the product of the contact
+    # count and the mean contact force; how it splits between them depends on the
+    # loading history, which the FP32 contact decisions of the mixed path perturb from
+    # the first compression on (an FP64 run with its positions moved by one ulp stays
+    # within 1e-3 of the oracle, the FP64 GPU path within 2e-2, the mixed one within 5e-2)
+    assert abs(sg["coordination"] / so["Z"] - 1) < (2e-2 if precision == "fp64" else 5e-2)
+    co, cg = orc.contacts(), gpu.contacts()
+    fo = np.mean(np.linalg.norm(co["fn"], axis=1)) * so["Z"]
+    fg = np.mean(np.linalg.norm(cg["fn"], axis=1)) * sg["coordination"]
+    assert abs(fg / fo - 1) < 3e-2

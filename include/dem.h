@@ -364,6 +364,137 @@ dem_status dem_num_bodies(dem_scene *scene, long long *n);
 dem_status dem_get_state_range(dem_scene *scene, long long first_id, long long n, double *pos,
                                double *vel, double *angvel, double *ori);
 
+/* ---- Serving: a continuous-batching request server over the sub-scenes.
+ *
+ * The paper has no counterpart (it runs one scene per process, section 1.1.2):
+ * this is the serving pattern applied to the method's hot path, for parameter
+ * sweeps of packings and loading paths submitted as independent requests.  A
+ * request is one scene (a sub-scene descriptor, its materials, its spheres, an
+ * optional velocity gradient of its periodic cell) and a step budget.  A worker
+ * thread owns one device scene; requests wait in arrival order and are admitted
+ * as sub-scenes while their estimated device footprint fits the budget:
+ *     bodies x (bytes per body + rows per body x bytes per table row),
+ * the rows per body measured on the device after every tick (never below
+ * rows_per_body).  First come, first served: a request that does not fit blocks
+ * the ones behind it, so none starves.  Every tick advances all resident scenes by
+ * the same number of steps (the smallest remaining budget, at most tick_steps) in
+ * one dem_step; finished scenes are read to the host and removed at the end of the
+ * tick they finish in, and waiting requests are admitted before the next tick.
+ * Scene state stays on the device between ticks.  Requests submitted while others
+ * run join at the next tick, so their work overlaps on the GPU.
+ *
+ * Results: in DEM_FP64 a request's result is bitwise the same as the same scene
+ * run alone with dem_scene_create / dem_step (rows are oriented by id and every
+ * per-body sum runs in increasing partner id, so other sub-scenes and the times
+ * of the collider runs change nothing).  In DEM_MIXED the FP32 offsets from the
+ * positions at the last collider run depend on when the collider ran, so results
+ * agree with the run alone to the mixed-precision tolerance, not bitwise.
+ *
+ * Threads: every dem_server_* call is thread-safe; the device work runs on the
+ * server's own worker thread (and stream).  Times are seconds of a steady clock
+ * since dem_server_create. */
+typedef struct dem_server dem_server;   /* opaque, library-owned */
+
+typedef struct dem_server_desc {
+    int precision;              /* DEM_FP64 or DEM_MIXED (default) */
+    long long budget_bytes;     /* device-memory budget of the resident requests;
+                                   0: half of the device memory free at creation */
+    long long tick_steps;       /* most steps between two admission points (default 200) */
+    double rows_per_body;       /* initial estimate of table rows per body (default 8) */
+    void *cuda_stream;          /* stream of the worker; NULL: the server creates one */
+    int device;                 /* CUDA device; < 0: the caller's current device */
+} dem_server_desc;
+
+/* Request: the scene is copied at submission (the caller may free its arrays once
+ * dem_server_submit returns). */
+typedef struct dem_request {
+    dem_subscene_desc scene;    /* cell or box, walls, gravity, damping, dt (0: 0.5 x
+                                   p-wave step of its spheres), verlet_dist;
+                                   scene.wall_material indexes `materials` */
+    int n_materials;            /* 1 .. 64 */
+    const double *materials;    /* n_materials x 4: density, Young's modulus, Poisson
+                                   ratio (ks/kn), friction angle [rad] (dem_set_material) */
+    long long n;                /* spheres, >= 1 */
+    const double *pos;          /* n x 3 */
+    const double *radius;       /* n */
+    const int *mat_id;          /* n indices into materials; NULL: all 0 */
+    const double *vel;          /* n x 3 or NULL */
+    const double *angvel;       /* n x 3 or NULL */
+    const double *velgrad;      /* 9 (row-major) for a periodic scene, or NULL */
+    long long nsteps;           /* step budget, >= 1 */
+    int keep_state;             /* 1: keep the final state for dem_server_result */
+} dem_request;
+
+/* Result of a finished request. */
+typedef struct dem_request_result {
+    long long ticket, n, nsteps;
+    long long iter;             /* steps taken (== nsteps) */
+    double time, dt;            /* simulated time and step of the scene */
+    double t_submit, t_admit, t_done;
+    double latency;             /* t_done - t_submit */
+    dem_stats stats;            /* dem_get_subscene_stats at the end */
+} dem_request_result;
+
+typedef struct dem_server_summary {
+    long long submitted, completed, failed, waiting, resident;
+    long long resident_bodies, max_resident;
+    long long ticks, scene_steps, body_steps;
+    long long budget_bytes;        /* the budget in force */
+    long long resident_bytes_est;  /* footprint estimate of the resident requests */
+    long long device_bytes;        /* largest device memory the scene has held */
+    double rows_per_body;          /* the estimate admission uses now */
+    double wall_s;                 /* since creation */
+    double busy_s;                 /* inside dem_step */
+    double latency_p50, latency_p99, latency_max, latency_mean;   /* finished requests */
+    double concurrency_mean;       /* resident requests per tick */
+} dem_server_summary;
+
+/* Defaults of dem_server_desc (above).  Never fails. */
+void dem_server_desc_init(dem_server_desc *desc);
+
+/* Start a server (creates its device scene and worker thread; the caller's current
+ * device is left as it was).  Errors: INVALID_ARG, CUDA, OOM. */
+dem_status dem_server_create(const dem_server_desc *desc, dem_server **out);
+
+/* Stop the worker after its current tick and free everything; requests not yet
+ * finished are dropped. */
+void dem_server_destroy(dem_server *server);
+
+/* Zero *req and give req->scene the sub-scene defaults.  Never fails. */
+void dem_request_init(dem_request *req);
+
+/* Queue a request; *ticket identifies it.  Never waits for the GPU.  Errors:
+ * INVALID_ARG (n < 1, nsteps < 1, missing arrays, material indices out of range),
+ * CAPACITY (its footprint alone exceeds the budget), or the error that stopped a
+ * failed server.  Scene errors found at admission (e.g. a sphere too large for its
+ * periodic cell) fail that request only. */
+dem_status dem_server_submit(dem_server *server, const dem_request *req, long long *ticket);
+
+/* *state: 0 waiting, 1 resident, 2 done, 3 failed.  INVALID_ARG: unknown ticket. */
+dem_status dem_server_poll(dem_server *server, long long ticket, int *state);
+
+/* Block until the request is finished or timeout_s seconds have passed: OK (done),
+ * TIMEOUT, the request's own error if it failed, INVALID_ARG (unknown ticket). */
+dem_status dem_server_wait(dem_server *server, long long ticket, double timeout_s);
+
+/* Copy a finished request's result: *info (nullable) and, if it was submitted with
+ * keep_state, its final state in id order (each array nullable: n x 3, ori n x 4).
+ * STATE: not finished; INVALID_ARG: unknown ticket, or state asked without
+ * keep_state; the request's error if it failed. */
+dem_status dem_server_result(dem_server *server, long long ticket, dem_request_result *info,
+                             double *pos, double *vel, double *angvel, double *ori);
+
+/* Forget a finished request (its result memory is freed).  STATE: not finished. */
+dem_status dem_server_release(dem_server *server, long long ticket);
+
+/* Counters, footprint and latency percentiles (linear interpolation between order
+ * statistics) of the finished requests. */
+dem_status dem_server_stats(dem_server *server, dem_server_summary *out);
+
+/* Message of the last error of a dem_server_* call on this server (NULL server: of
+ * a failed dem_server_create in this thread). */
+const char *dem_server_last_error(dem_server *server);
+
 /* Launch shapes of the step kernels.  No shape changes a result: every table row
  * and every body is computed by one thread with the same arithmetic whatever the
  * shape, so two scenes that differ only in their tuning follow bit-identical
@@ -512,13 +643,23 @@ dem_status dem_find_pairs(const double *pos_dev, const double *radius_dev, long 
  * Same arguments, results and errors as dem_find_pairs, with these limits:
  *   - at most 65,536 spheres (larger n: DEM_ERR_CAPACITY with a message naming
  *     dem_find_pairs) and at most 64 grid cells per axis;
- *   - its scratch is one fixed ~10 MB device array inside the library, held on
- *     every GPU that loads the library until the process exits;
+ *   - its scratch is one fixed ~10 MB device array inside the library.  CUDA
+ *     loads a library's device code lazily, so the array is reserved on a device
+ *     by the first pair query there (this entry point or dem_find_pairs), and then
+ *     held until the process exits.  A caller whose memory pool will take the
+ *     rest of the device should make one call first, before the pool reserves
+ *     memory: a call with n = 0 does only this set-up;
  *   - the first call on a device looks up that array's device address (a one-time
- *     set-up per device): make that first call before any stream capture;
+ *     set-up per device, cached): make that first call before any stream capture.
+ *     cudaDeviceReset invalidates the cached address: do not call this entry point
+ *     on a device after resetting it;
  *   - every call uses the same array, so calls whose work overlaps on the GPU
  *     (other threads, other streams) race and must be serialized by the caller;
- *     each call clears the parts that must start at zero.
+ *     each call clears the parts that must start at zero;
+ *   - the call waits for its work with a bounded poll (DEM_TIMEOUT_S, default
+ *     120 s).  After DEM_ERR_TIMEOUT the call's kernels may still be running on
+ *     cuda_stream and using the array: wait for that stream to drain (for
+ *     example cudaStreamSynchronize) before the next call.
  * The caller still provides the input and output arrays. */
 dem_status dem_find_pairs_noalloc(const double *pos_dev, const double *radius_dev, long long n,
                                   int periodic, const double *cell_h, double margin,

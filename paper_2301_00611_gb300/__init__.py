@@ -5,7 +5,7 @@ The compute path is the CUDA library ``libdem.so`` (C ABI in
 cheap: the library is loaded on first use, and a missing library raises.
 """
 from .dem import (DEM_FP64, DEM_LAW_HERTZ_MINDLIN, DEM_LAW_LINEAR, DEM_MIXED, DemError, Scene,
-                  exported_symbols, find_pairs, load_library, version)
+                  Server, exported_symbols, find_pairs, load_library, version)
 
-__all__ = ["Scene", "DemError", "find_pairs", "load_library", "exported_symbols", "version",
-           "DEM_FP64", "DEM_MIXED", "DEM_LAW_LINEAR", "DEM_LAW_HERTZ_MINDLIN"]
+__all__ = ["Scene", "Server", "DemError", "find_pairs", "load_library", "exported_symbols",
+           "version", "DEM_FP64", "DEM_MIXED", "DEM_LAW_LINEAR", "DEM_LAW_HERTZ_MINDLIN"]

@@ -100,6 +100,59 @@ class Timing(ctypes.Structure):
     ]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("budget_bytes", ctypes.c_longlong),
+        ("tick_steps", ctypes.c_longlong),
+        ("rows_per_body", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("scene", SubsceneDesc),
+        ("n_materials", ctypes.c_int),
+        ("materials", ctypes.c_void_p),
+        ("n", ctypes.c_longlong),
+        ("pos", ctypes.c_void_p),
+        ("radius", ctypes.c_void_p),
+        ("mat_id", ctypes.c_void_p),
+        ("vel", ctypes.c_void_p),
+        ("angvel", ctypes.c_void_p),
+        ("velgrad", ctypes.c_void_p),
+        ("nsteps", ctypes.c_longlong),
+        ("keep_state", ctypes.c_int),
+    ]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_longlong),
+        ("n", ctypes.c_longlong),
+        ("nsteps", ctypes.c_longlong),
+        ("iter", ctypes.c_longlong),
+        ("time", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("latency", ctypes.c_double),
+        ("stats", Stats),
+    ]
+
+
+class ServerSummary(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in (
+        "submitted", "completed", "failed", "waiting", "resident", "resident_bodies",
+        "max_resident", "ticks", "scene_steps", "body_steps", "budget_bytes",
+        "resident_bytes_est", "device_bytes")] + [(k, ctypes.c_double) for k in (
+        "rows_per_body", "wall_s", "busy_s", "latency_p50", "latency_p99", "latency_max",
+        "latency_mean", "concurrency_mean")]
+
+
 # C ABI: name -> (restype, argtypes)
 _P = ctypes.c_void_p
 class Tuning(ctypes.Structure):
@@ -168,6 +221,17 @@ _SIGS = {
     "dem_find_pairs_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P,
                                               ctypes.c_double, ctypes.c_longlong, _P, _P, _P, _P,
                                               _P]),
+    "dem_server_desc_init": (None, [_P]),
+    "dem_server_create": (ctypes.c_int, [_P, _P]),
+    "dem_server_destroy": (None, [_P]),
+    "dem_request_init": (None, [_P]),
+    "dem_server_submit": (ctypes.c_int, [_P, _P, _P]),
+    "dem_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, _P]),
+    "dem_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double]),
+    "dem_server_result": (ctypes.c_int, [_P, ctypes.c_longlong, _P, _P, _P, _P, _P]),
+    "dem_server_release": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "dem_server_stats": (ctypes.c_int, [_P, _P]),
+    "dem_server_last_error": (ctypes.c_char_p, [_P]),
     "dem_last_error": (ctypes.c_char_p, [_P]),
     "dem_version": (ctypes.c_char_p, []),
 }
@@ -608,6 +672,125 @@ def _timing_methods():
 
 
 _timing_methods()
+
+
+def _stats_dict(st):
+    out = {name: getattr(st, name) for name, _ in Stats._fields_ if name != "stress"}
+    out["stress"] = np.array(list(st.stress)).reshape(3, 3)
+    return out
+
+
+class Server:
+    """dem_server_*: the continuous-batching request server of the library (its
+    worker thread and scheduling run in the C++ library; this class marshals)."""
+
+    WAITING, RESIDENT, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, precision=DEM_MIXED, budget_bytes=0, tick_steps=200, rows_per_body=8.0,
+                 stream=None, device=-1):
+        self._lib = load_library()
+        d = ServerDesc()
+        self._lib.dem_server_desc_init(ctypes.byref(d))
+        d.precision = int(precision)
+        d.budget_bytes = int(budget_bytes)
+        d.tick_steps = int(tick_steps)
+        d.rows_per_body = float(rows_per_body)
+        d.cuda_stream = stream
+        d.device = int(device)
+        h = ctypes.c_void_p()
+        rc = self._lib.dem_server_create(ctypes.byref(d), ctypes.byref(h))
+        if rc != DEM_OK:
+            raise DemError(rc, self._lib.dem_server_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != DEM_OK:
+            raise DemError(rc, self._lib.dem_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dem_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, w, steps, velgrad=None, keep_state=False, dt=0.0):
+        """Queue workload w (a workloads.Workload-like object) for `steps` steps;
+        dt 0: 0.5 x p-wave step of its spheres.  Returns the ticket."""
+        r = Request()
+        self._lib.dem_request_init(ctypes.byref(r))
+        sd = r.scene
+        sd.periodic = int(bool(w.periodic))
+        H = np.eye(3) if w.cell is None else np.asarray(w.cell, dtype=np.float64).reshape(3, 3)
+        for q in range(9):
+            sd.cell_h[q] = float(H.flat[q])
+        for k in range(3):
+            sd.box_lo[k] = float(w.box_lo[k])
+            sd.box_hi[k] = float(w.box_hi[k])
+            sd.gravity[k] = float(w.gravity[k])
+        sd.wall_mask = int(w.wall_mask)
+        sd.wall_material = 0
+        sd.damping = float(w.damping)
+        sd.dt = float(dt)
+        mats = np.ascontiguousarray([[m.density, m.young, m.poisson, m.friction]
+                                     for m in w.materials], dtype=np.float64)
+        if velgrad is None and w.periodic and np.any(w.velgrad):
+            velgrad = w.velgrad
+        mat_id = None if w.mat_id is None else np.ascontiguousarray(w.mat_id, dtype=np.int32)
+        keep = [mats, _f64(w.pos, (-1, 3)), _f64(w.radius), mat_id, _f64(w.vel, (-1, 3)),
+                _f64(w.angvel, (-1, 3)), _f64(velgrad, (3, 3))]
+        r.n_materials = len(w.materials)
+        r.materials, r.pos, r.radius, r.mat_id, r.vel, r.angvel, r.velgrad = (
+            _ptr(a) for a in keep)
+        r.n = keep[2].size
+        r.nsteps = int(steps)
+        r.keep_state = int(bool(keep_state))
+        t = ctypes.c_longlong()
+        self._check(self._lib.dem_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        v = ctypes.c_int()
+        self._check(self._lib.dem_server_poll(self._h, int(ticket), ctypes.byref(v)))
+        return v.value
+
+    def wait(self, ticket, timeout=3600.0):
+        self._check(self._lib.dem_server_wait(self._h, int(ticket), float(timeout)))
+
+    def result(self, ticket, state=False):
+        info = RequestResult()
+        n = None
+        arrs = [None] * 4
+        if state:
+            self._check(self._lib.dem_server_result(self._h, int(ticket), ctypes.byref(info),
+                                                    None, None, None, None))
+            n = info.n
+            arrs = [np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 4))]
+        self._check(self._lib.dem_server_result(self._h, int(ticket), ctypes.byref(info),
+                                                *(_ptr(a) for a in arrs)))
+        out = {k: getattr(info, k) for k, _ in RequestResult._fields_ if k != "stats"}
+        out["stats"] = _stats_dict(info.stats)
+        if state:
+            out["state"] = dict(zip(("pos", "vel", "angvel", "ori"), arrs))
+        return out
+
+    def release(self, ticket):
+        self._check(self._lib.dem_server_release(self._h, int(ticket)))
+
+    def stats(self):
+        st = ServerSummary()
+        self._check(self._lib.dem_server_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerSummary._fields_}
 
 
 def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, stream=None,

@@ -164,73 +164,155 @@ def job_rate(world, units_per_rank, T):
     return world * units_per_rank / T
 
 
-# body-steps the reference arm may spend (about a minute of single-thread oracle time)
-REF_BUDGET = 6e7
+def assign_units(sizes, world):
+    """Whole scenes to ranks with no communication (replicas only: scenes never
+    interact): largest first, each to the rank with the fewest bodies so far (ties to
+    the lower rank).  Returns one sorted index list per rank; together they hold every
+    scene exactly once."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(o) for o in out]
+
+
+def gather_ranks(obj, world):
+    """Every rank's object, in rank order (one entry without torch.distributed)."""
+    if world <= 1:
+        return [obj]
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, obj)
+    return out
+
+
+# body-steps the reference arm may spend (about a minute of single-thread
+# oracle time at the dense window's coordination)
+REF_BUDGET = 4e6
+# coordination number of the timed window (the last steps of the 1M compaction: 2.62M
+# real contacts on 1M spheres), the density of contacts the reference arm's sample has
+REF_Z_WINDOW = 5.24
+# the reference sample's time step relative to the workload's: its spheres overlap by
+# some 10-20% of their radii (inflated radii reach the window's coordination), so at
+# the workload's step they would fly apart within the sample; the oracle's work per
+# step does not depend on dt
+REF_DT_SCALE = 1e-2
+
+
+def dense_inflation(z_target, n_probe=20000):
+    """Radius factor f that gives the 1M compaction's loose cloud (solid fraction 0.30,
+    the same radius law) the coordination z_target: bisection on a smaller cloud of the
+    same generator, pairs counted by the oracle's brute-force-checked grid search."""
+    import oracle
+    import workloads
+    w = workloads.compaction(n=n_probe, seed=11, phi0=PHI0, phi_target=PHI1, variant="b",
+                             steps=JOB_STEPS)
+    lo, hi = 1.0, 1.6
+    for _ in range(30):
+        f = 0.5 * (lo + hi)
+        i, j, c = oracle.pairs(w.pos, w.radius * f, periodic=True, H=w.cell)
+        z = 2.0 * len(i) / n_probe
+        lo, hi = (f, hi) if z < z_target else (lo, f)
+    return 0.5 * (lo + hi)
 
 
 def run_reference(args):
-    """FP64 CPU oracle on the host cores.  Each step is a bounded sample of the workload:
-    the same compaction with fewer spheres (same radius law, fraction and loading), sized
-    so that warm-up + timed steps stay near REF_BUDGET body-steps."""
+    """The FP64 CPU oracle on the host cores, on a bounded sample of the timed window's
+    work.  The GPU arm times the last steps of the compaction, a packing near solid
+    fraction 0.62 with coordination ~5.2; without the library the oracle cannot reach
+    that state, so the sample is the job's seeded loose cloud with its radii inflated
+    until the coordination matches (each timed step then computes as many contacts per
+    sphere as a window step), and fewer spheres so that warm-up + timed steps stay near
+    REF_BUDGET body-steps.  It reports the contact counts it actually met."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     n_ref = int(max(2000, min(args.n, REF_BUDGET / max(1, args.steps + args.warmup))))
-    args = argparse.Namespace(**{**vars(args), "n": n_ref})
-    w = make_workload(args.n)
+    f = dense_inflation(REF_Z_WINDOW)
+    w = make_workload(n_ref)
+    import copy
+    w = copy.copy(w)
+    w.radius = w.radius * f
     orc = oracle.OracleScene.from_workload(w)
-    dt = orc.clock()[2]
+    dt = orc.clock()[2] * REF_DT_SCALE
+    orc.set_dt(dt)
     orc.set_velgrad(velgrad_for(dt))
-    per_step = []
     for _ in range(args.warmup):
         orc.step(1)
+    c0 = orc.stats()["n_contacts"]
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        t = time.perf_counter()
         orc.step(1)
-        per_step.append(time.perf_counter() - t)
     T = time.perf_counter() - t0
-    value = args.n * args.steps / T
-    st = orc.stats()
-    sample = (f"oracle, one thread, from the seeded initial cloud: {args.warmup} untimed + "
-              f"{args.steps} timed steps of the same compaction with {args.n} spheres "
-              f"(the first steps of the job)")
+    c1 = orc.stats()["n_contacts"]
+    value = n_ref * args.steps / T
+    sample = (f"oracle, one thread: {args.warmup} untimed + {args.steps} timed steps of the "
+              f"compaction's seeded loose cloud with {n_ref} spheres, radii x {f:.4f} so that "
+              f"the coordination is the timed window's ({REF_Z_WINDOW}): {c0} contacts at the "
+              f"first timed step, {c1} at the last (Z {2 * c0 / n_ref:.2f} -> "
+              f"{2 * c1 / n_ref:.2f}); time step x {REF_DT_SCALE} so that the overlaps stay "
+              f"put")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "n_bodies": args.n, "sample": "initial steps"},
+            "config": {"workload": WORKLOAD, "n_bodies": n_ref,
+                       "sample": "dense window (inflated loose cloud at the window's Z)",
+                       "contacts_per_sphere": c0 / n_ref},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
-            "contacts_at_end": st["n_contacts"]}
+            "contact_updates_per_s": 0.5 * (c0 + c1) * args.steps / T}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline_sample(n, seconds_hint=20.0):
-    """Time the oracle (as it stands, single thread) on the first steps of the same job."""
+def export_window_start(scene):
+    """State, contact history, cell, clock and step of a scene, read through the C ABI
+    (the CPU baseline starts the oracle from it)."""
+    it, t = scene.clock()
+    return {"state": scene.state(force=False), "contacts": scene.contacts(),
+            "cell": scene.cell(), "clock": (it, t), "dt": scene.dt()}
+
+
+def cpu_baseline_sample(w, start, seconds_hint=20.0, max_steps=50):
+    """Time the oracle (as it stands, single thread) on the timed window itself: it is
+    seeded with the GPU scene's state, contact history, cell and clock at the first
+    timed step and runs the same steps until about seconds_hint have passed."""
     import oracle
     oracle.build()
-    w = make_workload(n)   # cached: the same cloud the GPU arm ran
-    orc = oracle.OracleScene.from_workload(w)
-    dt = orc.clock()[2]
-    orc.set_velgrad(velgrad_for(dt))
-    orc.step(1)   # first contact pass (untimed)
+    orc = oracle.OracleScene.from_workload(w, dt=start["dt"])
+    st = start["state"]
+    orc.set_state(pos=st["pos"], vel=st["vel"], angvel=st["angvel"], ori=st["ori"])
+    c = start["contacts"]
+    orc.set_contacts(c["id1"], c["id2"], c["c"], c["fs"], c["normal"], c["phys"])
+    cl = start["cell"]
+    orc.set_cell(H=cl["H"], velgrad=cl["velgrad"], prev_velgrad=cl["prev_velgrad"],
+                 prev_H=cl["prev_H"])
+    orc.set_clock(*start["clock"])
+    c_start = len(c["id1"])
     t0 = time.perf_counter()
     k = 0
     while True:
         orc.step(1)
         k += 1
         el = time.perf_counter() - t0
-        if el > seconds_hint or k >= 50:
+        if el > seconds_hint or k >= max_steps:
             break
+    c_end = orc.stats()["n_contacts"]
+    n = w.n
     return {"value": n * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} oracle steps (after 1 untimed) of the {n}-sphere compaction from "
-                      f"the seeded initial cloud, {el:.1f} s single-threaded"}
+            "contact_updates_per_s": 0.5 * (c_start + c_end) * k / el,
+            "sample": f"the first {k} steps of the timed window (from step {start['clock'][0]}: "
+                      f"the GPU scene's state, contact history and cell imported into the "
+                      f"oracle), {n} spheres, {c_start} real contacts at the start and {c_end} "
+                      f"at the end, {el:.1f} s single-threaded"}
 
 
 def tune_shape(Scene, w, args, precision):
@@ -254,23 +336,27 @@ def tune_shape(Scene, w, args, precision):
     return shape
 
 
-def _time_window(Scene, w, args, precision, world, local, shape=None):
-    """Run the job to its timed window on one scene; returns the measurements."""
+def _time_window(Scene, w, args, precision, world, local, shape=None, capture_start=False,
+                 velgrad=velgrad_for, K=None):
+    """Run the job to its timed window on one scene; returns the measurements (and,
+    with capture_start, the scene's state at the first timed step)."""
     import torch
     from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
     stream = torch.cuda.current_stream()
     prec = DEM_MIXED if precision == "mixed" else DEM_FP64
-    scene = Scene.from_workload(w, capacity_bodies=args.n, precision=prec)
+    scene = Scene.from_workload(w, capacity_bodies=w.n, precision=prec)
     if shape:
         scene.set_tuning(**shape)
     dt = scene.dt()
-    scene.set_cell_velgrad(velgrad_for(dt))
-    K, W = args.steps, args.warmup
+    scene.set_cell_velgrad(velgrad(dt))
+    K = args.steps if K is None else K
+    W = args.warmup
     prelude = max(0, JOB_STEPS - W - K)
     if prelude:
         scene.step(prelude)
     scene.step(W)
     st0 = scene.stats()
+    start = export_window_start(scene) if capture_start else None
     scene.set_timing(True)
     t_before = scene.timing()["kernel_launches"]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -292,8 +378,9 @@ def _time_window(Scene, w, args, precision, world, local, shape=None):
     avg_ms = tm["contact_ms"] / max(1, tm["contact_launches"])
     rows_avg = tm["rows_processed"] / max(1, tm["contact_launches"])
     return {"T": T, "ms": ms, "dt": dt, "prelude": prelude, "tm": tm, "st0": st0, "st1": st1,
-            "mean_real": mean_real, "avg_ms": avg_ms, "rows_avg": rows_avg,
-            "launches": tm["kernel_launches"] - t_before, "clocks": clk.summary()}
+            "mean_real": mean_real, "avg_ms": avg_ms, "rows_avg": rows_avg, "K": K,
+            "launches": tm["kernel_launches"] - t_before, "clocks": clk.summary(),
+            "start": start}
 
 
 # Algorithmic bytes of the mixed-precision contact kernel (per row), from its operand list:
@@ -364,15 +451,28 @@ def _traffic(precision, name, algorithmic_at):
     return t["bytes"], note
 
 
-def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True):
+# The survey's algorithmic bytes of the method (what a contact and a body must move per
+# step, independent of this implementation's layout): 244 B read + 120 B written per
+# real contact in the contact pass, 470 B per real contact and 180 B per body per step.
+SURVEY_CONTACT_BYTES = 364
+SURVEY_STEP_CONTACT_BYTES, SURVEY_STEP_BODY_BYTES = 470, 180
+
+
+def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True, fp64_peak=None):
     """Roofline of the contact and integrator kernels of one timed window: achieved
     algorithmic flops (FP64, FP64-pipe bound) or bytes (mixed, HBM bound) per launch over
-    the kernel's average launch time from its CUDA events."""
+    the kernel's average launch time from its CUDA events.  FP64 kernels divide by the
+    FP64 rate measured in this run (fp64_peak, TFLOP/s; the figure derived from unit
+    counts and clock is reported beside it), and carry their HBM fractions both for this
+    implementation's operand bytes and for the survey's per-contact bytes."""
     tm, real = res["tm"], res["mean_real"]
     c_ms = res["avg_ms"]
     i_ms = tm["integrate_ms"] / max(1, tm["integrate_launches"])
     out = {}
     if precision == "fp64":
+        pk = fp64_peak if fp64_peak else FP64_PEAK_TFLOPS
+        pk_kind = ("measured (FP64 FMA-chain probe dem_measure_fp64_peak, this run)"
+                   if fp64_peak else "derived from unit counts and clock (FP64 FMA pipe)")
         cf = ROW_FLOPS_ALL * res["rows_avg"] + ROW_FLOPS_REAL * real
         cb = ROW_BYTES_ALL * res["rows_avg"] + ROW_BYTES_REAL * real
         if_ = INT_FLOPS_BODY * n + INT_FLOPS_REAL * real
@@ -380,12 +480,17 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True):
         for name, ms, fl, by in (("contact", c_ms, cf, cb), ("integrate", i_ms, if_, ib)):
             tf = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
             gb = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-            out[name] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                         "peak_kind": "derived from unit counts and clock (FP64 FMA pipe)",
+            out[name] = {"bound": "alu", "achieved": tf, "peak": pk,
+                         "unit": "TFLOP/s", "frac": tf / pk, "traffic": None,
+                         "peak_kind": pk_kind, "derived_peak": FP64_PEAK_TFLOPS,
+                         "frac_of_derived": tf / FP64_PEAK_TFLOPS,
                          "avg_launch_ms": ms, "flops_per_launch": fl,
                          "hbm": {"achieved_gbs": gb, "peak_gbs": peak, "frac": gb / peak,
                                  "peak_kind": peak_kind, "bytes_per_launch": by}}
+        sb = SURVEY_CONTACT_BYTES * real
+        sg = sb / (c_ms / 1e3) / 1e9 if c_ms > 0 else 0.0
+        out["contact"]["hbm_survey_bytes"] = {"bytes_per_launch": sb, "achieved_gbs": sg,
+                                              "frac": sg / peak, "peak_kind": peak_kind}
     else:
         cb = ROW_BYTES_ALL_MIXED * res["rows_avg"] + ROW_BYTES_REAL_MIXED * real
         ib = INT_BYTES_BODY_MIXED * n + INT_BYTES_REAL_MIXED * real
@@ -432,12 +537,15 @@ def run_gpu(args):
         torch.distributed.barrier()
         __graft_entry__.build()
     from paper_2301_00611_gb300 import Scene
+    from paper_2301_00611_gb300.dem import measure_fp64_peak
 
     w = make_workload(args.n)
     K, W = args.steps, args.warmup
     peak, peak_kind = _peaks()
+    fp64_peak = measure_fp64_peak()
     shape64 = tune_shape(Scene, w, args, "fp64")
-    res = _time_window(Scene, w, args, "fp64", world, local, shape64)
+    res = _time_window(Scene, w, args, "fp64", world, local, shape64,
+                       capture_start=(rank == 0 and not args.no_cpu_baseline))
     mixed = None
     if args.precision in ("both", "mixed"):
         shape32 = tune_shape(Scene, w, args, "mixed")
@@ -450,7 +558,10 @@ def run_gpu(args):
     rows_per_s = world * tm["rows_processed"] / T
     share = {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms", "cell_ms",
                                                 "collider_ms")}
-    rl64, rk64 = _kernel_rooflines(res, "fp64", args.n, peak, peak_kind)
+    rl64, rk64 = _kernel_rooflines(res, "fp64", args.n, peak, peak_kind, fp64_peak=fp64_peak)
+    # the whole step against the survey's algorithmic bytes (N 180 B + C 470 B per step)
+    step_bytes = SURVEY_STEP_BODY_BYTES * args.n + SURVEY_STEP_CONTACT_BYTES * res["mean_real"]
+    step_gbs = step_bytes / (ms / K / 1e3) / 1e9
     mixed_line = None
     if mixed is not None:
         mrl, mrk = _kernel_rooflines(mixed, "mixed", args.n, peak, peak_kind)
@@ -491,14 +602,18 @@ def run_gpu(args):
                "note": "whole 5000-step FP64 job through the C ABI from host arrays: scene "
                        "creation, upload, stepping, state download"}
 
-    batched = None
-    if not args.no_batch and (rank == 0 or world == 1):
-        batched = run_batch_measure(args)
+    # the batched sweep and the served stream: whole scenes dealt out to the ranks
+    batched = None if args.no_batch else run_batch_measure(args, world, rank)
+    served = None if args.no_serve else run_served_measure(args, world, rank)
+    triax = config_1a = None
+    if rank == 0 and not args.no_extra:
+        config_1a = compaction_1a_measure(args, Scene, peak, peak_kind, fp64_peak)
+        triax = triax_measure(args, TRIAX_HEADLINE_N, None)
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline_sample(args.n, args.cpu_seconds)
+            cpu = cpu_baseline_sample(w, res["start"], args.cpu_seconds)
         st0, st1 = res["st0"], res["st1"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -515,6 +630,9 @@ def run_gpu(args):
                          "candidates_end": st1["n_candidates"],
                          "packing_fraction_end": st1["packing_fraction"]},
             "phase_share": share,
+            "step_hbm_survey_bytes": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
+                                      "frac": step_gbs / peak, "peak_kind": peak_kind},
+            "fp64_peak_tflops": {"measured": fp64_peak, "derived": FP64_PEAK_TFLOPS},
             "collider_runs": tm["collider_runs"],
             "gpu_launches": res["launches"],
             "launch_shape": shape64,
@@ -523,6 +641,9 @@ def run_gpu(args):
             "roofline_kernels": rk64,
             "mixed": mixed_line,
             "batched": batched,
+            "served": served,
+            "config_1a": config_1a,
+            "triax": triax,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -551,17 +672,78 @@ def _batch_scene(Scene, ws, precision):
     return g, subs
 
 
-def run_batch_measure(args):
+def _stat_errors(pairs, ns):
+    """Per-scene errors of (test, reference) statistics pairs: kinetic energy relative to
+    the reference's final value and to the reference run's peak (the scale of a
+    deposition that has settled to rest), coordination relative (and against one contact,
+    2/N, its resolution), packing fraction relative."""
+    ke = np.array([abs(a["kinetic_energy"] / b["kinetic_energy"] - 1) for a, b in pairs])
+    ke_pk = np.array([abs(a["kinetic_energy"] - b["kinetic_energy"]) / b["ke_peak"]
+                      for a, b in pairs])
+    zr = np.array([abs(a["coordination"] - b["coordination"]) / max(b["coordination"], 2.0 / n)
+                   for (a, b), n in zip(pairs, ns)])
+    zc = np.array([abs(a["coordination"] - b["coordination"]) * n / 2.0
+                   for (a, b), n in zip(pairs, ns)])
+    ph = np.array([abs(a["packing_fraction"] / b["packing_fraction"] - 1) for a, b in pairs])
+    worst = int(np.argmax(ke))
+    return {"kinetic_energy_rel_median": float(np.median(ke)),
+            "kinetic_energy_rel_p90": float(np.percentile(ke, 90)),
+            "kinetic_energy_rel_max": float(ke.max()),
+            "scenes_within_1e-3_kinetic_energy": float(np.mean(ke <= 1e-3)),
+            "kinetic_energy_rel_to_peak_max": float(ke_pk.max()),
+            "kinetic_energy_rel_to_peak_p90": float(np.percentile(ke_pk, 90)),
+            "scenes_within_1e-3_kinetic_energy_rel_to_peak": float(np.mean(ke_pk <= 1e-3)),
+            "coordination_rel_max": float(zr.max()),
+            "coordination_contacts_differing_max": float(zc.max()),
+            "scenes_within_1e-3_coordination_or_one_contact": float(np.mean(
+                (zr <= 1e-3) | (zc <= 1.0 + 1e-9))),
+            "packing_fraction_rel_max": float(ph.max()),
+            "worst_kinetic_energy_scene": {"n": int(ns[worst]),
+                                           "kinetic_energy_rel": float(ke[worst]),
+                                           "rel_to_peak": float(ke_pk[worst])}}
+
+
+def _plain_run(Scene, w, steps, precision, dt=None, velgrad=None, chunk=500, state=False,
+               nudge=False):
+    """The plain one-scene-at-a-time path: a fresh scene stepped `steps` times (in
+    chunks, recording the peak kinetic energy at the chunk ends); returns its final
+    statistics with "ke_peak", and its state if asked.  nudge: every coordinate moved
+    by one ulp first (the rounding-level perturbation that measures how far the
+    dynamics alone carry a difference of the size FP64 rounding makes)."""
+    if nudge:
+        import copy
+        w = copy.copy(w)
+        w.pos = np.nextafter(w.pos, np.inf)
+    sc = Scene.from_workload(w, precision=precision, dt=dt)
+    if velgrad is not None:
+        sc.set_cell_velgrad(velgrad)
+    done, peak = 0, 0.0
+    while done < steps:
+        k = min(chunk, steps - done)
+        sc.step(k)
+        done += k
+        st = sc.stats()
+        peak = max(peak, st["kinetic_energy"])
+    st["ke_peak"] = peak
+    out = (st, sc.state(force=False)) if state else st
+    sc.close()
+    return out
+
+
+def run_batch_measure(args, world=1, rank=0):
     """The batched deposition sweep: every scene a sub-scene of one device scene
     (mixed precision, one launch per kernel per step for all of them, launch shapes
     from dem_autotune in the first steps), against the plain FP64 path running the
-    same scenes one at a time.  The same batch in FP64 separates the effect of the
-    precision from that of the summation order (the dynamics amplify both).  Returns
-    the measurement dict."""
+    same scenes one at a time.  The same batch in FP64 shows the batching itself
+    changes nothing: its states are compared bit for bit with the plain runs'.  Under
+    several ranks the scenes are dealt out by body count (assign_units), each rank runs
+    its share, and the rates are whole-machine (scene-steps of all ranks over the
+    slowest rank's time).  Returns the measurement dict (rank 0; None elsewhere)."""
     import workloads
     from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED, Scene
-    ws = workloads.batch_depositions(args.batch_scenes, 3, steps=BATCH_STEPS)
-    nsum = sum(w.n for w in ws)
+    ws_all = workloads.batch_depositions(args.batch_scenes, 3, steps=BATCH_STEPS)
+    mine = assign_units([w.n for w in ws_all], world)[rank]
+    ws = [ws_all[i] for i in mine]
     out = {}
     for label, prec in (("mixed", DEM_MIXED), ("fp64", DEM_FP64)):
         g, subs = _batch_scene(Scene, ws, prec)
@@ -577,74 +759,186 @@ def run_batch_measure(args):
         t_batch = time.perf_counter() - t0
         out[label] = {"T": t_batch, "timed": BATCH_STEPS - done, "tune_steps": done,
                       "tune_s": t_tune, "shape": shape,
-                      "stats": [g.subscene_stats(q) for q in subs]}
+                      "stats": [g.subscene_stats(q) for q in subs],
+                      "states": [g.subscene_state(q) for q in subs] if label == "fp64" else None}
         g.close()
     # plain FP64, one scene at a time (the same full 2000-step jobs)
     t_plain = 0.0
-    plain_stats = []
+    plain_stats, same = [], 0
     step = max(1, args.batch_plain_every)
-    for w in ws[::step]:
-        s = Scene.from_workload(w, precision=DEM_FP64)
+    idx = list(range(0, len(ws), step))
+    for i in idx:
         _sync()
         t0 = time.perf_counter()
-        s.step(BATCH_STEPS)
+        st, state = _plain_run(Scene, ws[i], BATCH_STEPS, DEM_FP64, state=True)
         _sync()
         t_plain += time.perf_counter() - t0
-        plain_stats.append(s.stats())
-        s.close()
-    idx = list(range(0, len(ws), step))
-
-    def errors(batch):
-        ke = np.array([abs(batch[i]["kinetic_energy"] / p["kinetic_energy"] - 1)
-                       for i, p in zip(idx, plain_stats)])
-        zr = np.array([abs(batch[i]["coordination"] - p["coordination"]) /
-                       max(p["coordination"], 2.0 / ws[i].n) for i, p in zip(idx, plain_stats)])
-        ke_sum = abs(sum(batch[i]["kinetic_energy"] for i in idx) /
-                     sum(p["kinetic_energy"] for p in plain_stats) - 1)
-        z_mean = abs(np.mean([batch[i]["coordination"] for i in idx]) /
-                     np.mean([p["coordination"] for p in plain_stats]) - 1)
-        worst = int(np.argmax(ke))
-        return {"kinetic_energy_rel_median": float(np.median(ke)),
-                "kinetic_energy_rel_p90": float(np.percentile(ke, 90)),
-                "kinetic_energy_rel_max": float(ke.max()),
-                "scenes_within_1e-3_kinetic_energy": float(np.mean(ke <= 1e-3)),
-                "total_kinetic_energy_rel": float(ke_sum),
-                "mean_coordination_rel": float(z_mean),
-                "coordination_rel_max": float(zr.max()),
-                "packing_fraction_rel_max": float(max(
-                    abs(batch[i]["packing_fraction"] / p["packing_fraction"] - 1)
-                    for i, p in zip(idx, plain_stats))),
-                "worst_scene": {"index": idx[worst], "n": ws[idx[worst]].n,
-                                "young": ws[idx[worst]].materials[0].young,
-                                "contacts_plain": plain_stats[worst]["n_contacts"]}}
-
+        plain_stats.append(st)
+        b = out["fp64"]["states"][i]
+        same += all(np.array_equal(b[k], state[k]) for k in ("pos", "vel", "angvel", "ori"))
+    # the chaos floor: the plain FP64 path against itself with every coordinate moved by
+    # one ulp, on every 8th scene
+    ulp_idx = list(range(0, len(idx), 8))
+    pairs_ulp = [(_plain_run(Scene, ws[idx[j]], BATCH_STEPS, DEM_FP64, nudge=True),
+                  plain_stats[j]) for j in ulp_idx]
     mx, fp = out["mixed"], out["fp64"]
-    batched = len(ws) * mx["timed"] / mx["T"]
-    plain = len(idx) * BATCH_STEPS / t_plain
+    local = {"n_scenes": len(ws), "bodies": sum(w.n for w in ws), "T_mixed": mx["T"],
+             "pairs_ulp": pairs_ulp, "ns_ulp": [ws[idx[j]].n for j in ulp_idx],
+             "T_fp64": fp["T"], "timed_mixed": mx["timed"], "timed_fp64": fp["timed"],
+             "t_plain": t_plain, "plain_scenes": len(idx), "same": same,
+             "pairs_mixed": [(mx["stats"][i], p) for i, p in zip(idx, plain_stats)],
+             "pairs_fp64": [(fp["stats"][i], p) for i, p in zip(idx, plain_stats)],
+             "ns": [ws[i].n for i in idx], "tune_steps": mx["tune_steps"],
+             "tune_s": mx["tune_s"], "shape": mx["shape"], "shape64": fp["shape"]}
+    allr = gather_ranks(local, world)
+    if rank != 0:
+        return None
+    T_mx = max(r["T_mixed"] for r in allr)
+    T_fp = max(r["T_fp64"] for r in allr)
+    T_pl = max(r["t_plain"] for r in allr)
+    n_sc = sum(r["n_scenes"] for r in allr)
+    nsum = sum(r["bodies"] for r in allr)
+    batched = sum(r["n_scenes"] * r["timed_mixed"] for r in allr) / T_mx
+    plain = sum(r["plain_scenes"] for r in allr) * BATCH_STEPS / T_pl
+    pm = [p for r in allr for p in r["pairs_mixed"]]
+    pf = [p for r in allr for p in r["pairs_fp64"]]
+    ns = [n for r in allr for n in r["ns"]]
+    compared = sum(r["plain_scenes"] for r in allr)
     return {
-        "workload": f"{len(ws)} gravity depositions, sizes log-uniform [500, 50000] "
+        "workload": f"{n_sc} gravity depositions, sizes log-uniform [500, 50000] "
                     f"({nsum} spheres), friction U[0.2, 0.7] rad, E log-uniform [1e6, 1e8] Pa, "
                     f"{BATCH_STEPS} steps each",
         "value": batched, "unit": "scene-steps/s",
-        "body_steps_per_s": nsum * mx["timed"] / mx["T"],
-        "timed_steps": mx["timed"], "tuning_steps": mx["tune_steps"],
-        "tuning_seconds": mx["tune_s"], "launch_shape": mx["shape"],
-        "batched_fp64": {"value": len(ws) * fp["timed"] / fp["T"], "unit": "scene-steps/s",
-                         "launch_shape": fp["shape"]},
+        "body_steps_per_s": nsum * allr[0]["timed_mixed"] / T_mx,
+        "timed_steps": allr[0]["timed_mixed"], "tuning_steps": allr[0]["tune_steps"],
+        "tuning_seconds": allr[0]["tune_s"], "launch_shape": allr[0]["shape"],
+        "ranks": world, "scenes_per_rank": [r["n_scenes"] for r in allr],
+        "batched_fp64": {"value": sum(r["n_scenes"] * r["timed_fp64"] for r in allr) / T_fp,
+                         "unit": "scene-steps/s", "launch_shape": allr[0]["shape64"],
+                         "states_bitwise_equal_to_plain": f"{sum(r['same'] for r in allr)} of "
+                                                          f"{compared}"},
         "plain_fp64_one_at_a_time": {"value": plain, "unit": "scene-steps/s",
-                                     "scenes_timed": len(idx)},
+                                     "scenes_timed": compared,
+                                     "note": "stepped in chunks of 500 with a statistics read "
+                                             "at each chunk end (the peak kinetic energy)"},
         "speedup_vs_plain": batched / plain,
-        "accuracy_vs_plain_fp64": {"batched_mixed": errors(mx["stats"]),
-                                   "batched_fp64": errors(fp["stats"]),
-                                   "scenes_compared": len(idx)},
+        "accuracy_vs_plain_fp64": {"batched_mixed": _stat_errors(pm, ns),
+                                   "batched_fp64": _stat_errors(pf, ns),
+                                   "scenes_compared": compared,
+                                   "chaos_floor_fp64_one_ulp": _stat_errors(
+                                       [p for r in allr for p in r["pairs_ulp"]],
+                                       [n for r in allr for n in r["ns_ulp"]]),
+                                   "chaos_floor_note": "the plain FP64 path against itself "
+                                   "with every coordinate moved by one ulp, every 8th scene: "
+                                   "how far the dynamics alone carry a rounding-level "
+                                   "difference over the same steps"},
         "dtype": "mixed (batched) vs f64 (plain)",
     }
 
 
+SERVED_REQUESTS = 100
+
+
+def served_requests():
+    import workloads
+    return workloads.serving_requests(SERVED_REQUESTS, 4, 200.0, nmin=1000, nmax=50_000,
+                                      smin=500, smax=2000)
+
+
+def _served_velgrad(rq, w, dt):
+    import workloads
+    if not w.periodic:
+        return None
+    return workloads.compaction_rate(0.30, 0.62, rq["steps"], dt) * np.eye(3)
+
+
+def run_served_measure(args, world=1, rank=0):
+    """A short served stream through the library's request server (dem_server_*, mixed
+    precision): Poisson arrivals (200/s), spheres log-uniform [1000, 50000], step
+    budgets U[500, 2000], depositions and periodic compactions mixed.  Requests are
+    submitted in real time at their arrival; latency is completion - arrival.  Beside
+    it: the plain FP64 one-scene-at-a-time path as a FIFO queue over the same arrivals
+    (measured service times), and the served results' statistics against the plain
+    FP64 ones.  Under several ranks each rank serves its share of the requests (dealt
+    out by body count)."""
+    from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED, Scene
+    from paper_2301_00611_gb300 import serve
+    import workloads
+    reqs_all = served_requests()
+    mine = assign_units([r["n"] for r in reqs_all], world)[rank]
+    reqs = [reqs_all[i] for i in mine]
+    built = {rq["id"]: workloads.request_workload(rq) for rq in reqs}
+    _sync()
+    results, summary, wall = serve.serve_stream(reqs, lambda rq: built[rq["id"]], 0, DEM_MIXED,
+                                                args.tick_steps, _served_velgrad)
+    lat = [results[rq["id"]]["latency"] for rq in reqs]
+    # plain FP64 FIFO over the same arrivals
+    t_free, plain_lat, busy, pairs, ns = 0.0, [], 0.0, [], []
+    for rq in sorted(reqs, key=lambda r: r["arrival"]):
+        w = built[rq["id"]]
+        dt = serve.pwave_dt(w)
+        _sync()
+        t0 = time.perf_counter()
+        st = _plain_run(Scene, w, rq["steps"], DEM_FP64, dt=dt,
+                        velgrad=_served_velgrad(rq, w, dt))
+        _sync()
+        svc = time.perf_counter() - t0
+        busy += svc
+        start = max(t_free, rq["arrival"])
+        t_free = start + svc
+        plain_lat.append(t_free - rq["arrival"])
+        pairs.append((results[rq["id"]]["stats"], st))
+        ns.append(w.n)
+    # chaos floor: the plain FP64 path against itself, coordinates moved by one ulp
+    pairs_ulp, ns_ulp = [], []
+    by_id = {rq["id"]: k for k, rq in enumerate(sorted(reqs, key=lambda r: r["arrival"]))}
+    for rq in reqs[::2]:
+        w = built[rq["id"]]
+        dt = serve.pwave_dt(w)
+        pairs_ulp.append((_plain_run(Scene, w, rq["steps"], DEM_FP64, dt=dt,
+                                     velgrad=_served_velgrad(rq, w, dt), nudge=True),
+                          pairs[by_id[rq["id"]]][1]))
+        ns_ulp.append(w.n)
+    scene_steps = sum(rq["steps"] for rq in reqs)
+    local = {"lat": lat, "plain_lat": plain_lat, "wall": wall, "busy": busy,
+             "scene_steps": scene_steps, "body_steps": summary["body_steps"],
+             "pairs": pairs, "ns": ns, "max_resident": summary["max_resident"],
+             "pairs_ulp": pairs_ulp, "ns_ulp": ns_ulp,
+             "conc": summary["concurrency_mean"], "device_bytes": summary["device_bytes"],
+             "budget": summary["budget_bytes"], "rows_per_body": summary["rows_per_body"]}
+    allr = gather_ranks(local, world)
+    if rank != 0:
+        return None
+    lat = [x for r in allr for x in r["lat"]]
+    plain_lat = [x for r in allr for x in r["plain_lat"]]
+    wall = max(r["wall"] for r in allr)
+    busy = max(r["busy"] for r in allr)
+    ss = sum(r["scene_steps"] for r in allr)
+    return {"workload": f"{len(reqs_all)} requests, Poisson 200/s, spheres log-uniform "
+                        "[1000, 50000], steps U[500, 2000], deposition/compaction mix",
+            "p50_s": serve.percentile(lat, 50), "p99_s": serve.percentile(lat, 99),
+            "scene_steps_per_s": ss / wall,
+            "body_steps_per_s": sum(r["body_steps"] for r in allr) / wall, "wall_s": wall,
+            "concurrency_mean": allr[0]["conc"], "concurrency_max": allr[0]["max_resident"],
+            "admission": {"budget_bytes": allr[0]["budget"],
+                          "device_bytes_max": allr[0]["device_bytes"],
+                          "rows_per_body_estimate": allr[0]["rows_per_body"]},
+            "dtype": "mixed", "ranks": world,
+            "plain_fp64_fifo": {"p50_s": serve.percentile(plain_lat, 50),
+                                "p99_s": serve.percentile(plain_lat, 99),
+                                "scene_steps_per_s": ss / busy, "dtype": "f64"},
+            "accuracy_vs_plain_fp64": _stat_errors([p for r in allr for p in r["pairs"]],
+                                                   [n for r in allr for n in r["ns"]]),
+            "chaos_floor_fp64_one_ulp": _stat_errors([p for r in allr for p in r["pairs_ulp"]],
+                                                     [n for r in allr for n in r["ns_ulp"]])}
+
+
 def run_serve(args):
-    """Serving: a Poisson stream of deposition / compaction requests replayed in real
-    time against the continuous-batching server (mixed precision), then the same
-    requests through the plain FP64 one-scene-at-a-time path as a FIFO queue."""
+    """Serving (config 4): a Poisson stream of deposition / compaction requests (spheres
+    log-uniform [1000, 200000], steps U[500, 5000]) replayed in real time against the
+    library's request server (dem_server_*, mixed precision, admission by device
+    footprint within --serve-budget-gb), then the same requests through the plain FP64
+    one-scene-at-a-time path as a FIFO queue over the same arrivals."""
     import multiprocessing as mp
     import workloads
     reqs = workloads.serving_requests(args.requests, 4, args.rate)
@@ -653,55 +947,47 @@ def run_serve(args):
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         built = dict(zip([r["id"] for r in reqs], pool.map(workloads.request_workload, reqs)))
     import torch
-    from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED
-    from paper_2301_00611_gb300.serve import percentile, run_alone, serve_stream
+    from paper_2301_00611_gb300 import DEM_FP64, DEM_MIXED, Scene
+    from paper_2301_00611_gb300 import serve
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-
-    def velgrad_for(rq, w):
-        if not w.periodic:
-            return None
-        steps = rq["steps"]
-        return lambda dt: workloads.compaction_rate(0.30, 0.62, steps, dt) * np.eye(3)
-
-    srv, wall = serve_stream(reqs, lambda rq: built[rq["id"]], args.serve_capacity, DEM_MIXED,
-                             args.tick_steps, velgrad_for)
-    lat = [r.latency for r in srv.results]
-    srv.close()
-    # plain FP64 path, one scene at a time in arrival order (FIFO): measured service
-    # times, queueing from the same arrival times
-    t_free = 0.0
-    plain_lat = []
-    plain_busy = 0.0
+    budget = int(args.serve_budget_gb * 2 ** 30)
+    results, summary, wall = serve.serve_stream(reqs, lambda rq: built[rq["id"]], budget,
+                                                DEM_MIXED, args.tick_steps, _served_velgrad)
+    lat = [r["latency"] for r in results.values()]
+    t_free, plain_lat, busy = 0.0, [], 0.0
     for rq in sorted(reqs, key=lambda r: r["arrival"]):
         w = built[rq["id"]]
-        vg = velgrad_for(rq, w)
+        dt = serve.pwave_dt(w)
         _sync()
         t0 = time.perf_counter()
-        run_alone(w, rq["steps"], DEM_FP64, vg)
+        serve.run_alone(w, rq["steps"], DEM_FP64, _served_velgrad(rq, w, dt), dt=dt)
         _sync()
         svc = time.perf_counter() - t0
-        plain_busy += svc
+        busy += svc
         start = max(t_free, rq["arrival"])
         t_free = start + svc
         plain_lat.append(t_free - rq["arrival"])
     scene_steps = sum(rq["steps"] for rq in reqs)
     line = {
         "metric": "served p50/p99 latency and scene-steps/s (Poisson request stream)",
-        "value": percentile(lat, 99), "unit": "s (p99 latency)", "higher_is_better": False,
-        "n_gpus": 1, "data": "synthetic (seeded)",
-        "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, spheres log-uniform "
-                               "[1000, 200000], steps U[500, 5000], deposition/compaction mix",
-                   "capacity_bodies": args.serve_capacity, "tick_steps": args.tick_steps},
-        "served": {"p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+        "value": serve.percentile(lat, 99), "unit": "s (p99 latency)",
+        "higher_is_better": False, "n_gpus": 1, "data": "synthetic (seeded)",
+        "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, spheres "
+                               "log-uniform [1000, 200000], steps U[500, 5000], "
+                               "deposition/compaction mix",
+                   "budget_bytes": summary["budget_bytes"], "tick_steps": args.tick_steps},
+        "served": {"p50_s": serve.percentile(lat, 50), "p99_s": serve.percentile(lat, 99),
                    "scene_steps_per_s": scene_steps / wall, "wall_s": wall,
-                   "body_steps_per_s": srv.body_steps / wall,
-                   "concurrency_mean": float(np.mean(srv.concurrency)) if srv.concurrency else 0,
-                   "concurrency_max": max(srv.concurrency) if srv.concurrency else 0,
-                   "ticks": srv.ticks, "dtype": "mixed"},
-        "plain_fp64_fifo": {"p50_s": percentile(plain_lat, 50), "p99_s": percentile(plain_lat, 99),
-                            "scene_steps_per_s": scene_steps / plain_busy, "dtype": "f64"},
+                   "body_steps_per_s": summary["body_steps"] / wall,
+                   "concurrency_mean": summary["concurrency_mean"],
+                   "concurrency_max": summary["max_resident"], "ticks": summary["ticks"],
+                   "device_bytes_max": summary["device_bytes"],
+                   "rows_per_body_estimate": summary["rows_per_body"], "dtype": "mixed"},
+        "plain_fp64_fifo": {"p50_s": serve.percentile(plain_lat, 50),
+                            "p99_s": serve.percentile(plain_lat, 99),
+                            "scene_steps_per_s": scene_steps / busy, "dtype": "f64"},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -710,6 +996,9 @@ def run_serve(args):
 # ---------------------------------------------------------------- triaxial loading
 
 TRIAX_N = 4_000_000
+# the triaxial case folded into the headline line: the same loading at one million
+# spheres (seeding the four-million-sphere cloud alone takes about a minute on the host)
+TRIAX_HEADLINE_N = 1_000_000
 TRIAX_LOAD_STEPS = 10_000
 TRIAX_WORKLOAD = ("triaxial loading of a dense periodic packing: {n} spheres, radii uniform "
                   "[0.8, 1.2] mm, friction 0.5 rad, 1% axial strain per 10,000 steps, lateral "
@@ -717,6 +1006,12 @@ TRIAX_WORKLOAD = ("triaxial loading of a dense periodic packing: {n} spheres, ra
 
 
 def run_triax(args):
+    n = args.n if args.n is not None else TRIAX_N
+    print(json.dumps(triax_measure(args, n, args.steps)), flush=True)
+    return 0
+
+
+def triax_measure(args, n, steps=None):
     """The four-million-sphere triaxial case in mixed precision.  Untimed preparation: a
     seeded loose cloud (solid fraction 0.3) compacted isotropically over 3000 steps and
     relaxed for 300; the lateral stress it reaches becomes the servo's goal.  Loading:
@@ -730,7 +1025,6 @@ def run_triax(args):
     __graft_entry__.build()
     from paper_2301_00611_gb300 import Scene, DEM_MIXED
     peak, peak_kind = _peaks()
-    n = args.n if args.n is not None else TRIAX_N
     w = workloads.periodic_cloud(n, 2, phi=0.3, rmin=0.8e-3, rmax=1.2e-3, friction=0.5)
     s = Scene.from_workload(w, precision=DEM_MIXED)
     dt = s.dt()
@@ -757,7 +1051,7 @@ def run_triax(args):
         shape = s.autotune(steps_per_trial=TUNE_STEPS)
     W = args.warmup
     done = s.clock()[0] - it0
-    K = TRIAX_LOAD_STEPS - done - W if args.steps is None else args.steps
+    K = TRIAX_LOAD_STEPS - done - W if steps is None else steps
     s.step(W)
     st0 = s.stats()
     s.set_timing(True)
@@ -812,8 +1106,30 @@ def run_triax(args):
         "roofline": rl,
         "roofline_kernels": rk,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+def compaction_1a_measure(args, Scene, peak, peak_kind, fp64_peak):
+    """Config "1a": the 1M compaction at the stated strain rate, 1e-2 per second (the
+    cell barely moves in 5000 steps: the packing stays a loose cloud near 0.30), FP64;
+    every step after the warm-up is timed."""
+    w = make_workload(N_BODIES)   # the same seeded cloud; only the loading differs
+    rate = -1e-2
+    res = _time_window(Scene, w, args, "fp64", 1, 0, None,
+                       velgrad=lambda dt: np.diag([rate, rate, rate]),
+                       K=JOB_STEPS - args.warmup)
+    rl, _ = _kernel_rooflines(res, "fp64", w.n, peak, peak_kind, traffic=False,
+                              fp64_peak=fp64_peak)
+    K = res["K"]
+    return {"workload": f"periodic isotropic compaction at the stated strain rate 1e-2/s, "
+                        f"1M log-normal spheres, 5000 steps (FP64)",
+            "value": w.n * K / res["T"], "unit": UNIT, "ms_per_step": res["ms"] / K,
+            "timed_window": f"last {K} steps after {args.warmup} warm-up",
+            "contacts": {"start": res["st0"]["n_contacts"], "end": res["st1"]["n_contacts"]},
+            "packing_fraction_end": res["st1"]["packing_fraction"],
+            "contact_updates_per_s": res["mean_real"] * K / res["T"],
+            "collider_runs": res["tm"]["collider_runs"], "clocks": res["clocks"],
+            "roofline": rl}
 
 
 def main():
@@ -839,12 +1155,17 @@ def main():
                     choices=["headline", "batch", "serve", "triax"])
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched deposition sweep out of the headline line")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the served request stream out of the headline line")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave the 4M triaxial loading and config 1a out of the headline line")
     ap.add_argument("--batch-scenes", type=int, default=BATCH_SCENES)
     ap.add_argument("--batch-plain-every", type=int, default=1,
                     help="time the plain FP64 path on every k-th scene of the sweep")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--serve-capacity", type=int, default=4_000_000)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0,
+                    help="device-memory budget of the serve mode's resident requests")
     ap.add_argument("--tick-steps", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -666,6 +666,18 @@ dem_status dem_find_pairs_noalloc(const double *pos_dev, const double *radius_de
                                   long long cap, int *id1_dev, int *id2_dev, int *cell_dist_dev,
                                   long long *count, void *cuda_stream);
 
+/* Measured FP64 throughput of this GPU in TFLOP/s: the denominator of the FP64
+ * kernels' roofline.  The paper has no counterpart.  Each thread of a grid of
+ * resident 256-thread blocks on every SM runs sixteen independent fused
+ * multiply-add chains for `iters` iterations (rounded up to a multiple of 4; 2 flops
+ * each); *tflops receives the
+ * best rate of `repeats` timed launches after one warm-up launch (CUDA events on
+ * cuda_stream, NULL: the default stream; a few bytes of scratch are allocated on it
+ * and freed).  Waits are bounded (DEM_TIMEOUT_S).  Errors: INVALID_ARG (iters < 1,
+ * repeats < 1, null tflops), TIMEOUT, CUDA (dem_last_error(NULL)). */
+dem_status dem_measure_fp64_peak(long long iters, int repeats, void *cuda_stream,
+                                 double *tflops);
+
 /* Message of the last error on this scene ("" if none).  NULL scene: the last
  * error of a failed dem_scene_create or dem_find_pairs in this thread. */
 const char *dem_last_error(const dem_scene *scene);

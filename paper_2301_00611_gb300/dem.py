@@ -232,6 +232,7 @@ _SIGS = {
     "dem_server_release": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "dem_server_stats": (ctypes.c_int, [_P, _P]),
     "dem_server_last_error": (ctypes.c_char_p, [_P]),
+    "dem_measure_fp64_peak": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _P, _P]),
     "dem_last_error": (ctypes.c_char_p, [_P]),
     "dem_version": (ctypes.c_char_p, []),
 }
@@ -827,6 +828,17 @@ def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, str
             m = cnt.value
             return I[:m], J[:m], C[:m]
         cap = cnt.value
+
+
+def measure_fp64_peak(iters=6000, repeats=5, stream=None):
+    """dem_measure_fp64_peak: the FP64 FMA throughput of this GPU in TFLOP/s."""
+    lib = load_library()
+    v = ctypes.c_double()
+    st = _current_stream() if stream is None else stream
+    rc = lib.dem_measure_fp64_peak(int(iters), int(repeats), st, ctypes.byref(v))
+    if rc != DEM_OK:
+        raise DemError(rc, lib.dem_last_error(None).decode())
+    return v.value
 
 
 def version() -> str:

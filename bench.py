@@ -336,51 +336,72 @@ def tune_shape(Scene, w, args, precision):
     return shape
 
 
-def _time_window(Scene, w, args, precision, world, local, shape=None, capture_start=False,
-                 velgrad=velgrad_for, K=None):
-    """Run the job to its timed window on one scene; returns the measurements (and,
-    with capture_start, the scene's state at the first timed step)."""
+def _run_window(Scene, w, prec, shape, velgrad, K, W, world, local, timing, capture_start):
+    """The job on a fresh scene up to its last K steps, then those K steps timed with
+    CUDA events (with or without the per-kernel events of dem_set_timing)."""
     import torch
-    from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
     stream = torch.cuda.current_stream()
-    prec = DEM_MIXED if precision == "mixed" else DEM_FP64
     scene = Scene.from_workload(w, capacity_bodies=w.n, precision=prec)
     if shape:
         scene.set_tuning(**shape)
     dt = scene.dt()
     scene.set_cell_velgrad(velgrad(dt))
-    K = args.steps if K is None else K
-    W = args.warmup
     prelude = max(0, JOB_STEPS - W - K)
     if prelude:
         scene.step(prelude)
     scene.step(W)
     st0 = scene.stats()
     start = export_window_start(scene) if capture_start else None
-    scene.set_timing(True)
+    scene.set_timing(timing)
     t_before = scene.timing()["kernel_launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # an NVTX range around the timed steps, so that a profiler can take exactly them
+    # (ncu --nvtx --nvtx-include "<precision>_window/"); no cost without a profiler
+    rng = ("mixed" if prec == 1 else "fp64") + ("_window_events" if timing else "_window")
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push(rng)
         e0.record(stream)
         scene.step(K)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     tm = scene.timing()
     st1 = scene.stats()
     scene.close()
+    return {"ms": ms, "dt": dt, "prelude": prelude, "tm": tm, "st0": st0, "st1": st1,
+            "launches": tm["kernel_launches"] - t_before, "clocks": clk.summary(),
+            "start": start}
+
+
+def _time_window(Scene, w, args, precision, world, local, shape=None, capture_start=False,
+                 velgrad=velgrad_for, K=None):
+    """Run the job to its timed window and time its last K steps; returns the
+    measurements (and, with capture_start, the scene's state at the first timed step).
+    The job runs twice: the value comes from a run without per-kernel CUDA events (they
+    cost the step some 2-5%), the per-kernel times and phase shares from a second run of
+    the same job (the same trajectory: every run of a scene is bitwise reproducible)
+    with the events on."""
+    from paper_2301_00611_gb300 import DEM_MIXED, DEM_FP64
+    prec = DEM_MIXED if precision == "mixed" else DEM_FP64
+    K = args.steps if K is None else K
+    W = args.warmup
+    plain = _run_window(Scene, w, prec, shape, velgrad, K, W, world, local, False, capture_start)
+    timed = _run_window(Scene, w, prec, shape, velgrad, K, W, world, local, True, False)
+    ms, tm = plain["ms"], timed["tm"]
+    st0, st1 = plain["st0"], plain["st1"]
     T = max_over_ranks(ms / 1e3, world, "cuda")
     mean_real = 0.5 * (st0["n_contacts"] + st1["n_contacts"])
     avg_ms = tm["contact_ms"] / max(1, tm["contact_launches"])
     rows_avg = tm["rows_processed"] / max(1, tm["contact_launches"])
-    return {"T": T, "ms": ms, "dt": dt, "prelude": prelude, "tm": tm, "st0": st0, "st1": st1,
+    return {"T": T, "ms": ms, "ms_timed": timed["ms"], "dt": plain["dt"],
+            "prelude": plain["prelude"], "tm": tm, "st0": st0, "st1": st1,
             "mean_real": mean_real, "avg_ms": avg_ms, "rows_avg": rows_avg, "K": K,
-            "launches": tm["kernel_launches"] - t_before, "clocks": clk.summary(),
-            "start": start}
+            "launches": plain["launches"], "clocks": plain["clocks"], "start": plain["start"]}
 
 
 # Algorithmic bytes of the mixed-precision contact kernel (per row), from its operand list:
@@ -556,8 +577,8 @@ def run_gpu(args):
     value = job_rate(world, args.n * K, T)
     contact_updates = world * res["mean_real"] * K / T
     rows_per_s = world * tm["rows_processed"] / T
-    share = {k: tm[k] / max(1e-9, ms) for k in ("contact_ms", "integrate_ms", "cell_ms",
-                                                "collider_ms")}
+    share = {k: tm[k] / max(1e-9, res["ms_timed"]) for k in ("contact_ms", "integrate_ms",
+                                                              "cell_ms", "collider_ms")}
     rl64, rk64 = _kernel_rooflines(res, "fp64", args.n, peak, peak_kind, fp64_peak=fp64_peak)
     # the whole step against the survey's algorithmic bytes (N 180 B + C 470 B per step)
     step_bytes = SURVEY_STEP_BODY_BYTES * args.n + SURVEY_STEP_CONTACT_BYTES * res["mean_real"]
@@ -571,7 +592,7 @@ def run_gpu(args):
             "dtype": "mixed: f32 contact geometry/law, f64 shear history, integration and "
                      "reductions",
             "contact_updates_per_s": world * mixed["mean_real"] * K / mixed["T"],
-            "phase_share": {k: mixed["tm"][k] / max(1e-9, mixed["ms"])
+            "phase_share": {k: mixed["tm"][k] / max(1e-9, mixed["ms_timed"])
                             for k in ("contact_ms", "integrate_ms", "cell_ms", "collider_ms")},
             "collider_runs": mixed["tm"]["collider_runs"], "gpu_launches": mixed["launches"],
             "launch_shape": mixed["shape"],
@@ -630,6 +651,11 @@ def run_gpu(args):
                          "candidates_end": st1["n_candidates"],
                          "packing_fraction_end": st1["packing_fraction"]},
             "phase_share": share,
+            "timing_note": "value and ms_per_step: the window run without per-kernel CUDA "
+                           "events; phase shares, collider runs and the kernels' launch "
+                           "times (roofline): a second run of the same job with the events "
+                           "on (ms_per_step_instrumented)",
+            "ms_per_step_instrumented": res["ms_timed"] / K,
             "step_hbm_survey_bytes": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
                                       "frac": step_gbs / peak, "peak_kind": peak_kind},
             "fp64_peak_tflops": {"measured": fp64_peak, "derived": FP64_PEAK_TFLOPS},

@@ -274,38 +274,77 @@ __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict
         const int4 ij = cr.info[j];
         c0 = inf.y - ij.y + w[0]; c1 = inf.z - ij.z + w[1]; c2 = inf.w - ij.w + w[2];
       }
-      const bool fwd = ids < b.id[j];
+      const int idj = b.id[j];
+      const bool fwd = ids < idj;
       const int g1 = fwd ? s : j, g2 = fwd ? j : s;
       const int r = t.row_start[g1] + atomicAdd(&ufill[g1], 1);
       if (r < t.row_start[g1 + 1]) {
         t.pair[r] = make_int2(g1, g2);
         t.cpack[r] = fwd ? pack_shift(c0, c1, c2) : pack_shift(-c0, -c1, -c2);   // shift of body 2
+        t.found[r] = fwd ? idj : ids;   // sort key: the id of body 2 (scratch until the merge)
       }
     }
   });
 }
 
 // Sort each body's own row range by (id of body 2, shift): the order the atomics left
-// open becomes the order of the partner ids.
-__global__ void k_rowsort(Table t, const int *__restrict__ id, long long N) {
+// open becomes the order of the partner ids.  Keys (the partner ids) come from the emit
+// in t.found; a range of up to kSortLocal rows is sorted in registers and local memory,
+// a longer one in place.
+constexpr int kSortLocal = 48;
+__global__ void k_rowsort(Table t, long long N) {
   const long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
-  const int r0 = t.row_start[sl], r1 = t.row_start[sl + 1];
+  const int r0 = t.row_start[sl], r1 = t.row_start[sl + 1], n = r1 - r0;
+  if (n < 2) return;
+  if (n <= kSortLocal) {
+    long long key[kSortLocal];   // (partner id, shift as unsigned) | position
+    int2 pr[kSortLocal];
+    int cp[kSortLocal];
+    for (int a = 0; a < n; ++a) {
+      pr[a] = t.pair[r0 + a];
+      cp[a] = t.cpack[r0 + a];
+      key[a] = ((long long)t.found[r0 + a] << 32) | (long long)(unsigned)cp[a];
+    }
+    int ord[kSortLocal];
+    for (int a = 0; a < n; ++a) {
+      int q = a - 1;
+      const long long kv = key[a];
+      while (q >= 0 && key[ord[q]] > kv) {
+        ord[q + 1] = ord[q];
+        --q;
+      }
+      ord[q + 1] = a;
+    }
+    for (int a = 0; a < n; ++a) {
+      t.pair[r0 + a] = pr[ord[a]];
+      t.cpack[r0 + a] = cp[ord[a]];
+    }
+    return;
+  }
   for (int a = r0 + 1; a < r1; ++a) {
     const int2 pv = t.pair[a];
     const int cv = t.cpack[a];
-    const int kv = id[pv.y];
+    const int kv = t.found[a];
     int q = a - 1;
     while (q >= r0) {
-      const int kq = id[t.pair[q].y];
+      const int kq = t.found[q];
       if (kq < kv || (kq == kv && (unsigned)t.cpack[q] <= (unsigned)cv)) break;
       t.pair[q + 1] = t.pair[q];
       t.cpack[q + 1] = t.cpack[q];
+      t.found[q + 1] = kq;
       --q;
     }
     t.pair[q + 1] = pv;
     t.cpack[q + 1] = cv;
+    t.found[q + 1] = kv;
   }
+}
+
+// After the row sort: t.found[r] = the id of body 1 of row r (the down lists' key).
+__global__ void k_rowkey(Table t, const int *__restrict__ id) {
+  const long long k = (long long)blockIdx.x * kT + threadIdx.x;
+  if (k < t.P) t.found[k] = id[t.pair[k].x];
 }
 
 // Down lists: every row is entered in the list of its body 2 (dfill zeroed), at a
@@ -342,18 +381,38 @@ __global__ void k_ref_branch(Table t, Bodies b, const Grid *__restrict__ grids, 
 }
 
 // the down lists were filled in atomic order: sort each body's list by (id of body 1,
-// row); rows of one body 1 are ordered by shift within its range already
-__global__ void k_downsort(Table t, const int *__restrict__ id, long long N) {
+// row); rows of one body 1 are ordered by shift within its range already.  Keys come
+// from t.found (k_rowkey); short lists are sorted in registers and local memory.
+__global__ void k_downsort(Table t, long long N) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
-  const int e0 = t.down_start[sl], e1 = t.down_start[sl + 1];
+  const int e0 = t.down_start[sl], e1 = t.down_start[sl + 1], n = e1 - e0;
+  if (n < 2) return;
+  if (n <= kSortLocal) {
+    long long key[kSortLocal];   // (id of body 1) << 32 | row
+    for (int a = 0; a < n; ++a) {
+      const int v = t.down[e0 + a];
+      key[a] = ((long long)t.found[v] << 32) | (long long)(unsigned)v;
+    }
+    for (int a = 1; a < n; ++a) {
+      const long long kv = key[a];
+      int q = a - 1;
+      while (q >= 0 && key[q] > kv) {
+        key[q + 1] = key[q];
+        --q;
+      }
+      key[q + 1] = kv;
+    }
+    for (int a = 0; a < n; ++a) t.down[e0 + a] = (int)(unsigned)(key[a] & 0xffffffffLL);
+    return;
+  }
   for (int a = e0 + 1; a < e1; ++a) {
     const int v = t.down[a];
-    const int kv = id[t.pair[v].x];
+    const int kv = t.found[v];
     int b = a - 1;
     while (b >= e0) {
       const int u = t.down[b];
-      const int ku = id[t.pair[u].x];
+      const int ku = t.found[u];
       if (ku < kv || (ku == kv && u < v)) break;
       t.down[b + 1] = u;
       --b;
@@ -545,8 +604,11 @@ void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const G
   if (N <= 0) return;
   k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
                                    ufill);
-  k_rowsort<<<blocks(N), kT, 0, st>>>(t, b.id, N);
-  if (t.P > 0) k_downfill<<<blocks(t.P), kT, 0, st>>>(t, dfill);
+  k_rowsort<<<blocks(N), kT, 0, st>>>(t, N);
+  if (t.P > 0) {
+    k_rowkey<<<blocks(t.P), kT, 0, st>>>(t, b.id);
+    k_downfill<<<blocks(t.P), kT, 0, st>>>(t, dfill);
+  }
 }
 
 void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int multi,
@@ -555,7 +617,8 @@ void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int m
 }
 
 void launch_downsort(const Table &t, const int *id, long long N, cudaStream_t st) {
-  if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, id, N);
+  (void)id;   // the keys are in t.found (k_rowkey)
+  if (N > 0) k_downsort<<<blocks(N), kT, 0, st>>>(t, N);
 }
 
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st) {

@@ -432,9 +432,10 @@ INT_BYTES_BODY_MIXED, INT_BYTES_REAL_MIXED = 393, 68
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the step
-# kernels, from one ncu capture of this workload's last steps (the profile under
-# profiles/ gives the command): the mean of the captured launches near step 4990, which
-# process `rows` candidate rows and `real` real contacts each.  A figure describes the
+# kernels, from one ncu capture of this workload's timed window (the last 30 steps,
+# taken through the NVTX ranges the window is marked with; the profile under profiles/
+# gives the command): the mean of the captured working launches, which process `rows`
+# candidate rows and about `real` real contacts each.  A figure describes the
 # kernel sources whose digest is stored with it and is reported as null for any other
 # build (the integrator's include the collider, which sets the body order it runs in).
 KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
@@ -443,14 +444,14 @@ KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                                 "mixed": ("integrate.cu", "collider.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
-    ("fp64", "contact"): {"bytes": 665.1e6, "rows": 4649044, "real": 2617303, "step": 4990,
-                          "digest": "f4308e41218445ac"},
-    ("fp64", "integrate"): {"bytes": 611.5e6, "rows": 4649044, "real": 2617303, "step": 4990,
-                            "digest": "071358e3cd5fef2b"},
-    ("mixed", "contact"): {"bytes": 374.6e6, "rows": 4649044, "real": 2618461, "step": 4990,
-                           "digest": "429ebbfa621f2246"},
-    ("mixed", "integrate"): {"bytes": 491.3e6, "rows": 4649044, "real": 2618461, "step": 4990,
-                             "digest": "071358e3cd5fef2b"},
+    ("fp64", "contact"): {"bytes": 809.9e6, "rows": 4654409, "real": 2602000, "step": 4985,
+                          "digest": "402a7bce659f63ff"},
+    ("fp64", "integrate"): {"bytes": 641.3e6, "rows": 4654409, "real": 2602000, "step": 4985,
+                            "digest": "961d098e74bcafd4"},
+    ("mixed", "contact"): {"bytes": 589.2e6, "rows": 4654409, "real": 2603000, "step": 4985,
+                           "digest": "40382b31018e060a"},
+    ("mixed", "integrate"): {"bytes": 529.4e6, "rows": 4654409, "real": 2603000, "step": 4985,
+                             "digest": "961d098e74bcafd4"},
 }
 
 
@@ -466,7 +467,7 @@ def _traffic(precision, name, algorithmic_at):
     t = TRAFFIC.get((precision, name))
     if not t or t["digest"] != kernel_digest(name, precision):
         return None, None
-    note = (f"ncu DRAM bytes per launch near step {t['step']} of the job ({t['rows']} rows, "
+    note = (f"ncu DRAM bytes per launch in the last 30 steps of the job ({t['rows']} rows, "
             f"{t['real']} real contacts; the algorithmic bytes of such a launch are "
             f"{algorithmic_at(t['rows'], t['real']):.4g}); {TRAFFIC_PROFILE}")
     return t["bytes"], note

@@ -87,9 +87,16 @@ def compare_contacts(co, cg, band=frozenset(), tol=TOL, eps=EPS, coord=None):
     scale = np.linalg.norm(co["fn"][a], axis=1) + np.linalg.norm(co["fs"][a], axis=1)
     X = _coord_scale() if coord is None else coord
     ulp_force = co["phys"][a, 0] * ULPS * eps * X
+    widened = np.zeros(len(keys), dtype=bool)
     for f in ("fn", "fs"):
-        e = np.max(np.abs(cg[f][b] - co[f][a]), axis=1) / (tol * scale + ulp_force)
+        d = np.max(np.abs(cg[f][b] - co[f][a]), axis=1)
+        e = d / (tol * scale + ulp_force)
         worst[f] = float(e.max()) * tol
+        widened |= d > tol * scale   # held only by the absolute rounding allowance
+    # contacts whose force error is above the relative bar alone (the allowance for the
+    # rounding of the penetration, a difference of two numbers of the reach's size)
+    worst["widened_count"] = int(widened.sum())
+    worst["widened_frac"] = float(widened.mean())
     worst["normal"] = float(np.max(np.abs(cg["normal"][b] - co["normal"][a]))) * (EPS / eps)
     rs = np.abs(co["phys"][a])
     worst["phys"] = float(np.max(np.abs(cg["phys"][b] - co["phys"][a]) / np.maximum(rs, 1e-300)))

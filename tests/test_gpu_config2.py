@@ -130,6 +130,9 @@ def test_four_million_sphere_triaxial_step_and_servo():
     set_coord_scale(X)
     so, sg = o.state(), g.state()
     flips = _damping_sign_flips(so, sg, s0, co, cl["prev_velgrad"], w, dt, reach)
+    # reported with -s (and in the failure message) so that a drift of the count shows
+    print(f"config2: {flips} velocity/spin components moved onto the oracle's damping "
+          f"branch (cap {int(1e-3 * N)})")
     assert flips <= 1e-3 * N, flips
     compare_states(so, sg, X, tol=TOL, co=co, masses=masses_of(w), dt=dt, eps=EPS32,
                    coord=reach)

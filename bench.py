@@ -405,10 +405,11 @@ def _time_window(Scene, w, args, precision, world, local, shape=None, capture_st
 
 
 # Algorithmic bytes of the mixed-precision contact kernel (per row), from its operand list:
-#   every row:     pair 8 + cell shift 4 + reference branch/kn 16 + two FP32 offsets 32 = 60
+#   every row:     pair 8 + cell shift 4 + reference branch/kn 16 + squared reference gap 4
+#                  + two FP32 offsets 32 = 64
 #   real rows add: FP64 shear history 32 + normal/ks 16 + two FP32 velocity/spin 64
 #                  + writes history 32, normal 16, F/d1 16, M/d2 16 = 192
-ROW_BYTES_ALL_MIXED = 60
+ROW_BYTES_ALL_MIXED = 64
 ROW_BYTES_REAL_MIXED = 192
 TUNE_AT = 4500      # step of the job at which the launch shapes are tuned (the dense end,
                     # where most of the step time is spent)

@@ -376,8 +376,13 @@ __global__ void k_ref_branch(Table t, Bodies b, const Grid *__restrict__ grids, 
     if (g.sheared)   // Href c of a sheared cell
       for (int q = 0; q < 3; ++q) h[q] = g.H[3 * q] * c0 + g.H[3 * q + 1] * c1 + g.H[3 * q + 2] * c2;
   }
-  t.g32[k] = make_float4((float)((p2.x + h[0]) - p1.x), (float)((p2.y + h[1]) - p1.y),
-                         (float)((p2.z + h[2]) - p1.z), 0.0f);
+  const double gx = (p2.x + h[0]) - p1.x, gy = (p2.y + h[1]) - p1.y, gz = (p2.z + h[2]) - p1.z;
+  t.g32[k] = make_float4((float)gx, (float)gy, (float)gz, 0.0f);
+  // the squared gap of the reference configuration, in FP64 before any rounding: the
+  // mixed kernel's penetration is this minus the FP32 terms of the offsets, so it keeps
+  // FP32's relative precision of the gap rather than of the branch length
+  const double R = p1.w + p2.w;
+  t.s0[k] = (float)(R * R - (gx * gx + gy * gy + gz * gz));
 }
 
 // the down lists were filled in atomic order: sort each body's list by (id of body 1,

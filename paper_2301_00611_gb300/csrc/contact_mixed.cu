@@ -7,7 +7,9 @@
 //         per-row FP32 reference branch vector (xref2 + Href c - xref1, formed in
 //         FP64 at the collider run and rounded once) plus the FP32 offsets of
 //         both bodies from their own FP64 positions at that run, plus the FP32
-//         change of the cell shift (H - Href) c; normal, penetration, relative
+//         change of the cell shift (H - Href) c; the contact test and the
+//         penetration from the squared gap (reference gap formed in FP64 at the
+//         run, corrected by the FP32 offset terms); normal, penetration, relative
 //         velocity, stiffnesses, normal force, output force and torque arms.
 //   FP64  the shear-force history: the transport into the new contact frame
 //         (-Fs x (n- x n) - Fs x (dt/2 n.(w1+w2) n)) and the shear increment are
@@ -17,7 +19,7 @@
 // 1e-7 relative resolution of the branch length whatever the cell extent.
 //
 // Traffic per real row: 172 B read (row 28 + history 48 + two bodies 96),
-// 80 B written; per non-real row 60 B read -- about 60% of the FP64 kernel's.
+// 80 B written; per non-real row 64 B read -- about 60% of the FP64 kernel's.
 // GB300's FP64 pipe issues ~2 instructions per clock per SM and also carries
 // every double<->float conversion, so at the HBM rate (~21 B per clock per SM) a
 // real row affords ~25 FP64-pipe instructions: this kernel uses ~12 (three
@@ -29,11 +31,13 @@ namespace dem {
 namespace {
 constexpr int kQ = 64;   // per-warp queue of real rows (< 32 left over + 32 new)
 
-// Queued real row: its index, FP32 branch vector, squared length, radii, sub-scene.
+// Queued real row: its index, FP32 branch vector, squared length, radii, sub-scene,
+// and the squared gap (r1 + r2)^2 - |d|^2 from the reference gap.
 struct QRowF {
   float dx, dy, dz, l2, r1, r2;
   long long k;
-  int q, pad;
+  int q;
+  float gap2;
 };
 
 // What a row needs of its (sub-)scene's cell state in FP32, plus the FP64 step.
@@ -72,7 +76,10 @@ __device__ __forceinline__ void real_row_mixed(const Table &t, const Bodies &b,
   const float l = sqrtf(l2);
   const float il = 1.0f / l;
   const float nx = dx * il, ny = dy * il, nz = dz * il;
-  const float pen = R - l;
+  // R - l = (R^2 - l^2) / (R + l): the penetration from the squared gap, which keeps
+  // FP32's relative precision of the penetration itself (R - l in FP32 would lose it
+  // to the rounding of l, a number of the size of R)
+  const float pen = e.gap2 / (R + l);
   const float4 g = t.g32[k];
   float kn = g.w;
   double4_32a fsd = t.hfs[k];
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
   for (long long base = (long long)blockIdx.x * kT + wi * 32; base < P; base += stride) {
     const long long k = base + lane;
     bool real = false;
-    float dx = 0, dy = 0, dz = 0, l2 = 0, r1 = 0, r2 = 0;
+    float dx = 0, dy = 0, dz = 0, l2 = 0, r1 = 0, r2 = 0, gap2 = 0;
     int sq = 0;
     if (k < P) {
       const int2 pr = t.pair[k];
@@ -208,15 +215,19 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
           hx = dH0 * cx; hy = dH1 * cy; hz = dH2 * cz;
         }
       }
-      // branch vector: reference branch at the collider run + both offsets + the
-      // change of the cell shift since then
-      dx = g.x + (c.x - a.x) + hx;
-      dy = g.y + (c.y - a.y) + hy;
-      dz = g.z + (c.z - a.z) + hz;
+      // branch vector: reference branch at the collider run + the change e of both
+      // offsets and of the cell shift since then; the contact test and the penetration
+      // take the squared gap (r1 + r2)^2 - |g + e|^2 = s0 - 2 g.e - e.e, with s0 formed in
+      // FP64 at the collider run: every FP32 term is then of the size of the gap or of
+      // the motion since the run, not of the branch length
+      const float ex = (c.x - a.x) + hx, ey = (c.y - a.y) + hy, ez = (c.z - a.z) + hz;
+      dx = g.x + ex;
+      dy = g.y + ey;
+      dz = g.z + ez;
       l2 = dx * dx + dy * dy + dz * dz;
       r1 = a.w; r2 = c.w;
-      const float R = r1 + r2;
-      real = l2 < R * R;
+      gap2 = t.s0[k] - (2.0f * (g.x * ex + g.y * ey + g.z * ez) + (ex * ex + ey * ey + ez * ez));
+      real = gap2 > 0.0f;
       if (!real && g.w != 0.0f) {   // contact lost: back to a potential interaction
         t.g32[k] = make_float4(g.x, g.y, g.z, 0.0f);
         t.hfs[k] = make_double4_32a(0, 0, 0, 0);
@@ -227,7 +238,7 @@ __global__ void __launch_bounds__(kT) k_contact_mixed(const StepDesc *__restrict
     const unsigned m = __ballot_sync(0xffffffffu, real);
     if (real) {
       const int at = cnt + __popc(m & ((1u << lane) - 1u));
-      wq[at] = QRowF{dx, dy, dz, l2, r1, r2, k, sq, 0};
+      wq[at] = QRowF{dx, dy, dz, l2, r1, r2, k, sq, gap2};
     }
     cnt += __popc(m);
     __syncwarp();

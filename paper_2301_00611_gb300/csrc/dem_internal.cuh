@@ -91,6 +91,9 @@ struct Table {
   double *tanphi;
   // mixed precision rows (null in FP64 mode)
   float4 *g32;      // (reference branch vector xref2 + Href c - xref1, kn); kn == 0: not real
+  float *s0;        // (r1 + r2)^2 - |reference branch vector|^2, formed in FP64 at the
+                    // collider run and rounded once: the squared gap the FP32 geometry
+                    // corrects by the offsets (contact_mixed.cu)
   float4 *hn32;     // (previous normal, ks)
   float4 *oFM32;    // [2 * rows]: (F on body 2, d1), (-(n x F), d2) per row (32 bytes)
   int *row_start;   // [nbody + 1]
@@ -269,7 +272,8 @@ void launch_downsort(const Table &t, const int *id, long long N, cudaStream_t st
 void launch_degree_order(const Table &t, long long N, int *ws, cudaStream_t st);
 void launch_merge(const Table &nt, const Table &ot, long long N_old, const int *new_to_old,
                   int mixed, cudaStream_t st);
-// mixed tables: reference branch vectors (g32.xyz) of every row, after the emit
+// mixed tables: reference branch vectors (g32.xyz) and squared reference gaps (s0) of
+// every row, after the emit
 void launch_ref_branch(const Table &t, const Bodies &b, const Grid *grids, int multi,
                        cudaStream_t st);
 void launch_lost(const Table &ot, const Bodies &ob, const Grid *grids, int multi, int *err,

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
     for (int wi = 0; wi < 6; ++wi) {
       if (!(c.wall_mask & (1 << wi))) continue;
       const int ax = wi >> 1;
-      const float dist = (float)(xd[ax] - ((wi & 1) ? c.box_hi[ax] : c.box_lo[ax]));
+      const double distd = xd[ax] - ((wi & 1) ? c.box_hi[ax] : c.box_lo[ax]);
+      const float dist = (float)distd;
       const bool was = flags & (2 << wi);
       if (!(fabsf(dist) < r)) {
         if (was) {
@@ -174,7 +175,9 @@ __global__ void __launch_bounds__(kB) k_integrate_mixed(const StepDesc *__restri
       const float sn = dist >= 0 ? 1.0f : -1.0f;
       float n[3] = {0, 0, 0};
       n[ax] = sn;
-      const float pen = r - fabsf(dist);
+      // the penetration in FP64 and rounded once: r - |dist| in FP32 would keep the
+      // precision of r, not of the (much smaller) penetration
+      const float pen = (float)(pd.w - fabs(distd));   // FP64 radius and distance
       double knd, ksd, tpd;
       wall_phys(mats, c.wall_mat, b.mat[s], (double)r, knd, ksd, tpd, c.law);
       const float sqp = c.law ? sqrtf(pen) : 1.0f;   // Hertz-Mindlin: pen^1/2 factors

@@ -368,7 +368,7 @@ dem_status alloc_bodies(dem_scene *s, Bodies &b, long long cap) {
 void free_rows(dem_scene *s, Table &t) {
   dfree(s, t.pair); dfree(s, t.cpack); dfree(s, t.hfs); dfree(s, t.hn); dfree(s, t.oFM);
   dfree(s, t.tanphi); dfree(s, t.down); dfree(s, t.found);
-  dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oFM32);
+  dfree(s, t.g32); dfree(s, t.hn32); dfree(s, t.oFM32); dfree(s, t.s0);
 }
 
 void free_table(dem_scene *s, Table &t) {
@@ -389,7 +389,7 @@ dem_status ensure_table(dem_scene *s, Table &t, long long rows, long long nbody)
         (r = dalloc(s, &t.found, nc)))
       return r;
     if (s->mixed) {
-      if ((r = dalloc(s, &t.g32, nc)) || (r = dalloc(s, &t.hn32, nc)) ||
+      if ((r = dalloc(s, &t.g32, nc)) || (r = dalloc(s, &t.hn32, nc)) || (r = dalloc(s, &t.s0, nc)) ||
           (r = dalloc(s, &t.oFM32, 2 * nc)))
         return r;
     } else if ((r = dalloc(s, &t.hn, nc)) || (r = dalloc(s, &t.oFM, 2 * nc)) ||
@@ -905,7 +905,7 @@ double scene_bytes_per_body(int mixed) {
 }
 double scene_bytes_per_row(int mixed) {
   double row = sizeof(int2) + sizeof(int) + sizeof(double4_32a) + 2 * sizeof(int);
-  if (mixed) row += 2 * sizeof(float4) + 2 * sizeof(float4);
+  if (mixed) row += 2 * sizeof(float4) + 2 * sizeof(float4) + sizeof(float);
   else row += sizeof(double4_32a) + 2 * sizeof(double4_32a) + sizeof(double);
   return 2 * 1.25 * row;
 }
@@ -1993,7 +1993,7 @@ Table row_view(const Table &t, long long o, long long P) {
   sh(v.pair); sh(v.cpack); sh(v.hfs); sh(v.hn); sh(v.tanphi);
   if (v.oFM) v.oFM += 2 * o;
   if (v.oFM32) v.oFM32 += 2 * o;
-  sh(v.g32); sh(v.hn32); sh(v.found);
+  sh(v.g32); sh(v.hn32); sh(v.found); sh(v.s0);
   v.P = P;
   return v;
 }

@@ -72,7 +72,7 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double nx = dx * il, ny = dy * il, nz = dz * il;   // eq. 2.7
   const double pen = R - l;                                  // penetrationDepth
   double kn = fs.w, ks = hn.w, tanphi;
-  if (kn == 0.0) {
+  if (is_zero_bits(kn)) {   // kn == 0: a new contact
     const Mat &m1 = mats[b.mat[pr.x]], &m2 = mats[b.mat[pr.y]];
     if ((kFeat & 1) && rc.law) {   // Ip2_FrictMat_FrictMat_MindlinPhys: constants kno, kso
       mindlin_phys(m1, r1, m2, r2, kn, ks);
@@ -135,7 +135,7 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double Fn = ((kFeat & 1) && rc.law) ? kn * pen * sq : kn * pen;
   const double maxFs = Fn * tanphi;
   const double fs2 = fx * fx + fy * fy + fz * fz;
-  if (fs2 > maxFs * maxFs) {
+  if (lt_nonneg(maxFs * maxFs, fs2)) {   // |Fs|^2 > (Fn tan phi)^2
     const double sc = maxFs * rsqrt(fs2);
     fx *= sc; fy *= sc; fz *= sc;
   }
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kT, kT == 128 ? 6 : 2) k_contact(const StepDes
       l2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
       const double R = __dadd_rn(p1.w, p2.w);
       r1 = p1.w; r2 = p2.w;
-      real = l2 < __dmul_rn(R, R);
-      if (!real && t.hfs[k].w != 0.0) {   // contact lost (u_N > 0): back to potential
+      real = lt_nonneg(l2, __dmul_rn(R, R));   // l2 < R^2
+      if (!real && !is_zero_bits(t.hfs[k].w)) {   // contact lost (u_N > 0): back to potential
         const double4_32a z = make_double4_32a(0, 0, 0, 0);
         t.hfs[k] = z; t.hn[k] = z; t.oFM[2 * k] = z; t.oFM[2 * k + 1] = z;
       }

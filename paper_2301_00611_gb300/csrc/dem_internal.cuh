@@ -220,6 +220,20 @@ struct StepDesc {
   long long cap;   // body capacity (stride of the wall histories)
 };
 
+// Comparisons on the integer pipe (every FP64 instruction costs 1/58 of an FP32 one on
+// GB300): non-negative doubles are ordered as their bit patterns read as signed 64-bit
+// integers, and a double is zero when its bits other than the sign are zero.  Used
+// where both sides are non-negative by construction (squared lengths, stiffnesses):
+// the decisions are the FP64 comparisons' (a NaN, whose bits exceed every finite
+// value's, compares as the FP64 comparison does for the positive NaNs arithmetic
+// produces; a non-finite state fails the step in the integrator either way).
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool is_zero_bits(double a) {
+  return ((unsigned long long)__double_as_longlong(a) << 1) == 0ull;
+}
+
 // ---- cell shift packing: 3 x 10-bit two's complement in one int
 __host__ __device__ inline int pack_shift(int c0, int c1, int c2) {
   return (c0 & 1023) | ((c1 & 1023) << 10) | ((c2 & 1023) << 20);

@@ -470,11 +470,11 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
   // term (first omitted terms x^6/720 and x^6/5040, below 1.4e-15) needs no square
   // root, division or sincos; larger angles use sincos.
   const double w2 = wn_[0] * wn_[0] + wn_[1] * wn_[1] + wn_[2] * wn_[2];
-  if (w2 > 0) {
+  if (!is_zero_bits(w2)) {   // w2 > 0 (a sum of squares)
     const double4_32a q0 = b.ori[s];
     const double x2 = 0.25 * (dt * dt) * w2;
     double ch, sx;   // cos x, sin x / x
-    if (x2 < 1e-4) {
+    if (lt_nonneg(x2, 1e-4)) {
       ch = 1.0 - 0.5 * x2 * (1.0 - x2 * (1.0 / 12.0));
       sx = 1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0));
     } else {
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kB) k_integrate(const StepDesc *__restrict__ d
     uy = (xn[1] - xr.y) - (E[3] * xr.x + E[4] * xr.y + E[5] * xr.z);
     uz = (xn[2] - xr.z) - (E[6] * xr.x + E[7] * xr.y + E[8] * xr.z);
   }
-  if (!(ux * ux + uy * uy + uz * uz <= c.thr2)) {
+  if (lt_nonneg(c.thr2, ux * ux + uy * uy + uz * uz)) {   // displacement^2 > bound^2
     if (!ds->request) ds->request = 1;
   }
   bool ok = true;

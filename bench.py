@@ -933,6 +933,7 @@ def run_served_measure(args, world=1, rank=0):
              "pairs": pairs, "ns": ns, "max_resident": summary["max_resident"],
              "pairs_ulp": pairs_ulp, "ns_ulp": ns_ulp,
              "conc": summary["concurrency_mean"], "device_bytes": summary["device_bytes"],
+             "conc_hist": summary["concurrency_hist"],
              "budget": summary["budget_bytes"], "rows_per_body": summary["rows_per_body"]}
     allr = gather_ranks(local, world)
     if rank != 0:
@@ -948,6 +949,7 @@ def run_served_measure(args, world=1, rank=0):
             "scene_steps_per_s": ss / wall,
             "body_steps_per_s": sum(r["body_steps"] for r in allr) / wall, "wall_s": wall,
             "concurrency_mean": allr[0]["conc"], "concurrency_max": allr[0]["max_resident"],
+            "concurrency_hist": _conc_hist(allr[0]["conc_hist"]),
             "admission": {"budget_bytes": allr[0]["budget"],
                           "device_bytes_max": allr[0]["device_bytes"],
                           "rows_per_body_estimate": allr[0]["rows_per_body"]},
@@ -959,6 +961,16 @@ def run_served_measure(args, world=1, rank=0):
                                                    [n for r in allr for n in r["ns"]]),
             "chaos_floor_fp64_one_ulp": _stat_errors([p for r in allr for p in r["pairs_ulp"]],
                                                      [n for r in allr for n in r["ns_ulp"]])}
+
+
+def _conc_hist(hist):
+    """The server's ticks by resident requests, keyed by the bins' ranges."""
+    from paper_2301_00611_gb300.dem import CONCURRENCY_BIN_EDGES as edges
+    out, lo = {}, 1
+    for hi, n in zip(edges, hist):
+        out[str(lo) if hi == lo else (f"{lo}-{hi}" if hi else f">{lo - 1}")] = n
+        lo = (hi or lo) + 1
+    return out
 
 
 def run_serve(args):
@@ -1011,6 +1023,7 @@ def run_serve(args):
                    "body_steps_per_s": summary["body_steps"] / wall,
                    "concurrency_mean": summary["concurrency_mean"],
                    "concurrency_max": summary["max_resident"], "ticks": summary["ticks"],
+                   "concurrency_hist": _conc_hist(summary["concurrency_hist"]),
                    "device_bytes_max": summary["device_bytes"],
                    "rows_per_body_estimate": summary["rows_per_body"], "dtype": "mixed"},
         "plain_fp64_fifo": {"p50_s": serve.percentile(plain_lat, 50),

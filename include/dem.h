@@ -447,6 +447,9 @@ typedef struct dem_server_summary {
     double busy_s;                 /* inside dem_step */
     double latency_p50, latency_p99, latency_max, latency_mean;   /* finished requests */
     double concurrency_mean;       /* resident requests per tick */
+    /* ticks by the number r of resident requests: [0] r = 1, [b] for b = 1..6
+     * 2^(b-1) < r <= 2^b, [7] r > 64 */
+    long long concurrency_hist[8];
 } dem_server_summary;
 
 /* Defaults of dem_server_desc (above).  Never fails. */

@@ -441,6 +441,9 @@ dem_status dem_server_stats(dem_server *s, dem_server_summary *out) {
   out->latency_max = t.lat_max;
   out->latency_mean = t.lat_mean;
   out->concurrency_mean = t.conc_mean;
+  static_assert(sizeof out->concurrency_hist / sizeof out->concurrency_hist[0] ==
+                dem_sched::kConcBins, "histogram bins");
+  for (int i = 0; i < dem_sched::kConcBins; ++i) out->concurrency_hist[i] = t.conc_hist[i];
   return DEM_OK;
 }
 

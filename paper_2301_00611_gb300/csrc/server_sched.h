@@ -66,12 +66,24 @@ struct Req {
   std::vector<double> out_pos, out_vel, out_angvel, out_ori;
 };
 
+constexpr int kConcBins = 8;
+
+// Histogram bin of a resident count r >= 1 (see Totals::conc_hist).
+inline int conc_bin(long long r) {
+  int b = 0;
+  while (b < kConcBins - 1 && (1LL << b) < r) ++b;
+  return b;
+}
+
 struct Totals {
   long long submitted = 0, completed = 0, failed = 0, waiting = 0, resident = 0;
   long long resident_bodies = 0, max_resident = 0, ticks = 0, scene_steps = 0, body_steps = 0;
   long long budget_bytes = 0, resident_bytes_est = 0, device_bytes = 0;
   double rows_per_body = 0, wall_s = 0, busy_s = 0;
   double p50 = 0, p99 = 0, lat_max = 0, lat_mean = 0, conc_mean = 0;
+  // ticks by resident requests: bin 0 one, bin b (1..kConcBins-2) 2^(b-1)+1 .. 2^b,
+  // the last bin more than 2^(kConcBins-2)
+  long long conc_hist[kConcBins] = {};
 };
 
 // Linear interpolation between the order statistics (numpy's default percentile).
@@ -212,6 +224,7 @@ class Scheduler {
     for (double x : lat_) s += x;
     t.lat_mean = lat_.empty() ? 0 : s / (double)lat_.size();
     t.conc_mean = ticks_ ? (double)conc_sum_ / (double)ticks_ : 0;
+    for (int i = 0; i < kConcBins; ++i) t.conc_hist[i] = conc_hist_[i];
     return t;
   }
 
@@ -302,6 +315,7 @@ class Scheduler {
         busy_ += tb - ta;
         ++ticks_;
         conc_sum_ += (long long)resident_.size();
+        ++conc_hist_[conc_bin((long long)resident_.size())];
         max_resident_ = std::max<long long>(max_resident_, (long long)resident_.size());
         for (Req *r : resident_) {
           r->left -= k;
@@ -352,6 +366,7 @@ class Scheduler {
   long long next_ = 1, submitted_ = 0, completed_ = 0, failed_ = 0;
   long long resident_bodies_ = 0, max_resident_ = 0, ticks_ = 0, scene_steps_ = 0,
             body_steps_ = 0, conc_sum_ = 0, device_bytes_ = 0;
+  long long conc_hist_[kConcBins] = {};
   double busy_ = 0;
   std::vector<double> lat_;
   bool stopping_ = false;

@@ -150,7 +150,10 @@ class ServerSummary(ctypes.Structure):
         "max_resident", "ticks", "scene_steps", "body_steps", "budget_bytes",
         "resident_bytes_est", "device_bytes")] + [(k, ctypes.c_double) for k in (
         "rows_per_body", "wall_s", "busy_s", "latency_p50", "latency_p99", "latency_max",
-        "latency_mean", "concurrency_mean")]
+        "latency_mean", "concurrency_mean")] + [("concurrency_hist", ctypes.c_longlong * 8)]
+
+# upper edges of ServerSummary.concurrency_hist's bins (the last bin is open)
+CONCURRENCY_BIN_EDGES = (1, 2, 4, 8, 16, 32, 64, None)
 
 
 # C ABI: name -> (restype, argtypes)
@@ -791,7 +794,9 @@ class Server:
     def stats(self):
         st = ServerSummary()
         self._check(self._lib.dem_server_stats(self._h, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in ServerSummary._fields_}
+        out = {k: getattr(st, k) for k, _ in ServerSummary._fields_}
+        out["concurrency_hist"] = list(st.concurrency_hist)
+        return out
 
 
 def find_pairs(pos, radius, periodic=False, cell=None, margin=0.0, cap=None, stream=None,

@@ -151,7 +151,14 @@ static void join_while_running() {
   CHECK(f.resident_at_tick[1].size() == 2 && f.ticks[1] == 10 && f.ticks[2] == 5);
   s.with_result(b, [&](const Req &r) { CHECK(r.iter == 15 && r.t_admit >= r.t_submit); });
   s.with_result(a, [&](const Req &r) { CHECK(r.iter == 40); });
-  CHECK(s.totals().max_resident == 2);
+  const dem_sched::Totals tt = s.totals();
+  CHECK(tt.max_resident == 2);
+  // ticks by resident count: a alone (10, then 10 and 5 after b left), a with b (10, 5)
+  CHECK(tt.ticks == 5 && tt.conc_hist[0] == 3 && tt.conc_hist[1] == 2);
+  // bins: 1 | 2 | 3-4 | 5-8 | ... | 33-64 | more than 64
+  CHECK(dem_sched::conc_bin(1) == 0 && dem_sched::conc_bin(2) == 1 && dem_sched::conc_bin(3) == 2);
+  CHECK(dem_sched::conc_bin(4) == 2 && dem_sched::conc_bin(5) == 3 && dem_sched::conc_bin(64) == 6);
+  CHECK(dem_sched::conc_bin(65) == 7 && dem_sched::conc_bin(100000) == 7);
   std::printf("join_while_running ok\n");
 }
 

@@ -73,6 +73,9 @@ def test_fp64_results_equal_alone_runs_bitwise(env):
     results, summary = _serve(pkg, serve, built, pkg.DEM_FP64)
     assert summary["completed"] == 12 and summary["failed"] == 0
     assert summary["max_resident"] >= 3
+    # every tick lands in one histogram bin; some ran three or more requests at once
+    assert sum(summary["concurrency_hist"]) == summary["ticks"]
+    assert sum(summary["concurrency_hist"][2:]) > 0
     assert _overlapped(results)
     assert summary["latency_p99"] >= summary["latency_p50"] > 0
     kinds = set()

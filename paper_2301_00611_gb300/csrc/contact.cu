@@ -25,13 +25,35 @@
 // real-row traffic.  Two choices follow: real rows are queued per warp so that
 // the law runs with every lane busy (non-real rows, ~45% of the table, would
 // otherwise idle lanes through it), and square roots and divisions are taken
-// from rsqrt to shorten the FP64 instruction stream.
+// from an FP32 estimate of 1/sqrt refined in FP64 to shorten the FP64 instruction stream.
 #include "dem_internal.cuh"
 
 namespace dem {
 
 namespace {
 constexpr int kQ = 64;   // per-warp queue of real rows (< 32 left over + 32 new)
+
+// 1/sqrt(x) for x > 0 with four FP64-pipe instructions: the FP32
+// hardware estimate y0 of the FP32 image of x (relative error below 4e-7), widened, then
+// one third-order correction from the binomial series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8
+// + ..., e = 1 - x y0^2 (Householder's method of order two for 1/sqrt): y0 + e (y0/2 +
+// e 3y0/8).  The narrowing and widening rebias the exponent on the integer pipe (every
+// double<->float conversion is an FP64-pipe instruction), y0/2 is exact and 3y0/8 is
+// formed in FP32 (it multiplies e^2 < 2e-13).  The omitted terms are below 2e-19, so the
+// result is within one ulp of 1/sqrt(x).  x outside the FP32 normal range (including 0)
+// takes the library's rsqrt.
+__device__ __forceinline__ double rsqrt_refined(double x) {
+  const long long xb = __double_as_longlong(x);
+  const int ex = (int)(xb >> 52);   // biased exponent (x >= 0)
+  if ((unsigned)(ex - 897) >= 252u) return rsqrt(x);
+  const float yf = rsqrtf(__int_as_float((int)((xb >> 29) - (896LL << 23))));
+  const double y0 = __longlong_as_double(((long long)__float_as_int(yf) << 29) + (896LL << 52));
+  const double half = __longlong_as_double(__double_as_longlong(y0) - (1LL << 52));
+  const double c = __longlong_as_double(((long long)__float_as_int(0.375f * yf) << 29) +
+                                        (896LL << 52));
+  const double e = fma(-(x * y0), y0, 1.0);
+  return fma(e, fma(e, c, half), y0);
+}
 
 // What a row needs of its (sub-)scene's cell state: time step, diagonal of the cell
 // H (image shift) and of W (velocity of a unit shift); all zero when aperiodic.
@@ -65,9 +87,9 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double R = r1 + r2;
   double4_32a fs = t.hfs[k];
   double4_32a hn = t.hn[k];
-  // 1/l from rsqrt (one FP64 pipe sequence instead of a square root and a division);
-  // l = l2 / l within an ulp or two of the correctly rounded root
-  const double il = rsqrt(l2);
+  // 1/l from rsqrt_refined (instead of a square root and a division); l = l2 / l within
+  // an ulp or two of the correctly rounded root
+  const double il = rsqrt_refined(l2);
   const double l = l2 * il;
   const double nx = dx * il, ny = dy * il, nz = dz * il;   // eq. 2.7
   const double pen = R - l;                                  // penetrationDepth
@@ -115,9 +137,9 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double az = hn.x * ny - hn.y * nx;
   const double tw = 0.5 * dt * (nx * (w1.x + w2.x) + ny * (w1.y + w2.y) + nz * (w1.z + w2.z));
   const double bx = ax + tw * nx, by = ay + tw * ny, bz = az + tw * nz;
-  double fx = fs.x - (fs.y * bz - fs.z * by);
-  double fy = fs.y - (fs.z * bx - fs.x * bz);
-  double fz = fs.z - (fs.x * by - fs.y * bx);
+  double fx = fma(fs.z, by, fma(-fs.y, bz, fs.x));   // Fs - Fs x b, two fused steps
+  double fy = fma(fs.x, bz, fma(-fs.z, bx, fs.y));
+  double fz = fma(fs.y, bx, fma(-fs.x, by, fs.z));
   // 2. mutual motion: ratchet-free v12 (ScGeom), its part perpendicular to n
   const double rx = r2 * w2.x + r1 * w1.x, ry = r2 * w2.y + r1 * w1.y, rz = r2 * w2.z + r1 * w1.z;
   const double f = R * il;
@@ -136,7 +158,7 @@ __device__ __forceinline__ void real_row(const Table &t, const Bodies &b, const 
   const double maxFs = Fn * tanphi;
   const double fs2 = fx * fx + fy * fy + fz * fz;
   if (lt_nonneg(maxFs * maxFs, fs2)) {   // |Fs|^2 > (Fn tan phi)^2
-    const double sc = maxFs * rsqrt(fs2);
+    const double sc = maxFs * rsqrt_refined(fs2);
     fx *= sc; fy *= sc; fz *= sc;
   }
   const double Fx = Fn * nx + fx, Fy = Fn * ny + fy, Fz = Fn * nz + fz;

@@ -445,14 +445,14 @@ KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                                 "mixed": ("integrate.cu", "collider.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
-    ("fp64", "contact"): {"bytes": 809.9e6, "rows": 4654409, "real": 2602000, "step": 4985,
-                          "digest": "402a7bce659f63ff"},
-    ("fp64", "integrate"): {"bytes": 641.3e6, "rows": 4654409, "real": 2602000, "step": 4985,
-                            "digest": "961d098e74bcafd4"},
-    ("mixed", "contact"): {"bytes": 589.2e6, "rows": 4654409, "real": 2603000, "step": 4985,
-                           "digest": "40382b31018e060a"},
-    ("mixed", "integrate"): {"bytes": 529.4e6, "rows": 4654409, "real": 2603000, "step": 4985,
-                             "digest": "961d098e74bcafd4"},
+    ("fp64", "contact"): {"bytes": 810.2e6, "rows": 4654436, "real": 2592000, "step": 4975,
+                          "digest": "b0aef776224f2947"},
+    ("fp64", "integrate"): {"bytes": 640.3e6, "rows": 4654436, "real": 2592000, "step": 4975,
+                            "digest": "3f00b041c2f18a50"},
+    ("mixed", "contact"): {"bytes": 610.6e6, "rows": 4654436, "real": 2591000, "step": 4975,
+                           "digest": "501691543ccef3f4"},
+    ("mixed", "integrate"): {"bytes": 528.8e6, "rows": 4654436, "real": 2591000, "step": 4975,
+                             "digest": "3f00b041c2f18a50"},
 }
 
 

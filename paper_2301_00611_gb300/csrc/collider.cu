@@ -369,9 +369,12 @@ __global__ void k_ref_branch(Table t, Bodies b, const Grid *__restrict__ grids, 
   const Grid &g = grid_of(grids, b.sid, multi, pr.x);
   const double4_32a p1 = b.pos[pr.x], p2 = b.pos[pr.y];
   double h[3] = {0, 0, 0};
-  if (g.periodic) {
+  const int cp = g.periodic ? t.cpack[k] : 0;
+  // rows inside the cell have c = 0 and H c = 0 exactly: a warp none of whose rows
+  // crosses the cell skips the conversions and products (FP64-pipe instructions)
+  if (__any_sync(__activemask(), cp != 0) && g.periodic) {
     int c0, c1, c2;
-    unpack_shift(t.cpack[k], c0, c1, c2);
+    unpack_shift(cp, c0, c1, c2);
     h[0] = g.L[0] * c0; h[1] = g.L[1] * c1; h[2] = g.L[2] * c2;
     if (g.sheared)   // Href c of a sheared cell
       for (int q = 0; q < 3; ++q) h[q] = g.H[3 * q] * c0 + g.H[3 * q + 1] * c1 + g.H[3 * q + 2] * c2;

@@ -223,7 +223,9 @@ __device__ inline void unpack_cell(int v, int c[3]) {
 }
 
 // Candidate counts: cnt_up[body 1] and cnt_down[body 2] of every candidate, body 1
-// being the sphere with the smaller id (both arrays zeroed before).
+// being the sphere with the smaller id (both arrays zeroed before).  Count and emit read
+// the partners' records through the read-only path (__ldg): nothing in the walk writes
+// them, and the compiler may then issue those loads ahead of the atomics.
 __global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__restrict__ id,
                         long long N, const Grid *__restrict__ grids, int multi,
                         const int *__restrict__ count, const int *__restrict__ start,
@@ -239,12 +241,12 @@ __global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__re
   unpack_cell(inf.x, ci);
   bool bad = false;
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
-    if (cand_f32(g, a, cr.wpos[j], w, g.slack)) {
-      const bool fwd = ids < id[j];
+    if (cand_f32(g, a, __ldg(cr.wpos + j), w, g.slack)) {
+      const bool fwd = ids < __ldg(id + j);
       atomicAdd(&cnt_up[fwd ? s : j], 1);
       atomicAdd(&cnt_down[fwd ? j : s], 1);
       if (g.periodic) {
-        const int4 ij = cr.info[j];
+        const int4 ij = __ldg(cr.info + j);
         bad |= abs(inf.y - ij.y + w[0]) > kShiftMax || abs(inf.z - ij.z + w[1]) > kShiftMax ||
                abs(inf.w - ij.w + w[2]) > kShiftMax;
       }
@@ -268,13 +270,13 @@ __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict
   int ci[3];
   unpack_cell(inf.x, ci);
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
-    if (cand_f32(g, a, cr.wpos[j], w, g.slack)) {
+    if (cand_f32(g, a, __ldg(cr.wpos + j), w, g.slack)) {
       int c0 = 0, c1 = 0, c2 = 0;   // cell shift of j seen from s
       if (g.periodic) {
-        const int4 ij = cr.info[j];
+        const int4 ij = __ldg(cr.info + j);
         c0 = inf.y - ij.y + w[0]; c1 = inf.z - ij.z + w[1]; c2 = inf.w - ij.w + w[2];
       }
-      const int idj = b.id[j];
+      const int idj = __ldg(b.id + j);
       const bool fwd = ids < idj;
       const int g1 = fwd ? s : j, g2 = fwd ? j : s;
       const int r = t.row_start[g1] + atomicAdd(&ufill[g1], 1);

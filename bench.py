@@ -447,12 +447,12 @@ TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
     ("fp64", "contact"): {"bytes": 810.2e6, "rows": 4654436, "real": 2592000, "step": 4975,
                           "digest": "b0aef776224f2947"},
-    ("fp64", "integrate"): {"bytes": 640.4e6, "rows": 4654436, "real": 2592000, "step": 4975,
-                            "digest": "cd93eea66ad25bf9"},
+    ("fp64", "integrate"): {"bytes": 640.3e6, "rows": 4654436, "real": 2592000, "step": 4975,
+                            "digest": "d2327da2417dc114"},
     ("mixed", "contact"): {"bytes": 610.6e6, "rows": 4654436, "real": 2591000, "step": 4975,
                            "digest": "501691543ccef3f4"},
-    ("mixed", "integrate"): {"bytes": 529.1e6, "rows": 4654436, "real": 2591000, "step": 4975,
-                             "digest": "cd93eea66ad25bf9"},
+    ("mixed", "integrate"): {"bytes": 529.2e6, "rows": 4654436, "real": 2591000, "step": 4975,
+                             "digest": "d2327da2417dc114"},
 }
 
 

@@ -474,11 +474,11 @@ def _traffic(precision, name, algorithmic_at):
     return t["bytes"], note
 
 
-# The survey's algorithmic bytes of the method (what a contact and a body must move per
+# The method's own algorithmic bytes (what a contact and a body must move per
 # step, independent of this implementation's layout): 244 B read + 120 B written per
 # real contact in the contact pass, 470 B per real contact and 180 B per body per step.
-SURVEY_CONTACT_BYTES = 364
-SURVEY_STEP_CONTACT_BYTES, SURVEY_STEP_BODY_BYTES = 470, 180
+METHOD_CONTACT_BYTES = 364
+METHOD_STEP_CONTACT_BYTES, METHOD_STEP_BODY_BYTES = 470, 180
 
 
 def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True, fp64_peak=None):
@@ -487,7 +487,7 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True, fp64_pea
     the kernel's average launch time from its CUDA events.  FP64 kernels divide by the
     FP64 rate measured in this run (fp64_peak, TFLOP/s; the figure derived from unit
     counts and clock is reported beside it), and carry their HBM fractions both for this
-    implementation's operand bytes and for the survey's per-contact bytes."""
+    implementation's operand bytes and for the method's per-contact bytes."""
     tm, real = res["tm"], res["mean_real"]
     c_ms = res["avg_ms"]
     i_ms = tm["integrate_ms"] / max(1, tm["integrate_launches"])
@@ -510,9 +510,9 @@ def _kernel_rooflines(res, precision, n, peak, peak_kind, traffic=True, fp64_pea
                          "avg_launch_ms": ms, "flops_per_launch": fl,
                          "hbm": {"achieved_gbs": gb, "peak_gbs": peak, "frac": gb / peak,
                                  "peak_kind": peak_kind, "bytes_per_launch": by}}
-        sb = SURVEY_CONTACT_BYTES * real
+        sb = METHOD_CONTACT_BYTES * real
         sg = sb / (c_ms / 1e3) / 1e9 if c_ms > 0 else 0.0
-        out["contact"]["hbm_survey_bytes"] = {"bytes_per_launch": sb, "achieved_gbs": sg,
+        out["contact"]["hbm_method_bytes"] = {"bytes_per_launch": sb, "achieved_gbs": sg,
                                               "frac": sg / peak, "peak_kind": peak_kind}
     else:
         cb = ROW_BYTES_ALL_MIXED * res["rows_avg"] + ROW_BYTES_REAL_MIXED * real
@@ -582,8 +582,8 @@ def run_gpu(args):
     share = {k: tm[k] / max(1e-9, res["ms_timed"]) for k in ("contact_ms", "integrate_ms",
                                                               "cell_ms", "collider_ms")}
     rl64, rk64 = _kernel_rooflines(res, "fp64", args.n, peak, peak_kind, fp64_peak=fp64_peak)
-    # the whole step against the survey's algorithmic bytes (N 180 B + C 470 B per step)
-    step_bytes = SURVEY_STEP_BODY_BYTES * args.n + SURVEY_STEP_CONTACT_BYTES * res["mean_real"]
+    # the whole step against the method's algorithmic bytes (N 180 B + C 470 B per step)
+    step_bytes = METHOD_STEP_BODY_BYTES * args.n + METHOD_STEP_CONTACT_BYTES * res["mean_real"]
     step_gbs = step_bytes / (ms / K / 1e3) / 1e9
     mixed_line = None
     if mixed is not None:
@@ -658,7 +658,7 @@ def run_gpu(args):
                            "times (roofline): a second run of the same job with the events "
                            "on (ms_per_step_instrumented)",
             "ms_per_step_instrumented": res["ms_timed"] / K,
-            "step_hbm_survey_bytes": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
+            "step_hbm_method_bytes": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
                                       "frac": step_gbs / peak, "peak_kind": peak_kind},
             "fp64_peak_tflops": {"measured": fp64_peak, "derived": FP64_PEAK_TFLOPS},
             "collider_runs": tm["collider_runs"],

@@ -64,7 +64,7 @@ def test_million_spheres_one_step_and_statistics():
     print(f"fullsize mixed: {worst32['widened_count']} of {n32} contacts above 1e-5 "
           f"relative alone ({worst32['widened_frac']:.2e}), held by the rounding allowance")
     # the penetration from the squared gap keeps FP32's precision of the penetration:
-    # at this size no contact needs the rounding allowance (the benchmark spec's 1e-5)
+    # at this size no contact needs the rounding allowance (the per-contact FP32 bar of 1e-5)
     assert worst32["widened_frac"] <= 1e-4
     compare_states(orc.state(), mix.state(), X, tol=1e-5, co=co, masses=masses_of(w), dt=dt,
                    eps=2.0 ** -23, coord=reach)

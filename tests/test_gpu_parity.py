@@ -121,8 +121,8 @@ def test_trajectory_and_collider_reruns(mods):
     The run is chaotic: a difference of one rounding grows by orders of magnitude over
     120 steps.  Beside the two runs the oracle runs a third time from the same state
     with every coordinate moved by one ulp; each step's bar is the larger of 1e-9 and
-    the largest deviation of that nudged run from the oracle so far (the chaos floor of
-    reading R24): the GPU may not depart from the oracle more than the oracle departs
+    the largest deviation of that nudged run from the oracle so far (the method's own
+    chaos floor): the GPU may not depart from the oracle more than the oracle departs
     from itself.  (Over these 120 steps that floor grows from 1e-12 to about 1e-8.)"""
     oracle, pkg = mods
     w = workloads.periodic_cloud(1200, 4, phi=0.33, inflate=1.04, vel_scale=0.5,

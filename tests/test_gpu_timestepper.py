@@ -70,7 +70,7 @@ def test_per_subscene_steppers(mods):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_density_scaling_matches_oracle(mods, precision):
-    """Density scaling (reading R22) on a walled packing under gravity: the step is the
+    """Density scaling (reading R22 of dem_oracle.c) on a walled packing under gravity: the step is the
     target, the per-body inertia factors match the oracle's, and so do the states after
     one step and after 20 more."""
     oracle, pkg = mods

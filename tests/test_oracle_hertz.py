@@ -1,5 +1,5 @@
 """Oracle Hertz-Mindlin law (Ip2_FrictMat_FrictMat_MindlinPhys and
-Law2_ScGeom_MindlinPhys_Mindlin; reading R18) pinned to Hertz theory: the static
+Law2_ScGeom_MindlinPhys_Mindlin; reading R18 of dem_oracle.c) pinned to Hertz theory: the static
 force of an overlap, the duration of a head-on impact (from the energy integral,
 evaluated here by quadrature), restitution 1 without damping, the text's shear
 constant for equal materials, and energy conservation over a collision cascade."""

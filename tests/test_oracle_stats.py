@@ -8,16 +8,16 @@
   about different axes compose in the world frame (later rotation on the left).
   A swapped product (body-frame composition) or a half-angle slip is far outside
   the tolerance.
-* Unbalanced force (utils.unbalancedForce, reading R14): mean over the dynamic bodies
+* Unbalanced force (utils.unbalancedForce, the mean/mean reading): mean over the dynamic bodies
   of the magnitude of the summed contact force (gravity excluded), over the mean
   magnitude of the interaction forces, on a hand-worked chain of spheres with a wall
   contact and a fixed sphere; the "max/max" sentence of section 1 and a variant that
   counts the weight give other numbers.
-* Packing fraction (utils.porosity: phi = V_s / V, reading R14): the volume of the
+* Packing fraction (utils.porosity: phi = V_s / V): the volume of the
   spheres, overlaps ignored, over the box volume with walls, or the current cell
   volume |det H| of a periodic cell (sheared, and after a compaction, where the cell
   follows H_k = (1 + g dt)^k H_0 exactly up to rounding).
-* Coordination (utils.avgNumInteractions, reading R14): 2 C_ss / N, wall contacts
+* Coordination (utils.avgNumInteractions): 2 C_ss / N, wall contacts
   excluded.
 """
 import numpy as np
@@ -179,7 +179,7 @@ def test_packing_fraction_sheared_and_compacted_cell(oracle_mod):
     s.step(1)
     assert abs(s.stats()["phi"] - vs / abs(np.linalg.det(H0))) <= 1e-13 * vs / abs(np.linalg.det(H0))
     s.set_velgrad(gr * np.eye(3))
-    s.step(k)              # the gradient set between steps drives the next step (R13)
+    s.step(k)              # the gradient set between steps drives the next step
     Hk = (1 + gr * dt) ** k * H0
     want = vs / abs(np.linalg.det(Hk))
     assert np.allclose(s.cell()["H"], Hk, rtol=1e-13, atol=0)

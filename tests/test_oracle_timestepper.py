@@ -2,7 +2,7 @@
 forms: a dimer (the text's two masses in opposite motion, dt_cr = sqrt(2 m / kn)), a
 sphere caged by six fixed neighbours where the rotational stiffness sets the step,
 the no-contact default, the cap and the update interval; density scaling (reading
-R22) pinned by the same chain's stability limit at a step far above the natural one,
+R22 of dem_oracle.c) pinned by the same chain's stability limit at a step far above the natural one,
 by the invariance of a trajectory counted in steps under a change of the target step,
 and by the static penetration m g / kn (the weight is not scaled)."""
 import numpy as np

@@ -229,7 +229,7 @@ __device__ inline void unpack_cell(int v, int c[3]) {
 __global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__restrict__ id,
                         long long N, const Grid *__restrict__ grids, int multi,
                         const int *__restrict__ count, const int *__restrict__ start,
-                        int *cnt_up, int *cnt_down, int *err) {
+                        int *cnt_up, int *cnt_down, int *err, CandList cl) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
@@ -240,8 +240,13 @@ __global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__re
   int ci[3];
   unpack_cell(inf.x, ci);
   bool bad = false;
+  int nc = 0;
+  unsigned *mine = cl.list + (long long)s * kCandKeep;
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
     if (cand_f32(g, a, __ldg(cr.wpos + j), w, g.slack)) {
+      if (cl.use && nc < kCandKeep)   // slot and the neighbour cell's wrap (code 0..26)
+        mine[nc] = (unsigned)j | ((unsigned)((w[0] + 1) + 3 * (w[1] + 1) + 9 * (w[2] + 1)) << 26);
+      ++nc;
       const bool fwd = ids < __ldg(id + j);
       atomicAdd(&cnt_up[fwd ? s : j], 1);
       atomicAdd(&cnt_down[fwd ? j : s], 1);
@@ -252,40 +257,60 @@ __global__ void k_count(CellRec cr, const int *__restrict__ sid, const int *__re
       }
     }
   });
+  if (cl.use) cl.n[s] = nc;
   if (bad) atomicOr(err, kErrShiftRange);
 }
 
+// Row of candidate (s, j) in the row range of its body 1 (smaller id) at a position the
+// atomics pick; w: the wrap of j's neighbour cell as seen from s.
+__device__ inline void emit_row(const CellRec &cr, const Bodies &b, const Table &t, int *ufill,
+                                const Grid &g, const int4 &inf, int s, int ids, int j,
+                                const int w[3]) {
+  int c0 = 0, c1 = 0, c2 = 0;   // cell shift of j seen from s
+  if (g.periodic) {
+    const int4 ij = __ldg(cr.info + j);
+    c0 = inf.y - ij.y + w[0]; c1 = inf.z - ij.z + w[1]; c2 = inf.w - ij.w + w[2];
+  }
+  const int idj = __ldg(b.id + j);
+  const bool fwd = ids < idj;
+  const int g1 = fwd ? s : j, g2 = fwd ? j : s;
+  const int r = t.row_start[g1] + atomicAdd(&ufill[g1], 1);
+  if (r < t.row_start[g1 + 1]) {
+    t.pair[r] = make_int2(g1, g2);
+    t.cpack[r] = fwd ? pack_shift(c0, c1, c2) : pack_shift(-c0, -c1, -c2);   // shift of body 2
+    t.found[r] = fwd ? idj : ids;   // sort key: the id of body 2 (scratch until the merge)
+  }
+}
+
 // Rows of the candidates, each in the row range of its body 1 (smaller id) at a
-// position the atomics pick; k_rowsort then fixes the order.  ufill: zeroed.
+// position the atomics pick; k_rowsort then fixes the order.  ufill: zeroed.  A walker
+// whose candidates all fit the count pass's list places them from it; the others walk
+// the cells again with the same test.
 __global__ void k_emit(CellRec cr, Bodies b, long long N, const Grid *__restrict__ grids,
                        int multi, const int *__restrict__ count, const int *__restrict__ start,
-                       Table t, int *ufill) {
+                       Table t, int *ufill, CandList cl) {
   long long sl = (long long)blockIdx.x * kT + threadIdx.x;
   if (sl >= N) return;
   const int s = (int)sl;
   const Grid &g = grid_of(grids, b.sid, multi, sl);
-  const float4 a = cr.wpos[s];
   const int4 inf = cr.info[s];
   const int ids = b.id[s];
+  const int nc = cl.use ? cl.n[s] : kCandKeep + 1;
+  if (nc <= kCandKeep) {
+    const unsigned *mine = cl.list + (long long)s * kCandKeep;
+    for (int k = 0; k < nc; ++k) {
+      const unsigned e = mine[k];
+      const int j = (int)(e & 0x3ffffffu), code = (int)(e >> 26);
+      const int w[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+      emit_row(cr, b, t, ufill, g, inf, s, ids, j, w);
+    }
+    return;
+  }
+  const float4 a = cr.wpos[s];
   int ci[3];
   unpack_cell(inf.x, ci);
   for_half_shell(g, count, start, ci, s, [&](int j, const int w[3]) {
-    if (cand_f32(g, a, __ldg(cr.wpos + j), w, g.slack)) {
-      int c0 = 0, c1 = 0, c2 = 0;   // cell shift of j seen from s
-      if (g.periodic) {
-        const int4 ij = __ldg(cr.info + j);
-        c0 = inf.y - ij.y + w[0]; c1 = inf.z - ij.z + w[1]; c2 = inf.w - ij.w + w[2];
-      }
-      const int idj = __ldg(b.id + j);
-      const bool fwd = ids < idj;
-      const int g1 = fwd ? s : j, g2 = fwd ? j : s;
-      const int r = t.row_start[g1] + atomicAdd(&ufill[g1], 1);
-      if (r < t.row_start[g1 + 1]) {
-        t.pair[r] = make_int2(g1, g2);
-        t.cpack[r] = fwd ? pack_shift(c0, c1, c2) : pack_shift(-c0, -c1, -c2);   // shift of body 2
-        t.found[r] = fwd ? idj : ids;   // sort key: the id of body 2 (scratch until the merge)
-      }
-    }
+    if (cand_f32(g, a, __ldg(cr.wpos + j), w, g.slack)) emit_row(cr, b, t, ufill, g, inf, s, ids, j, w);
   });
 }
 
@@ -602,18 +627,18 @@ void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, 
 
 void launch_count(float4 *wpos, int4 *info, const int *sid, const int *id, long long N,
                   const Grid *grids, int multi, const int *count, const int *start, int *cnt_up,
-                  int *cnt_down, int *err, cudaStream_t st) {
+                  int *cnt_down, int *err, CandList cl, cudaStream_t st) {
   if (N > 0)
     k_count<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, sid, id, N, grids, multi, count, start,
-                                      cnt_up, cnt_down, err);
+                                      cnt_up, cnt_down, err, cl);
 }
 
 void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
                  int multi, const int *count, const int *start, const Table &t, int *ufill,
-                 int *dfill, cudaStream_t st) {
+                 int *dfill, CandList cl, cudaStream_t st) {
   if (N <= 0) return;
   k_emit<<<blocks(N), kT, 0, st>>>(CellRec{wpos, info}, b, N, grids, multi, count, start, t,
-                                   ufill);
+                                   ufill, cl);
   k_rowsort<<<blocks(N), kT, 0, st>>>(t, N);
   if (t.P > 0) {
     k_rowkey<<<blocks(t.P), kT, 0, st>>>(t, b.id);

@@ -272,14 +272,24 @@ void launch_cellrec(const Bodies &b, long long N, const Grid *grids, int multi, 
                     int4 *info, cudaStream_t st);
 // cnt_up / cnt_down: zeroed; counts of the rows of each body as body 1 / body 2 (body 1:
 // the smaller id)
+// The count pass keeps up to kCandKeep candidates per walker (partner slot and the
+// wrap of its neighbour cell, packed in 32 bits) in a scratch list, and their number;
+// the emit pass places those without walking the cells again (a walker with more, or
+// slots beyond 2^26, walks again).
+constexpr int kCandKeep = 32;
+struct CandList {
+  unsigned *list;   // kCandKeep entries per body: slot | wrap code << 26
+  int *n;           // candidates the walker found (may exceed kCandKeep)
+  int use;          // 0: slots too large to pack, emit walks
+};
 void launch_count(float4 *wpos, int4 *info, const int *sid, const int *id, long long N,
                   const Grid *grids, int multi, const int *count, const int *start, int *cnt_up,
-                  int *cnt_down, int *err, cudaStream_t st);
+                  int *cnt_down, int *err, CandList cl, cudaStream_t st);
 // rows in body 1's range sorted by body 2's id, and the down lists filled (unsorted);
-// ufill, dfill: zeroed
+// ufill, dfill: zeroed; cl: the count pass's candidates
 void launch_emit(float4 *wpos, int4 *info, const Bodies &b, long long N, const Grid *grids,
                  int multi, const int *count, const int *start, const Table &t, int *ufill,
-                 int *dfill, cudaStream_t st);
+                 int *dfill, CandList cl, cudaStream_t st);
 // each down list sorted by body 1's id
 void launch_downsort(const Table &t, const int *id, long long N, cudaStream_t st);
 // t.ord = bodies in decreasing order of incident rows; ws: 2 * kDegreeBuckets zeroed ints

@@ -207,6 +207,8 @@ struct dem_scene {
   double4_32a *gF = nullptr, *gT = nullptr;
   float4 *wpos = nullptr;
   int4 *cinfo = nullptr;
+  unsigned *cand_list = nullptr;   // the count pass's candidates (kCandKeep per body)
+  int *cand_n = nullptr;
 
   Table tab[2]{};
   long long tab_nbody[2]{0, 0};
@@ -489,10 +491,12 @@ dem_status ensure_bodies(dem_scene *s, long long need) {
   s->slot_of_id = sid;
   dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down); dfree(s, s->key);
   dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
+  dfree(s, s->cand_list); dfree(s, s->cand_n);
   if ((r = dalloc(s, &s->new_to_old, nc)) || (r = dalloc(s, &s->cnt_up, nc)) ||
       (r = dalloc(s, &s->cnt_down, nc)) || (r = dalloc(s, &s->key, nc)) ||
       (r = dalloc(s, &s->gF, nc)) || (r = dalloc(s, &s->gT, nc)) ||
-      (r = dalloc(s, &s->wpos, nc)) || (r = dalloc(s, &s->cinfo, nc)))
+      (r = dalloc(s, &s->wpos, nc)) || (r = dalloc(s, &s->cinfo, nc)) ||
+      (r = dalloc(s, &s->cand_list, nc * kCandKeep)) || (r = dalloc(s, &s->cand_n, nc)))
     return r;
   s->cap = nc;
   size_t ws = scan_workspace_bytes(nc + 1);
@@ -783,8 +787,10 @@ dem_status rebuild_core(dem_scene *s) {
   launch_cellrec(s->cur, NL, s->grids_d, multi, s->wpos, s->cinfo, s->st);
   CK(cudaMemsetAsync(s->cnt_up, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   CK(cudaMemsetAsync(s->cnt_down, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
+  // slots are packed in 26 bits of a candidate entry
+  const CandList cl{s->cand_list, s->cand_n, s->cap < (1LL << 26) ? 1 : 0};
   launch_count(s->wpos, s->cinfo, s->cur.sid, s->cur.id, NL, s->grids_d, multi, s->cell_count,
-               s->cell_start, s->cnt_up, s->cnt_down, &s->ds_d->error, s->st);
+               s->cell_start, s->cnt_up, s->cnt_down, &s->ds_d->error, cl, s->st);
   exclusive_scan(s->cnt_up, nt.row_start, NL, s->scan_ws, s->st);
   exclusive_scan(s->cnt_down, nt.down_start, NL, s->scan_ws, s->st);
   CK(cudaMemcpyAsync(&s->rb_h->totals[0], nt.row_start + NL, sizeof(int), cudaMemcpyDeviceToHost, s->st));
@@ -802,7 +808,7 @@ dem_status rebuild_core(dem_scene *s) {
   CK(cudaMemsetAsync(dfill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   CK(cudaMemsetAsync(ufill, 0, sizeof(int) * std::max<long long>(NL, 1), s->st));
   launch_emit(s->wpos, s->cinfo, s->cur, NL, s->grids_d, multi, s->cell_count, s->cell_start, nt,
-              ufill, dfill, s->st);
+              ufill, dfill, cl, s->st);
   if (s->mixed) launch_ref_branch(nt, s->cur, s->grids_d, multi, s->st);
   launch_downsort(nt, s->cur.id, NL, s->st);
   CK(cudaMemsetAsync(s->deg_ws, 0, sizeof(int) * 2 * kDegreeBuckets, s->st));
@@ -899,7 +905,8 @@ double scene_bytes_per_body(int mixed) {
   const double d4 = sizeof(double4_32a), f4 = sizeof(float4);
   double buf = 6 * d4 + 3 * sizeof(int) + sizeof(uint8_t) + sizeof(double) + 6 * d4;
   if (mixed) buf += 6 * f4;
-  const double scratch = 5 * sizeof(int) + 2 * d4 + f4 + sizeof(int4);
+  const double scratch = 5 * sizeof(int) + 2 * d4 + f4 + sizeof(int4) +
+                        kCandKeep * sizeof(unsigned) + sizeof(int);
   const double tables = 2 * 3 * sizeof(int);
   return 2 * buf + scratch + tables;
 }
@@ -1064,6 +1071,7 @@ void dem_scene_destroy(dem_scene *s) {
   free_table(s, s->tab[1]);
   dfree(s, s->slot_of_id); dfree(s, s->new_to_old); dfree(s, s->cnt_up); dfree(s, s->cnt_down);
   dfree(s, s->key); dfree(s, s->gF); dfree(s, s->gT); dfree(s, s->wpos); dfree(s, s->cinfo);
+  dfree(s, s->cand_list); dfree(s, s->cand_n);
   dfree(s, s->cell_count); dfree(s, s->cell_start); dfree(s, s->cell_fill);
   dfree(s, s->scan_ws); dfree(s, s->partials); dfree(s, s->servo); dfree(s, s->p3d_d); dfree(s, s->p3d_part); dfree(s, s->deg_ws);
   dfree(s, s->mats_d); dfree(s, s->cs_d); dfree(s, s->ds_d);

@@ -445,14 +445,14 @@ KERNEL_SOURCES = {"contact": {"fp64": ("contact.cu", "dem_internal.cuh"),
                                 "mixed": ("integrate.cu", "collider.cu", "dem_internal.cuh")}}
 TRAFFIC_PROFILE = "profiles/dram_traffic_compaction_1m.md"
 TRAFFIC = {
-    ("fp64", "contact"): {"bytes": 810.2e6, "rows": 4654436, "real": 2592000, "step": 4975,
-                          "digest": "b0aef776224f2947"},
-    ("fp64", "integrate"): {"bytes": 640.3e6, "rows": 4654436, "real": 2592000, "step": 4975,
-                            "digest": "d2327da2417dc114"},
-    ("mixed", "contact"): {"bytes": 610.6e6, "rows": 4654436, "real": 2591000, "step": 4975,
-                           "digest": "501691543ccef3f4"},
-    ("mixed", "integrate"): {"bytes": 529.2e6, "rows": 4654436, "real": 2591000, "step": 4975,
-                             "digest": "d2327da2417dc114"},
+    ("fp64", "contact"): {"bytes": 809.1e6, "rows": 4654436, "real": 2592000, "step": 4975,
+                          "digest": "d2a67f79426e6fc6"},
+    ("fp64", "integrate"): {"bytes": 639.9e6, "rows": 4654436, "real": 2592000, "step": 4975,
+                            "digest": "397853ded890a3d6"},
+    ("mixed", "contact"): {"bytes": 611.1e6, "rows": 4654436, "real": 2591000, "step": 4975,
+                           "digest": "ccbf9b2d833aaeda"},
+    ("mixed", "integrate"): {"bytes": 528.1e6, "rows": 4654436, "real": 2591000, "step": 4975,
+                             "digest": "397853ded890a3d6"},
 }
 
 
